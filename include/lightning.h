@@ -1,0 +1,303 @@
+/*
+ * lightning.h -- C ABI of the single-GPU annotated-launch engine.
+ *
+ * The model follows the Lightning paper (arXiv 2202.05549):
+ *   - a kernel launch is cut into superblocks, rectangular disjoint sub-grids
+ *     of thread blocks (Sec. 2.1 "Distributed Kernel Launches");
+ *   - arrays are 1-3-D, made of rectangular chunks defined by a
+ *     distribution policy; chunks may overlap in halo cells whose replicas
+ *     the runtime keeps coherent (Sec. 2.2 "Multi-Dimensional Distributed
+ *     Arrays");
+ *   - a data annotation gives each thread's affine read / write / readwrite /
+ *     reduce(f) region; the access region of a superblock is the dense box of
+ *     elements its threads touch (Sec. 2.3 "Data Annotations");
+ *   - a planner turns each launch into tasks (Execute, Copy, Create/Delete of
+ *     temporary chunks, Reduce) and adds dependencies on earlier launches for
+ *     read-write / write-write / write-read conflicts on chunks (Sec. 2.4
+ *     "Execution Planner");
+ *   - a memory manager stages chunks in GPU memory from pre-allocated pools and
+ *     evicts least-recently-used chunks to pinned host memory
+ *     (Sec. 3.4 "Memory Management");
+ *   - the kernel runs on an offset sub-grid with views whose base pointer has
+ *     the chunk offset subtracted once (Sec. 3.5, Listing 3).
+ * Everything runs on one GPU in one process.  There is no transport, no
+ * worker process and no collective.
+ *
+ * Conventions for every call:
+ *   - Each returns an lt_status: LT_OK (0) or a negative LT_ERR_* code.  No C++
+ *     exception crosses the ABI.  lt_last_error() returns a message for the
+ *     calling thread's most recent failure.
+ *   - Pointers are host pointers unless the parameter says "device".
+ *   - Objects (contexts, arrays, kernels) are owned by the library.  They are
+ *     released by the matching *_destroy call; destroying a context releases
+ *     everything created in it.
+ *   - A context is not thread-safe: calls on one context must not overlap.
+ *   - After an LT_ERR_CUDA or LT_ERR_TIMEOUT the context is poisoned: every
+ *     further call except lt_ctx_destroy returns LT_ERR_BUSY.
+ */
+#ifndef LIGHTNING_H
+#define LIGHTNING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+typedef int32_t lt_status;
+#define LT_OK 0
+#define LT_ERR_INVALID_ARG (-1)  /* bad argument, shape, handle or dtype */
+#define LT_ERR_PARSE (-2)        /* annotation text does not parse */
+#define LT_ERR_OOM_DEVICE (-3)   /* HBM budget or device pool too small */
+#define LT_ERR_OOM_HOST (-4)     /* pinned host pool too small */
+#define LT_ERR_CUDA (-5)         /* a CUDA call failed; context poisoned */
+#define LT_ERR_TIMEOUT (-6)      /* a bounded device-side wait expired */
+#define LT_ERR_BUSY (-7)         /* context poisoned by an earlier error */
+#define LT_ERR_UNSUPPORTED (-8)  /* valid request this build does not do */
+#define LT_ERR_DEVICE_CHECK (-9) /* a kernel recorded a bounds violation */
+
+/* ---- element types (Sec. 2.2: arrays hold a primitive type) ------------- */
+typedef enum {
+    LT_F32 = 0,
+    LT_BF16 = 1,
+    LT_U8 = 2,
+    LT_U32 = 3
+} lt_dtype;
+
+/* ---- distributions (Sec. 2.2; StencilDist / row-wise / column-wise /
+ * tiled of Fig. 2 and the host code of Sec. 3.6) --------------------------
+ * chunk[d]: extent of one chunk along axis d (axis 0 is the slowest, i.e.
+ * rows of a 2-D array); 0 means the whole axis.  ROWS splits axis 0 only,
+ * COLS axis 1 only, TILES every axis, BLOCK makes one chunk.  halo[d] widens
+ * every chunk by that many cells on both sides along axis d (clipped to the
+ * array), so neighbouring chunks overlap in replicated halo cells.
+ * order: LT_ORDER_ROW stores each chunk row-major (last axis contiguous);
+ * LT_ORDER_COL (2-D only) stores each chunk column-major (axis 0
+ * contiguous).  The storage layout never changes results. */
+typedef enum {
+    LT_DIST_BLOCK = 0,
+    LT_DIST_ROWS = 1,
+    LT_DIST_COLS = 2,
+    LT_DIST_TILES = 3
+} lt_dist_kind;
+
+typedef enum { LT_ORDER_ROW = 0, LT_ORDER_COL = 1 } lt_order;
+
+typedef struct {
+    int32_t kind;      /* lt_dist_kind */
+    int32_t order;     /* lt_order */
+    int64_t chunk[3];  /* chunk extent per axis, 0 = whole axis */
+    int64_t halo[3];   /* halo width per axis */
+} lt_dist;
+
+/* ---- context ------------------------------------------------------------- */
+/* hbm_budget_bytes: size of the device chunk pool (0 = 90% of free HBM).
+ * host_pool_bytes: size of the pinned host pool that evicted chunks move to
+ *   (0 = none: nothing may spill).
+ * staging_cap_bytes: at most this many bytes of tasks may be enqueued ahead
+ *   of the GPU before lt_launch waits (Sec. 3.4's staging throttle, 2 GB in
+ *   the paper; 0 = 2 GiB).
+ * flags: LT_FLAG_TIMING records CUDA events around every kernel and copy
+ *   (read with lt_stats); LT_FLAG_DRYRUN runs planner, dependency tracker and
+ *   memory manager without any device (no CUDA call is made; nothing is
+ *   computed; lt_array_read/write/fill only update bookkeeping), for tests of
+ *   the host logic; LT_FLAG_FIXED_SWEEP visits superblocks in index order
+ *   every launch (default: the order alternates between launches, so the
+ *   chunks used last are reused first). */
+#define LT_FLAG_TIMING 1
+#define LT_FLAG_DRYRUN 2
+#define LT_FLAG_FIXED_SWEEP 4
+
+typedef struct {
+    size_t hbm_budget_bytes;
+    size_t host_pool_bytes;
+    size_t staging_cap_bytes;
+    int32_t device;
+    int32_t flags;
+} lt_config;
+
+typedef struct lt_ctx lt_ctx;
+typedef struct lt_array lt_array;
+typedef struct lt_kernel lt_kernel;
+
+/* Create a context on `device`: allocates the HBM pool and the pinned host
+ * pool up front (allocation is expensive, Sec. 3.4) and three streams
+ * (compute, host-to-device, device-to-host).  *out is set on success. */
+lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out);
+/* Waits for all work, then frees every object of the context. */
+lt_status lt_ctx_destroy(lt_ctx *ctx);
+/* Message of the calling thread's last failure ("" if none).  Valid until
+ * the thread's next lt_* call. */
+const char *lt_last_error(void);
+
+/* ---- arrays (Sec. 2.2; context.ones / context.zeros of Sec. 3.6) -------- */
+/* Create an ndim (1..3) array of `shape` elements distributed by `dist`.
+ * Its contents start as zero (chunks materialise lazily). */
+lt_status lt_array_create(lt_ctx *ctx, lt_dtype dtype, int32_t ndim, const int64_t shape[3],
+                          const lt_dist *dist, lt_array **out);
+lt_status lt_array_destroy(lt_ctx *ctx, lt_array *arr);
+
+/* Copy the whole array from / to a dense row-major host buffer of exactly
+ * `bytes` bytes.  Synchronous: waits for all earlier work; the buffer is
+ * borrowed only during the call. */
+lt_status lt_array_write(lt_ctx *ctx, lt_array *arr, const void *host, size_t bytes);
+lt_status lt_array_read(lt_ctx *ctx, lt_array *arr, void *host, size_t bytes);
+
+/* Fill every element from its global row-major index g with a seeded
+ * counter-based generator (SplitMix64, Steele, Lea & Flood 2014): element g
+ * takes output x = mix(key + (g+1)*0x9E3779B97F4A7C15), key = first output
+ * of SplitMix64 seeded with (seed ^ (stream << 32)).
+ *   LT_INIT_ZERO, LT_INIT_CONST (value): constants;
+ *   LT_INIT_UNIFORM: f32 (x >> 40) * 2^-24 in [0,1);
+ *   LT_INIT_KAPPA: f32 of 0.05 + 0.15 * u (u as above, in fp64);
+ *   LT_INIT_NORMAL_BF16: bf16 of N(0,1)*scale by Box-Muller from counters
+ *     2g and 2g+1, rounded to f32 then to bf16 (RNE);
+ *   LT_INIT_U8: u8 x >> 56.
+ * Asynchronous (ordered like a launch that writes the whole array). */
+typedef enum {
+    LT_INIT_ZERO = 0,
+    LT_INIT_CONST = 1,
+    LT_INIT_UNIFORM = 2,
+    LT_INIT_KAPPA = 3,
+    LT_INIT_NORMAL_BF16 = 4,
+    LT_INIT_U8 = 5
+} lt_init_kind;
+
+typedef struct {
+    int32_t kind;
+    uint64_t seed;
+    uint64_t stream;
+    double value;
+    double scale;
+} lt_init;
+
+lt_status lt_array_fill(lt_ctx *ctx, lt_array *arr, const lt_init *init);
+
+/* Number of chunks, and the box of chunk `index`: lo/hi inclusive per axis
+ * (the halo included) and where it currently lives (0 none, 1 device,
+ * 2 host). */
+lt_status lt_array_num_chunks(lt_ctx *ctx, const lt_array *arr, int64_t *n);
+lt_status lt_array_chunk_info(lt_ctx *ctx, const lt_array *arr, int64_t index, int64_t lo[3],
+                              int64_t hi[3], int32_t *location);
+
+/* ---- kernels (Sec. 3.5-3.6: CudaKernelDef ... .param_value / .param_array
+ * / .annotate / .compile) -------------------------------------------------
+ * The kernel bodies are built in, compiled ahead of time for sm_103a; each
+ * one is written in the paper's convention (a device function of the
+ * virtual block index and of array views).  The annotation is parsed and
+ * checked here: it must name every array parameter once, and its regions
+ * must contain the accesses the built-in actually makes.
+ *
+ * Annotation grammar (Sec. 2.3):
+ *   annotation := bindings "=>" stmt ("," stmt)*
+ *   bindings   := binding ("," binding)*
+ *   binding    := ("global" | "block" | "local") (var | "[" var ("," var)* "]")
+ *   stmt       := mode name "[" index ("," index)* "]"
+ *   mode       := "read" | "write" | "readwrite" | "reduce(" ("+"|"*"|"min"|"max") ")"
+ *   index      := affine | [affine] ":" [affine]     (bounds inclusive)
+ *   affine     := integer linear combination of bound variables plus a constant
+ * A bracketed list binds its LAST variable to the x grid dimension, the one
+ * before to y, then z (so "global [i, j]" gives j = x, the contiguous axis of
+ * a row-major array); a single variable binds x.  Omitted slice bounds are
+ * the array's first / last index. */
+typedef enum {
+    LT_K_PLAN_ONLY = 0,      /* no body: any annotation, any arrays; plans and dry-run launches only */
+    LT_K_STENCIL1D = 1,      /* out[i] = (in[i-1]+in[i]+in[i+1])/3.0 (Listing 1), f32 */
+    LT_K_JACOBI2D = 2,       /* V = ((((U+Un)+Us)+Uw)+Ue)/5, zero ghosts, f32 */
+    LT_K_JACOBI3D = 3,       /* 7-point analogue, /7 */
+    LT_K_GEMM_BF16 = 4,      /* C[i,j] = sum_k A[i,k] B[k,j]; bf16 in, f32 accumulate/out */
+    LT_K_HIST256 = 5,        /* reduce(+) H[:] of one count per u8 element */
+    LT_K_DIFFUSION2D = 6,    /* u1 = u + K*(Lu), f32 */
+    LT_K_DIFFUSION2D_ADJ = 7 /* adjoint step: reduce(+) of the transposed stencil */
+} lt_builtin;
+
+typedef struct {
+    const char *name;
+    int32_t is_array; /* 1: array parameter (param_array), 0: value (param_value) */
+    int32_t dtype;    /* lt_dtype of the array, or of the value (LT_F32 / LT_U32) */
+} lt_param;
+
+lt_status lt_kernel_register(lt_ctx *ctx, int32_t builtin, const char *annotation, const lt_param *params,
+                             int32_t nparams, lt_kernel **out);
+lt_status lt_kernel_destroy(lt_ctx *ctx, lt_kernel *k);
+
+/* ---- launches (Sec. 2.1, Sec. 2.4; kernel.launch of Sec. 3.6) ------------
+ * grid: number of threads along x, y, z (like launch(n, 16, ...) in the
+ * host code of Sec. 3.6); block: threads per block.  workdist.superblock:
+ * threads per superblock along x, y, z (BlockDist), rounded up to whole
+ * blocks; 0 = the whole grid.  args[i] matches params[i] of the kernel.
+ * The launch is planned, enqueued and returns without waiting for the GPU
+ * (Sec. 2.4: plan construction overlaps execution).  It may block only when
+ * the staging throttle is reached. */
+typedef struct {
+    uint64_t x, y, z;
+} lt_dim3;
+
+typedef struct {
+    int64_t superblock[3];
+} lt_workdist;
+
+typedef struct {
+    lt_array *array; /* for array parameters */
+    double f;        /* for value parameters of type LT_F32 */
+    int64_t i;       /* for value parameters of type LT_U32 / integers */
+} lt_arg;
+
+lt_status lt_launch(lt_ctx *ctx, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const lt_workdist *wd,
+                    const lt_arg *args, int32_t nargs);
+
+/* Blocks until every enqueued task has finished (context.synchronize() of
+ * Sec. 3.6).  Reports device-side error words (bounds checks, timeouts). */
+lt_status lt_synchronize(lt_ctx *ctx);
+
+/* ---- statistics and plan inspection -------------------------------------- */
+typedef struct {
+    uint64_t launches;        /* lt_launch calls */
+    uint64_t tasks_execute;   /* Execute tasks (superblocks run) */
+    uint64_t tasks_copy;      /* Copy tasks: pack, unpack, replica updates */
+    uint64_t tasks_reduce;    /* Reduce tasks */
+    uint64_t deps;            /* dependency edges added between tasks */
+    uint64_t fetches;         /* chunk host -> device transfers */
+    uint64_t evictions;       /* chunk device -> host transfers */
+    uint64_t dead_skips;      /* transfers skipped because the data was dead */
+    uint64_t bytes_h2d;       /* host -> device bytes */
+    uint64_t bytes_d2h;       /* device -> host bytes */
+    uint64_t bytes_d2d;       /* device -> device copy bytes (pack/unpack/replica) */
+    uint64_t kernels;         /* kernels launched by the library */
+    uint64_t hbm_in_use;      /* bytes of the HBM pool in use now */
+    uint64_t hbm_peak;        /* high-water mark of hbm_in_use */
+    uint64_t host_in_use;     /* bytes of the host pool in use now */
+    /* with LT_FLAG_TIMING, measured with CUDA events on the launching stream
+     * (valid after lt_synchronize): */
+    double ms_execute;        /* sum of Execute kernel durations */
+    uint64_t n_execute_kernels;
+    double ms_copy_kernels;   /* pack/unpack/replica/reduce kernels */
+    uint64_t n_copy_kernels;
+    double ms_h2d;            /* sum of host->device copy durations */
+    double ms_d2h;            /* sum of device->host copy durations */
+    double ms_fill;           /* fill kernels */
+} lt_stats;
+
+lt_status lt_stats_get(lt_ctx *ctx, lt_stats *out);
+lt_status lt_stats_reset(lt_ctx *ctx);
+
+/* Plan a launch without enqueueing it and write a JSON description into
+ * buf (NUL-terminated, truncated to cap bytes; *needed receives the full
+ * length): superblocks, each argument's access region, the chunk decision
+ * (direct / pack / temp-write / reduce) and the replica copies.  Host-only;
+ * valid in LT_FLAG_DRYRUN contexts. */
+lt_status lt_plan_explain(lt_ctx *ctx, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const lt_workdist *wd,
+                          const lt_arg *args, int32_t nargs, char *buf, size_t cap, size_t *needed);
+
+/* JSON log of the tasks enqueued since the last reset: kind, superblock,
+ * chunks, predecessor task ids, memory actions (fetch / evict / dead).
+ * Kept only while `enable` is 1 (lt_debug_log_enable), for tests. */
+lt_status lt_debug_log_enable(lt_ctx *ctx, int32_t enable);
+lt_status lt_debug_log(lt_ctx *ctx, char *buf, size_t cap, size_t *needed);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIGHTNING_H */

@@ -1,0 +1,123 @@
+// Descriptors shared by the runtime (host) and the CUDA kernels.
+//
+// A DView is the paper's view type (Sec. 3.5, Listing 3): the chunk's base
+// address with the chunk's global offset already subtracted, so a kernel
+// indexes it with GLOBAL indices and pays nothing per access:
+//     address(i0, i1, i2) = base + (i0*s0 + i1*s1 + i2*s2) * element_size
+// (axis 0 is the slowest axis of the array).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lt {
+
+struct DView {
+    uint64_t base;  // byte address of global element (0,0,0) (may lie outside the allocation)
+    int64_t s[3];   // element strides
+};
+
+#define LT_MAX_ARRAYS 5
+
+// One Execute task: a superblock's thread box and its argument views.
+struct ExecTask {
+    int64_t t_lo[3], t_hi[3];     // thread box (x, y, z), inclusive
+    DView v[LT_MAX_ARRAYS];       // views, in array-parameter order
+    uint32_t cta_begin;           // first CTA of this task in the launch
+    uint32_t cta_count;
+};
+
+// Per-launch constants of an Execute kernel.
+struct ExecParams {
+    int64_t shape[LT_MAX_ARRAYS][3];  // global shapes of the array parameters
+    int32_t nd[LT_MAX_ARRAYS];
+    int64_t block[3];                 // launch block dims (x, y, z)
+    double f[4];                      // value parameters (float)
+    int64_t i[4];                     // value parameters (integer)
+    uint32_t* err;                    // device error word (bounds checks)
+    int32_t ntasks;
+    int32_t variant;                  // kernel variant chosen by prepare_*
+};
+
+// Box copy (pack / unpack / replica update): copy the global box [lo, hi]
+// from src to dst.
+struct CopyPiece {
+    DView src, dst;
+    int64_t lo[3], hi[3];
+    int32_t nd;
+    int32_t esize;
+    uint64_t unit_begin; // prefix sum of work units (see copy_piece_units)
+};
+
+// Work units of one copy piece: the box is linearised with the last axis
+// fastest and cut into units of LT_COPY_UNIT elements (or 16-byte vectors
+// when both sides are contiguous and aligned along the last axis).
+#define LT_COPY_UNIT 4096
+__host__ __device__ inline bool copy_piece_vec(const CopyPiece &p) {
+    int inner = p.nd - 1;
+    int64_t w = p.hi[inner] - p.lo[inner] + 1;
+    if (p.src.s[inner] != 1 || p.dst.s[inner] != 1) return false;
+    if ((w * p.esize) % 16 != 0) return false;
+    uint64_t a = p.src.base, b = p.dst.base;
+    int64_t off_s = 0, off_d = 0;
+    for (int d = 0; d < p.nd; ++d) {
+        off_s += p.lo[d] * p.src.s[d];
+        off_d += p.lo[d] * p.dst.s[d];
+        if (d < inner && ((p.src.s[d] * p.esize) % 16 != 0 || (p.dst.s[d] * p.esize) % 16 != 0)) return false;
+    }
+    a += (uint64_t)(off_s * p.esize);
+    b += (uint64_t)(off_d * p.esize);
+    return (a % 16 == 0) && (b % 16 == 0);
+}
+__host__ __device__ inline uint64_t copy_piece_items(const CopyPiece &p) {
+    uint64_t n = 1;
+    for (int d = 0; d < p.nd; ++d) n *= (uint64_t)(p.hi[d] - p.lo[d] + 1);
+    return copy_piece_vec(p) ? n * (uint64_t)p.esize / 16 : n;
+}
+__host__ __device__ inline uint64_t copy_piece_units(const CopyPiece &p) {
+    return (copy_piece_items(p) + LT_COPY_UNIT - 1) / LT_COPY_UNIT;
+}
+
+// Reduce: dst[box] = src_0 (op) src_1 (op) ... in the listed order.
+struct ReducePiece {
+    DView dst;
+    int64_t lo[3], hi[3];
+    int32_t nd;
+    int32_t op;
+    int32_t dtype;
+    int32_t nsrc;
+    uint32_t src_begin;  // index into the source-view table
+    uint32_t pad;
+    uint64_t elem_begin; // prefix sum of elements
+};
+
+// Seeded fill of a box of one chunk (see lt_array_fill).
+struct FillDesc {
+    DView dst;
+    int64_t lo[3], hi[3];
+    int64_t gstride[3];  // row-major strides of the global array (for the counter)
+    int32_t nd;
+    int32_t kind;
+    int32_t dtype;
+    int32_t pad;
+    uint64_t key;
+    double value, scale;
+};
+
+namespace k {
+
+// All launchers return the CUDA error of the launch (cudaSuccess on success).
+cudaError_t fill(const FillDesc &d, cudaStream_t st);
+cudaError_t copy_pieces(const CopyPiece *dev, int n, uint64_t total_units, cudaStream_t st);
+cudaError_t reduce_pieces(const ReducePiece *dev, const DView *srcs, int n, uint64_t total_elems, cudaStream_t st);
+
+// Execute kernels of the built-ins.  prepare_* fills cta_begin / cta_count
+// of every task (host side) and returns the total CTA count; launch_* runs
+// all tasks of one launch in one kernel.
+uint32_t prepare_stencil1d(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_stencil1d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
+uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_jacobi2d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
+
+}  // namespace k
+}  // namespace lt

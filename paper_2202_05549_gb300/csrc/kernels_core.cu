@@ -1,0 +1,271 @@
+// Data-movement kernels of the engine: seeded fill, box copy (pack, unpack,
+// replica update; Sec. 2.4 "Execution Planner") and the ordered reduction of
+// per-superblock partials (reduce(f) of Sec. 2.3, first level of the
+// hierarchical reduction of Sec. 2.4).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace lt {
+namespace {
+
+// SplitMix64 output mix (Steele, Lea & Flood 2014)
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t sm64_elem(uint64_t key, uint64_t g) {
+    return sm64_mix(key + (g + 1) * 0x9E3779B97F4A7C15ULL);
+}
+
+__device__ __forceinline__ float u01_f32(uint64_t x) { return (float)(x >> 40) * 0x1p-24f; }
+
+__device__ __forceinline__ unsigned short f32_to_bf16_rne(float f) {
+    uint32_t b = __float_as_uint(f);
+    uint32_t lsb = (b >> 16) & 1u;
+    return (unsigned short)((b + 0x7FFFu + lsb) >> 16);
+}
+
+__global__ void fill_kernel(FillDesc d) {
+    int nd = d.nd;
+    int inner = nd - 1;
+    int64_t w = d.hi[inner] - d.lo[inner] + 1;
+    int64_t rows = 1;
+    for (int k = 0; k < inner; ++k) rows *= d.hi[k] - d.lo[k] + 1;
+    const int64_t SEG = 8192;
+    int64_t segs = (w + SEG - 1) / SEG;
+    for (int64_t unit = blockIdx.x; unit < rows * segs; unit += gridDim.x) {
+        int64_t r = unit / segs, seg = unit % segs;
+        int64_t c0 = seg * SEG, c1 = c0 + SEG < w ? c0 + SEG : w;
+        int64_t idx[3] = {0, 0, 0};
+        int64_t rr = r;
+        for (int k = inner - 1; k >= 0; --k) {
+            int64_t e = d.hi[k] - d.lo[k] + 1;
+            idx[k] = d.lo[k] + rr % e;
+            rr /= e;
+        }
+        int64_t g0 = 0, a0 = 0;
+        for (int k = 0; k < inner; ++k) {
+            g0 += idx[k] * d.gstride[k];
+            a0 += idx[k] * d.dst.s[k];
+        }
+        for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            int64_t col = d.lo[inner] + c;
+            uint64_t g = (uint64_t)(g0 + col * d.gstride[inner]);
+            uint64_t addr_el = (uint64_t)(a0 + col * d.dst.s[inner]);
+            uint64_t x = sm64_elem(d.key, g);
+            switch (d.dtype) {
+                case 0: {  // f32
+                    float v;
+                    if (d.kind == 0)
+                        v = 0.0f;
+                    else if (d.kind == 1)
+                        v = (float)d.value;
+                    else if (d.kind == 2)
+                        v = u01_f32(x);
+                    else {  // kappa = 0.05 + 0.15 u in fp64, no contraction
+                        double u = (double)u01_f32(x);
+                        v = __double2float_rn(__dadd_rn(0.05, __dmul_rn(0.15, u)));
+                    }
+                    ((float *)d.dst.base)[addr_el] = v;
+                    break;
+                }
+                case 1: {  // bf16
+                    unsigned short h;
+                    if (d.kind == 0)
+                        h = 0;
+                    else if (d.kind == 1)
+                        h = f32_to_bf16_rne((float)d.value);
+                    else {  // N(0,1)*scale by Box-Muller from counters 2g, 2g+1
+                        uint64_t x1 = sm64_elem(d.key, 2 * g), x2 = sm64_elem(d.key, 2 * g + 1);
+                        double u1 = ((double)(x1 >> 11) + 1.0) * 0x1p-53;
+                        double u2 = (double)(x2 >> 11) * 0x1p-53;
+                        double z = __dmul_rn(sqrt(-2.0 * log(u1)), cos(__dmul_rn(6.283185307179586, u2)));
+                        h = f32_to_bf16_rne(__double2float_rn(__dmul_rn(z, d.scale)));
+                    }
+                    ((unsigned short *)d.dst.base)[addr_el] = h;
+                    break;
+                }
+                case 2: {  // u8
+                    unsigned char v = d.kind == 5 ? (unsigned char)(x >> 56)
+                                                  : (d.kind == 1 ? (unsigned char)d.value : (unsigned char)0);
+                    ((unsigned char *)d.dst.base)[addr_el] = v;
+                    break;
+                }
+                default: {  // u32
+                    uint32_t v = d.kind == 1 ? (uint32_t)d.value : 0u;
+                    ((uint32_t *)d.dst.base)[addr_el] = v;
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int find_piece_u(const CopyPiece *p, int n, uint64_t u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (p[mid].unit_begin <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// One CTA per work unit; the piece is found by binary search.
+__global__ void __launch_bounds__(256) copy_kernel(const CopyPiece *__restrict__ pieces, int n) {
+    uint64_t u = blockIdx.x;
+    int pi = find_piece_u(pieces, n, u);
+    const CopyPiece p = pieces[pi];
+    bool vec = copy_piece_vec(p);
+    uint64_t items = copy_piece_items(p);
+    uint64_t first = (u - p.unit_begin) * LT_COPY_UNIT;
+    uint64_t last = first + LT_COPY_UNIT < items ? first + LT_COPY_UNIT : items;
+    int inner = p.nd - 1;
+    int64_t w = p.hi[inner] - p.lo[inner] + 1;
+    int64_t e1 = p.nd == 3 ? p.hi[1] - p.lo[1] + 1 : 1;
+    if (vec) {
+        int64_t wv = w * p.esize / 16;  // vectors per row
+        for (uint64_t it = first + threadIdx.x; it < last; it += blockDim.x) {
+            int64_t row = (int64_t)(it / (uint64_t)wv), cv = (int64_t)(it % (uint64_t)wv);
+            int64_t idx[3] = {0, 0, 0};
+            if (p.nd == 3) {
+                idx[0] = p.lo[0] + row / e1;
+                idx[1] = p.lo[1] + row % e1;
+            } else if (p.nd == 2) {
+                idx[0] = p.lo[0] + row;
+            }
+            int64_t os = 0, od = 0;
+            for (int d = 0; d < inner; ++d) {
+                os += idx[d] * p.src.s[d];
+                od += idx[d] * p.dst.s[d];
+            }
+            os += p.lo[inner];
+            od += p.lo[inner];
+            const uint4 *s = (const uint4 *)(p.src.base + (uint64_t)(os * p.esize)) + cv;
+            uint4 *dd = (uint4 *)(p.dst.base + (uint64_t)(od * p.esize)) + cv;
+            *dd = __ldg(s);
+        }
+        return;
+    }
+    for (uint64_t it = first + threadIdx.x; it < last; it += blockDim.x) {
+        int64_t row = (int64_t)(it / (uint64_t)w), col = (int64_t)(it % (uint64_t)w);
+        int64_t idx[3] = {0, 0, 0};
+        if (p.nd == 3) {
+            idx[0] = p.lo[0] + row / e1;
+            idx[1] = p.lo[1] + row % e1;
+        } else if (p.nd == 2) {
+            idx[0] = p.lo[0] + row;
+        }
+        idx[inner] = p.lo[inner] + col;
+        int64_t os = 0, od = 0;
+        for (int d = 0; d < p.nd; ++d) {
+            os += idx[d] * p.src.s[d];
+            od += idx[d] * p.dst.s[d];
+        }
+        const char *s = (const char *)(p.src.base + (uint64_t)(os * p.esize));
+        char *dd = (char *)(p.dst.base + (uint64_t)(od * p.esize));
+        switch (p.esize) {
+            case 1: *dd = *s; break;
+            case 2: *(unsigned short *)dd = *(const unsigned short *)s; break;
+            case 4: *(uint32_t *)dd = *(const uint32_t *)s; break;
+            default: *(uint64_t *)dd = *(const uint64_t *)s;
+        }
+    }
+}
+
+__device__ __forceinline__ int find_rpiece(const ReducePiece *p, int n, uint64_t e) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (p[mid].elem_begin <= e)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T red_apply(int op, T a, T b) {
+    switch (op) {
+        case 0: return a + b;
+        case 1: return a * b;
+        case 2: return b < a ? b : a;
+        default: return b > a ? b : a;
+    }
+}
+
+template <typename T>
+__device__ void reduce_one(const ReducePiece &p, const DView *srcs, const int64_t idx[3]) {
+    int64_t od = 0;
+    for (int d = 0; d < p.nd; ++d) od += idx[d] * p.dst.s[d];
+    T acc = T(0);
+    for (int k = 0; k < p.nsrc; ++k) {
+        const DView &v = srcs[p.src_begin + k];
+        int64_t os = 0;
+        for (int d = 0; d < p.nd; ++d) os += idx[d] * v.s[d];
+        T x = ((const T *)v.base)[os];
+        acc = k == 0 ? x : red_apply<T>(p.op, acc, x);
+    }
+    ((T *)p.dst.base)[od] = acc;
+}
+
+__global__ void __launch_bounds__(256) reduce_kernel(const ReducePiece *__restrict__ pieces,
+                                                     const DView *__restrict__ srcs, int n, uint64_t total) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        int pi = find_rpiece(pieces, n, e);
+        const ReducePiece &p = pieces[pi];
+        uint64_t l = e - p.elem_begin;
+        int64_t ext[3] = {1, 1, 1};
+        for (int d = 0; d < p.nd; ++d) ext[d] = p.hi[d] - p.lo[d] + 1;
+        int64_t idx[3] = {0, 0, 0};
+        for (int d = p.nd - 1; d >= 0; --d) {
+            idx[d] = p.lo[d] + (int64_t)(l % (uint64_t)ext[d]);
+            l /= (uint64_t)ext[d];
+        }
+        if (p.dtype == 0)
+            reduce_one<float>(p, srcs, idx);
+        else if (p.dtype == 3)
+            reduce_one<uint32_t>(p, srcs, idx);
+        else if (p.dtype == 2)
+            reduce_one<unsigned char>(p, srcs, idx);
+    }
+}
+
+}  // namespace
+
+namespace k {
+
+cudaError_t fill(const FillDesc &d, cudaStream_t st) {
+    int64_t rows = 1;
+    for (int k2 = 0; k2 < d.nd - 1; ++k2) rows *= d.hi[k2] - d.lo[k2] + 1;
+    int64_t w = d.hi[d.nd - 1] - d.lo[d.nd - 1] + 1;
+    int64_t units = rows * ((w + 8191) / 8192);
+    int64_t grid = units < 152 * 64 ? units : 152 * 64;
+    fill_kernel<<<(unsigned)grid, 256, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t copy_pieces(const CopyPiece *dev, int n, uint64_t total_units, cudaStream_t st) {
+    if (!n || !total_units) return cudaSuccess;
+    if (total_units > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    copy_kernel<<<(unsigned)total_units, 256, 0, st>>>(dev, n);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_pieces(const ReducePiece *dev, const DView *srcs, int n, uint64_t total_elems, cudaStream_t st) {
+    if (!n || !total_elems) return cudaSuccess;
+    uint64_t blocks = (total_elems + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(dev, srcs, n, total_elems);
+    return cudaGetLastError();
+}
+
+}  // namespace k
+}  // namespace lt

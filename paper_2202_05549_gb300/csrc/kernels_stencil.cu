@@ -1,0 +1,208 @@
+// Stencil built-ins, written in the paper's convention (Sec. 3.5): the body
+// is a device function of the virtual (global) index and of views whose
+// base already has the chunk offset subtracted (DView), so the same code
+// runs on any superblock of any chunking.
+//
+//   stencil1d (Listings 1-2):  out[i] = (in[i-1] + in[i] + in[i+1]) / 3.0
+//   jacobi2d  (HotSpot-like 5-point stencil of Sec. 4.2):
+//       V[i,j] = ((((U[i,j] + U[i-1,j]) + U[i+1,j]) + U[i,j-1]) + U[i,j+1]) / 5
+// Out-of-domain reads are 0.  Sums use __fadd_rn and the division __fdiv_rn,
+// so no FMA contraction changes the order: chunked and unchunked results are
+// bit-identical, and equal to the CPU definition.
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace lt {
+namespace {
+
+__device__ __forceinline__ int find_task(const ExecTask *t, int n, uint32_t cta) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (t[mid].cta_begin <= cta)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------ 1-D example
+__device__ __forceinline__ void stencil1d_body(int64_t i, int64_t n, const DView &out, const DView &in) {
+    const float *ip = (const float *)in.base;
+    float left = i - 1 >= 0 ? ip[(i - 1) * in.s[0]] : 0.0f;
+    float mid = ip[i * in.s[0]];
+    float right = i + 1 < n ? ip[(i + 1) * in.s[0]] : 0.0f;
+    float s = __fadd_rn(__fadd_rn(left, mid), right);
+    ((float *)out.base)[i * out.s[0]] = __double2float_rn(__ddiv_rn((double)s, 3.0));
+}
+
+__global__ void __launch_bounds__(256) stencil1d_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    int ti = find_task(tasks, p.ntasks, blockIdx.x);
+    const ExecTask &t = tasks[ti];
+    int64_t n = p.shape[0][0];
+    int64_t i = t.t_lo[0] + (int64_t)(blockIdx.x - t.cta_begin) * blockDim.x + threadIdx.x;
+    if (i > t.t_hi[0] || i >= n) return;
+    stencil1d_body(i, n, t.v[0], t.v[1]);
+}
+
+// ------------------------------------------------------------------ 2-D Jacobi
+constexpr int JR = 16;       // output rows per warp tile
+constexpr int JWARPS = 4;    // warps per CTA, side by side along x
+constexpr int JCOLS = 128;   // columns per warp (4 per lane)
+
+__device__ __forceinline__ float j5(float c, float n, float s, float w, float e) {
+    float acc = __fadd_rn(c, n);
+    acc = __fadd_rn(acc, s);
+    acc = __fadd_rn(acc, w);
+    acc = __fadd_rn(acc, e);
+    return __fdiv_rn(acc, 5.0f);
+}
+
+// Vector variant: every lane owns 4 adjacent columns of a 128-column strip and
+// sweeps JR rows, keeping JR+2 input rows in registers (all loads issued
+// before any arithmetic); horizontal neighbours come from the adjacent lanes.
+__global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    int ti = find_task(tasks, p.ntasks, blockIdx.x);
+    const ExecTask &t = tasks[ti];
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
+    const int64_t xe = min(t.t_hi[0], NX - 1), ye = min(t.t_hi[1], NY - 1);  // last output column / row
+    const int64_t width = t.t_hi[0] - x0 + 1;
+    const int64_t gx = (width + JWARPS * JCOLS - 1) / (JWARPS * JCOLS);
+    const int64_t local = blockIdx.x - t.cta_begin;
+    const int64_t tx = local % gx, ty = local / gx;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t js = x0 + (tx * JWARPS + warp) * JCOLS;  // first column of this warp's strip
+    const int64_t j0 = js + lane * 4;
+    const int64_t r0 = y0 + ty * JR;
+    const int64_t rlast = min(r0 + JR - 1, ye);
+    const int64_t cmax = min(xe + 1, NX - 1);  // last column that may be read
+    if (js > xe || r0 > ye) return;  // warp-uniform: nothing to write
+    const DView U = t.v[0], V = t.v[1];
+    const float *ub = (const float *)U.base;
+    const bool ld = j0 <= cmax;
+
+    float4 row[JR + 2];
+    float wl[JR], er[JR];
+#pragma unroll
+    for (int k = 0; k < JR + 2; ++k) {
+        int64_t r = r0 - 1 + k;
+        row[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ld && r >= 0 && r < NY && r <= rlast + 1) row[k] = *(const float4 *)(ub + r * U.s[0] + j0);
+    }
+#pragma unroll
+    for (int k = 0; k < JR; ++k) {
+        int64_t r = r0 + k;
+        wl[k] = 0.f;
+        er[k] = 0.f;
+        if (r <= rlast) {
+            if (lane == 0 && j0 - 1 >= 0 && ld) wl[k] = ub[r * U.s[0] + j0 - 1];
+            if (lane == 31 && j0 + 4 <= cmax) er[k] = ub[r * U.s[0] + j0 + 4];
+        }
+    }
+    // columns of this lane that lie outside the domain read as 0
+#pragma unroll
+    for (int k = 0; k < JR + 2; ++k) {
+        if (j0 + 1 > NX - 1) row[k].y = 0.f;
+        if (j0 + 2 > NX - 1) row[k].z = 0.f;
+        if (j0 + 3 > NX - 1) row[k].w = 0.f;
+    }
+    float *vb = (float *)V.base;
+#pragma unroll
+    for (int k = 0; k < JR; ++k) {
+        int64_t r = r0 + k;
+        const float4 up = row[k], mid = row[k + 1], dn = row[k + 2];
+        float w_in = __shfl_up_sync(0xffffffffu, mid.w, 1);
+        float e_in = __shfl_down_sync(0xffffffffu, mid.x, 1);
+        float w = lane == 0 ? wl[k] : w_in;
+        float e = lane == 31 ? er[k] : e_in;
+        if (r > rlast || j0 > xe) continue;
+        float4 o;
+        o.x = j5(mid.x, up.x, dn.x, w, mid.y);
+        o.y = j5(mid.y, up.y, dn.y, mid.x, mid.z);
+        o.z = j5(mid.z, up.z, dn.z, mid.y, mid.w);
+        o.w = j5(mid.w, up.w, dn.w, mid.z, e);
+        float *dst = vb + r * V.s[0] + j0;
+        if (j0 + 3 <= xe) {
+            *(float4 *)dst = o;
+        } else {
+            dst[0] = o.x;
+            if (j0 + 1 <= xe) dst[1] = o.y;
+            if (j0 + 2 <= xe) dst[2] = o.z;
+        }
+    }
+}
+
+// Scalar variant for unaligned tasks: one thread per output cell.
+__global__ void __launch_bounds__(256) jacobi2d_scalar_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    int ti = find_task(tasks, p.ntasks, blockIdx.x);
+    const ExecTask &t = tasks[ti];
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    const int64_t width = t.t_hi[0] - t.t_lo[0] + 1;
+    const int64_t cell = (int64_t)(blockIdx.x - t.cta_begin) * blockDim.x + threadIdx.x;
+    const int64_t j = t.t_lo[0] + cell % width, i = t.t_lo[1] + cell / width;
+    if (i > t.t_hi[1] || i >= NY || j >= NX) return;
+    const DView U = t.v[0], V = t.v[1];
+    const float *u = (const float *)U.base;
+    auto at = [&](int64_t a, int64_t b) { return u[a * U.s[0] + b * U.s[1]]; };
+    float c = at(i, j);
+    float n = i > 0 ? at(i - 1, j) : 0.f;
+    float s = i + 1 < NY ? at(i + 1, j) : 0.f;
+    float w = j > 0 ? at(i, j - 1) : 0.f;
+    float e = j + 1 < NX ? at(i, j + 1) : 0.f;
+    ((float *)V.base)[i * V.s[0] + j * V.s[1]] = j5(c, n, s, w, e);
+}
+
+}  // namespace
+
+namespace k {
+
+uint32_t prepare_stencil1d(ExecTask *t, int n, ExecParams &p) {
+    (void)p;
+    uint32_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        int64_t len = t[i].t_hi[0] - t[i].t_lo[0] + 1;
+        t[i].cta_begin = total;
+        t[i].cta_count = (uint32_t)((len + 255) / 256);
+        total += t[i].cta_count;
+    }
+    return total;
+}
+
+cudaError_t launch_stencil1d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
+    stencil1d_kernel<<<ctas, 256, 0, st>>>(dev, p);
+    return cudaGetLastError();
+}
+
+uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p) {
+    bool vec = true;
+    for (int i = 0; i < n && vec; ++i) {
+        if (t[i].t_lo[0] % 4 != 0) vec = false;
+        for (int a = 0; a < 2; ++a)
+            if (t[i].v[a].s[1] != 1 || (t[i].v[a].s[0] % 4) != 0 || (t[i].v[a].base % 16) != 0) vec = false;
+    }
+    p.variant = vec ? 1 : 0;
+    uint32_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        int64_t w = t[i].t_hi[0] - t[i].t_lo[0] + 1, h = t[i].t_hi[1] - t[i].t_lo[1] + 1;
+        uint64_t c = vec ? (uint64_t)((w + JWARPS * JCOLS - 1) / (JWARPS * JCOLS)) * (uint64_t)((h + JR - 1) / JR)
+                         : (uint64_t)((w * h + 255) / 256);
+        t[i].cta_begin = total;
+        t[i].cta_count = (uint32_t)c;
+        total += (uint32_t)c;
+    }
+    return total;
+}
+
+cudaError_t launch_jacobi2d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
+    if (p.variant == 1)
+        jacobi2d_vec_kernel<<<ctas, JWARPS * 32, 0, st>>>(dev, p);
+    else
+        jacobi2d_scalar_kernel<<<ctas, 256, 0, st>>>(dev, p);
+    return cudaGetLastError();
+}
+
+}  // namespace k
+}  // namespace lt

@@ -1,0 +1,1716 @@
+// Runtime of the single-GPU annotated-launch engine: context, stream-ordered
+// fences, pooled memory with LRU spilling, the launch executor and the C ABI.
+//
+// Scheduling model (Sec. 3.3 "Scheduling", Sec. 3.4 "Memory Management"),
+// re-designed for one GPU: the planner runs on the calling thread and turns
+// each launch into operations on three CUDA streams (compute, host->device,
+// device->host).  Every chunk carries two fence sets: `ready` (operations
+// that produced its current contents) and `busy` (operations that read or
+// wrote the memory it occupies).  A task waits on the fences its accesses
+// conflict with (read-after-write, write-after-read, write-after-write), so
+// the dependency DAG of Sec. 2.4 is realised as CUDA event waits between the
+// three in-order streams, and lt_launch returns before the GPU runs it.
+// Memory decisions (which chunk to evict, where a fetch lands) are made at
+// enqueue time in program order; freed memory keeps the fences of its last
+// users, so reuse never races with them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "core.hpp"
+#include "kernels.cuh"
+#include "lightning.h"
+
+using namespace lt;
+
+static thread_local std::string g_err;
+
+static lt_status fail(lt_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+extern "C" const char *lt_last_error(void) { return g_err.c_str(); }
+
+namespace {
+
+enum { S_COMP = 0, S_H2D = 1, S_D2H = 2, NSTREAM = 3 };
+enum { LOC_NONE = 0, LOC_DEV = 1, LOC_HOST = 2 };
+const int RING = 1024;
+const size_t ALIGN = 1024;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Allocation size class: requests are rounded up to 1/128 of their power of
+// two (under 1% waste), so chunks of nearly equal size (a band with one halo
+// row fewer) fit each other's holes and the pool does not fragment.
+size_t size_class(size_t sz) {
+    if (sz == 0) sz = 1;
+    size_t g = ALIGN;
+    if (sz > ((size_t)1 << 17)) {
+        int lg = 63 - __builtin_clzll((unsigned long long)sz);
+        g = (size_t)1 << (lg - 7);
+    }
+    return align_up(sz, g);
+}
+
+struct FenceSet {
+    uint64_t q[NSTREAM] = {0, 0, 0};
+    void add(int s, uint64_t v) {
+        if (v > q[s]) q[s] = v;
+    }
+    void merge(const FenceSet &o) {
+        for (int s = 0; s < NSTREAM; ++s) add(s, o.q[s]);
+    }
+    static FenceSet one(int s, uint64_t v) {
+        FenceSet f;
+        f.add(s, v);
+        return f;
+    }
+};
+
+// Pool of one pre-allocated region; best-fit with coalescing.  Each free
+// block remembers the fences of the operations that last used its memory.
+struct Arena {
+    size_t cap = 0;
+    char *base = nullptr;
+    std::map<size_t, std::pair<size_t, FenceSet>> free_;
+    size_t used = 0, peak = 0;
+
+    void init(size_t c, char *b) {
+        cap = c / ALIGN * ALIGN;
+        base = b;
+        free_.clear();
+        if (cap) free_[0] = {cap, FenceSet()};
+        used = peak = 0;
+    }
+    bool alloc(size_t sz, size_t *off, FenceSet *f) {
+        sz = size_class(sz);
+        auto best = free_.end();
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second.first >= sz && (best == free_.end() || it->second.first < best->second.first)) best = it;
+        if (best == free_.end()) return false;
+        *off = best->first;
+        *f = best->second.second;
+        size_t rem = best->second.first - sz;
+        FenceSet keep = best->second.second;
+        free_.erase(best);
+        if (rem) free_[*off + sz] = {rem, keep};
+        used += sz;
+        peak = std::max(peak, used);
+        return true;
+    }
+    void release(size_t off, size_t sz, const FenceSet &f) {
+        sz = size_class(sz);
+        used -= sz;
+        FenceSet fs = f;
+        auto it = free_.lower_bound(off);
+        if (it != free_.end() && it->first == off + sz) {
+            sz += it->second.first;
+            fs.merge(it->second.second);
+            it = free_.erase(it);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second.first == off) {
+                pv->second.first += sz;
+                pv->second.second.merge(fs);
+                return;
+            }
+        }
+        free_[off] = {sz, fs};
+    }
+    size_t largest_free() const {
+        size_t m = 0;
+        for (auto &kv : free_) m = std::max(m, kv.second.first);
+        return m;
+    }
+};
+
+struct CState {
+    int loc = LOC_NONE;
+    size_t off = 0;
+    FenceSet ready, busy;
+    uint64_t lru = 0;
+    int pin = 0;
+    int64_t dead_launch = -1;
+};
+
+struct BuiltinDef {
+    int id;
+    const char *canon;
+    int narr;
+    int dtype[LT_MAX_ARRAYS];
+    int nd[LT_MAX_ARRAYS];
+    uint32_t (*prepare)(ExecTask *, int, ExecParams &);
+    cudaError_t (*launch)(const ExecTask *, uint32_t, const ExecParams &, cudaStream_t);
+};
+
+const BuiltinDef kBuiltins[] = {
+    {LT_K_PLAN_ONLY, nullptr, 0, {0}, {0}, nullptr, nullptr},
+    {LT_K_STENCIL1D, "global i => write A0[i], read A1[i-1:i+1]", 2, {LT_F32, LT_F32}, {1, 1},
+     k::prepare_stencil1d, k::launch_stencil1d},
+    {LT_K_JACOBI2D, "global [i, j] => read A0[i-1:i+1, j-1:j+1], write A1[i, j]", 2, {LT_F32, LT_F32}, {2, 2},
+     k::prepare_jacobi2d, k::launch_jacobi2d},
+};
+
+const BuiltinDef *find_builtin(int id) {
+    for (const auto &b : kBuiltins)
+        if (b.id == id) return &b;
+    return nullptr;
+}
+
+}  // namespace
+
+struct lt_array {
+    ArrayGeom g;
+    std::vector<CState> cs;
+    int64_t id = 0;
+};
+
+struct lt_kernel {
+    const BuiltinDef *def = nullptr;
+    Annotation ann, canon;
+    std::vector<lt_param> params;
+    std::vector<std::string> names;
+    std::vector<int> stmt_of_param;  // annotation statement of each parameter (-1 = value)
+    std::vector<int> slot_of_param;  // array slot of each parameter (-1 = value)
+    std::vector<int> canon_stmt;     // canonical statement of each array slot
+};
+
+struct TimedOp {
+    int cat;
+    cudaEvent_t a, b;
+};
+
+struct UploadUse {
+    size_t off, end;
+    uint64_t seq;
+};
+
+struct lt_ctx {
+    lt_config cfg{};
+    bool dry = false;
+    bool poisoned = false;
+    cudaStream_t st[NSTREAM] = {nullptr, nullptr, nullptr};
+    uint64_t seq[NSTREAM] = {0, 0, 0};
+    std::vector<cudaEvent_t> ev[NSTREAM];
+    std::vector<uint64_t> evseq[NSTREAM];
+    std::vector<int64_t> evtask[NSTREAM];
+    Arena dev, host;
+    char *dev_base = nullptr;
+    char *host_base = nullptr;
+    // descriptor upload ring
+    char *up_host = nullptr, *up_dev = nullptr;
+    size_t up_cap = 0, up_head = 0;
+    std::deque<UploadUse> up_inflight;
+    uint32_t *err_word = nullptr;  // device error word
+    std::vector<std::unique_ptr<lt_array>> arrays;
+    std::vector<std::unique_ptr<lt_kernel>> kernels;
+    uint64_t clock = 0;
+    int64_t launch_id = 0;
+    int64_t task_id = 0;
+    int64_t next_array_id = 1;
+    lt_stats stats{};
+    bool log_on = false;
+    std::ostringstream log;
+    int log_n = 0;
+    std::vector<TimedOp> timed;
+    std::vector<cudaEvent_t> tev_pool;
+    // current operation (between op_begin and op_end)
+    int cur_stream = 0;
+    int64_t cur_task = -1;
+    std::vector<int64_t> cur_deps;
+};
+
+namespace {
+
+#define CK(ctx, expr)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            (ctx)->poisoned = true;                                                            \
+            return fail(LT_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));      \
+        }                                                                                      \
+    } while (0)
+
+// ---------------------------------------------------------------- fences
+lt_status op_begin(lt_ctx *c, int s, const char *kind) {
+    c->cur_stream = s;
+    c->cur_task = ++c->task_id;
+    c->cur_deps.clear();
+    if (c->log_on) {
+        c->log << (c->log_n++ ? "," : "") << "{\"id\":" << c->cur_task << ",\"kind\":\"" << kind
+               << "\",\"stream\":" << s << ",\"launch\":" << c->launch_id;
+    }
+    return LT_OK;
+}
+
+lt_status op_wait(lt_ctx *c, const FenceSet &f) {
+    int s = c->cur_stream;
+    for (int t = 0; t < NSTREAM; ++t) {
+        uint64_t q = f.q[t];
+        if (!q) continue;
+        int slot = (int)(q % RING);
+        bool live = c->evseq[t][slot] == q;
+        if (live) {
+            int64_t pt = c->evtask[t][slot];
+            if (pt >= 0 && std::find(c->cur_deps.begin(), c->cur_deps.end(), pt) == c->cur_deps.end()) {
+                c->cur_deps.push_back(pt);
+                c->stats.deps++;
+            }
+        }
+        if (t == s || c->dry || !live) continue;
+        CK(c, cudaStreamWaitEvent(c->st[s], c->ev[t][slot], 0));
+    }
+    return LT_OK;
+}
+
+// Finish the current operation: record its fence on its stream.
+lt_status op_end(lt_ctx *c, uint64_t *out_seq, const std::string &extra = "") {
+    int s = c->cur_stream;
+    uint64_t q = ++c->seq[s];
+    int slot = (int)(q % RING);
+    if (!c->dry) {
+        if (c->evseq[s][slot] != 0) CK(c, cudaEventSynchronize(c->ev[s][slot]));  // bounded run-ahead
+        CK(c, cudaEventRecord(c->ev[s][slot], c->st[s]));
+    }
+    c->evseq[s][slot] = q;
+    c->evtask[s][slot] = c->cur_task;
+    if (c->log_on) {
+        c->log << ",\"deps\":[";
+        for (size_t i = 0; i < c->cur_deps.size(); ++i) c->log << (i ? "," : "") << c->cur_deps[i];
+        c->log << "]" << extra << "}";
+    }
+    *out_seq = q;
+    return LT_OK;
+}
+
+lt_status host_wait(lt_ctx *c, int s, uint64_t q) {
+    if (c->dry || !q) return LT_OK;
+    int slot = (int)(q % RING);
+    if (c->evseq[s][slot] == q) CK(c, cudaEventSynchronize(c->ev[s][slot]));
+    return LT_OK;
+}
+
+// timing events around one operation (LT_FLAG_TIMING)
+cudaEvent_t tev_get(lt_ctx *c) {
+    if (!c->tev_pool.empty()) {
+        cudaEvent_t e = c->tev_pool.back();
+        c->tev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+enum { CAT_EXEC = 0, CAT_COPYK = 1, CAT_H2D = 2, CAT_D2H = 3, CAT_FILL = 4 };
+
+struct TimeScope {
+    lt_ctx *c;
+    int cat;
+    cudaEvent_t a = nullptr;
+    TimeScope(lt_ctx *ctx, int category) : c(ctx), cat(category) {
+        if (!c->dry && (c->cfg.flags & LT_FLAG_TIMING)) {
+            a = tev_get(c);
+            if (a) cudaEventRecord(a, c->st[c->cur_stream]);
+        }
+    }
+    void end() {
+        if (!a) return;
+        cudaEvent_t b = tev_get(c);
+        if (b) {
+            cudaEventRecord(b, c->st[c->cur_stream]);
+            c->timed.push_back({cat, a, b});
+        }
+        a = nullptr;
+    }
+    ~TimeScope() { end(); }
+};
+
+lt_status collect_timing(lt_ctx *c) {
+    for (auto &t : c->timed) {
+        float ms = 0;
+        CK(c, cudaEventElapsedTime(&ms, t.a, t.b));
+        switch (t.cat) {
+            case CAT_EXEC:
+                c->stats.ms_execute += ms;
+                c->stats.n_execute_kernels++;
+                break;
+            case CAT_COPYK:
+                c->stats.ms_copy_kernels += ms;
+                c->stats.n_copy_kernels++;
+                break;
+            case CAT_H2D: c->stats.ms_h2d += ms; break;
+            case CAT_D2H: c->stats.ms_d2h += ms; break;
+            default: c->stats.ms_fill += ms;
+        }
+        c->tev_pool.push_back(t.a);
+        c->tev_pool.push_back(t.b);
+    }
+    c->timed.clear();
+    return LT_OK;
+}
+
+// ---------------------------------------------------------------- views
+DView view_of(lt_ctx *c, const ArrayGeom &g, const ChunkGeom &cg, size_t off) {
+    DView v;
+    uint64_t p = (uint64_t)(uintptr_t)(c->dev_base + off);
+    int64_t o = 0;
+    for (int d = 0; d < 3; ++d) {
+        v.s[d] = d < g.nd ? cg.stride[d] : 0;
+        o += (d < g.nd ? cg.s_origin[d] : 0) * v.s[d];
+    }
+    v.base = p - (uint64_t)(o * (int64_t)g.esize());
+    return v;
+}
+
+// ---------------------------------------------------------------- memory manager
+lt_status evict(lt_ctx *c, lt_array *a, int64_t ci);
+
+// Pick the least-recently-used unpinned resident chunk.
+bool pick_victim(lt_ctx *c, lt_array **va, int64_t *vc) {
+    uint64_t best = UINT64_MAX;
+    *va = nullptr;
+    for (auto &ap : c->arrays) {
+        lt_array *a = ap.get();
+        for (size_t i = 0; i < a->cs.size(); ++i) {
+            const CState &s = a->cs[i];
+            if (s.loc == LOC_DEV && s.pin == 0 && s.lru < best) {
+                best = s.lru;
+                *va = a;
+                *vc = (int64_t)i;
+            }
+        }
+    }
+    return *va != nullptr;
+}
+
+lt_status dev_alloc(lt_ctx *c, size_t bytes, size_t *off, FenceSet *f) {
+    for (;;) {
+        if (c->dev.alloc(bytes, off, f)) return LT_OK;
+        lt_array *va;
+        int64_t vc;
+        if (!pick_victim(c, &va, &vc))
+            return fail(LT_ERR_OOM_DEVICE, "HBM budget too small: no evictable chunk left for a request of " +
+                                               std::to_string(bytes) + " bytes");
+        lt_status st = evict(c, va, vc);
+        if (st) return st;
+    }
+}
+
+lt_status evict(lt_ctx *c, lt_array *a, int64_t ci) {
+    CState &s = a->cs[(size_t)ci];
+    const ChunkGeom &cg = a->g.chunks[(size_t)ci];
+    if (s.dead_launch == c->launch_id) {
+        // contents will be fully overwritten in this launch: drop them
+        FenceSet f = s.busy;
+        f.merge(s.ready);
+        c->dev.release(s.off, cg.bytes, f);
+        s.loc = LOC_NONE;
+        s.ready = FenceSet();
+        s.busy = FenceSet();
+        c->stats.dead_skips++;
+        return LT_OK;
+    }
+    size_t hoff;
+    FenceSet hf;
+    if (!c->host.alloc(cg.bytes, &hoff, &hf))
+        return fail(LT_ERR_OOM_HOST, "pinned host pool too small to evict a chunk of " + std::to_string(cg.bytes) +
+                                         " bytes (host pool " + std::to_string(c->host.cap) + " bytes)");
+    op_begin(c, S_D2H, "evict");
+    FenceSet w = s.ready;
+    w.merge(hf);
+    lt_status st = op_wait(c, w);
+    if (st) return st;
+    if (!c->dry) {
+        TimeScope ts(c, CAT_D2H);
+        CK(c, cudaMemcpyAsync(c->host_base + hoff, c->dev_base + s.off, cg.bytes, cudaMemcpyDeviceToHost,
+                              c->st[S_D2H]));
+    }
+    uint64_t q;
+    std::ostringstream ex;
+    ex << ",\"array\":" << a->id << ",\"chunk\":" << ci << ",\"bytes\":" << cg.bytes;
+    st = op_end(c, &q, ex.str());
+    if (st) return st;
+    FenceSet rel = s.busy;
+    rel.merge(s.ready);
+    rel.add(S_D2H, q);
+    c->dev.release(s.off, cg.bytes, rel);
+    s.loc = LOC_HOST;
+    s.off = hoff;
+    s.ready = FenceSet::one(S_D2H, q);
+    s.busy = FenceSet::one(S_D2H, q);
+    c->stats.evictions++;
+    c->stats.bytes_d2h += cg.bytes;
+    return LT_OK;
+}
+
+// Materialise chunk ci of a in device memory.  need_data: its current
+// contents must be preserved (fetched from host, or zero if never written).
+lt_status ensure_dev(lt_ctx *c, lt_array *a, int64_t ci, bool need_data) {
+    CState &s = a->cs[(size_t)ci];
+    const ChunkGeom &cg = a->g.chunks[(size_t)ci];
+    s.lru = ++c->clock;
+    if (s.dead_launch == c->launch_id) need_data = false;
+    s.dead_launch = -1;  // first touch in this launch done
+    if (s.loc == LOC_DEV) return LT_OK;
+    s.pin++;
+    size_t off;
+    FenceSet bf;
+    lt_status st = dev_alloc(c, cg.bytes, &off, &bf);
+    s.pin--;
+    if (st) return st;
+    if (s.loc == LOC_HOST) {
+        if (need_data) {
+            op_begin(c, S_H2D, "fetch");
+            FenceSet w = s.ready;
+            w.merge(bf);
+            st = op_wait(c, w);
+            if (st) return st;
+            if (!c->dry) {
+                TimeScope ts(c, CAT_H2D);
+                CK(c, cudaMemcpyAsync(c->dev_base + off, c->host_base + s.off, cg.bytes, cudaMemcpyHostToDevice,
+                                      c->st[S_H2D]));
+            }
+            uint64_t q;
+            std::ostringstream ex;
+            ex << ",\"array\":" << a->id << ",\"chunk\":" << ci << ",\"bytes\":" << cg.bytes;
+            st = op_end(c, &q, ex.str());
+            if (st) return st;
+            FenceSet rel = s.busy;
+            rel.merge(s.ready);
+            rel.add(S_H2D, q);
+            c->host.release(s.off, cg.bytes, rel);
+            s.ready = FenceSet::one(S_H2D, q);
+            s.busy = FenceSet::one(S_H2D, q);
+            c->stats.fetches++;
+            c->stats.bytes_h2d += cg.bytes;
+        } else {
+            FenceSet rel = s.busy;
+            rel.merge(s.ready);
+            c->host.release(s.off, cg.bytes, rel);
+            s.ready = FenceSet();
+            s.busy = bf;
+            c->stats.dead_skips++;
+        }
+    } else {  // never materialised: contents are zero
+        if (need_data) {
+            op_begin(c, S_COMP, "zero");
+            st = op_wait(c, bf);
+            if (st) return st;
+            if (!c->dry) CK(c, cudaMemsetAsync(c->dev_base + off, 0, cg.bytes, c->st[S_COMP]));
+            uint64_t q;
+            st = op_end(c, &q);
+            if (st) return st;
+            s.ready = FenceSet::one(S_COMP, q);
+            s.busy = FenceSet::one(S_COMP, q);
+        } else {
+            s.ready = FenceSet();
+            s.busy = bf;
+        }
+    }
+    s.loc = LOC_DEV;
+    s.off = off;
+    return LT_OK;
+}
+
+// Upload a descriptor table for the next compute-stream kernel.
+lt_status upload(lt_ctx *c, const void *src, size_t n, void **dev_ptr, size_t *ring_off) {
+    if (c->dry) {
+        *dev_ptr = nullptr;
+        return LT_OK;
+    }
+    size_t sz = align_up(n ? n : 1, 256);
+    if (sz > c->up_cap) return fail(LT_ERR_UNSUPPORTED, "descriptor table larger than the upload ring");
+    if (c->up_head + sz > c->up_cap) c->up_head = 0;
+    size_t off = c->up_head;
+    for (auto it = c->up_inflight.begin(); it != c->up_inflight.end();) {
+        if (it->off < off + sz && it->end > off) {
+            lt_status st = host_wait(c, S_COMP, it->seq);
+            if (st) return st;
+            it = c->up_inflight.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    std::memcpy(c->up_host + off, src, n);
+    CK(c, cudaMemcpyAsync(c->up_dev + off, c->up_host + off, n, cudaMemcpyHostToDevice, c->st[S_COMP]));
+    c->up_head = off + sz;
+    *dev_ptr = c->up_dev + off;
+    *ring_off = off;
+    return LT_OK;
+}
+
+void upload_done(lt_ctx *c, size_t off, size_t n, uint64_t seq) {
+    if (c->dry) return;
+    c->up_inflight.push_back({off, off + align_up(n ? n : 1, 256), seq});
+}
+
+lt_status check_ctx(lt_ctx *c) {
+    if (!c) return fail(LT_ERR_INVALID_ARG, "null context");
+    if (c->poisoned) return fail(LT_ERR_BUSY, "context poisoned by an earlier CUDA error or timeout");
+    return LT_OK;
+}
+
+lt_array *find_array(lt_ctx *c, const lt_array *a) {
+    for (auto &p : c->arrays)
+        if (p.get() == a) return p.get();
+    return nullptr;
+}
+
+lt_kernel *find_kernel(lt_ctx *c, const lt_kernel *k) {
+    for (auto &p : c->kernels)
+        if (p.get() == k) return p.get();
+    return nullptr;
+}
+
+lt_status sync_all(lt_ctx *c) {
+    if (c->dry) return LT_OK;
+    for (int s = 0; s < NSTREAM; ++s) CK(c, cudaStreamSynchronize(c->st[s]));
+    uint32_t e = 0;
+    CK(c, cudaMemcpy(&e, c->err_word, 4, cudaMemcpyDeviceToHost));
+    if (e) {
+        CK(c, cudaMemset(c->err_word, 0, 4));
+        return fail(LT_ERR_DEVICE_CHECK, "a kernel recorded an out-of-region access (code " + std::to_string(e) + ")");
+    }
+    return collect_timing(c);
+}
+
+// ---------------------------------------------------------------- host transfers
+// Copy between the dense row-major host buffer `hb` (whole array) and the
+// part `box` of chunk ci that lives in device memory.
+lt_status xfer_chunk(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *hb, bool to_dev) {
+    const ArrayGeom &g = a->g;
+    const ChunkGeom &cg = g.chunks[(size_t)ci];
+    CState &s = a->cs[(size_t)ci];
+    size_t es = g.esize();
+    int64_t gs[3] = {1, 1, 1};
+    for (int d = g.nd - 2; d >= 0; --d) gs[d] = gs[d + 1] * g.shape[d + 1];
+    char *dev = c->dev_base + s.off;
+    auto dev_addr = [&](int64_t i0, int64_t i1, int64_t i2) {
+        int64_t idx[3] = {i0, i1, i2};
+        int64_t o = 0;
+        for (int d = 0; d < g.nd; ++d) o += (idx[d] - cg.s_origin[d]) * cg.stride[d];
+        return dev + o * (int64_t)es;
+    };
+    auto host_addr = [&](int64_t i0, int64_t i1, int64_t i2) {
+        int64_t idx[3] = {i0, i1, i2};
+        int64_t o = 0;
+        for (int d = 0; d < g.nd; ++d) o += idx[d] * gs[d];
+        return hb + o * (int64_t)es;
+    };
+    cudaStream_t st = c->st[S_COMP];
+    if (g.dist.order == LT_ORDER_COL) {
+        // column-major chunk: transpose on the host through a staging vector
+        int64_t R = box.extent(0), Cn = box.extent(1);
+        std::vector<char> tmp((size_t)(R * Cn) * es);
+        if (to_dev) {
+            for (int64_t j = 0; j < Cn; ++j)
+                for (int64_t i = 0; i < R; ++i)
+                    std::memcpy(&tmp[(size_t)(j * R + i) * es], host_addr(box.lo[0] + i, box.lo[1] + j, 0), es);
+            CK(c, cudaMemcpy2DAsync(dev_addr(box.lo[0], box.lo[1], 0), (size_t)cg.stride[1] * es, tmp.data(),
+                                    (size_t)R * es, (size_t)R * es, (size_t)Cn, cudaMemcpyHostToDevice, st));
+            CK(c, cudaStreamSynchronize(st));
+        } else {
+            CK(c, cudaMemcpy2DAsync(tmp.data(), (size_t)R * es, dev_addr(box.lo[0], box.lo[1], 0),
+                                    (size_t)cg.stride[1] * es, (size_t)R * es, (size_t)Cn, cudaMemcpyDeviceToHost,
+                                    st));
+            CK(c, cudaStreamSynchronize(st));
+            for (int64_t j = 0; j < Cn; ++j)
+                for (int64_t i = 0; i < R; ++i)
+                    std::memcpy(host_addr(box.lo[0] + i, box.lo[1] + j, 0), &tmp[(size_t)(j * R + i) * es], es);
+        }
+        return LT_OK;
+    }
+    int nd = g.nd;
+    int64_t n0 = nd == 3 ? box.extent(0) : 1;
+    for (int64_t z = 0; z < n0; ++z) {
+        int64_t i0 = nd == 3 ? box.lo[0] + z : (nd == 2 ? box.lo[0] : box.lo[0]);
+        size_t width, rows, dpitch, hpitch;
+        char *dp, *hp;
+        if (nd == 1) {
+            width = (size_t)box.extent(0) * es;
+            rows = 1;
+            dpitch = hpitch = width;
+            dp = dev_addr(box.lo[0], 0, 0);
+            hp = host_addr(box.lo[0], 0, 0);
+        } else if (nd == 2) {
+            width = (size_t)box.extent(1) * es;
+            rows = (size_t)box.extent(0);
+            dpitch = (size_t)cg.stride[0] * es;
+            hpitch = (size_t)gs[0] * es;
+            dp = dev_addr(box.lo[0], box.lo[1], 0);
+            hp = host_addr(box.lo[0], box.lo[1], 0);
+        } else {
+            width = (size_t)box.extent(2) * es;
+            rows = (size_t)box.extent(1);
+            dpitch = (size_t)cg.stride[1] * es;
+            hpitch = (size_t)gs[1] * es;
+            dp = dev_addr(i0, box.lo[1], box.lo[2]);
+            hp = host_addr(i0, box.lo[1], box.lo[2]);
+        }
+        if (to_dev)
+            CK(c, cudaMemcpy2DAsync(dp, dpitch, hp, hpitch, width, rows, cudaMemcpyHostToDevice, st));
+        else
+            CK(c, cudaMemcpy2DAsync(hp, hpitch, dp, dpitch, width, rows, cudaMemcpyDeviceToHost, st));
+    }
+    CK(c, cudaStreamSynchronize(st));
+    return LT_OK;
+}
+
+// Same for a chunk resident in the pinned host pool (plain CPU copy).
+void xfer_chunk_host(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *hb, bool to_chunk) {
+    const ArrayGeom &g = a->g;
+    const ChunkGeom &cg = g.chunks[(size_t)ci];
+    size_t es = g.esize();
+    char *base = c->host_base + a->cs[(size_t)ci].off;
+    int64_t gs[3] = {1, 1, 1};
+    for (int d = g.nd - 2; d >= 0; --d) gs[d] = gs[d + 1] * g.shape[d + 1];
+    int64_t e0 = box.extent(0), e1 = g.nd > 1 ? box.extent(1) : 1, e2 = g.nd > 2 ? box.extent(2) : 1;
+    for (int64_t x = 0; x < e0; ++x)
+        for (int64_t y = 0; y < e1; ++y)
+            for (int64_t z = 0; z < e2; ++z) {
+                int64_t idx[3] = {box.lo[0] + x, box.lo[1] + y, box.lo[2] + z};
+                int64_t co = 0, ho = 0;
+                for (int d = 0; d < g.nd; ++d) {
+                    co += (idx[d] - cg.s_origin[d]) * cg.stride[d];
+                    ho += idx[d] * gs[d];
+                }
+                if (to_chunk)
+                    std::memcpy(base + co * (int64_t)es, hb + ho * (int64_t)es, es);
+                else
+                    std::memcpy(hb + ho * (int64_t)es, base + co * (int64_t)es, es);
+            }
+}
+
+// ---------------------------------------------------------------- launches
+struct ArgUse {
+    lt_array *a;
+    int64_t chunk;
+    bool write;
+};
+
+struct TempAlloc {
+    size_t off, bytes;
+    ChunkGeom geom;
+};
+
+// Mark for every written array the chunks whose contents this launch fully
+// overwrites without reading them (no fetch is needed on first touch).
+void mark_dead(lt_ctx *c, lt_kernel *k, const LaunchPlan &plan, const std::vector<lt_array *> &parr) {
+    std::vector<lt_array *> uniq;
+    for (lt_array *a : parr)
+        if (a && std::find(uniq.begin(), uniq.end(), a) == uniq.end()) uniq.push_back(a);
+    for (lt_array *a : uniq) {
+        std::vector<Box> wr, rd;
+        for (const auto &sb : plan.sbs)
+            for (const auto &ap : sb.args) {
+                if (ap.kind == ARG_VALUE || ap.kind == ARG_NONE || parr[(size_t)ap.param] != a) continue;
+                if (ap.mode == MODE_WRITE || ap.mode == MODE_REDUCE)
+                    wr.push_back(ap.region);
+                else
+                    rd.push_back(ap.region);
+            }
+        if (wr.empty()) continue;
+        for (size_t ci = 0; ci < a->g.chunks.size(); ++ci) {
+            const Box &cb = a->g.chunks[ci].box;
+            bool read = false;
+            for (const Box &r : rd)
+                if (!cb.intersect(r).empty()) {
+                    read = true;
+                    break;
+                }
+            if (read) continue;
+            std::vector<Box> parts;
+            for (const Box &w : wr)
+                if (!cb.intersect(w).empty()) parts.push_back(w);
+            if (!parts.empty() && box_covered(cb, parts)) a->cs[ci].dead_launch = c->launch_id;
+        }
+    }
+    (void)k;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
+    if (!cfg || !out) return fail(LT_ERR_INVALID_ARG, "null argument");
+    auto c = std::make_unique<lt_ctx>();
+    c->cfg = *cfg;
+    c->dry = (cfg->flags & LT_FLAG_DRYRUN) != 0;
+    for (int s = 0; s < NSTREAM; ++s) {
+        c->ev[s].assign(RING, nullptr);
+        c->evseq[s].assign(RING, 0);
+        c->evtask[s].assign(RING, -1);
+    }
+    size_t budget = cfg->hbm_budget_bytes;
+    if (c->dry) {
+        if (!budget) budget = (size_t)1 << 34;
+        c->dev.init(budget, nullptr);
+        c->host.init(cfg->host_pool_bytes, nullptr);
+        *out = c.release();
+        return LT_OK;
+    }
+    lt_ctx *cp = c.get();
+    CK(cp, cudaSetDevice(cfg->device));
+    int major = 0, minor = 0;
+    CK(cp, cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, cfg->device));
+    CK(cp, cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, cfg->device));
+    if (major * 10 + minor != 103)
+        return fail(LT_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300) only; device is sm_" +
+                                            std::to_string(major) + std::to_string(minor));
+    for (int s = 0; s < NSTREAM; ++s) {
+        CK(cp, cudaStreamCreateWithFlags(&c->st[s], cudaStreamNonBlocking));
+        for (int i = 0; i < RING; ++i) CK(cp, cudaEventCreateWithFlags(&c->ev[s][i], cudaEventDisableTiming));
+    }
+    size_t fr = 0, tot = 0;
+    CK(cp, cudaMemGetInfo(&fr, &tot));
+    if (!budget) budget = fr / 10 * 9;
+    budget = budget / ALIGN * ALIGN;
+    if (budget > fr) return fail(LT_ERR_OOM_DEVICE, "HBM budget exceeds free device memory");
+    if (cudaMalloc((void **)&c->dev_base, budget) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LT_ERR_OOM_DEVICE, "cudaMalloc of the HBM pool failed");
+    }
+    c->dev.init(budget, c->dev_base);
+    if (cfg->host_pool_bytes) {
+        if (cudaHostAlloc((void **)&c->host_base, cfg->host_pool_bytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->dev_base);
+            return fail(LT_ERR_OOM_HOST, "cudaHostAlloc of the pinned host pool failed");
+        }
+    }
+    c->host.init(cfg->host_pool_bytes, c->host_base);
+    c->up_cap = (size_t)32 << 20;
+    CK(cp, cudaHostAlloc((void **)&c->up_host, c->up_cap, cudaHostAllocDefault));
+    CK(cp, cudaMalloc((void **)&c->up_dev, c->up_cap));
+    CK(cp, cudaMalloc((void **)&c->err_word, 16));
+    CK(cp, cudaMemset(c->err_word, 0, 16));
+    *out = c.release();
+    return LT_OK;
+}
+
+lt_status lt_ctx_destroy(lt_ctx *c) {
+    if (!c) return LT_OK;
+    if (!c->dry) {
+        for (int s = 0; s < NSTREAM; ++s)
+            if (c->st[s]) cudaStreamSynchronize(c->st[s]);
+        for (auto &t : c->timed) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+        for (auto e : c->tev_pool) cudaEventDestroy(e);
+        for (int s = 0; s < NSTREAM; ++s) {
+            for (auto e : c->ev[s])
+                if (e) cudaEventDestroy(e);
+            if (c->st[s]) cudaStreamDestroy(c->st[s]);
+        }
+        if (c->dev_base) cudaFree(c->dev_base);
+        if (c->host_base) cudaFreeHost(c->host_base);
+        if (c->up_host) cudaFreeHost(c->up_host);
+        if (c->up_dev) cudaFree(c->up_dev);
+        if (c->err_word) cudaFree(c->err_word);
+    }
+    delete c;
+    return LT_OK;
+}
+
+lt_status lt_array_create(lt_ctx *c, lt_dtype dtype, int32_t ndim, const int64_t shape[3], const lt_dist *dist,
+                          lt_array **out) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    if (!shape || !dist || !out) return fail(LT_ERR_INVALID_ARG, "null argument");
+    auto a = std::make_unique<lt_array>();
+    std::string err;
+    if (!make_geometry((int)dtype, ndim, shape, *dist, &a->g, &err)) return fail(LT_ERR_INVALID_ARG, err);
+    for (const auto &cg : a->g.chunks)
+        if (cg.bytes > c->dev.cap)
+            return fail(LT_ERR_OOM_DEVICE, "a chunk (" + std::to_string(cg.bytes) + " bytes) exceeds the HBM budget");
+    a->cs.resize(a->g.chunks.size());
+    a->id = c->next_array_id++;
+    *out = a.get();
+    c->arrays.push_back(std::move(a));
+    return LT_OK;
+}
+
+lt_status lt_array_destroy(lt_ctx *c, lt_array *arr) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    lt_array *a = find_array(c, arr);
+    if (!a) return fail(LT_ERR_INVALID_ARG, "unknown array");
+    for (size_t i = 0; i < a->cs.size(); ++i) {
+        CState &s = a->cs[i];
+        FenceSet f = s.busy;
+        f.merge(s.ready);
+        if (s.loc == LOC_DEV) c->dev.release(s.off, a->g.chunks[i].bytes, f);
+        if (s.loc == LOC_HOST) c->host.release(s.off, a->g.chunks[i].bytes, f);
+        s.loc = LOC_NONE;
+    }
+    for (auto it = c->arrays.begin(); it != c->arrays.end(); ++it)
+        if (it->get() == a) {
+            c->arrays.erase(it);
+            break;
+        }
+    return LT_OK;
+}
+
+static size_t array_bytes(const lt_array *a) {
+    size_t n = a->g.esize();
+    for (int d = 0; d < a->g.nd; ++d) n *= (size_t)a->g.shape[d];
+    return n;
+}
+
+lt_status lt_array_write(lt_ctx *c, lt_array *arr, const void *host, size_t bytes) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    lt_array *a = find_array(c, arr);
+    if (!a || (!host && !c->dry)) return fail(LT_ERR_INVALID_ARG, "unknown array or null buffer");
+    if (bytes != array_bytes(a)) return fail(LT_ERR_INVALID_ARG, "buffer size does not match the array");
+    if ((st = sync_all(c))) return st;
+    ++c->launch_id;
+    for (size_t ci = 0; ci < a->cs.size(); ++ci) a->cs[ci].dead_launch = c->launch_id;
+    for (size_t ci = 0; ci < a->cs.size(); ++ci) {
+        CState &s = a->cs[ci];
+        if (s.loc == LOC_HOST && !c->dry) {
+            // rewrite in place in the host pool once earlier copies are done
+            if ((st = sync_all(c))) return st;
+            xfer_chunk_host(c, a, (int64_t)ci, a->g.chunks[ci].box, (char *)host, true);
+            s.dead_launch = -1;
+            continue;
+        }
+        s.pin++;
+        st = ensure_dev(c, a, (int64_t)ci, false);
+        s.pin--;
+        if (st) return st;
+        op_begin(c, S_COMP, "write");
+        FenceSet w = s.ready;
+        w.merge(s.busy);
+        if ((st = op_wait(c, w))) return st;
+        if (!c->dry) {
+            for (int s2 = 0; s2 < NSTREAM; ++s2) CK(c, cudaStreamSynchronize(c->st[s2]));
+            if ((st = xfer_chunk(c, a, (int64_t)ci, a->g.chunks[ci].box, (char *)host, true))) return st;
+        }
+        uint64_t q;
+        if ((st = op_end(c, &q))) return st;
+        s.ready = FenceSet::one(S_COMP, q);
+        s.busy = FenceSet::one(S_COMP, q);
+        c->stats.bytes_h2d += a->g.chunks[ci].box.volume() * a->g.esize();
+    }
+    return sync_all(c);
+}
+
+lt_status lt_array_read(lt_ctx *c, lt_array *arr, void *host, size_t bytes) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    lt_array *a = find_array(c, arr);
+    if (!a || (!host && !c->dry)) return fail(LT_ERR_INVALID_ARG, "unknown array or null buffer");
+    if (bytes != array_bytes(a)) return fail(LT_ERR_INVALID_ARG, "buffer size does not match the array");
+    if ((st = sync_all(c))) return st;
+    if (c->dry) return LT_OK;
+    for (size_t ci = 0; ci < a->cs.size(); ++ci) {
+        const CState &s = a->cs[ci];
+        const Box &ob = a->g.chunks[ci].owned;
+        if (s.loc == LOC_DEV) {
+            if ((st = xfer_chunk(c, a, (int64_t)ci, ob, (char *)host, false))) return st;
+        } else if (s.loc == LOC_HOST) {
+            xfer_chunk_host(c, a, (int64_t)ci, ob, (char *)host, false);
+        } else {
+            // never written: zero
+            std::vector<char> z(a->g.esize(), 0);
+            int64_t gs[3] = {1, 1, 1};
+            for (int d = a->g.nd - 2; d >= 0; --d) gs[d] = gs[d + 1] * a->g.shape[d + 1];
+            int64_t e0 = ob.extent(0), e1 = a->g.nd > 1 ? ob.extent(1) : 1, e2 = a->g.nd > 2 ? ob.extent(2) : 1;
+            for (int64_t x = 0; x < e0; ++x)
+                for (int64_t y = 0; y < e1; ++y) {
+                    int64_t idx[3] = {ob.lo[0] + x, ob.lo[1] + y, ob.lo[2]};
+                    int64_t ho = 0;
+                    for (int d = 0; d < a->g.nd; ++d) ho += idx[d] * gs[d];
+                    std::memset((char *)host + ho * (int64_t)a->g.esize(), 0, (size_t)e2 * a->g.esize());
+                }
+        }
+    }
+    return LT_OK;
+}
+
+lt_status lt_array_fill(lt_ctx *c, lt_array *arr, const lt_init *init) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    lt_array *a = find_array(c, arr);
+    if (!a || !init) return fail(LT_ERR_INVALID_ARG, "unknown array or null init");
+    int kind = init->kind;
+    int dt = a->g.dtype;
+    bool ok = kind == LT_INIT_ZERO || kind == LT_INIT_CONST || (kind == LT_INIT_UNIFORM && dt == LT_F32) ||
+              (kind == LT_INIT_KAPPA && dt == LT_F32) || (kind == LT_INIT_NORMAL_BF16 && dt == LT_BF16) ||
+              (kind == LT_INIT_U8 && dt == LT_U8);
+    if (!ok) return fail(LT_ERR_INVALID_ARG, "fill kind does not match the array dtype");
+    ++c->launch_id;
+    c->stats.launches++;
+    for (size_t ci = 0; ci < a->cs.size(); ++ci) a->cs[ci].dead_launch = c->launch_id;
+    uint64_t key;
+    {
+        uint64_t s0 = init->seed ^ (init->stream << 32);
+        s0 += 0x9E3779B97F4A7C15ULL;
+        uint64_t z = s0;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        key = z ^ (z >> 31);
+    }
+    bool rev = !(c->cfg.flags & LT_FLAG_FIXED_SWEEP) && (c->launch_id & 1);
+    size_t n = a->cs.size();
+    for (size_t kk = 0; kk < n; ++kk) {
+        size_t ci = rev ? n - 1 - kk : kk;
+        CState &s = a->cs[ci];
+        const ChunkGeom &cg = a->g.chunks[ci];
+        s.pin++;
+        st = ensure_dev(c, a, (int64_t)ci, false);
+        s.pin--;
+        if (st) return st;
+        op_begin(c, S_COMP, "fill");
+        FenceSet w = s.ready;
+        w.merge(s.busy);
+        if ((st = op_wait(c, w))) return st;
+        if (!c->dry) {
+            FillDesc d{};
+            d.dst = view_of(c, a->g, cg, s.off);
+            d.nd = a->g.nd;
+            for (int dd = 0; dd < 3; ++dd) {
+                d.lo[dd] = dd < a->g.nd ? cg.box.lo[dd] : 0;
+                d.hi[dd] = dd < a->g.nd ? cg.box.hi[dd] : 0;
+            }
+            int64_t gs = 1;
+            for (int dd = a->g.nd - 1; dd >= 0; --dd) {
+                d.gstride[dd] = gs;
+                gs *= a->g.shape[dd];
+            }
+            d.kind = kind;
+            d.dtype = dt;
+            d.key = key;
+            d.value = init->value;
+            d.scale = init->scale;
+            TimeScope ts(c, CAT_FILL);
+            CK(c, k::fill(d, c->st[S_COMP]));
+            c->stats.kernels++;
+        }
+        uint64_t q;
+        std::ostringstream ex;
+        ex << ",\"array\":" << a->id << ",\"chunk\":" << ci;
+        if ((st = op_end(c, &q, ex.str()))) return st;
+        s.ready = FenceSet::one(S_COMP, q);
+        s.busy = FenceSet::one(S_COMP, q);
+    }
+    return LT_OK;
+}
+
+lt_status lt_array_num_chunks(lt_ctx *c, const lt_array *arr, int64_t *n) {
+    if (!c || !n) return fail(LT_ERR_INVALID_ARG, "null argument");
+    lt_array *a = find_array(c, arr);
+    if (!a) return fail(LT_ERR_INVALID_ARG, "unknown array");
+    *n = (int64_t)a->cs.size();
+    return LT_OK;
+}
+
+lt_status lt_array_chunk_info(lt_ctx *c, const lt_array *arr, int64_t index, int64_t lo[3], int64_t hi[3],
+                              int32_t *location) {
+    if (!c || !lo || !hi || !location) return fail(LT_ERR_INVALID_ARG, "null argument");
+    lt_array *a = find_array(c, arr);
+    if (!a || index < 0 || index >= (int64_t)a->cs.size()) return fail(LT_ERR_INVALID_ARG, "bad array or index");
+    const ChunkGeom &cg = a->g.chunks[(size_t)index];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = d < a->g.nd ? cg.box.lo[d] : 0;
+        hi[d] = d < a->g.nd ? cg.box.hi[d] : 0;
+    }
+    *location = a->cs[(size_t)index].loc;
+    return LT_OK;
+}
+
+lt_status lt_kernel_register(lt_ctx *c, int32_t builtin, const char *annotation, const lt_param *params,
+                             int32_t nparams, lt_kernel **out) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    if (!annotation || (!params && nparams) || !out || nparams < 0 || nparams > 16)
+        return fail(LT_ERR_INVALID_ARG, "bad kernel registration arguments");
+    const BuiltinDef *def = find_builtin(builtin);
+    if (!def) return fail(LT_ERR_UNSUPPORTED, "unknown built-in kernel id " + std::to_string(builtin));
+    auto k = std::make_unique<lt_kernel>();
+    k->def = def;
+    std::string err;
+    if (!parse_annotation(annotation, &k->ann, &err)) return fail(LT_ERR_PARSE, "annotation: " + err);
+    bool plan_only = def->canon == nullptr;
+    if (!plan_only && !parse_annotation(def->canon, &k->canon, &err))
+        return fail(LT_ERR_PARSE, "internal canonical: " + err);
+    int slot = 0;
+    for (int p = 0; p < nparams; ++p) {
+        if (!params[p].name) return fail(LT_ERR_INVALID_ARG, "parameter without a name");
+        k->params.push_back(params[p]);
+        k->names.push_back(params[p].name);
+        if (!params[p].is_array) {
+            k->stmt_of_param.push_back(-1);
+            k->slot_of_param.push_back(-1);
+            continue;
+        }
+        int si = -1;
+        for (size_t s = 0; s < k->ann.stmts.size(); ++s)
+            if (k->ann.stmts[s].array == params[p].name) si = (int)s;
+        if (si < 0) return fail(LT_ERR_INVALID_ARG, std::string("array parameter '") + params[p].name +
+                                                       "' is not named in the annotation");
+        if (!plan_only) {
+            if (slot >= def->narr) return fail(LT_ERR_INVALID_ARG, "too many array parameters for this built-in");
+            if (params[p].dtype != def->dtype[slot])
+                return fail(LT_ERR_INVALID_ARG,
+                            std::string("dtype of '") + params[p].name + "' does not match the built-in");
+            if ((int)k->ann.stmts[(size_t)si].idx.size() != def->nd[slot])
+                return fail(LT_ERR_INVALID_ARG, std::string("'") + params[p].name + "' is indexed with the wrong rank");
+        } else if (slot >= LT_MAX_ARRAYS) {
+            return fail(LT_ERR_INVALID_ARG, "too many array parameters");
+        }
+        k->stmt_of_param.push_back(si);
+        k->slot_of_param.push_back(slot);
+        slot++;
+    }
+    if (!plan_only && slot != def->narr)
+        return fail(LT_ERR_INVALID_ARG, "the built-in needs " + std::to_string(def->narr) + " array parameters");
+    for (const auto &s : k->ann.stmts) {
+        bool found = false;
+        for (const auto &nm : k->names)
+            if (nm == s.array) found = true;
+        if (!found) return fail(LT_ERR_INVALID_ARG, "annotation names unknown array '" + s.array + "'");
+    }
+    // canonical statement of each slot, and mode compatibility
+    k->canon_stmt.assign((size_t)std::max(def->narr, slot), -1);
+    for (size_t p = 0; p < k->params.size() && !plan_only; ++p) {
+        int sl = k->slot_of_param[p];
+        if (sl < 0) continue;
+        std::string nm = "A" + std::to_string(sl);
+        for (size_t s = 0; s < k->canon.stmts.size(); ++s)
+            if (k->canon.stmts[s].array == nm) k->canon_stmt[(size_t)sl] = (int)s;
+        const Stmt &cs = k->canon.stmts[(size_t)k->canon_stmt[(size_t)sl]];
+        const Stmt &us = k->ann.stmts[(size_t)k->stmt_of_param[p]];
+        bool ok;
+        switch (cs.mode) {
+            case MODE_READ: ok = us.mode == MODE_READ || us.mode == MODE_READWRITE; break;
+            case MODE_WRITE: ok = us.mode == MODE_WRITE || us.mode == MODE_READWRITE; break;
+            case MODE_READWRITE: ok = us.mode == MODE_READWRITE; break;
+            default: ok = us.mode == MODE_REDUCE && us.op == cs.op;
+        }
+        if (!ok)
+            return fail(LT_ERR_INVALID_ARG, "access mode of '" + us.array + "' does not allow what the kernel does");
+    }
+    *out = k.get();
+    c->kernels.push_back(std::move(k));
+    return LT_OK;
+}
+
+lt_status lt_kernel_destroy(lt_ctx *c, lt_kernel *kk) {
+    if (!c) return fail(LT_ERR_INVALID_ARG, "null context");
+    for (auto it = c->kernels.begin(); it != c->kernels.end(); ++it)
+        if (it->get() == kk) {
+            c->kernels.erase(it);
+            return LT_OK;
+        }
+    return fail(LT_ERR_INVALID_ARG, "unknown kernel");
+}
+
+static lt_status prepare_plan(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const lt_workdist *wd,
+                              const lt_arg *args, int32_t nargs, LaunchPlan *plan, std::vector<lt_array *> *parr) {
+    if (!k || !find_kernel(c, k)) return fail(LT_ERR_INVALID_ARG, "unknown kernel");
+    if (nargs != (int32_t)k->params.size() || (nargs && !args))
+        return fail(LT_ERR_INVALID_ARG, "argument count does not match the kernel's parameters");
+    std::vector<PlanArray> pa((size_t)nargs);
+    parr->assign((size_t)nargs, nullptr);
+    for (int p = 0; p < nargs; ++p) {
+        if (!k->params[(size_t)p].is_array) continue;
+        lt_array *a = find_array(c, args[p].array);
+        if (!a) return fail(LT_ERR_INVALID_ARG, "argument " + std::to_string(p) + " is not an array of this context");
+        if (a->g.dtype != k->params[(size_t)p].dtype)
+            return fail(LT_ERR_INVALID_ARG, "argument " + std::to_string(p) + " has the wrong dtype");
+        if (a->g.nd != (int)k->ann.stmts[(size_t)k->stmt_of_param[(size_t)p]].idx.size())
+            return fail(LT_ERR_INVALID_ARG, "argument " + std::to_string(p) + " has the wrong rank");
+        pa[(size_t)p].geom = &a->g;
+        (*parr)[(size_t)p] = a;
+    }
+    uint64_t g3[3] = {grid.x, grid.y, grid.z}, b3[3] = {block.x, block.y, block.z};
+    int64_t sb3[3] = {0, 0, 0};
+    if (wd)
+        for (int d = 0; d < 3; ++d) sb3[d] = wd->superblock[d];
+    std::string err;
+    if (!plan_launch(k->ann, k->stmt_of_param, pa, g3, b3, sb3, plan, &err)) return fail(LT_ERR_INVALID_ARG, err);
+    // the annotation must contain every access the built-in makes
+    int64_t B[3];
+    for (int d = 0; d < 3; ++d) B[d] = (int64_t)(b3[d] ? b3[d] : 1);
+    std::vector<int64_t> vlo, vhi;
+    for (const auto &sb : plan->sbs) {
+        if (!k->def->canon) break;
+        var_ranges(k->canon, sb.threads, B, &vlo, &vhi);
+        for (const auto &ap : sb.args) {
+            if (ap.kind == ARG_VALUE) continue;
+            int sl = k->slot_of_param[(size_t)ap.param];
+            const Stmt &cs = k->canon.stmts[(size_t)k->canon_stmt[(size_t)sl]];
+            Box need = eval_region(cs, vlo, vhi, (*parr)[(size_t)ap.param]->g.shape);
+            if (!need.empty() && !ap.region.contains(need))
+                return fail(LT_ERR_INVALID_ARG, "the annotation's region for '" +
+                                                    k->names[(size_t)ap.param] +
+                                                    "' does not contain what the kernel accesses");
+        }
+    }
+    return LT_OK;
+}
+
+lt_status lt_plan_explain(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const lt_workdist *wd,
+                          const lt_arg *args, int32_t nargs, char *buf, size_t cap, size_t *needed) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    LaunchPlan plan;
+    std::vector<lt_array *> parr;
+    if ((st = prepare_plan(c, k, grid, block, wd, args, nargs, &plan, &parr))) return st;
+    std::string js = plan_to_json(plan);
+    if (needed) *needed = js.size() + 1;
+    if (buf && cap) {
+        size_t n = std::min(cap - 1, js.size());
+        std::memcpy(buf, js.data(), n);
+        buf[n] = 0;
+    }
+    return LT_OK;
+}
+
+lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const lt_workdist *wd, const lt_arg *args,
+                    int32_t nargs) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    LaunchPlan plan;
+    std::vector<lt_array *> parr;
+    if ((st = prepare_plan(c, k, grid, block, wd, args, nargs, &plan, &parr))) return st;
+    if (!k->def->launch && !c->dry)
+        return fail(LT_ERR_UNSUPPORTED, "a plan-only kernel can be launched only in a dry-run context");
+    ++c->launch_id;
+    c->stats.launches++;
+    mark_dead(c, k, plan, parr);
+    const BuiltinDef *def = k->def;
+
+    ExecParams ep{};
+    for (size_t p = 0; p < parr.size(); ++p) {
+        int sl = k->slot_of_param[p];
+        if (sl < 0) continue;
+        for (int d = 0; d < 3; ++d) ep.shape[sl][d] = parr[p]->g.shape[d];
+        ep.nd[sl] = parr[p]->g.nd;
+    }
+    {
+        int nf = 0, ni = 0;
+        for (size_t p = 0; p < parr.size(); ++p) {
+            if (k->params[p].is_array) continue;
+            if (k->params[p].dtype == LT_F32 && nf < 4) ep.f[nf++] = args[p].f;
+            if (k->params[p].dtype != LT_F32 && ni < 4) ep.i[ni++] = args[p].i;
+        }
+    }
+    ep.block[0] = (int64_t)(block.x ? block.x : 1);
+    ep.block[1] = (int64_t)(block.y ? block.y : 1);
+    ep.block[2] = (int64_t)(block.z ? block.z : 1);
+    ep.err = c->err_word;
+
+    // footprint: every distinct chunk and temporary of the launch
+    size_t foot = 0;
+    {
+        std::vector<std::pair<lt_array *, int64_t>> seen;
+        auto touch = [&](lt_array *a, int64_t ci) {
+            for (auto &s : seen)
+                if (s.first == a && s.second == ci) return;
+            seen.push_back({a, ci});
+            foot += align_up(a->g.chunks[(size_t)ci].bytes, ALIGN);
+        };
+        for (const auto &sb : plan.sbs)
+            for (const auto &ap : sb.args) {
+                if (ap.kind == ARG_VALUE || ap.kind == ARG_NONE) continue;
+                lt_array *a = parr[(size_t)ap.param];
+                if (ap.kind == ARG_DIRECT) touch(a, ap.chunk);
+                for (auto &pc : ap.pieces) touch(a, pc.chunk);
+                for (auto &pc : ap.replicas) touch(a, pc.chunk);
+                if (ap.kind != ARG_DIRECT) foot += align_up(temp_geometry(a->g, ap.region).bytes, ALIGN);
+            }
+    }
+    bool batched = foot <= c->dev.cap / 20 * 19;
+    size_t nsb = plan.sbs.size();
+    std::vector<size_t> order(nsb);
+    bool rev = !(c->cfg.flags & LT_FLAG_FIXED_SWEEP) && (c->launch_id & 1);
+    for (size_t i = 0; i < nsb; ++i) order[i] = rev ? nsb - 1 - i : i;
+
+    // reduce partials: one block for the whole launch
+    std::vector<std::vector<ChunkGeom>> red_geom(nsb);
+    std::vector<std::vector<size_t>> red_off(nsb);
+    size_t red_bytes = 0;
+    for (size_t s = 0; s < nsb; ++s)
+        for (const auto &ap : plan.sbs[s].args)
+            if (ap.kind == ARG_REDUCE) {
+                ChunkGeom g = temp_geometry(parr[(size_t)ap.param]->g, ap.region);
+                red_geom[s].push_back(g);
+                red_off[s].push_back(red_bytes);
+                red_bytes += align_up(g.bytes, 256);
+            }
+    size_t red_base = 0;
+    FenceSet red_fence;
+    if (red_bytes) {
+        if ((st = dev_alloc(c, red_bytes, &red_base, &red_fence))) return st;
+        op_begin(c, S_COMP, "reduce_init");
+        if ((st = op_wait(c, red_fence))) return st;
+        if (!c->dry) CK(c, cudaMemsetAsync(c->dev_base + red_base, 0, red_bytes, c->st[S_COMP]));
+        uint64_t q;
+        if ((st = op_end(c, &q))) return st;
+        red_fence = FenceSet::one(S_COMP, q);
+    }
+
+    // process superblocks in groups: all at once when the launch fits in
+    // the HBM budget, else one at a time (streaming through host memory)
+    size_t gsz = batched ? nsb : 1;
+    for (size_t g0 = 0; g0 < nsb; g0 += gsz) {
+        size_t g1 = std::min(nsb, g0 + gsz);
+        std::vector<ArgUse> uses;
+        auto add_use = [&](lt_array *a, int64_t ci, bool w) {
+            for (auto &u : uses)
+                if (u.a == a && u.chunk == ci) {
+                    u.write = u.write || w;
+                    return;
+                }
+            uses.push_back({a, ci, w});
+        };
+        for (size_t oi = g0; oi < g1; ++oi) {
+            const auto &sb = plan.sbs[order[oi]];
+            for (const auto &ap : sb.args) {
+                if (ap.kind == ARG_VALUE || ap.kind == ARG_NONE || ap.kind == ARG_REDUCE) continue;
+                lt_array *a = parr[(size_t)ap.param];
+                bool w = ap.mode != MODE_READ;
+                if (ap.kind == ARG_DIRECT) add_use(a, ap.chunk, w);
+                if (ap.kind == ARG_PACK)
+                    for (auto &pc : ap.pieces) add_use(a, pc.chunk, false);
+                if (ap.kind == ARG_TEMPW)
+                    for (auto &pc : ap.pieces) add_use(a, pc.chunk, true);
+                for (auto &pc : ap.replicas) add_use(a, pc.chunk, ap.kind == ARG_DIRECT);
+            }
+        }
+        for (auto &u : uses) u.a->cs[(size_t)u.chunk].pin++;
+        for (auto &u : uses) {
+            // a chunk whose region is only partly written must keep its data
+            st = ensure_dev(c, u.a, u.chunk, true);
+            if (st) {
+                for (auto &v : uses) v.a->cs[(size_t)v.chunk].pin--;
+                return st;
+            }
+        }
+        // temporaries for pack / temp-write
+        std::vector<TempAlloc> temps;
+        std::vector<std::vector<int>> temp_of(g1 - g0);
+        FenceSet temp_fences;
+        for (size_t oi = g0; oi < g1; ++oi) {
+            const auto &sb = plan.sbs[order[oi]];
+            temp_of[oi - g0].assign(sb.args.size(), -1);
+            for (size_t ai = 0; ai < sb.args.size(); ++ai) {
+                const auto &ap = sb.args[ai];
+                if (ap.kind != ARG_PACK && ap.kind != ARG_TEMPW) continue;
+                TempAlloc t;
+                t.geom = temp_geometry(parr[(size_t)ap.param]->g, ap.region);
+                t.bytes = t.geom.bytes;
+                FenceSet f;
+                st = dev_alloc(c, t.bytes, &t.off, &f);
+                if (st) {
+                    for (auto &v : uses) v.a->cs[(size_t)v.chunk].pin--;
+                    return st;
+                }
+                temp_fences.merge(f);
+                temp_of[oi - g0][ai] = (int)temps.size();
+                temps.push_back(t);
+            }
+        }
+        // --- pack (read regions spanning several chunks; readwrite temps)
+        std::vector<CopyPiece> packs;
+        FenceSet pack_wait = temp_fences;
+        for (size_t oi = g0; oi < g1; ++oi) {
+            const auto &sb = plan.sbs[order[oi]];
+            for (size_t ai = 0; ai < sb.args.size(); ++ai) {
+                const auto &ap = sb.args[ai];
+                const std::vector<Piece> *src = nullptr;
+                if (ap.kind == ARG_PACK) src = &ap.pieces;
+                if (ap.kind == ARG_TEMPW && ap.mode == MODE_READWRITE) src = &ap.replicas;
+                if (!src) continue;
+                lt_array *a = parr[(size_t)ap.param];
+                const TempAlloc &t = temps[(size_t)temp_of[oi - g0][ai]];
+                for (const auto &pc : *src) {
+                    CopyPiece cp{};
+                    const CState &cs = a->cs[(size_t)pc.chunk];
+                    cp.src = view_of(c, a->g, a->g.chunks[(size_t)pc.chunk], cs.off);
+                    cp.dst = view_of(c, a->g, t.geom, t.off);
+                    cp.nd = a->g.nd;
+                    cp.esize = (int32_t)a->g.esize();
+                    for (int d = 0; d < 3; ++d) {
+                        cp.lo[d] = d < a->g.nd ? pc.box.lo[d] : 0;
+                        cp.hi[d] = d < a->g.nd ? pc.box.hi[d] : 0;
+                    }
+                    packs.push_back(cp);
+                    pack_wait.merge(cs.ready);
+                    c->stats.bytes_d2d += (uint64_t)pc.box.volume() * a->g.esize();
+                }
+            }
+        }
+        FenceSet temp_ready;
+        if (!packs.empty()) {
+            uint64_t rows = 0;
+            for (auto &p : packs) {
+                p.unit_begin = rows;
+                rows += copy_piece_units(p);
+            }
+            op_begin(c, S_COMP, "pack");
+            if ((st = op_wait(c, pack_wait))) return st;
+            void *dptr;
+            size_t roff;
+            if ((st = upload(c, packs.data(), packs.size() * sizeof(CopyPiece), &dptr, &roff))) return st;
+            if (!c->dry) {
+                TimeScope ts(c, CAT_COPYK);
+                CK(c, k::copy_pieces((const CopyPiece *)dptr, (int)packs.size(), rows, c->st[S_COMP]));
+                c->stats.kernels++;
+            }
+            uint64_t q;
+            if ((st = op_end(c, &q))) return st;
+            upload_done(c, roff, packs.size() * sizeof(CopyPiece), q);
+            c->stats.tasks_copy++;
+            temp_ready.add(S_COMP, q);
+            for (size_t oi = g0; oi < g1; ++oi)
+                for (const auto &ap : plan.sbs[order[oi]].args) {
+                    const std::vector<Piece> *src = nullptr;
+                    if (ap.kind == ARG_PACK) src = &ap.pieces;
+                    if (ap.kind == ARG_TEMPW && ap.mode == MODE_READWRITE) src = &ap.replicas;
+                    if (!src) continue;
+                    for (const auto &pc : *src) parr[(size_t)ap.param]->cs[(size_t)pc.chunk].busy.add(S_COMP, q);
+                }
+        }
+        // --- execute (all superblocks of the group in one kernel)
+        std::vector<ExecTask> tasks;
+        FenceSet ex_wait = temp_fences;
+        ex_wait.merge(temp_ready);
+        ex_wait.merge(red_fence);
+        for (size_t oi = g0; oi < g1; ++oi) {
+            size_t s = order[oi];
+            const auto &sb = plan.sbs[s];
+            ExecTask t{};
+            for (int d = 0; d < 3; ++d) {
+                t.t_lo[d] = sb.threads.lo[d];
+                t.t_hi[d] = sb.threads.hi[d];
+            }
+            size_t ri = 0;
+            for (size_t ai = 0; ai < sb.args.size(); ++ai) {
+                const auto &ap = sb.args[ai];
+                int sl = k->slot_of_param[(size_t)ap.param];
+                if (sl < 0) continue;
+                lt_array *a = parr[(size_t)ap.param];
+                if (ap.kind == ARG_DIRECT) {
+                    CState &cs = a->cs[(size_t)ap.chunk];
+                    t.v[sl] = view_of(c, a->g, a->g.chunks[(size_t)ap.chunk], cs.off);
+                    ex_wait.merge(cs.ready);
+                    if (ap.mode != MODE_READ) ex_wait.merge(cs.busy);
+                } else if (ap.kind == ARG_PACK || ap.kind == ARG_TEMPW) {
+                    const TempAlloc &tm = temps[(size_t)temp_of[oi - g0][ai]];
+                    t.v[sl] = view_of(c, a->g, tm.geom, tm.off);
+                } else if (ap.kind == ARG_REDUCE) {
+                    t.v[sl] = view_of(c, a->g, red_geom[s][ri], red_base + red_off[s][ri]);
+                    ri++;
+                }
+            }
+            tasks.push_back(t);
+        }
+        uint64_t exq = 0;
+        {
+            op_begin(c, S_COMP, "execute");
+            if ((st = op_wait(c, ex_wait))) return st;
+            ep.ntasks = (int32_t)tasks.size();
+            uint32_t ctas = def->prepare ? def->prepare(tasks.data(), (int)tasks.size(), ep) : 0;
+            void *dptr;
+            size_t roff;
+            if ((st = upload(c, tasks.data(), tasks.size() * sizeof(ExecTask), &dptr, &roff))) return st;
+            if (!c->dry && ctas) {
+                TimeScope ts(c, CAT_EXEC);
+                CK(c, def->launch((const ExecTask *)dptr, ctas, ep, c->st[S_COMP]));
+                c->stats.kernels++;
+            }
+            std::ostringstream ex;
+            ex << ",\"superblocks\":[";
+            for (size_t oi = g0; oi < g1; ++oi) ex << (oi > g0 ? "," : "") << plan.sbs[order[oi]].index;
+            ex << "]";
+            if ((st = op_end(c, &exq, ex.str()))) return st;
+            upload_done(c, roff, tasks.size() * sizeof(ExecTask), exq);
+            c->stats.tasks_execute += tasks.size();
+            for (auto &u : uses) {
+                CState &cs = u.a->cs[(size_t)u.chunk];
+                cs.busy.add(S_COMP, exq);
+            }
+            for (size_t oi = g0; oi < g1; ++oi)
+                for (const auto &ap : plan.sbs[order[oi]].args)
+                    if (ap.kind == ARG_DIRECT && ap.mode != MODE_READ) {
+                        CState &cs = parr[(size_t)ap.param]->cs[(size_t)ap.chunk];
+                        cs.ready = FenceSet::one(S_COMP, exq);
+                    }
+            red_fence.add(S_COMP, exq);
+        }
+        // --- replica updates and temp scatters (unpack)
+        std::vector<CopyPiece> outs;
+        FenceSet out_wait;
+        out_wait.add(S_COMP, exq);
+        for (size_t oi = g0; oi < g1; ++oi) {
+            const auto &sb = plan.sbs[order[oi]];
+            for (size_t ai = 0; ai < sb.args.size(); ++ai) {
+                const auto &ap = sb.args[ai];
+                lt_array *a = ap.param >= 0 && ap.kind != ARG_VALUE ? parr[(size_t)ap.param] : nullptr;
+                if (ap.kind == ARG_DIRECT && ap.mode != MODE_READ) {
+                    for (const auto &pc : ap.replicas) {
+                        CopyPiece cp{};
+                        cp.src = view_of(c, a->g, a->g.chunks[(size_t)ap.chunk], a->cs[(size_t)ap.chunk].off);
+                        CState &dcs = a->cs[(size_t)pc.chunk];
+                        cp.dst = view_of(c, a->g, a->g.chunks[(size_t)pc.chunk], dcs.off);
+                        cp.nd = a->g.nd;
+                        cp.esize = (int32_t)a->g.esize();
+                        for (int d = 0; d < 3; ++d) {
+                            cp.lo[d] = d < a->g.nd ? pc.box.lo[d] : 0;
+                            cp.hi[d] = d < a->g.nd ? pc.box.hi[d] : 0;
+                        }
+                        out_wait.merge(dcs.ready);
+                        out_wait.merge(dcs.busy);
+                        outs.push_back(cp);
+                        c->stats.bytes_d2d += (uint64_t)pc.box.volume() * a->g.esize();
+                    }
+                } else if (ap.kind == ARG_TEMPW) {
+                    const TempAlloc &tm = temps[(size_t)temp_of[oi - g0][ai]];
+                    for (const auto &pc : ap.pieces) {
+                        CopyPiece cp{};
+                        cp.src = view_of(c, a->g, tm.geom, tm.off);
+                        CState &dcs = a->cs[(size_t)pc.chunk];
+                        cp.dst = view_of(c, a->g, a->g.chunks[(size_t)pc.chunk], dcs.off);
+                        cp.nd = a->g.nd;
+                        cp.esize = (int32_t)a->g.esize();
+                        for (int d = 0; d < 3; ++d) {
+                            cp.lo[d] = d < a->g.nd ? pc.box.lo[d] : 0;
+                            cp.hi[d] = d < a->g.nd ? pc.box.hi[d] : 0;
+                        }
+                        out_wait.merge(dcs.ready);
+                        out_wait.merge(dcs.busy);
+                        outs.push_back(cp);
+                        c->stats.bytes_d2d += (uint64_t)pc.box.volume() * a->g.esize();
+                    }
+                }
+            }
+        }
+        uint64_t outq = 0;
+        if (!outs.empty()) {
+            uint64_t rows = 0;
+            for (auto &p : outs) {
+                p.unit_begin = rows;
+                rows += copy_piece_units(p);
+            }
+            op_begin(c, S_COMP, "unpack");
+            if ((st = op_wait(c, out_wait))) return st;
+            void *dptr;
+            size_t roff;
+            if ((st = upload(c, outs.data(), outs.size() * sizeof(CopyPiece), &dptr, &roff))) return st;
+            if (!c->dry) {
+                TimeScope ts(c, CAT_COPYK);
+                CK(c, k::copy_pieces((const CopyPiece *)dptr, (int)outs.size(), rows, c->st[S_COMP]));
+                c->stats.kernels++;
+            }
+            if ((st = op_end(c, &outq))) return st;
+            upload_done(c, roff, outs.size() * sizeof(CopyPiece), outq);
+            c->stats.tasks_copy++;
+            for (size_t oi = g0; oi < g1; ++oi)
+                for (const auto &ap : plan.sbs[order[oi]].args) {
+                    if (ap.kind == ARG_VALUE) continue;
+                    lt_array *a = parr[(size_t)ap.param];
+                    if (ap.kind == ARG_DIRECT && ap.mode != MODE_READ) {
+                        a->cs[(size_t)ap.chunk].busy.add(S_COMP, outq);
+                        for (const auto &pc : ap.replicas) {
+                            CState &d = a->cs[(size_t)pc.chunk];
+                            d.ready = FenceSet::one(S_COMP, outq);
+                            d.busy.add(S_COMP, outq);
+                        }
+                    } else if (ap.kind == ARG_TEMPW) {
+                        for (const auto &pc : ap.pieces) {
+                            CState &d = a->cs[(size_t)pc.chunk];
+                            d.ready = FenceSet::one(S_COMP, outq);
+                            d.busy.add(S_COMP, outq);
+                        }
+                    }
+                }
+        }
+        // release temporaries and pins
+        FenceSet rel;
+        rel.add(S_COMP, outq ? outq : exq);
+        for (auto &t : temps) c->dev.release(t.off, t.bytes, rel);
+        for (auto &u : uses) u.a->cs[(size_t)u.chunk].pin--;
+    }
+
+    // --- reduce: combine the per-superblock partials in superblock order
+    if (red_bytes) {
+        std::vector<ReducePiece> rp;
+        std::vector<DView> srcs;
+        FenceSet rw = red_fence;
+        // per destination chunk, the (superblock, box) contributions
+        struct Contrib {
+            size_t sb, ri;
+            Box box;
+        };
+        std::map<std::pair<lt_array *, int64_t>, std::vector<Contrib>> per;
+        std::vector<std::pair<lt_array *, int64_t>> dest_order;
+        int red_op = RED_ADD;
+        for (size_t s = 0; s < nsb; ++s) {
+            size_t ri = 0;
+            for (const auto &ap : plan.sbs[s].args) {
+                if (ap.kind != ARG_REDUCE) continue;
+                red_op = ap.op;
+                lt_array *a = parr[(size_t)ap.param];
+                for (const auto &pc : ap.pieces) {
+                    auto key = std::make_pair(a, pc.chunk);
+                    if (!per.count(key)) dest_order.push_back(key);
+                    per[key].push_back({s, ri, pc.box});
+                }
+                ri++;
+            }
+        }
+        std::vector<std::pair<lt_array *, int64_t>> dests = dest_order;
+        for (auto &d : dests) d.first->cs[(size_t)d.second].pin++;
+        for (auto &d : dests) {
+            if ((st = ensure_dev(c, d.first, d.second, true))) {
+                for (auto &e : dests) e.first->cs[(size_t)e.second].pin--;
+                return st;
+            }
+        }
+        for (auto &d : dests) {
+            lt_array *a = d.first;
+            const ChunkGeom &cg = a->g.chunks[(size_t)d.second];
+            CState &cs = a->cs[(size_t)d.second];
+            rw.merge(cs.ready);
+            rw.merge(cs.busy);
+            const auto &cl = per[d];
+            // coordinate compression of the contribution boxes
+            std::vector<int64_t> cuts[3];
+            for (int dd = 0; dd < a->g.nd; ++dd) {
+                for (const auto &cb : cl) {
+                    cuts[dd].push_back(cb.box.lo[dd]);
+                    cuts[dd].push_back(cb.box.hi[dd] + 1);
+                }
+                std::sort(cuts[dd].begin(), cuts[dd].end());
+                cuts[dd].erase(std::unique(cuts[dd].begin(), cuts[dd].end()), cuts[dd].end());
+            }
+            for (int dd = a->g.nd; dd < 3; ++dd) cuts[dd] = {0, 1};
+            for (size_t x = 0; x + 1 < cuts[0].size(); ++x)
+                for (size_t y = 0; y + 1 < cuts[1].size(); ++y)
+                    for (size_t z = 0; z + 1 < cuts[2].size(); ++z) {
+                        Box cell;
+                        cell.nd = a->g.nd;
+                        size_t ix[3] = {x, y, z};
+                        for (int dd = 0; dd < a->g.nd; ++dd) {
+                            cell.lo[dd] = cuts[dd][ix[dd]];
+                            cell.hi[dd] = cuts[dd][ix[dd] + 1] - 1;
+                        }
+                        ReducePiece p{};
+                        p.src_begin = (uint32_t)srcs.size();
+                        for (const auto &cb : cl)
+                            if (cb.box.contains(cell)) {
+                                srcs.push_back(
+                                    view_of(c, a->g, red_geom[cb.sb][cb.ri], red_base + red_off[cb.sb][cb.ri]));
+                                p.nsrc++;
+                            }
+                        if (!p.nsrc) continue;
+                        p.dst = view_of(c, a->g, cg, cs.off);
+                        p.nd = a->g.nd;
+                        p.op = red_op;
+                        p.dtype = a->g.dtype;
+                        for (int dd = 0; dd < 3; ++dd) {
+                            p.lo[dd] = dd < a->g.nd ? cell.lo[dd] : 0;
+                            p.hi[dd] = dd < a->g.nd ? cell.hi[dd] : 0;
+                        }
+                        rp.push_back(p);
+                    }
+        }
+        uint64_t elems = 0;
+        for (auto &p : rp) {
+            p.elem_begin = elems;
+            uint64_t e = 1;
+            for (int d = 0; d < p.nd; ++d) e *= (uint64_t)(p.hi[d] - p.lo[d] + 1);
+            elems += e;
+        }
+        op_begin(c, S_COMP, "reduce");
+        if ((st = op_wait(c, rw))) return st;
+        void *dp1, *dp2;
+        size_t ro1, ro2;
+        if ((st = upload(c, rp.data(), rp.size() * sizeof(ReducePiece), &dp1, &ro1))) return st;
+        if ((st = upload(c, srcs.data(), srcs.size() * sizeof(DView), &dp2, &ro2))) return st;
+        if (!c->dry && !rp.empty()) {
+            TimeScope ts(c, CAT_COPYK);
+            CK(c, k::reduce_pieces((const ReducePiece *)dp1, (const DView *)dp2, (int)rp.size(), elems,
+                                   c->st[S_COMP]));
+            c->stats.kernels++;
+        }
+        uint64_t q;
+        if ((st = op_end(c, &q))) return st;
+        upload_done(c, ro1, rp.size() * sizeof(ReducePiece), q);
+        upload_done(c, ro2, srcs.size() * sizeof(DView), q);
+        c->stats.tasks_reduce++;
+        for (auto &d : dests) {
+            CState &cs = d.first->cs[(size_t)d.second];
+            cs.ready = FenceSet::one(S_COMP, q);
+            cs.busy.add(S_COMP, q);
+            cs.pin--;
+        }
+        c->dev.release(red_base, red_bytes, FenceSet::one(S_COMP, q));
+    }
+    return LT_OK;
+}
+
+lt_status lt_synchronize(lt_ctx *c) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    return sync_all(c);
+}
+
+lt_status lt_stats_get(lt_ctx *c, lt_stats *out) {
+    if (!c || !out) return fail(LT_ERR_INVALID_ARG, "null argument");
+    c->stats.hbm_in_use = c->dev.used;
+    c->stats.hbm_peak = c->dev.peak;
+    c->stats.host_in_use = c->host.used;
+    *out = c->stats;
+    return LT_OK;
+}
+
+lt_status lt_stats_reset(lt_ctx *c) {
+    if (!c) return fail(LT_ERR_INVALID_ARG, "null context");
+    c->stats = lt_stats{};
+    c->dev.peak = c->dev.used;
+    return LT_OK;
+}
+
+lt_status lt_debug_log_enable(lt_ctx *c, int32_t enable) {
+    if (!c) return fail(LT_ERR_INVALID_ARG, "null context");
+    c->log_on = enable != 0;
+    c->log.str("");
+    c->log.clear();
+    c->log_n = 0;
+    return LT_OK;
+}
+
+lt_status lt_debug_log(lt_ctx *c, char *buf, size_t cap, size_t *needed) {
+    if (!c) return fail(LT_ERR_INVALID_ARG, "null context");
+    std::string js = "[" + c->log.str() + "]";
+    if (needed) *needed = js.size() + 1;
+    if (buf && cap) {
+        size_t n = std::min(cap - 1, js.size());
+        std::memcpy(buf, js.data(), n);
+        buf[n] = 0;
+    }
+    return LT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,175 @@
+"""GPU parity of the stencil path through the C ABI against the CPU oracle.
+
+Bar: bit-exact (same per-cell f32 operation order) for chunked and unchunked
+runs, every distribution, the spill path, and the full 4096^2 x 10 config.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth_inputs as si
+from paper_2202_05549_gb300 import _lib as L
+from paper_2202_05549_gb300 import lightning as lt
+
+pytestmark = pytest.mark.gpu
+
+ANN = "global [i, j] => read U[i-1:i+1, j-1:j+1], write V[i, j]"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def run_jacobi(ctx, u0, dist, iters, block=(128, 4), superblock=(0, 0), fill_seed=None):
+    ny, nx = u0.shape
+    U = ctx.array(lt.F32, (ny, nx), dist)
+    V = ctx.array(lt.F32, (ny, nx), dist)
+    if fill_seed is None:
+        U.write(u0)
+    else:
+        U.fill(L.LT_INIT_UNIFORM, seed=fill_seed, stream=0)
+    k = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+    for _ in range(iters):
+        k.launch(grid=(nx, ny), block=block, superblock=superblock, args=[U, V])
+        U, V = V, U
+    ctx.synchronize()
+    out = U.read()
+    U.destroy()
+    V.destroy()
+    return out
+
+
+def test_fill_generators_match_input_module():
+    with lt.Context() as ctx:
+        n = 1 << 20
+        a = ctx.array(lt.F32, (n,), lt.Dist.rows(300_000, halo=3))
+        a.fill(L.LT_INIT_UNIFORM, seed=2204, stream=0)
+        assert np.array_equal(a.read(), si.gen_uniform_f32(2204, 0, np.arange(n)))
+        a.fill(L.LT_INIT_KAPPA, seed=2207, stream=1)
+        assert np.array_equal(a.read(), si.gen_kappa_f32(2207, 1, np.arange(n)))
+        b = ctx.array(lt.U8, (1000, 1000), lt.Dist.tiles((333, 500)))
+        b.fill(L.LT_INIT_U8, seed=2206, stream=10003)
+        assert np.array_equal(b.read().ravel(), si.gen_u8(2206, 10003, np.arange(10**6)))
+        c = ctx.array(lt.BF16, (512, 768), lt.Dist.cols(256))
+        c.fill(L.LT_INIT_NORMAL_BF16, seed=2205, stream=1, scale=1 / 256)
+        want = si.gen_normal_bf16_bits(2205, 1, np.arange(512 * 768), 1 / 256).reshape(512, 768)
+        # fp64 log/cos of two libraries may differ in the last ulp; a bf16
+        # rounding decision flips only if that ulp straddles a tie
+        assert np.mean(c.read() != want) < 1e-5
+
+
+def test_paper_host_example_1d_stencil():
+    # host code of Sec. 3.6: n = 1e6 ones, StencilDist(64000, 1), BlockDist(64000), 10 launches
+    n = 1_000_000
+    x = np.ones(n, np.float32)
+    want = x
+    for _ in range(10):
+        want = oracle.stencil1d_paper(want)
+    with lt.Context() as ctx:
+        dist = lt.Dist.rows(64_000, halo=1)
+        inp = ctx.array(lt.F32, (n,), dist)
+        out = ctx.array(lt.F32, (n,), dist)
+        inp.fill(L.LT_INIT_CONST, value=1.0)
+        k = ctx.kernel(lt.STENCIL1D, "global i => read input[i-1:i+1], write output[i]",
+                       [("output", lt.F32), ("input", lt.F32)])
+        for _ in range(10):
+            k.launch(grid=(n,), block=(16,), superblock=(64_000,), args=[out, inp])
+            inp, out = out, inp
+        ctx.synchronize()
+        got = inp.read()
+    assert np.array_equal(got, want)
+
+
+DISTS = {
+    "block": lt.Dist.block(),
+    "rows_halo": lt.Dist.rows(64, halo=1),
+    "cols_halo": lt.Dist.cols(96, halo=1),
+    "tiles_halo": lt.Dist.tiles((64, 128), halo=(1, 1)),
+    "tiles_nohalo": lt.Dist.tiles((64, 128)),     # reads span chunks: pack path
+    "rows_nohalo": lt.Dist.rows(50),              # ragged bands, pack path
+    "tiles_wide_halo": lt.Dist.tiles((100, 100), halo=(3, 2)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(DISTS))
+@pytest.mark.parametrize("sbshape", [(0, 0), (128, 64), (96, 32)])
+def test_jacobi_all_distributions_bit_exact(name, sbshape):
+    ny, nx, iters = 301, 517, 4           # several tiles and ragged tails
+    u0 = si.uniform_field(si.SEED_JACOBI_INCORE, 0, ny, nx)
+    want = oracle.jacobi2d(u0, iters)
+    block = (32, 4) if sbshape == (96, 32) else (128, 4)
+    with lt.Context() as ctx:
+        got = run_jacobi(ctx, u0, DISTS[name], iters, block=block, superblock=sbshape)
+    assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
+
+
+def test_jacobi_degenerate_shapes():
+    with lt.Context() as ctx:
+        for (ny, nx) in [(1, 1), (1, 7), (9, 1), (2, 3), (5, 129)]:
+            u0 = si.uniform_field(2203, 5, ny, nx)
+            for dist in (lt.Dist.block(), lt.Dist.tiles((2, 2), halo=(1, 1)), lt.Dist.tiles((1, 2))):
+                got = run_jacobi(ctx, u0, dist, 3, block=(1, 1), superblock=(2, 2))
+                assert np.array_equal(got, oracle.jacobi2d(u0, 3)), (ny, nx)
+
+
+def test_jacobi_grid_larger_than_array_and_superblock_order():
+    ny, nx = 130, 260
+    u0 = si.uniform_field(2203, 9, ny, nx)
+    want = oracle.jacobi2d(u0, 2)
+    with lt.Context(flags=L.LT_FLAG_FIXED_SWEEP) as ctx:
+        U = ctx.array(lt.F32, (ny, nx), lt.Dist.rows(32, halo=1))
+        V = ctx.array(lt.F32, (ny, nx), lt.Dist.rows(32, halo=1))
+        U.write(u0)
+        k = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        k.launch(grid=(512, 256), block=(128, 4), superblock=(512, 32), args=[U, V])
+        k.launch(grid=(512, 256), block=(128, 4), superblock=(512, 32), args=[V, U])
+        ctx.synchronize()
+        assert np.array_equal(U.read(), want)
+
+
+def test_spill_through_host_memory_bit_exact():
+    # 16 bands of 64 x 2048 f32; HBM budget of 6 bands: every launch streams
+    ny, nx, band, iters = 1024, 2048, 64, 5
+    cb = (band + 2) * nx * 4
+    u0 = si.uniform_field(si.SEED_JACOBI_OOC, 0, ny, nx)
+    want = oracle.jacobi2d(u0, iters)
+    with lt.Context(hbm_budget=6 * cb + (1 << 20), host_pool=24 * cb) as ctx:
+        got = run_jacobi(ctx, u0, lt.Dist.rows(band, halo=1), iters, superblock=(nx, band),
+                         fill_seed=si.SEED_JACOBI_OOC)
+        s = ctx.stats()
+    assert s["evictions"] > 0 and s["fetches"] > 0 and s["dead_skips"] > 0
+    assert np.array_equal(got, want)
+
+
+def test_full_size_incore_1_chunk_and_4x4_tiles():
+    n, iters = 4096, 10
+    u0 = si.uniform_field(si.SEED_JACOBI_INCORE, 0, n, n)
+    want = oracle.jacobi2d(u0, iters)
+    with lt.Context() as ctx:
+        one = run_jacobi(ctx, u0, lt.Dist.block(), iters, superblock=(0, 0), fill_seed=si.SEED_JACOBI_INCORE)
+        tiled = run_jacobi(ctx, u0, lt.Dist.tiles((1024, 1024), halo=(1, 1)), iters, superblock=(1024, 1024),
+                           fill_seed=si.SEED_JACOBI_INCORE)
+    assert np.array_equal(one, tiled)
+    assert np.array_equal(one, want)
+
+
+def test_out_of_core_lightcone_samples_small():
+    # the out-of-core launch shape (row bands + 1-row halo, budget < data) on a
+    # grid the oracle checks cell by cell through its light cone
+    NY, NX, band, iters = 4096, 4096, 512, 20
+    cb = (band + 2) * NX * 4
+    with lt.Context(hbm_budget=5 * cb, host_pool=14 * cb) as ctx:
+        U = ctx.array(lt.F32, (NY, NX), lt.Dist.rows(band, halo=1))
+        V = ctx.array(lt.F32, (NY, NX), lt.Dist.rows(band, halo=1))
+        U.fill(L.LT_INIT_UNIFORM, seed=si.SEED_JACOBI_OOC, stream=0)
+        k = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=(NX, NY), block=(128, 4), superblock=(NX, band), args=[U, V])
+            U, V = V, U
+        ctx.synchronize()
+        got = U.read()
+    si_, sj_ = si.sample_cells(2204, NY, NX, 512, seams_every=band)
+    want = oracle.jacobi2d_lightcone(NY, NX, si.SEED_JACOBI_OOC, 0, iters, si_, sj_)
+    assert np.array_equal(got[si_, sj_], want)

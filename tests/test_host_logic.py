@@ -1,0 +1,320 @@
+"""Host logic of the engine, run without a GPU (dry-run contexts).
+
+Covers: the C ABI exports, the annotation parser, access regions against the
+oracle's brute-force enumeration, the chunk decisions of the planner
+(direct / pack / temp-write / reduce, replica copies), dependency edges
+between launches and the memory manager's spill bookkeeping.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_05549_gb300 import _lib as L
+from paper_2202_05549_gb300 import lightning as lt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def dry(budget=1 << 30, host=0, flags=0):
+    return lt.Context(hbm_budget=budget, host_pool=host, flags=L.LT_FLAG_DRYRUN | flags)
+
+
+# ----------------------------------------------------------------- ABI
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "lightning.h")).read()
+    names = set(re.findall(r"^\s*(?:lt_status|const char \*)\s*(lt_\w+)\s*\(", hdr, re.M))
+    assert len(names) >= 18
+    lib = C.CDLL(L.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert names == set(L.SIGNATURES), names ^ set(L.SIGNATURES)
+
+
+# ----------------------------------------------------------------- parser
+@pytest.mark.parametrize("bad", [
+    "global i => read A[i*i]",            # not affine
+    "global i => read A[k]",              # unknown variable
+    "global i => peek A[i]",              # unknown mode
+    "global i => reduce(/) A[i]",         # unknown reduction
+    "global i read A[i]",                 # missing arrow
+    "global [i, i] => read A[i]",         # bound twice
+    "global i => read A[i], write A[i]",  # same array twice
+    "global i => read A[i,i,i,i]",        # rank > 3
+])
+def test_parse_errors(bad):
+    with dry() as ctx:
+        ctx.array(lt.F32, (10,))
+        with pytest.raises(lt.LightningError) as e:
+            ctx.kernel(lt.PLAN_ONLY, bad, [("A", lt.F32)])
+        assert e.value.code == L.LT_ERR_PARSE
+
+
+def test_annotation_must_name_every_array():
+    with dry() as ctx:
+        with pytest.raises(lt.LightningError) as e:
+            ctx.kernel(lt.PLAN_ONLY, "global i => read A[i]", [("A", lt.F32), ("B", lt.F32)])
+        assert e.value.code == L.LT_ERR_INVALID_ARG
+
+
+# ----------------------------------------------------------------- regions vs brute force
+def _brute(tlo, thi, acc, shape):
+    box = [(tlo[d], thi[d]) for d in range(len(tlo))]
+    return oracle.access_region_bruteforce(box, acc, shape)
+
+
+def _region(a):
+    r = a["region"]
+    return list(zip(r["lo"], r["hi"]))
+
+
+def test_paper_stencil_regions_and_wrapper_offsets():
+    g = {}
+    for line in open(os.path.join(GOLDEN, "paper_wrapper_offsets.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split(" ", 1)
+            g[k] = v.strip()
+    n = 1_000_000
+    with dry() as ctx:
+        out = ctx.array(lt.F32, (n,), lt.Dist.rows(64_000, halo=1))
+        inp = ctx.array(lt.F32, (n,), lt.Dist.rows(64_000, halo=1))
+        k = ctx.kernel(lt.STENCIL1D, g["annotation"], [("output", lt.F32), ("input", lt.F32)])
+        first = int(g["first_thread"])
+        # superblocks of `first` threads (blocks of 16), like BlockDist
+        plan = k.explain(grid=(n,), block=(16,), superblock=(first,), args=[out, inp])
+        sb = plan["superblocks"][1]
+        assert sb["threads"]["lo"][0] == first
+        a_out, a_in = sb["args"]
+        assert a_in["region"]["lo"][0] == int(g["input_offset"])
+        assert a_out["region"]["lo"][0] == int(g["output_offset"])
+        # every superblock's regions equal the enumeration of its threads
+        for sb in plan["superblocks"][:3] + plan["superblocks"][-2:]:
+            lo, hi = sb["threads"]["lo"][0], sb["threads"]["hi"][0]
+            assert _region(sb["args"][1]) == _brute([lo], [hi], lambda i: [(i - 1,), (i,), (i + 1,)], (n,))
+            assert _region(sb["args"][0]) == _brute([lo], [hi], lambda i: [(i,)], (n,))
+            assert sb["args"][0]["kind"] == "direct" and sb["args"][1]["kind"] == "direct"
+
+
+def test_paper_matmul_and_rowsum_regions_vs_bruteforce():
+    M, N, K = 12, 10, 7
+    with dry() as ctx:
+        A = ctx.array(lt.F32, (M, K), lt.Dist.rows(4))
+        B = ctx.array(lt.F32, (K, N), lt.Dist.cols(5))
+        Cm = ctx.array(lt.F32, (M, N), lt.Dist.tiles((4, 5)))
+        k = ctx.kernel(lt.PLAN_ONLY, "global [i, j] => read A[i,:], read B[:,j], write C[i,j]",
+                       [("A", lt.F32), ("B", lt.F32), ("C", lt.F32)])
+        plan = k.explain(grid=(N, M), block=(5, 4), superblock=(5, 4), args=[A, B, Cm])
+        assert len(plan["superblocks"]) == 6
+        for sb in plan["superblocks"]:
+            (x0, y0, _), (x1, y1, _) = sb["threads"]["lo"], sb["threads"]["hi"]
+            # "global [i, j]": j is x (columns), i is y (rows)
+            acc_a = lambda i, j: [(i, k2) for k2 in range(K)]
+            acc_b = lambda i, j: [(k2, j) for k2 in range(K)]
+            acc_c = lambda i, j: [(i, j)]
+            assert _region(sb["args"][0]) == _brute([y0, x0], [y1, x1], acc_a, (M, K))
+            assert _region(sb["args"][1]) == _brute([y0, x0], [y1, x1], acc_b, (K, N))
+            assert _region(sb["args"][2]) == _brute([y0, x0], [y1, x1], acc_c, (M, N))
+            assert [a["kind"] for a in sb["args"]] == ["direct", "direct", "direct"]
+        S = ctx.array(lt.F32, (M,), lt.Dist.rows(6))
+        k2 = ctx.kernel(lt.PLAN_ONLY, "global [i, j] => read A[i,j], reduce(+) sum[i]",
+                        [("A", lt.F32), ("sum", lt.F32)])
+        plan = k2.explain(grid=(K, M), block=(7, 4), superblock=(7, 4), args=[A, S])
+        for sb in plan["superblocks"]:
+            (x0, y0, _), (x1, y1, _) = sb["threads"]["lo"], sb["threads"]["hi"]
+            assert _region(sb["args"][1]) == _brute([y0, x0], [y1, x1], lambda i, j: [(i,)], (M,))
+            assert sb["args"][1]["kind"] == "reduce"
+
+
+def test_block_and_local_bindings_regions():
+    # thread (b, l) of block size 8 touches A[8*b + l - 2 : 8*b + l]
+    n = 100
+    with dry() as ctx:
+        A = ctx.array(lt.F32, (n,), lt.Dist.rows(25))
+        k = ctx.kernel(lt.PLAN_ONLY, "block b, local l => read A[8*b + l - 2 : 8*b + l]", [("A", lt.F32)])
+        plan = k.explain(grid=(n,), block=(8,), superblock=(24,), args=[A])
+        for sb in plan["superblocks"]:
+            t0, t1 = sb["threads"]["lo"][0], sb["threads"]["hi"][0]
+            want = _brute([t0], [t1], lambda t: [(t + d,) for d in (-2, -1, 0)], (n,))
+            assert _region(sb["args"][0]) == want
+
+
+def test_jacobi_regions_all_superblocks_vs_bruteforce():
+    ny, nx = 37, 53
+    with dry() as ctx:
+        U = ctx.array(lt.F32, (ny, nx), lt.Dist.tiles((16, 16), halo=(1, 1)))
+        V = ctx.array(lt.F32, (ny, nx), lt.Dist.tiles((16, 16), halo=(1, 1)))
+        k = ctx.kernel(lt.JACOBI2D, "global [i, j] => read U[i-1:i+1, j-1:j+1], write V[i, j]",
+                       [("U", lt.F32), ("V", lt.F32)])
+        plan = k.explain(grid=(nx, ny), block=(8, 4), superblock=(16, 16), args=[U, V])
+        assert len(plan["superblocks"]) == 4 * 3
+        for sb in plan["superblocks"]:
+            (x0, y0, _), (x1, y1, _) = sb["threads"]["lo"], sb["threads"]["hi"]
+            acc = lambda i, j: [(i + a, j + b) for a in (-1, 0, 1) for b in (-1, 0, 1)]
+            assert _region(sb["args"][0]) == _brute([y0, x0], [min(y1, ny - 1), min(x1, nx - 1)], acc, (ny, nx))
+            assert sb["args"][0]["kind"] == "direct"
+
+
+def test_pack_pieces_partition_the_read_region():
+    ny, nx = 40, 40
+    with dry() as ctx:
+        U = ctx.array(lt.F32, (ny, nx), lt.Dist.tiles((10, 10)))   # no halo: reads span chunks
+        V = ctx.array(lt.F32, (ny, nx), lt.Dist.tiles((10, 10)))
+        k = ctx.kernel(lt.JACOBI2D, "global [i, j] => read U[i-1:i+1, j-1:j+1], write V[i, j]",
+                       [("U", lt.F32), ("V", lt.F32)])
+        plan = k.explain(grid=(nx, ny), block=(10, 10), superblock=(10, 10), args=[U, V])
+        for sb in plan["superblocks"]:
+            a = sb["args"][0]
+            assert a["kind"] == "pack"
+            reg = np.zeros((ny, nx), np.int32)
+            for p in a["pieces"]:
+                (r0, c0), (r1, c1) = p["box"]["lo"], p["box"]["hi"]
+                reg[r0:r1 + 1, c0:c1 + 1] += 1
+            (r0, c0), (r1, c1) = a["region"]["lo"], a["region"]["hi"]
+            want = np.zeros_like(reg)
+            want[r0:r1 + 1, c0:c1 + 1] = 1
+            assert np.array_equal(reg, want)       # exact partition, no double copy
+            assert sb["args"][1]["kind"] == "direct" and not sb["args"][1]["replicas"]
+
+
+def test_replicas_cover_neighbour_halos_exactly():
+    ny, nx = 30, 30
+    with dry() as ctx:
+        dist = lt.Dist.tiles((10, 10), halo=(1, 1))
+        U = ctx.array(lt.F32, (ny, nx), dist)
+        V = ctx.array(lt.F32, (ny, nx), dist)
+        chunks = V.chunks()
+        k = ctx.kernel(lt.JACOBI2D, "global [i, j] => read U[i-1:i+1, j-1:j+1], write V[i, j]",
+                       [("U", lt.F32), ("V", lt.F32)])
+        plan = k.explain(grid=(nx, ny), block=(10, 10), superblock=(10, 10), args=[U, V])
+        # every halo cell of every chunk is refreshed by exactly one replica copy
+        copies = {c: np.zeros((ny, nx), np.int32) for c in range(len(chunks))}
+        for sb in plan["superblocks"]:
+            w = sb["args"][1]
+            assert w["kind"] == "direct"
+            for r in w["replicas"]:
+                (r0, c0), (r1, c1) = r["box"]["lo"], r["box"]["hi"]
+                copies[r["chunk"]][r0:r1 + 1, c0:c1 + 1] += 1
+        for c, (lo, hi, _) in enumerate(chunks):
+            cell = np.zeros((ny, nx), np.int32)
+            cell[lo[0]:hi[0] + 1, lo[1]:hi[1] + 1] = 1
+            own = np.zeros_like(cell)
+            tr, tc = divmod(c, 3)
+            own[tr * 10:tr * 10 + 10, tc * 10:tc * 10 + 10] = 1
+            assert np.array_equal(copies[c], cell - own), c
+
+
+def test_annotation_must_contain_the_kernels_accesses():
+    with dry() as ctx:
+        U = ctx.array(lt.F32, (32, 32), lt.Dist.tiles((16, 16), halo=(1, 1)))
+        V = ctx.array(lt.F32, (32, 32), lt.Dist.tiles((16, 16), halo=(1, 1)))
+        k = ctx.kernel(lt.JACOBI2D, "global [i, j] => read U[i, j-1:j+1], write V[i, j]",
+                       [("U", lt.F32), ("V", lt.F32)])
+        with pytest.raises(lt.LightningError) as e:
+            k.launch(grid=(32, 32), block=(16, 16), superblock=(16, 16), args=[U, V])
+        assert e.value.code == L.LT_ERR_INVALID_ARG
+        with pytest.raises(lt.LightningError):
+            ctx.kernel(lt.JACOBI2D, "global [i, j] => write U[i-1:i+1, j-1:j+1], write V[i, j]",
+                       [("U", lt.F32), ("V", lt.F32)])
+
+
+# ----------------------------------------------------------------- dependencies
+def _jacobi_ctx(ctx, ny, nx, dist):
+    U = ctx.array(lt.F32, (ny, nx), dist)
+    V = ctx.array(lt.F32, (ny, nx), dist)
+    k = ctx.kernel(lt.JACOBI2D, "global [i, j] => read U[i-1:i+1, j-1:j+1], write V[i, j]",
+                   [("U", lt.F32), ("V", lt.F32)])
+    return U, V, k
+
+
+def test_dependencies_between_successive_launches():
+    with dry(flags=L.LT_FLAG_FIXED_SWEEP) as ctx:
+        U, V, k = _jacobi_ctx(ctx, 64, 64, lt.Dist.rows(16, halo=1))
+        U.fill(L.LT_INIT_UNIFORM, seed=1)
+        ctx.log_enable()
+        k.launch(grid=(64, 64), block=(64, 4), superblock=(64, 16), args=[U, V])   # reads U, writes V
+        k.launch(grid=(64, 64), block=(64, 4), superblock=(64, 16), args=[V, U])   # reads V (RAW), writes U (WAR)
+        log = ctx.log()
+        ex = [t for t in log if t["kind"] == "execute"]
+        un = [t for t in log if t["kind"] == "unpack"]
+        assert len(ex) == 2 and len(un) == 2
+        l1, l2 = ex[0]["launch"], ex[1]["launch"]
+        assert l2 > l1
+        # launch 2 must wait for launch 1's writes of V (execute + replica copies)
+        assert un[0]["id"] in ex[1]["deps"] or ex[0]["id"] in ex[1]["deps"]
+        # its write of U (read by launch 1) must come after launch 1's reads
+        assert ex[0]["id"] in ex[1]["deps"] or un[0]["id"] in ex[1]["deps"]
+
+
+def test_write_only_chunks_are_not_fetched_and_spill_roundtrip():
+    # 8 row bands of 64 x 1024 f32 (256 KiB each); budget = 6 chunks, host = 16 chunks
+    ny, nx = 512, 1024
+    band = 64
+    cb = (band + 2) * nx * 4
+    with dry(budget=6 * cb + 4096, host=16 * cb) as ctx:
+        U, V, k = _jacobi_ctx(ctx, ny, nx, lt.Dist.rows(band, halo=1))
+        U.fill(L.LT_INIT_UNIFORM, seed=3)
+        s = ctx.stats()
+        assert s["evictions"] >= 8 - 6          # filling 8 bands through a 6-band budget spills
+        for it in range(4):
+            k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V])
+            U, V = V, U
+        ctx.synchronize()
+        s = ctx.stats()
+        assert s["fetches"] > 0 and s["evictions"] > 0
+        assert s["dead_skips"] > 0               # output bands are never fetched
+        assert s["hbm_peak"] <= 6 * cb + 4096
+        assert s["tasks_execute"] == 4 * 8
+
+
+def test_out_of_memory_is_reported():
+    ny, nx, band = 256, 1024, 64
+    cb = (band + 2) * nx * 4
+    with dry(budget=2 * cb, host=cb) as ctx:       # 2 device slots, 1 host slot: cannot run
+        U, V, k = _jacobi_ctx(ctx, ny, nx, lt.Dist.rows(band, halo=1))
+        with pytest.raises(lt.LightningError) as e:
+            U.fill(L.LT_INIT_UNIFORM, seed=3)
+            k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V])
+        assert e.value.code in (L.LT_ERR_OOM_HOST, L.LT_ERR_OOM_DEVICE)
+
+
+def test_alternating_sweep_reuses_resident_chunks():
+    ny, nx, band = 1024, 256, 64
+    cb = (band + 2) * nx * 4
+    res = {}
+    for flags in (0, L.LT_FLAG_FIXED_SWEEP):
+        with dry(budget=20 * cb, host=40 * cb, flags=flags) as ctx:
+            U, V, k = _jacobi_ctx(ctx, ny, nx, lt.Dist.rows(band, halo=1))
+            U.fill(L.LT_INIT_UNIFORM, seed=3)
+            ctx.reset_stats()
+            for it in range(6):
+                k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V])
+                U, V = V, U
+            s = ctx.stats()
+            res[flags] = s["bytes_h2d"] + s["bytes_d2h"]
+    assert res[0] < res[L.LT_FLAG_FIXED_SWEEP]
+
+
+def test_reduce_plan_pieces():
+    with dry() as ctx:
+        X = ctx.array(lt.U8, (1000,), lt.Dist.rows(300))
+        H = ctx.array(lt.U32, (256,))
+        k = ctx.kernel(lt.PLAN_ONLY, "global i => read X[i], reduce(+) H[:]", [("X", lt.U8), ("H", lt.U32)])
+        plan = k.explain(grid=(1000,), block=(100,), superblock=(300,), args=[X, H])
+        assert len(plan["superblocks"]) == 4
+        for sb in plan["superblocks"]:
+            assert sb["args"][1]["kind"] == "reduce"
+            assert sb["args"][1]["region"] == {"lo": [0], "hi": [255]}
+        ctx.log_enable()
+        k.launch(grid=(1000,), block=(100,), superblock=(300,), args=[X, H])
+        kinds = [t["kind"] for t in ctx.log()]
+        assert kinds.count("reduce") == 1 and "reduce_init" in kinds
