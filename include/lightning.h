@@ -144,6 +144,11 @@ lt_status lt_array_destroy(lt_ctx *ctx, lt_array *arr);
  * borrowed only during the call. */
 lt_status lt_array_write(lt_ctx *ctx, lt_array *arr, const void *host, size_t bytes);
 lt_status lt_array_read(lt_ctx *ctx, lt_array *arr, void *host, size_t bytes);
+/* Copy the box lo..hi (inclusive, per axis) of the array into a dense
+ * row-major host buffer of exactly (box volume * element size) bytes.
+ * Synchronous; reads each element from the chunk that owns it. */
+lt_status lt_array_read_box(lt_ctx *ctx, lt_array *arr, const int64_t lo[3], const int64_t hi[3], void *host,
+                            size_t bytes);
 
 /* Fill every element from its global row-major index g with a seeded
  * counter-based generator (SplitMix64, Steele, Lea & Flood 2014): element g
@@ -251,6 +256,14 @@ lt_status lt_launch(lt_ctx *ctx, lt_kernel *k, lt_dim3 grid, lt_dim3 block, cons
 /* Blocks until every enqueued task has finished (context.synchronize() of
  * Sec. 3.6).  Reports device-side error words (bounds checks, timeouts). */
 lt_status lt_synchronize(lt_ctx *ctx);
+
+/* Device-side timing of everything enqueued between the two calls, across
+ * the context's three streams.  lt_timer_start records a CUDA event on the
+ * compute stream and makes both copy streams wait for it; lt_timer_stop
+ * makes the compute stream wait for both copy streams, records a second
+ * event, waits for it on the host and returns the elapsed milliseconds. */
+lt_status lt_timer_start(lt_ctx *ctx);
+lt_status lt_timer_stop(lt_ctx *ctx, double *ms);
 
 /* ---- statistics and plan inspection -------------------------------------- */
 typedef struct {

@@ -87,6 +87,7 @@ SIGNATURES = {
     "lt_array_destroy": (_st, [_vp, _vp]),
     "lt_array_write": (_st, [_vp, _vp, _vp, C.c_size_t]),
     "lt_array_read": (_st, [_vp, _vp, _vp, C.c_size_t]),
+    "lt_array_read_box": (_st, [_vp, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp, C.c_size_t]),
     "lt_array_fill": (_st, [_vp, _vp, C.POINTER(lt_init)]),
     "lt_array_num_chunks": (_st, [_vp, _vp, C.POINTER(C.c_int64)]),
     "lt_array_chunk_info": (_st, [_vp, _vp, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -95,6 +96,8 @@ SIGNATURES = {
     "lt_kernel_destroy": (_st, [_vp, _vp]),
     "lt_launch": (_st, [_vp, _vp, lt_dim3, lt_dim3, C.POINTER(lt_workdist), C.POINTER(lt_arg), C.c_int32]),
     "lt_synchronize": (_st, [_vp]),
+    "lt_timer_start": (_st, [_vp]),
+    "lt_timer_stop": (_st, [_vp, C.POINTER(C.c_double)]),
     "lt_stats_get": (_st, [_vp, C.POINTER(lt_stats)]),
     "lt_stats_reset": (_st, [_vp]),
     "lt_plan_explain": (_st, [_vp, _vp, lt_dim3, lt_dim3, C.POINTER(lt_workdist), C.POINTER(lt_arg), C.c_int32,

@@ -226,6 +226,8 @@ struct lt_ctx {
     int log_n = 0;
     std::vector<TimedOp> timed;
     std::vector<cudaEvent_t> tev_pool;
+    cudaEvent_t timer[2] = {nullptr, nullptr};
+    cudaEvent_t timer_join[2] = {nullptr, nullptr};
     // current operation (between op_begin and op_end)
     int cur_stream = 0;
     int64_t cur_task = -1;
@@ -813,6 +815,10 @@ lt_status lt_ctx_destroy(lt_ctx *c) {
             cudaEventDestroy(t.b);
         }
         for (auto e : c->tev_pool) cudaEventDestroy(e);
+        for (int i = 0; i < 2; ++i) {
+            if (c->timer[i]) cudaEventDestroy(c->timer[i]);
+            if (c->timer_join[i]) cudaEventDestroy(c->timer_join[i]);
+        }
         for (int s = 0; s < NSTREAM; ++s) {
             for (auto e : c->ev[s])
                 if (e) cudaEventDestroy(e);
@@ -942,6 +948,71 @@ lt_status lt_array_read(lt_ctx *c, lt_array *arr, void *host, size_t bytes) {
                 }
         }
     }
+    return LT_OK;
+}
+
+lt_status lt_array_read_box(lt_ctx *c, lt_array *arr, const int64_t lo[3], const int64_t hi[3], void *host,
+                            size_t bytes) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    lt_array *a = find_array(c, arr);
+    if (!a || !lo || !hi || (!host && !c->dry)) return fail(LT_ERR_INVALID_ARG, "bad argument");
+    Box want;
+    want.nd = a->g.nd;
+    for (int d = 0; d < a->g.nd; ++d) {
+        want.lo[d] = lo[d];
+        want.hi[d] = hi[d];
+        if (lo[d] < 0 || hi[d] >= a->g.shape[d] || lo[d] > hi[d]) return fail(LT_ERR_INVALID_ARG, "box outside the array");
+    }
+    if (bytes != (size_t)want.volume() * a->g.esize()) return fail(LT_ERR_INVALID_ARG, "buffer size does not match the box");
+    if ((st = sync_all(c))) return st;
+    if (c->dry) return LT_OK;
+    // stage through a dense buffer shaped like the whole array's index space
+    // restricted to the box: address(idx) = host + row-major offset in the box
+    size_t es = a->g.esize();
+    for (size_t ci = 0; ci < a->cs.size(); ++ci) {
+        Box ob = a->g.chunks[ci].owned.intersect(want);
+        if (ob.empty()) continue;
+        const CState &s = a->cs[ci];
+        const ChunkGeom &cg = a->g.chunks[ci];
+        int64_t bs[3] = {1, 1, 1};
+        for (int d = a->g.nd - 2; d >= 0; --d) bs[d] = bs[d + 1] * want.extent(d + 1);
+        int64_t e0 = ob.extent(0), e1 = a->g.nd > 1 ? ob.extent(1) : 1;
+        int inner = a->g.nd - 1;
+        int64_t w = ob.extent(inner);
+        for (int64_t x = 0; x < (a->g.nd == 3 ? e0 : 1); ++x)
+            for (int64_t y = 0; y < (a->g.nd >= 2 ? (a->g.nd == 3 ? e1 : e0) : 1); ++y) {
+                int64_t idx[3] = {0, 0, 0};
+                if (a->g.nd == 3) {
+                    idx[0] = ob.lo[0] + x;
+                    idx[1] = ob.lo[1] + y;
+                } else if (a->g.nd == 2) {
+                    idx[0] = ob.lo[0] + y;
+                }
+                idx[inner] = ob.lo[inner];
+                int64_t ho = 0, co = 0;
+                for (int d = 0; d < a->g.nd; ++d) {
+                    ho += (idx[d] - want.lo[d]) * bs[d];
+                    co += (idx[d] - cg.s_origin[d]) * cg.stride[d];
+                }
+                char *dst = (char *)host + ho * (int64_t)es;
+                int64_t cstride = cg.stride[inner];
+                if (s.loc == LOC_DEV) {
+                    const char *src = c->dev_base + s.off + co * (int64_t)es;
+                    if (cstride == 1)
+                        CK(c, cudaMemcpyAsync(dst, src, (size_t)w * es, cudaMemcpyDeviceToHost, c->st[S_COMP]));
+                    else
+                        CK(c, cudaMemcpy2DAsync(dst, es, src, (size_t)cstride * es, es, (size_t)w,
+                                                cudaMemcpyDeviceToHost, c->st[S_COMP]));
+                } else if (s.loc == LOC_HOST) {
+                    const char *src = c->host_base + s.off + co * (int64_t)es;
+                    for (int64_t k = 0; k < w; ++k) std::memcpy(dst + k * (int64_t)es, src + k * cstride * (int64_t)es, es);
+                } else {
+                    std::memset(dst, 0, (size_t)w * es);
+                }
+            }
+    }
+    CK(c, cudaStreamSynchronize(c->st[S_COMP]));
     return LT_OK;
 }
 
@@ -1674,6 +1745,39 @@ lt_status lt_synchronize(lt_ctx *c) {
     lt_status st = check_ctx(c);
     if (st) return st;
     return sync_all(c);
+}
+
+lt_status lt_timer_start(lt_ctx *c) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    if (c->dry) return LT_OK;
+    for (int i = 0; i < 2; ++i) {
+        if (!c->timer[i]) CK(c, cudaEventCreate(&c->timer[i]));
+        if (!c->timer_join[i]) CK(c, cudaEventCreateWithFlags(&c->timer_join[i], cudaEventDisableTiming));
+    }
+    CK(c, cudaEventRecord(c->timer[0], c->st[S_COMP]));
+    CK(c, cudaStreamWaitEvent(c->st[S_H2D], c->timer[0], 0));
+    CK(c, cudaStreamWaitEvent(c->st[S_D2H], c->timer[0], 0));
+    return LT_OK;
+}
+
+lt_status lt_timer_stop(lt_ctx *c, double *ms) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    if (!ms) return fail(LT_ERR_INVALID_ARG, "null output");
+    *ms = 0.0;
+    if (c->dry) return LT_OK;
+    if (!c->timer[0]) return fail(LT_ERR_INVALID_ARG, "lt_timer_stop without lt_timer_start");
+    CK(c, cudaEventRecord(c->timer_join[0], c->st[S_H2D]));
+    CK(c, cudaEventRecord(c->timer_join[1], c->st[S_D2H]));
+    CK(c, cudaStreamWaitEvent(c->st[S_COMP], c->timer_join[0], 0));
+    CK(c, cudaStreamWaitEvent(c->st[S_COMP], c->timer_join[1], 0));
+    CK(c, cudaEventRecord(c->timer[1], c->st[S_COMP]));
+    CK(c, cudaEventSynchronize(c->timer[1]));
+    float f = 0.f;
+    CK(c, cudaEventElapsedTime(&f, c->timer[0], c->timer[1]));
+    *ms = f;
+    return LT_OK;
 }
 
 lt_status lt_stats_get(lt_ctx *c, lt_stats *out) {

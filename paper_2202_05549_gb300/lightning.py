@@ -94,6 +94,15 @@ class Array:
         check(L.load().lt_array_read(self.ctx.h, self.h, out.ctypes.data_as(C.c_void_p), out.nbytes))
         return out
 
+    def read_box(self, lo, hi) -> np.ndarray:
+        nd = len(self.shape)
+        shp = tuple(int(h) - int(l) + 1 for l, h in zip(lo, hi))
+        out = np.empty(shp, dtype=_NP[self.dtype])
+        clo = (C.c_int64 * 3)(*(list(lo) + [0] * (3 - nd)))
+        chi = (C.c_int64 * 3)(*(list(hi) + [0] * (3 - nd)))
+        check(L.load().lt_array_read_box(self.ctx.h, self.h, clo, chi, out.ctypes.data_as(C.c_void_p), out.nbytes))
+        return out
+
     def fill(self, kind: int, seed: int = 0, stream: int = 0, value: float = 0.0, scale: float = 1.0):
         init = L.lt_init(kind, seed, stream, value, scale)
         check(L.load().lt_array_fill(self.ctx.h, self.h, C.byref(init)))
@@ -193,6 +202,14 @@ class Context:
 
     def synchronize(self):
         check(L.load().lt_synchronize(self.h))
+
+    def timer_start(self):
+        check(L.load().lt_timer_start(self.h))
+
+    def timer_stop(self) -> float:
+        ms = C.c_double()
+        check(L.load().lt_timer_stop(self.h, C.byref(ms)))
+        return ms.value
 
     def stats(self) -> dict:
         s = L.lt_stats()
