@@ -310,6 +310,36 @@ lt_status lt_plan_explain(lt_ctx *ctx, lt_kernel *k, lt_dim3 grid, lt_dim3 block
 lt_status lt_debug_log_enable(lt_ctx *ctx, int32_t enable);
 lt_status lt_debug_log(lt_ctx *ctx, char *buf, size_t cap, size_t *needed);
 
+/* ---- allocation-free Jacobi step -------------------------------------------
+ * The paper has no counterpart to this call.  It serves callers that cannot
+ * allocate device memory (code running under another framework's allocator
+ * or memory budget, or a process that must not grow its device footprint
+ * after start-up).  It computes one 2-D 5-point Jacobi step
+ *     V[i,j] = ((((U[i,j] + U[i-1,j]) + U[i+1,j]) + U[i,j-1]) + U[i,j+1]) / 5
+ * (zero outside the ny x nx grid), bit-identical to lt_launch of
+ * LT_K_JACOBI2D, by the same pack-then-execute sequence as an annotated
+ * launch over tiles without halo: each tile_rows x tile_cols tile's read
+ * region (the tile plus a one-cell ring) is gathered into scratch and the
+ * tile is computed from that copy.
+ *   U, V: distinct DEVICE pointers to row-major f32 grids with leading
+ *         dimensions ld_u, ld_v >= nx (elements); the caller owns both.
+ *   stream: a cudaStream_t (NULL = the legacy default stream); the call is
+ *         asynchronous on it and returns once everything is enqueued.
+ * Scratch: a file-scope device array of LT_NOALLOC_SCRATCH_BYTES (64 MiB),
+ * present on every device that loads the library until the process exits.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).  Tiles are processed in batches that fit the scratch; a tile
+ * whose packed region exceeds it is rejected with LT_ERR_INVALID_ARG.
+ * Every call shares the scratch and leaves the last call's contents in it:
+ * calls that overlap on the GPU race, calls ordered on one stream do not.
+ * The first call on a device looks up the scratch's device address and
+ * caches it; make that first call before any stream capture.
+ * Errors: LT_ERR_INVALID_ARG (bad pointers or sizes), LT_ERR_CUDA (a CUDA
+ * call failed); lt_last_error() gives the message. */
+#define LT_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+lt_status lt_jacobi2d_packed_noalloc(const float *U, float *V, int64_t ny, int64_t nx, int64_t ld_u, int64_t ld_v,
+                                     int64_t tile_rows, int64_t tile_cols, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,8 @@ SIGNATURES = {
                               C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "lt_debug_log_enable": (_st, [_vp, C.c_int32]),
     "lt_debug_log": (_st, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "lt_jacobi2d_packed_noalloc": (_st, [_vp, _vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                         C.c_int64, _vp]),
 }
 
 _lib = None

@@ -2,6 +2,7 @@
 // distributions and launch plans.  Host-only C++17; no CUDA here.
 #pragma once
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -200,5 +201,8 @@ bool plan_launch(const Annotation &a, const std::vector<int> &stmt_of_param, con
                  std::string *err);
 
 std::string plan_to_json(const LaunchPlan &p);
+
+// Record the calling thread's error message (returned by lt_last_error).
+lt_status set_last_error(lt_status st, const std::string &msg);
 
 }  // namespace lt

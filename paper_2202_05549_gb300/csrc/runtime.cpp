@@ -41,6 +41,8 @@ static lt_status fail(lt_status st, const std::string &msg) {
 
 extern "C" const char *lt_last_error(void) { return g_err.c_str(); }
 
+lt_status lt::set_last_error(lt_status st, const std::string &msg) { return fail(st, msg); }
+
 namespace {
 
 enum { S_COMP = 0, S_H2D = 1, S_D2H = 2, NSTREAM = 3 };
