@@ -204,7 +204,7 @@ def plan_ooc(args, world):
     avail = mem_available() // world
     host = min(int(0.5 * avail), total)
     host_slots = host // chunk_c
-    dev_slots = 2 * nb - host_slots + 3
+    dev_slots = max(2 * nb - host_slots + 3, 6)  # a band task pins 4 chunks
     budget = dev_slots * chunk_c + (64 << 20)
     return dict(ny=ny, nx=nx, band=band, nbands=nb, chunk_bytes=chunk, budget=budget,
                 host=host_slots * chunk_c + (1 << 20), data_bytes=2 * ny * nx * 4)

@@ -144,7 +144,10 @@ struct CState {
     FenceSet ready, busy;
     uint64_t lru = 0;
     int pin = 0;
-    int64_t dead_launch = -1;
+    int64_t dead_launch = -1;       // launch whose first touch may skip the fetch
+    int64_t next_dead_launch = -1;  // launch after which the next launch overwrites it unread
+    int64_t last_use_launch = -1;   // launch and group of its last use in that launch
+    int64_t last_use_group = -1;
 };
 
 struct BuiltinDef {
@@ -194,6 +197,14 @@ struct TimedOp {
     cudaEvent_t a, b;
 };
 
+// A planned launch waiting for the next one (one launch of lookahead).
+struct PendingLaunch {
+    lt_kernel *k = nullptr;
+    LaunchPlan plan;
+    std::vector<lt_array *> parr;
+    ExecParams ep{};
+};
+
 struct UploadUse {
     size_t off, end;
     uint64_t seq;
@@ -228,6 +239,8 @@ struct lt_ctx {
     int log_n = 0;
     std::vector<TimedOp> timed;
     std::vector<cudaEvent_t> tev_pool;
+    std::unique_ptr<PendingLaunch> pending;
+    int64_t cur_group = 0;
     cudaEvent_t timer[2] = {nullptr, nullptr};
     cudaEvent_t timer_join[2] = {nullptr, nullptr};
     // current operation (between op_begin and op_end)
@@ -416,8 +429,11 @@ lt_status dev_alloc(lt_ctx *c, size_t bytes, size_t *off, FenceSet *f) {
 lt_status evict(lt_ctx *c, lt_array *a, int64_t ci) {
     CState &s = a->cs[(size_t)ci];
     const ChunkGeom &cg = a->g.chunks[(size_t)ci];
-    if (s.dead_launch == c->launch_id) {
-        // contents will be fully overwritten in this launch: drop them
+    bool next_dead = s.next_dead_launch == c->launch_id &&
+                     (s.last_use_launch != c->launch_id || s.last_use_group < c->cur_group);
+    if (s.dead_launch == c->launch_id || next_dead) {
+        // contents are overwritten unread in this launch, or in the next one
+        // after their last use here: drop them instead of writing them back
         FenceSet f = s.busy;
         f.merge(s.ready);
         c->dev.release(s.off, cg.bytes, f);
@@ -710,9 +726,9 @@ struct TempAlloc {
     ChunkGeom geom;
 };
 
-// Mark for every written array the chunks whose contents this launch fully
-// overwrites without reading them (no fetch is needed on first touch).
-void mark_dead(lt_ctx *c, lt_kernel *k, const LaunchPlan &plan, const std::vector<lt_array *> &parr) {
+// Chunks whose contents a launch fully overwrites without reading them.
+std::vector<std::pair<lt_array *, int64_t>> dead_chunks(const LaunchPlan &plan, const std::vector<lt_array *> &parr) {
+    std::vector<std::pair<lt_array *, int64_t>> out;
     std::vector<lt_array *> uniq;
     for (lt_array *a : parr)
         if (a && std::find(uniq.begin(), uniq.end(), a) == uniq.end()) uniq.push_back(a);
@@ -739,16 +755,23 @@ void mark_dead(lt_ctx *c, lt_kernel *k, const LaunchPlan &plan, const std::vecto
             std::vector<Box> parts;
             for (const Box &w : wr)
                 if (!cb.intersect(w).empty()) parts.push_back(w);
-            if (!parts.empty() && box_covered(cb, parts)) a->cs[ci].dead_launch = c->launch_id;
+            if (!parts.empty() && box_covered(cb, parts)) out.push_back({a, (int64_t)ci});
         }
     }
-    (void)k;
+    return out;
+}
+
+// Mark the chunks this launch overwrites unread (no fetch on first touch).
+void mark_dead(lt_ctx *c, const LaunchPlan &plan, const std::vector<lt_array *> &parr) {
+    for (auto &d : dead_chunks(plan, parr)) d.first->cs[(size_t)d.second].dead_launch = c->launch_id;
 }
 
 }  // namespace
 
 // ============================================================================ C ABI
 extern "C" {
+
+static lt_status flush_pending(lt_ctx *c);
 
 lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     if (!cfg || !out) return fail(LT_ERR_INVALID_ARG, "null argument");
@@ -809,6 +832,7 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
 
 lt_status lt_ctx_destroy(lt_ctx *c) {
     if (!c) return LT_OK;
+    if (!c->poisoned) flush_pending(c);
     if (!c->dry) {
         for (int s = 0; s < NSTREAM; ++s)
             if (c->st[s]) cudaStreamSynchronize(c->st[s]);
@@ -857,6 +881,7 @@ lt_status lt_array_create(lt_ctx *c, lt_dtype dtype, int32_t ndim, const int64_t
 lt_status lt_array_destroy(lt_ctx *c, lt_array *arr) {
     lt_status st = check_ctx(c);
     if (st) return st;
+    if ((st = flush_pending(c))) return st;
     lt_array *a = find_array(c, arr);
     if (!a) return fail(LT_ERR_INVALID_ARG, "unknown array");
     for (size_t i = 0; i < a->cs.size(); ++i) {
@@ -884,6 +909,7 @@ static size_t array_bytes(const lt_array *a) {
 lt_status lt_array_write(lt_ctx *c, lt_array *arr, const void *host, size_t bytes) {
     lt_status st = check_ctx(c);
     if (st) return st;
+    if ((st = flush_pending(c))) return st;
     lt_array *a = find_array(c, arr);
     if (!a || (!host && !c->dry)) return fail(LT_ERR_INVALID_ARG, "unknown array or null buffer");
     if (bytes != array_bytes(a)) return fail(LT_ERR_INVALID_ARG, "buffer size does not match the array");
@@ -923,6 +949,7 @@ lt_status lt_array_write(lt_ctx *c, lt_array *arr, const void *host, size_t byte
 lt_status lt_array_read(lt_ctx *c, lt_array *arr, void *host, size_t bytes) {
     lt_status st = check_ctx(c);
     if (st) return st;
+    if ((st = flush_pending(c))) return st;
     lt_array *a = find_array(c, arr);
     if (!a || (!host && !c->dry)) return fail(LT_ERR_INVALID_ARG, "unknown array or null buffer");
     if (bytes != array_bytes(a)) return fail(LT_ERR_INVALID_ARG, "buffer size does not match the array");
@@ -957,6 +984,7 @@ lt_status lt_array_read_box(lt_ctx *c, lt_array *arr, const int64_t lo[3], const
                             size_t bytes) {
     lt_status st = check_ctx(c);
     if (st) return st;
+    if ((st = flush_pending(c))) return st;
     lt_array *a = find_array(c, arr);
     if (!a || !lo || !hi || (!host && !c->dry)) return fail(LT_ERR_INVALID_ARG, "bad argument");
     Box want;
@@ -1021,6 +1049,7 @@ lt_status lt_array_read_box(lt_ctx *c, lt_array *arr, const int64_t lo[3], const
 lt_status lt_array_fill(lt_ctx *c, lt_array *arr, const lt_init *init) {
     lt_status st = check_ctx(c);
     if (st) return st;
+    if ((st = flush_pending(c))) return st;
     lt_array *a = find_array(c, arr);
     if (!a || !init) return fail(LT_ERR_INVALID_ARG, "unknown array or null init");
     int kind = init->kind;
@@ -1188,6 +1217,10 @@ lt_status lt_kernel_register(lt_ctx *c, int32_t builtin, const char *annotation,
 
 lt_status lt_kernel_destroy(lt_ctx *c, lt_kernel *kk) {
     if (!c) return fail(LT_ERR_INVALID_ARG, "null context");
+    if (c->pending && c->pending->k == kk && !c->poisoned) {
+        lt_status st = flush_pending(c);
+        if (st) return st;
+    }
     for (auto it = c->kernels.begin(); it != c->kernels.end(); ++it)
         if (it->get() == kk) {
             c->kernels.erase(it);
@@ -1258,21 +1291,27 @@ lt_status lt_plan_explain(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, 
     return LT_OK;
 }
 
+static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
+                             const std::vector<std::pair<lt_array *, int64_t>> *next_dead);
+
+// Enqueue the pending launch, if any, without lookahead.
+static lt_status flush_pending(lt_ctx *c) {
+    if (!c->pending) return LT_OK;
+    std::unique_ptr<PendingLaunch> p = std::move(c->pending);
+    return emit_launch(c, *p, nullptr);
+}
+
 lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const lt_workdist *wd, const lt_arg *args,
                     int32_t nargs) {
     lt_status st = check_ctx(c);
     if (st) return st;
-    LaunchPlan plan;
-    std::vector<lt_array *> parr;
-    if ((st = prepare_plan(c, k, grid, block, wd, args, nargs, &plan, &parr))) return st;
+    auto pl = std::make_unique<PendingLaunch>();
+    if ((st = prepare_plan(c, k, grid, block, wd, args, nargs, &pl->plan, &pl->parr))) return st;
     if (!k->def->launch && !c->dry)
         return fail(LT_ERR_UNSUPPORTED, "a plan-only kernel can be launched only in a dry-run context");
-    ++c->launch_id;
-    c->stats.launches++;
-    mark_dead(c, k, plan, parr);
-    const BuiltinDef *def = k->def;
-
-    ExecParams ep{};
+    pl->k = k;
+    ExecParams &ep = pl->ep;
+    const std::vector<lt_array *> &parr = pl->parr;
     for (size_t p = 0; p < parr.size(); ++p) {
         int sl = k->slot_of_param[p];
         if (sl < 0) continue;
@@ -1291,6 +1330,31 @@ lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const 
     ep.block[1] = (int64_t)(block.y ? block.y : 1);
     ep.block[2] = (int64_t)(block.z ? block.z : 1);
     ep.err = c->err_word;
+    // one launch of lookahead: the previous launch is enqueued now, knowing
+    // which chunks this one overwrites without reading them
+    if (c->pending) {
+        auto nd = dead_chunks(pl->plan, pl->parr);
+        std::unique_ptr<PendingLaunch> prev = std::move(c->pending);
+        c->pending = std::move(pl);
+        return emit_launch(c, *prev, &nd);
+    }
+    c->pending = std::move(pl);
+    return LT_OK;
+}
+
+static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
+                             const std::vector<std::pair<lt_array *, int64_t>> *next_dead) {
+    lt_status st = LT_OK;
+    lt_kernel *k = pl.k;
+    const LaunchPlan &plan = pl.plan;
+    const std::vector<lt_array *> &parr = pl.parr;
+    ExecParams &ep = pl.ep;
+    ++c->launch_id;
+    c->stats.launches++;
+    mark_dead(c, plan, parr);
+    if (next_dead)
+        for (auto &d : *next_dead) d.first->cs[(size_t)d.second].next_dead_launch = c->launch_id;
+    const BuiltinDef *def = k->def;
 
     // footprint: every distinct chunk and temporary of the launch
     size_t foot = 0;
@@ -1345,7 +1409,26 @@ lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const 
     // process superblocks in groups: all at once when the launch fits in
     // the HBM budget, else one at a time (streaming through host memory)
     size_t gsz = batched ? nsb : 1;
-    for (size_t g0 = 0; g0 < nsb; g0 += gsz) {
+    // last group that uses each chunk (evicting before it must write back)
+    for (size_t g0 = 0, gi = 0; g0 < nsb; g0 += gsz, ++gi) {
+        size_t g1 = std::min(nsb, g0 + gsz);
+        for (size_t oi = g0; oi < g1; ++oi)
+            for (const auto &ap : plan.sbs[order[oi]].args) {
+                if (ap.kind == ARG_VALUE || ap.kind == ARG_NONE) continue;
+                lt_array *a = parr[(size_t)ap.param];
+                int64_t grp = ap.kind == ARG_REDUCE ? (int64_t)((nsb + gsz - 1) / gsz) : (int64_t)gi;
+                auto mark = [&](int64_t ci) {
+                    CState &cs = a->cs[(size_t)ci];
+                    if (cs.last_use_launch != c->launch_id || cs.last_use_group < grp) cs.last_use_group = grp;
+                    cs.last_use_launch = c->launch_id;
+                };
+                if (ap.kind == ARG_DIRECT) mark(ap.chunk);
+                for (auto &pc : ap.pieces) mark(pc.chunk);
+                for (auto &pc : ap.replicas) mark(pc.chunk);
+            }
+    }
+    c->cur_group = 0;
+    for (size_t g0 = 0; g0 < nsb; g0 += gsz, ++c->cur_group) {
         size_t g1 = std::min(nsb, g0 + gsz);
         std::vector<ArgUse> uses;
         auto add_use = [&](lt_array *a, int64_t ci, bool w) {
@@ -1626,6 +1709,7 @@ lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const 
     }
 
     // --- reduce: combine the per-superblock partials in superblock order
+    c->cur_group = (int64_t)((nsb + gsz - 1) / gsz);
     if (red_bytes) {
         std::vector<ReducePiece> rp;
         std::vector<DView> srcs;
@@ -1746,12 +1830,14 @@ lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const 
 lt_status lt_synchronize(lt_ctx *c) {
     lt_status st = check_ctx(c);
     if (st) return st;
+    if ((st = flush_pending(c))) return st;
     return sync_all(c);
 }
 
 lt_status lt_timer_start(lt_ctx *c) {
     lt_status st = check_ctx(c);
     if (st) return st;
+    if ((st = flush_pending(c))) return st;
     if (c->dry) return LT_OK;
     for (int i = 0; i < 2; ++i) {
         if (!c->timer[i]) CK(c, cudaEventCreate(&c->timer[i]));
@@ -1766,6 +1852,7 @@ lt_status lt_timer_start(lt_ctx *c) {
 lt_status lt_timer_stop(lt_ctx *c, double *ms) {
     lt_status st = check_ctx(c);
     if (st) return st;
+    if ((st = flush_pending(c))) return st;
     if (!ms) return fail(LT_ERR_INVALID_ARG, "null output");
     *ms = 0.0;
     if (c->dry) return LT_OK;
@@ -1784,6 +1871,10 @@ lt_status lt_timer_stop(lt_ctx *c, double *ms) {
 
 lt_status lt_stats_get(lt_ctx *c, lt_stats *out) {
     if (!c || !out) return fail(LT_ERR_INVALID_ARG, "null argument");
+    if (!c->poisoned) {
+        lt_status st = flush_pending(c);
+        if (st) return st;
+    }
     c->stats.hbm_in_use = c->dev.used;
     c->stats.hbm_peak = c->dev.peak;
     c->stats.host_in_use = c->host.used;
@@ -1809,6 +1900,10 @@ lt_status lt_debug_log_enable(lt_ctx *c, int32_t enable) {
 
 lt_status lt_debug_log(lt_ctx *c, char *buf, size_t cap, size_t *needed) {
     if (!c) return fail(LT_ERR_INVALID_ARG, "null context");
+    if (!c->poisoned) {
+        lt_status st = flush_pending(c);
+        if (st) return st;
+    }
     std::string js = "[" + c->log.str() + "]";
     if (needed) *needed = js.size() + 1;
     if (buf && cap) {

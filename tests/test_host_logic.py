@@ -318,3 +318,28 @@ def test_reduce_plan_pieces():
         k.launch(grid=(1000,), block=(100,), superblock=(300,), args=[X, H])
         kinds = [t["kind"] for t in ctx.log()]
         assert kinds.count("reduce") == 1 and "reduce_init" in kinds
+
+
+def test_lookahead_skips_writeback_of_data_the_next_launch_overwrites():
+    # ping-pong Jacobi through a budget of 6 of 16 bands: with one launch of
+    # lookahead, bands read in launch t and overwritten unread in t+1 are
+    # dropped on eviction instead of written back
+    ny, nx, band = 1024, 512, 64
+    cb = (band + 2) * nx * 4
+    out = {}
+    for lookahead in (True, False):
+        with dry(budget=6 * cb + 8192, host=30 * cb) as ctx:
+            U, V, k = _jacobi_ctx(ctx, ny, nx, lt.Dist.rows(band, halo=1))
+            U.fill(L.LT_INIT_UNIFORM, seed=3)
+            ctx.synchronize()
+            ctx.reset_stats()
+            for it in range(6):
+                k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V])
+                U, V = V, U
+                if not lookahead:
+                    ctx.synchronize()        # flushes each launch before the next is seen
+            ctx.synchronize()
+            out[lookahead] = ctx.stats()
+    assert out[True]["tasks_execute"] == out[False]["tasks_execute"] == 6 * 16
+    assert out[True]["bytes_d2h"] < 0.8 * out[False]["bytes_d2h"]
+    assert out[True]["bytes_h2d"] <= out[False]["bytes_h2d"]
