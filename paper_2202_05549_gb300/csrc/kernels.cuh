@@ -13,8 +13,10 @@
 namespace lt {
 
 struct DView {
-    uint64_t base;  // byte address of global element (0,0,0) (may lie outside the allocation)
-    int64_t s[3];   // element strides
+    uint64_t base;   // byte address of global element (0,0,0) (may lie outside the allocation)
+    int64_t s[3];    // element strides
+    int64_t org[3];  // global index of the first stored element per axis
+    int64_t hi[3];   // last valid global index per axis (the chunk box)
 };
 
 #define LT_MAX_ARRAYS 5
@@ -23,8 +25,9 @@ struct DView {
 struct ExecTask {
     int64_t t_lo[3], t_hi[3];     // thread box (x, y, z), inclusive
     DView v[LT_MAX_ARRAYS];       // views, in array-parameter order
-    uint32_t cta_begin;           // first CTA of this task in the launch
+    uint32_t cta_begin;           // first CTA (or work tile) of this task in the launch
     uint32_t cta_count;
+    int32_t aux[4];               // kernel-specific per-task values set by prepare_*
 };
 
 // Per-launch constants of an Execute kernel.
@@ -117,6 +120,8 @@ cudaError_t reduce_pieces(const ReducePiece *dev, const DView *srcs, int n, uint
 uint32_t prepare_stencil1d(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_stencil1d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p);
+uint32_t prepare_gemm_bf16(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_gemm_bf16(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 cudaError_t launch_jacobi2d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 
 }  // namespace k

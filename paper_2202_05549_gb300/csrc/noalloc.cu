@@ -78,8 +78,8 @@ extern "C" lt_status lt_jacobi2d_packed_noalloc(const float *U, float *V, int64_
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
 
-    DView uv{(uint64_t)(uintptr_t)U, {ld_u, 1, 0}};
-    DView vv{(uint64_t)(uintptr_t)V, {ld_v, 1, 0}};
+    DView uv{(uint64_t)(uintptr_t)U, {ld_u, 1, 0}, {0, 0, 0}, {ny - 1, nx - 1, 0}};
+    DView vv{(uint64_t)(uintptr_t)V, {ld_v, 1, 0}, {0, 0, 0}, {ny - 1, nx - 1, 0}};
     ExecParams ep{};
     ep.shape[0][0] = ep.shape[1][0] = ny;
     ep.shape[0][1] = ep.shape[1][1] = nx;
@@ -107,7 +107,8 @@ extern "C" lt_status lt_jacobi2d_packed_noalloc(const float *U, float *V, int64_
             size_t bytes = up((size_t)((rr1 - rr0 + 1) * ext) * sizeof(float), 1024);
             if (used + bytes > kPackBytes || (packs.size() + 1) * per_tile_desc + 512 > kDescBytes) break;
             uint64_t tbase = (uint64_t)(uintptr_t)(scr + kDescBytes + used);
-            DView tv{tbase - (uint64_t)((rr0 * ext + org) * (int64_t)sizeof(float)), {ext, 1, 0}};
+            DView tv{tbase - (uint64_t)((rr0 * ext + org) * (int64_t)sizeof(float)), {ext, 1, 0}, {rr0, org, 0},
+                     {rr1, rc1, 0}};
             CopyPiece cp{};
             cp.src = uv;
             cp.dst = tv;

@@ -166,6 +166,8 @@ const BuiltinDef kBuiltins[] = {
      k::prepare_stencil1d, k::launch_stencil1d},
     {LT_K_JACOBI2D, "global [i, j] => read A0[i-1:i+1, j-1:j+1], write A1[i, j]", 2, {LT_F32, LT_F32}, {2, 2},
      k::prepare_jacobi2d, k::launch_jacobi2d},
+    {LT_K_GEMM_BF16, "global [i, j] => read A0[i, :], read A1[:, j], write A2[i, j]", 3, {LT_BF16, LT_BF16, LT_F32},
+     {2, 2, 2}, k::prepare_gemm_bf16, k::launch_gemm_bf16},
 };
 
 const BuiltinDef *find_builtin(int id) {
@@ -389,6 +391,10 @@ DView view_of(lt_ctx *c, const ArrayGeom &g, const ChunkGeom &cg, size_t off) {
         o += (d < g.nd ? cg.s_origin[d] : 0) * v.s[d];
     }
     v.base = p - (uint64_t)(o * (int64_t)g.esize());
+    for (int d = 0; d < 3; ++d) {
+        v.org[d] = d < g.nd ? cg.s_origin[d] : 0;
+        v.hi[d] = d < g.nd ? cg.box.hi[d] : 0;
+    }
     return v;
 }
 
@@ -602,7 +608,8 @@ lt_status sync_all(lt_ctx *c) {
     CK(c, cudaMemcpy(&e, c->err_word, 4, cudaMemcpyDeviceToHost));
     if (e) {
         CK(c, cudaMemset(c->err_word, 0, 4));
-        return fail(LT_ERR_DEVICE_CHECK, "a kernel recorded an out-of-region access (code " + std::to_string(e) + ")");
+        return fail(e >= 0x6700 && e < 0x6800 ? LT_ERR_TIMEOUT : LT_ERR_DEVICE_CHECK,
+                    "a kernel recorded an error (code " + std::to_string(e) + "; 0x67xx = a bounded wait expired)");
     }
     return collect_timing(c);
 }
@@ -772,6 +779,7 @@ void mark_dead(lt_ctx *c, const LaunchPlan &plan, const std::vector<lt_array *> 
 extern "C" {
 
 static lt_status flush_pending(lt_ctx *c);
+static bool pending_writes(lt_ctx *c, const lt_array *a);
 
 lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     if (!cfg || !out) return fail(LT_ERR_INVALID_ARG, "null argument");
@@ -949,7 +957,8 @@ lt_status lt_array_write(lt_ctx *c, lt_array *arr, const void *host, size_t byte
 lt_status lt_array_read(lt_ctx *c, lt_array *arr, void *host, size_t bytes) {
     lt_status st = check_ctx(c);
     if (st) return st;
-    if ((st = flush_pending(c))) return st;
+    // a read needs the pending launch enqueued only if that launch writes the array
+    if (pending_writes(c, arr) && (st = flush_pending(c))) return st;
     lt_array *a = find_array(c, arr);
     if (!a || (!host && !c->dry)) return fail(LT_ERR_INVALID_ARG, "unknown array or null buffer");
     if (bytes != array_bytes(a)) return fail(LT_ERR_INVALID_ARG, "buffer size does not match the array");
@@ -984,7 +993,8 @@ lt_status lt_array_read_box(lt_ctx *c, lt_array *arr, const int64_t lo[3], const
                             size_t bytes) {
     lt_status st = check_ctx(c);
     if (st) return st;
-    if ((st = flush_pending(c))) return st;
+    // a read needs the pending launch enqueued only if that launch writes the array
+    if (pending_writes(c, arr) && (st = flush_pending(c))) return st;
     lt_array *a = find_array(c, arr);
     if (!a || !lo || !hi || (!host && !c->dry)) return fail(LT_ERR_INVALID_ARG, "bad argument");
     Box want;
@@ -1247,6 +1257,17 @@ static lt_status prepare_plan(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 blo
         pa[(size_t)p].geom = &a->g;
         (*parr)[(size_t)p] = a;
     }
+    if (k->def->id == LT_K_GEMM_BF16) {
+        // the tensor-core operands must be K-contiguous: A row-major, B column-major chunks
+        lt_array *A = nullptr, *B = nullptr;
+        for (int p = 0; p < nargs; ++p) {
+            if (k->slot_of_param[(size_t)p] == 0) A = (*parr)[(size_t)p];
+            if (k->slot_of_param[(size_t)p] == 1) B = (*parr)[(size_t)p];
+        }
+        if (!A || !B || A->g.dist.order != LT_ORDER_ROW || B->g.dist.order != LT_ORDER_COL)
+            return fail(LT_ERR_UNSUPPORTED, "the BF16 GEMM needs A with row-major chunks and B with column-major "
+                                            "chunks (LT_ORDER_COL)");
+    }
     uint64_t g3[3] = {grid.x, grid.y, grid.z}, b3[3] = {block.x, block.y, block.z};
     int64_t sb3[3] = {0, 0, 0};
     if (wd)
@@ -1293,6 +1314,15 @@ lt_status lt_plan_explain(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, 
 
 static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                              const std::vector<std::pair<lt_array *, int64_t>> *next_dead);
+
+// Does the pending launch write array a?
+static bool pending_writes(lt_ctx *c, const lt_array *a) {
+    if (!c->pending) return false;
+    const lt_kernel *k = c->pending->k;
+    for (size_t p = 0; p < c->pending->parr.size(); ++p)
+        if (c->pending->parr[p] == a && k->ann.stmts[(size_t)k->stmt_of_param[p]].mode != MODE_READ) return true;
+    return false;
+}
 
 // Enqueue the pending launch, if any, without lookahead.
 static lt_status flush_pending(lt_ctx *c) {
@@ -1587,6 +1617,11 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             if ((st = op_wait(c, ex_wait))) return st;
             ep.ntasks = (int32_t)tasks.size();
             uint32_t ctas = def->prepare ? def->prepare(tasks.data(), (int)tasks.size(), ep) : 0;
+            if (ctas == 0xFFFFFFFFu)
+                return fail(LT_ERR_UNSUPPORTED, "this built-in cannot run these chunks (code " +
+                                                    std::to_string(ep.variant) +
+                                                    "; the GEMM needs A row-major and B column-major chunks, at "
+                                                    "most 15 distinct chunks of each per launch)");
             void *dptr;
             size_t roff;
             if ((st = upload(c, tasks.data(), tasks.size() * sizeof(ExecTask), &dptr, &roff))) return st;
