@@ -253,6 +253,37 @@ typedef struct {
 lt_status lt_launch(lt_ctx *ctx, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const lt_workdist *wd,
                     const lt_arg *args, int32_t nargs);
 
+/* ---- batched launches (an extension beyond the paper) --------------------
+ * One descriptor is one launch, issued `repeat` times; between repeats the
+ * first two array arguments swap (ping-pong), so {JACOBI2D, args {U, V},
+ * repeat 8} means U->V, V->U, ... eight launches.  lt_launch_batch(descs, n)
+ * has the meaning of issuing every descriptor's launches in order with
+ * lt_launch.  When every descriptor is a JACOBI2D or HIST256 launch over
+ * single-chunk arrays and no array appears in two descriptors, the whole
+ * batch runs as ONE persistent kernel fed by a device-side work queue
+ * (items ordered iteration-major; a tile waits, bounded, for the previous
+ * iteration of its instance), captured once in a CUDA graph and replayed
+ * while the same arrays stay at the same addresses.  Its tile height and
+ * histogram slice come from an autotuner that times candidates on the first
+ * iteration of the batch (which writes only data the real run overwrites)
+ * and caches the choice per batch shape.  Otherwise, or with
+ * LT_BATCH_PLAIN, the launches are issued one by one (the plain form).
+ * Asynchronous like lt_launch; the descriptors are read during the call. */
+typedef struct {
+    lt_kernel *kernel;
+    lt_dim3 grid, block;
+    lt_workdist wd;
+    const lt_arg *args;
+    int32_t nargs;
+    int32_t repeat;
+} lt_launch_desc;
+
+#define LT_BATCH_PLAIN 1    /* issue the launches one by one */
+#define LT_BATCH_NO_GRAPH 2 /* fused kernel, launched directly (no graph capture) */
+#define LT_BATCH_RETUNE 4   /* run the autotuner again for this batch shape */
+
+lt_status lt_launch_batch(lt_ctx *ctx, const lt_launch_desc *descs, int32_t n, int32_t flags);
+
 /* Blocks until every enqueued task has finished (context.synchronize() of
  * Sec. 3.6).  Reports device-side error words (bounds checks, timeouts). */
 lt_status lt_synchronize(lt_ctx *ctx);
@@ -291,6 +322,11 @@ typedef struct {
     double ms_h2d;            /* sum of host->device copy durations */
     double ms_d2h;            /* sum of device->host copy durations */
     double ms_fill;           /* fill kernels */
+    uint64_t batches_fused;   /* lt_launch_batch calls run as one persistent kernel */
+    uint64_t batches_plain;   /* lt_launch_batch calls issued launch by launch */
+    uint64_t graph_replays;   /* fused batches replayed from a cached CUDA graph */
+    int64_t tuned_tile_rows;  /* autotuner choice of the last fused batch */
+    int64_t tuned_hist_slice;
 } lt_stats;
 
 lt_status lt_stats_get(lt_ctx *ctx, lt_stats *out);

@@ -73,7 +73,17 @@ class lt_stats(C.Structure):
         "launches", "tasks_execute", "tasks_copy", "tasks_reduce", "deps", "fetches", "evictions", "dead_skips",
         "bytes_h2d", "bytes_d2h", "bytes_d2d", "kernels", "hbm_in_use", "hbm_peak", "host_in_use")] + [
         ("ms_execute", C.c_double), ("n_execute_kernels", C.c_uint64), ("ms_copy_kernels", C.c_double),
-        ("n_copy_kernels", C.c_uint64), ("ms_h2d", C.c_double), ("ms_d2h", C.c_double), ("ms_fill", C.c_double)]
+        ("n_copy_kernels", C.c_uint64), ("ms_h2d", C.c_double), ("ms_d2h", C.c_double), ("ms_fill", C.c_double),
+        ("batches_fused", C.c_uint64), ("batches_plain", C.c_uint64), ("graph_replays", C.c_uint64),
+        ("tuned_tile_rows", C.c_int64), ("tuned_hist_slice", C.c_int64)]
+
+
+class lt_launch_desc(C.Structure):
+    _fields_ = [("kernel", C.c_void_p), ("grid", lt_dim3), ("block", lt_dim3), ("wd", lt_workdist),
+                ("args", C.POINTER(lt_arg)), ("nargs", C.c_int32), ("repeat", C.c_int32)]
+
+
+LT_BATCH_PLAIN, LT_BATCH_NO_GRAPH, LT_BATCH_RETUNE = 1, 2, 4
 
 
 _vp = C.c_void_p
@@ -96,6 +106,7 @@ SIGNATURES = {
     "lt_kernel_destroy": (_st, [_vp, _vp]),
     "lt_launch": (_st, [_vp, _vp, lt_dim3, lt_dim3, C.POINTER(lt_workdist), C.POINTER(lt_arg), C.c_int32]),
     "lt_synchronize": (_st, [_vp]),
+    "lt_launch_batch": (_st, [_vp, C.c_void_p, C.c_int32, C.c_int32]),
     "lt_timer_start": (_st, [_vp]),
     "lt_timer_stop": (_st, [_vp, C.POINTER(C.c_double)]),
     "lt_stats_get": (_st, [_vp, C.POINTER(lt_stats)]),

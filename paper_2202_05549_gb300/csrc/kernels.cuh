@@ -107,7 +107,42 @@ struct FillDesc {
     double value, scale;
 };
 
+// Batched persistent kernel: instance tables and the work queue.
+struct BatchJacobi {
+    uint64_t u, v;     // views (global index base) of the two ping-pong buffers
+    int64_t su, sv;    // row strides (elements)
+    int64_t ny, nx;
+    uint32_t tiles;    // work items per iteration
+    uint32_t done_off; // first completion counter (one per iteration)
+};
+struct BatchHist {
+    uint64_t x;   // u8 array (contiguous, 128-byte aligned)
+    int64_t len;
+    uint64_t h;   // 256 u32 bins (contiguous)
+};
+struct BatchItem {
+    uint32_t kind_inst;  // kind << 30 | instance (0 Jacobi tile, 1 histogram slice)
+    uint32_t iter;       // Jacobi iteration
+    uint32_t row0;       // first row (Jacobi) or slice index (histogram)
+    uint32_t nrows;
+};
+struct BatchParams {
+    const BatchItem *items;
+    uint64_t nitems;
+    const BatchJacobi *jac;
+    const BatchHist *hist;
+    uint32_t *head;   // queue head (zeroed before every run)
+    uint32_t *done;   // completion counters (zeroed before every run)
+    uint32_t *abort;  // set when a bounded wait expires
+    uint32_t *err;
+    int64_t hist_slice;
+};
+
 namespace k {
+
+int batch_threads();
+cudaError_t launch_batch(const BatchParams &p, int ctas, cudaStream_t st);
+cudaError_t launch_batch_zero_hist(const BatchHist *hist, int n, cudaStream_t st);
 
 // All launchers return the CUDA error of the launch (cudaSuccess on success).
 cudaError_t fill(const FillDesc &d, cudaStream_t st);
@@ -120,6 +155,8 @@ cudaError_t reduce_pieces(const ReducePiece *dev, const DView *srcs, int n, uint
 uint32_t prepare_stencil1d(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_stencil1d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p);
+uint32_t prepare_hist256(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_hist256(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_gemm_bf16(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_gemm_bf16(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 cudaError_t launch_jacobi2d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);

@@ -1,0 +1,145 @@
+// Batched form of many independent annotated launches (an extension beyond
+// the paper, which schedules each launch's superblocks separately): one
+// persistent kernel pulls work items from a device-side queue.
+//   kind 0  Jacobi tile: rows [row0, row0+nrows) of one instance, one
+//           iteration (ping-pong between the instance's two buffers);
+//   kind 1  histogram slice: bytes [slice*HS, (slice+1)*HS) of one array,
+//           counted in shared memory and added to H with integer atomics
+//           (the reduce(+) of Sec. 2.3 folded into one level).
+// Items are queued iteration-major, so every item an item waits for was
+// dequeued before it by a resident CTA: a tile of iteration t waits (bounded)
+// until all tiles of iteration t-1 of its instance are done, and no wait can
+// deadlock.  Loads of Jacobi inputs bypass L1 (other SMs wrote them earlier
+// in the same kernel).  Every wait is bounded by %globaltimer; on expiry the
+// kernel records an error and every CTA returns.
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "stencil_body.cuh"
+
+namespace lt {
+namespace {
+
+constexpr int BT = 256;  // threads per CTA (8 warps)
+constexpr unsigned long long BWAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long btimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(BT, 1) batch_kernel(BatchParams P) {
+    __shared__ uint32_t s_item;
+    __shared__ int s_stop;
+    __shared__ uint32_t sh[BT / 32][256];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (;;) {
+        if (tid == 0) {
+            s_item = atomicAdd(P.head, 1u);
+            s_stop = s_item >= P.nitems || ld_acquire(P.abort) != 0;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const BatchItem w = P.items[s_item];
+        const uint32_t kind = w.kind_inst >> 30, inst = w.kind_inst & 0x3FFFFFFFu;
+        if (kind == 0) {
+            const BatchJacobi J = P.jac[inst];
+            if (w.iter > 0) {
+                if (tid == 0) {
+                    const uint32_t *cnt = P.done + J.done_off + w.iter - 1;
+                    unsigned long long t0 = btimer();
+                    while (ld_acquire(cnt) < J.tiles) {
+                        if (ld_acquire(P.abort) != 0 || btimer() - t0 > BWAIT_NS) {
+                            atomicCAS(P.err, 0u, 0x6801u);
+                            atomicExch(P.abort, 1u);
+                            s_stop = 1;
+                            break;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (s_stop) break;
+            }
+            const bool even = (w.iter & 1u) == 0;
+            const float *src = (const float *)(even ? J.u : J.v);
+            float *dst = (float *)(even ? J.v : J.u);
+            const int64_t ss = even ? J.su : J.sv, sd = even ? J.sv : J.su;
+            const int64_t ny = J.ny, nx = J.nx;
+            const int64_t ye = min((int64_t)(w.row0 + w.nrows) - 1, ny - 1);
+            const int64_t sx = (nx + JCOLS - 1) / JCOLS, sy = ((int64_t)w.nrows + JR - 1) / JR;
+            for (int64_t s = warp; s < sx * sy; s += BT / 32) {
+                const int64_t js = (s % sx) * JCOLS, r0 = w.row0 + (s / sx) * JR;
+                if (r0 <= ye) jacobi_strip<true>(src, ss, dst, sd, ny, nx, js, r0, nx - 1, ye, lane);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicAdd(P.done + J.done_off + w.iter, 1u);
+        } else {
+            const BatchHist H = P.hist[inst];
+            for (int i = tid; i < (BT / 32) * 256; i += BT) (&sh[0][0])[i] = 0;
+            __syncthreads();
+            const int64_t lo = (int64_t)w.row0 * P.hist_slice;
+            const int64_t hi = min(lo + (int64_t)P.hist_slice, H.len);
+            const uint8_t *x = (const uint8_t *)H.x;
+            uint32_t *h = sh[warp];
+            // H.x is 128-byte aligned and slices are multiples of 16 bytes
+            const int64_t nv = (hi - lo) / 16;
+            const uint4 *v = (const uint4 *)(x + lo);
+            for (int64_t i = tid; i < nv; i += BT) {
+                uint4 q = __ldg(v + i);
+                uint32_t ws[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int k2 = 0; k2 < 4; ++k2) {
+                    atomicAdd(&h[ws[k2] & 255u], 1u);
+                    atomicAdd(&h[(ws[k2] >> 8) & 255u], 1u);
+                    atomicAdd(&h[(ws[k2] >> 16) & 255u], 1u);
+                    atomicAdd(&h[ws[k2] >> 24], 1u);
+                }
+            }
+            for (int64_t i = lo + nv * 16 + tid; i < hi; i += BT) atomicAdd(&h[x[i]], 1u);
+            __syncthreads();
+            uint32_t *out = (uint32_t *)H.h;
+            for (int bin = tid; bin < 256; bin += BT) {
+                uint32_t s = 0;
+#pragma unroll
+                for (int k2 = 0; k2 < BT / 32; ++k2) s += sh[k2][bin];
+                if (s) atomicAdd(&out[bin], s);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void batch_zero_hist_kernel(const BatchHist *__restrict__ hist, int n) {
+    for (int h = blockIdx.x; h < n; h += gridDim.x) {
+        uint32_t *out = (uint32_t *)hist[h].h;
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) out[b] = 0u;
+    }
+}
+
+}  // namespace
+
+namespace k {
+
+int batch_threads() { return BT; }
+
+cudaError_t launch_batch_zero_hist(const BatchHist *hist, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    batch_zero_hist_kernel<<<n < 1024 ? n : 1024, 256, 0, st>>>(hist, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchParams &p, int ctas, cudaStream_t st) {
+    batch_kernel<<<ctas, BT, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace k
+}  // namespace lt

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "stencil_body.cuh"
 
 namespace lt {
 namespace {
@@ -48,21 +49,10 @@ __global__ void __launch_bounds__(256) stencil1d_kernel(const ExecTask *__restri
 }
 
 // ------------------------------------------------------------------ 2-D Jacobi
-constexpr int JR = 16;       // output rows per warp tile
 constexpr int JWARPS = 4;    // warps per CTA, side by side along x
-constexpr int JCOLS = 128;   // columns per warp (4 per lane)
-
-__device__ __forceinline__ float j5(float c, float n, float s, float w, float e) {
-    float acc = __fadd_rn(c, n);
-    acc = __fadd_rn(acc, s);
-    acc = __fadd_rn(acc, w);
-    acc = __fadd_rn(acc, e);
-    return __fdiv_rn(acc, 5.0f);
-}
 
 // Vector variant: every lane owns 4 adjacent columns of a 128-column strip and
-// sweeps JR rows, keeping JR+2 input rows in registers (all loads issued
-// before any arithmetic); horizontal neighbours come from the adjacent lanes.
+// sweeps JR rows (jacobi_strip in stencil_body.cuh).
 __global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     int ti = find_task(tasks, p.ntasks, blockIdx.x);
     const ExecTask &t = tasks[ti];
@@ -75,64 +65,10 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTas
     const int64_t tx = local % gx, ty = local / gx;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t js = x0 + (tx * JWARPS + warp) * JCOLS;  // first column of this warp's strip
-    const int64_t j0 = js + lane * 4;
     const int64_t r0 = y0 + ty * JR;
-    const int64_t rlast = min(r0 + JR - 1, ye);
-    const int64_t cmax = min(xe + 1, NX - 1);  // last column that may be read
     if (js > xe || r0 > ye) return;  // warp-uniform: nothing to write
-    const DView U = t.v[0], V = t.v[1];
-    const float *ub = (const float *)U.base;
-    const bool ld = j0 <= cmax;
-
-    float4 row[JR + 2];
-    float wl[JR], er[JR];
-#pragma unroll
-    for (int k = 0; k < JR + 2; ++k) {
-        int64_t r = r0 - 1 + k;
-        row[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ld && r >= 0 && r < NY && r <= rlast + 1) row[k] = *(const float4 *)(ub + r * U.s[0] + j0);
-    }
-#pragma unroll
-    for (int k = 0; k < JR; ++k) {
-        int64_t r = r0 + k;
-        wl[k] = 0.f;
-        er[k] = 0.f;
-        if (r <= rlast) {
-            if (lane == 0 && j0 - 1 >= 0 && ld) wl[k] = ub[r * U.s[0] + j0 - 1];
-            if (lane == 31 && j0 + 4 <= cmax) er[k] = ub[r * U.s[0] + j0 + 4];
-        }
-    }
-    // columns of this lane that lie outside the domain read as 0
-#pragma unroll
-    for (int k = 0; k < JR + 2; ++k) {
-        if (j0 + 1 > NX - 1) row[k].y = 0.f;
-        if (j0 + 2 > NX - 1) row[k].z = 0.f;
-        if (j0 + 3 > NX - 1) row[k].w = 0.f;
-    }
-    float *vb = (float *)V.base;
-#pragma unroll
-    for (int k = 0; k < JR; ++k) {
-        int64_t r = r0 + k;
-        const float4 up = row[k], mid = row[k + 1], dn = row[k + 2];
-        float w_in = __shfl_up_sync(0xffffffffu, mid.w, 1);
-        float e_in = __shfl_down_sync(0xffffffffu, mid.x, 1);
-        float w = lane == 0 ? wl[k] : w_in;
-        float e = lane == 31 ? er[k] : e_in;
-        if (r > rlast || j0 > xe) continue;
-        float4 o;
-        o.x = j5(mid.x, up.x, dn.x, w, mid.y);
-        o.y = j5(mid.y, up.y, dn.y, mid.x, mid.z);
-        o.z = j5(mid.z, up.z, dn.z, mid.y, mid.w);
-        o.w = j5(mid.w, up.w, dn.w, mid.z, e);
-        float *dst = vb + r * V.s[0] + j0;
-        if (j0 + 3 <= xe) {
-            *(float4 *)dst = o;
-        } else {
-            dst[0] = o.x;
-            if (j0 + 1 <= xe) dst[1] = o.y;
-            if (j0 + 2 <= xe) dst[2] = o.z;
-        }
-    }
+    jacobi_strip<false>((const float *)t.v[0].base, t.v[0].s[0], (float *)t.v[1].base, t.v[1].s[0], NY, NX, js, r0,
+                        xe, ye, lane);
 }
 
 // Scalar variant for unaligned tasks: one thread per output cell.

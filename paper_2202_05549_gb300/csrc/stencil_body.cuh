@@ -1,0 +1,100 @@
+// Device bodies shared by the stencil kernels (single launches and the
+// batched persistent kernel).
+//   V[i,j] = ((((U[i,j] + U[i-1,j]) + U[i+1,j]) + U[i,j-1]) + U[i,j+1]) / 5,
+// zero outside the NY x NX domain, __fadd_rn / __fdiv_rn (no contraction).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace lt {
+
+constexpr int JR = 16;      // output rows per warp strip
+constexpr int JCOLS = 128;  // columns per warp strip (4 per lane)
+
+__device__ __forceinline__ float j5(float c, float n, float s, float w, float e) {
+    float acc = __fadd_rn(c, n);
+    acc = __fadd_rn(acc, s);
+    acc = __fadd_rn(acc, w);
+    acc = __fadd_rn(acc, e);
+    return __fdiv_rn(acc, 5.0f);
+}
+
+template <bool L2ONLY>
+__device__ __forceinline__ float4 ld4(const float *p) {
+    if (L2ONLY) return __ldcg((const float4 *)p);
+    return *(const float4 *)p;
+}
+
+template <bool L2ONLY>
+__device__ __forceinline__ float ld1(const float *p) {
+    if (L2ONLY) return __ldcg(p);
+    return *p;
+}
+
+// One warp computes output rows r0 .. min(r0+JR-1, ye) of the 128-column
+// strip starting at column js (js <= xe, js % 4 == 0), reading U (row
+// stride su) and writing V (row stride sv); both are views indexed with
+// global indices whose rows are 16-byte aligned.  All JR+2 input rows are
+// loaded before any arithmetic; horizontal neighbours come from the
+// adjacent lanes.  L2ONLY loads bypass L1 (data written by other SMs in the
+// same kernel).  Columns read: up to min(xe+1, NX-1), in 4-aligned groups.
+template <bool L2ONLY>
+__device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float *vb, int64_t sv, int64_t NY,
+                                             int64_t NX, int64_t js, int64_t r0, int64_t xe, int64_t ye, int lane) {
+    const int64_t j0 = js + lane * 4;
+    const int64_t rlast = min(r0 + JR - 1, ye);
+    const int64_t cmax = min(xe + 1, NX - 1);  // last column that may be read
+    const bool ld = j0 <= cmax;
+    float4 row[JR + 2];
+    float wl[JR], er[JR];
+#pragma unroll
+    for (int k = 0; k < JR + 2; ++k) {
+        int64_t r = r0 - 1 + k;
+        row[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ld && r >= 0 && r < NY && r <= rlast + 1) row[k] = ld4<L2ONLY>(ub + r * su + j0);
+    }
+#pragma unroll
+    for (int k = 0; k < JR; ++k) {
+        int64_t r = r0 + k;
+        wl[k] = 0.f;
+        er[k] = 0.f;
+        if (r <= rlast) {
+            if (lane == 0 && j0 - 1 >= 0 && ld) wl[k] = ld1<L2ONLY>(ub + r * su + j0 - 1);
+            if (lane == 31 && j0 + 4 <= cmax) er[k] = ld1<L2ONLY>(ub + r * su + j0 + 4);
+        }
+    }
+    // columns of this lane that lie outside the domain read as 0
+#pragma unroll
+    for (int k = 0; k < JR + 2; ++k) {
+        if (j0 + 1 > NX - 1) row[k].y = 0.f;
+        if (j0 + 2 > NX - 1) row[k].z = 0.f;
+        if (j0 + 3 > NX - 1) row[k].w = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < JR; ++k) {
+        int64_t r = r0 + k;
+        const float4 up = row[k], mid = row[k + 1], dn = row[k + 2];
+        float w_in = __shfl_up_sync(0xffffffffu, mid.w, 1);
+        float e_in = __shfl_down_sync(0xffffffffu, mid.x, 1);
+        float w = lane == 0 ? wl[k] : w_in;
+        float e = lane == 31 ? er[k] : e_in;
+        if (r > rlast || j0 > xe) continue;
+        float4 o;
+        o.x = j5(mid.x, up.x, dn.x, w, mid.y);
+        o.y = j5(mid.y, up.y, dn.y, mid.x, mid.z);
+        o.z = j5(mid.z, up.z, dn.z, mid.y, mid.w);
+        o.w = j5(mid.w, up.w, dn.w, mid.z, e);
+        float *dst = vb + r * sv + j0;
+        if (j0 + 3 <= xe) {
+            *(float4 *)dst = o;
+        } else {
+            dst[0] = o.x;
+            if (j0 + 1 <= xe) dst[1] = o.y;
+            if (j0 + 2 <= xe) dst[2] = o.z;
+        }
+    }
+}
+
+}  // namespace lt

@@ -200,6 +200,23 @@ class Context:
     def kernel(self, builtin, annotation, params) -> Kernel:
         return Kernel(self, builtin, annotation, params)
 
+    def launch_batch(self, launches, flags=0):
+        """launches: list of (kernel, grid, block, superblock, args, repeat)."""
+        n = len(launches)
+        descs = (L.lt_launch_desc * n)()
+        keep = []
+        for i, (k, grid, block, sb, args, rep) in enumerate(launches):
+            a = k._args(args)
+            keep.append(a)
+            descs[i].kernel = k.h
+            descs[i].grid = _dim3(grid)
+            descs[i].block = _dim3(block)
+            descs[i].wd = L.lt_workdist((C.c_int64 * 3)(*(tuple(sb) + (0,) * (3 - len(sb)))))
+            descs[i].args = C.cast(a, C.POINTER(L.lt_arg))
+            descs[i].nargs = len(args)
+            descs[i].repeat = rep
+        check(L.load().lt_launch_batch(self.h, C.cast(descs, C.c_void_p), n, flags))
+
     def synchronize(self):
         check(L.load().lt_synchronize(self.h))
 

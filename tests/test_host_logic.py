@@ -343,3 +343,20 @@ def test_lookahead_skips_writeback_of_data_the_next_launch_overwrites():
     assert out[True]["tasks_execute"] == out[False]["tasks_execute"] == 6 * 16
     assert out[True]["bytes_d2h"] < 0.8 * out[False]["bytes_d2h"]
     assert out[True]["bytes_h2d"] <= out[False]["bytes_h2d"]
+
+
+def test_batch_in_dry_run_is_the_plain_sequence():
+    with dry() as ctx:
+        U, V, k = _jacobi_ctx(ctx, 64, 64, lt.Dist.block())
+        X = ctx.array(lt.U8, (1000,))
+        H = ctx.array(lt.U32, (256,))
+        kh = ctx.kernel(lt.HIST256, "global i => read X[i], reduce(+) H[:]", [("X", lt.U8), ("H", lt.U32)])
+        ctx.log_enable()
+        ctx.launch_batch([(k, (64, 64), (64, 4), (0, 0), [U, V], 5), (kh, (1000,), (256,), (0,), [X, H], 1)])
+        s = ctx.stats()
+        assert s["launches"] == 6 and s["batches_plain"] == 1 and s["batches_fused"] == 0
+        ex = [t for t in ctx.log() if t["kind"] == "execute"]
+        assert len(ex) == 6
+        # iteration t+1 depends on iteration t (ping-pong through U and V)
+        for a, b in zip(ex[:4], ex[1:5]):
+            assert a["id"] in b["deps"]
