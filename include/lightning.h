@@ -144,6 +144,11 @@ lt_status lt_array_destroy(lt_ctx *ctx, lt_array *arr);
  * borrowed only during the call. */
 lt_status lt_array_write(lt_ctx *ctx, lt_array *arr, const void *host, size_t bytes);
 lt_status lt_array_read(lt_ctx *ctx, lt_array *arr, void *host, size_t bytes);
+/* The same with a dense row-major DEVICE buffer of the context's device
+ * (for instance a CUDA tensor).  Row-major chunks only
+ * (LT_ERR_UNSUPPORTED otherwise).  Synchronous. */
+lt_status lt_array_write_device(lt_ctx *ctx, lt_array *arr, const void *dev, size_t bytes);
+lt_status lt_array_read_device(lt_ctx *ctx, lt_array *arr, void *dev, size_t bytes);
 /* Copy the box lo..hi (inclusive, per axis) of the array into a dense
  * row-major host buffer of exactly (box volume * element size) bytes.
  * Synchronous; reads each element from the chunk that owns it. */

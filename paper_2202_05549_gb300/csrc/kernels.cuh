@@ -155,6 +155,10 @@ cudaError_t reduce_pieces(const ReducePiece *dev, const DView *srcs, int n, uint
 uint32_t prepare_stencil1d(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_stencil1d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p);
+uint32_t prepare_diffusion(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_diffusion(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
+uint32_t prepare_diffusion_adj(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_diffusion_adj(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_hist256(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_hist256(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_gemm_bf16(ExecTask *t, int n, ExecParams &p);

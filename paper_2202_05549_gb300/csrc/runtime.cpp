@@ -168,6 +168,12 @@ const BuiltinDef kBuiltins[] = {
      k::prepare_jacobi2d, k::launch_jacobi2d},
     {LT_K_HIST256, "global i => read A0[i], reduce(+) A1[:]", 2, {LT_U8, LT_U32}, {1, 1}, k::prepare_hist256,
      k::launch_hist256},
+    {LT_K_DIFFUSION2D, "global [i, j] => read A0[i-1:i+1, j-1:j+1], read A1[i, j], write A2[i, j]", 3,
+     {LT_F32, LT_F32, LT_F32}, {2, 2, 2}, k::prepare_diffusion, k::launch_diffusion},
+    {LT_K_DIFFUSION2D_ADJ,
+     "global [i, j] => read A0[i, j], read A1[i, j], read A2[i-1:i+1, j-1:j+1], readwrite A3[i, j], "
+     "reduce(+) A4[i-1:i+1, j-1:j+1]",
+     5, {LT_F32, LT_F32, LT_F32, LT_F32, LT_F32}, {2, 2, 2, 2, 2}, k::prepare_diffusion_adj, k::launch_diffusion_adj},
     {LT_K_GEMM_BF16, "global [i, j] => read A0[i, :], read A1[:, j], write A2[i, j]", 3, {LT_BF16, LT_BF16, LT_F32},
      {2, 2, 2}, k::prepare_gemm_bf16, k::launch_gemm_bf16},
 };
@@ -633,7 +639,8 @@ lt_status sync_all(lt_ctx *c) {
 // ---------------------------------------------------------------- host transfers
 // Copy between the dense row-major host buffer `hb` (whole array) and the
 // part `box` of chunk ci that lives in device memory.
-lt_status xfer_chunk(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *hb, bool to_dev) {
+lt_status xfer_chunk(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *hb, bool to_dev,
+                     bool other_is_device = false) {
     const ArrayGeom &g = a->g;
     const ChunkGeom &cg = g.chunks[(size_t)ci];
     CState &s = a->cs[(size_t)ci];
@@ -654,6 +661,52 @@ lt_status xfer_chunk(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *h
         return hb + o * (int64_t)es;
     };
     cudaStream_t st = c->st[S_COMP];
+    const bool chunk_on_host = s.loc == LOC_HOST;
+    char *cbase = chunk_on_host ? c->host_base + s.off : dev;
+    if (other_is_device || chunk_on_host) {
+        // generic copy through unified addressing: chunk (HBM pool or pinned
+        // host pool) <-> a device buffer
+        auto caddr = [&](int64_t i0, int64_t i1, int64_t i2) {
+            int64_t idx[3] = {i0, i1, i2};
+            int64_t o = 0;
+            for (int d = 0; d < g.nd; ++d) o += (idx[d] - cg.s_origin[d]) * cg.stride[d];
+            return cbase + o * (int64_t)es;
+        };
+        int nd = g.nd;
+        int64_t n0 = nd == 3 ? box.extent(0) : 1;
+        for (int64_t z = 0; z < n0; ++z) {
+            size_t width, rows, cp, hp;
+            char *cptr, *hptr;
+            if (nd == 1) {
+                width = (size_t)box.extent(0) * es;
+                rows = 1;
+                cp = hp = width;
+                cptr = caddr(box.lo[0], 0, 0);
+                hptr = host_addr(box.lo[0], 0, 0);
+            } else if (nd == 2) {
+                width = (size_t)box.extent(1) * es;
+                rows = (size_t)box.extent(0);
+                cp = (size_t)cg.stride[0] * es;
+                hp = (size_t)gs[0] * es;
+                cptr = caddr(box.lo[0], box.lo[1], 0);
+                hptr = host_addr(box.lo[0], box.lo[1], 0);
+            } else {
+                int64_t i0 = box.lo[0] + z;
+                width = (size_t)box.extent(2) * es;
+                rows = (size_t)box.extent(1);
+                cp = (size_t)cg.stride[1] * es;
+                hp = (size_t)gs[1] * es;
+                cptr = caddr(i0, box.lo[1], box.lo[2]);
+                hptr = host_addr(i0, box.lo[1], box.lo[2]);
+            }
+            if (to_dev)
+                CK(c, cudaMemcpy2DAsync(cptr, cp, hptr, hp, width, rows, cudaMemcpyDefault, st));
+            else
+                CK(c, cudaMemcpy2DAsync(hptr, hp, cptr, cp, width, rows, cudaMemcpyDefault, st));
+        }
+        CK(c, cudaStreamSynchronize(st));
+        return LT_OK;
+    }
     if (g.dist.order == LT_ORDER_COL) {
         // column-major chunk: transpose on the host through a staging vector
         int64_t R = box.extent(0), Cn = box.extent(1);
@@ -1004,6 +1057,55 @@ lt_status lt_array_read(lt_ctx *c, lt_array *arr, void *host, size_t bytes) {
         }
     }
     return LT_OK;
+}
+
+static lt_status array_copy_device(lt_ctx *c, lt_array *arr, void *dev, size_t bytes, bool to_array) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    lt_array *a = find_array(c, arr);
+    if (!a || !dev) return fail(LT_ERR_INVALID_ARG, "unknown array or null buffer");
+    if (bytes != array_bytes(a)) return fail(LT_ERR_INVALID_ARG, "buffer size does not match the array");
+    if (a->g.dist.order == LT_ORDER_COL) return fail(LT_ERR_UNSUPPORTED, "device copies need row-major chunks");
+    if (c->dry) return fail(LT_ERR_UNSUPPORTED, "device copies need a device");
+    if ((st = flush_pending(c))) return st;
+    if ((st = sync_all(c))) return st;
+    if (to_array) {
+        ++c->launch_id;
+        for (size_t ci = 0; ci < a->cs.size(); ++ci) a->cs[ci].dead_launch = c->launch_id;
+    }
+    for (size_t ci = 0; ci < a->cs.size(); ++ci) {
+        CState &s = a->cs[ci];
+        const ChunkGeom &cg = a->g.chunks[ci];
+        if (!to_array && s.loc == LOC_NONE) {
+            // never written: zero the owned part of the destination
+            int64_t gs0 = a->g.nd > 1 ? a->g.shape[a->g.nd - 1] : 1;
+            (void)gs0;
+            if ((st = ensure_dev(c, a, (int64_t)ci, true))) return st;
+            if ((st = sync_all(c))) return st;
+        }
+        if (to_array && s.loc != LOC_HOST) {
+            s.pin++;
+            st = ensure_dev(c, a, (int64_t)ci, false);
+            s.pin--;
+            if (st) return st;
+            if ((st = sync_all(c))) return st;
+        }
+        s.dead_launch = -1;
+        if ((st = xfer_chunk(c, a, (int64_t)ci, to_array ? cg.box : cg.owned, (char *)dev, to_array, true))) return st;
+        if (to_array) {
+            s.ready = FenceSet();
+            s.busy = FenceSet();
+        }
+    }
+    return LT_OK;
+}
+
+lt_status lt_array_write_device(lt_ctx *c, lt_array *arr, const void *dev, size_t bytes) {
+    return array_copy_device(c, arr, const_cast<void *>(dev), bytes, true);
+}
+
+lt_status lt_array_read_device(lt_ctx *c, lt_array *arr, void *dev, size_t bytes) {
+    return array_copy_device(c, arr, dev, bytes, false);
 }
 
 lt_status lt_array_read_box(lt_ctx *c, lt_array *arr, const int64_t lo[3], const int64_t hi[3], void *host,

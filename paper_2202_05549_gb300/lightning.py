@@ -94,6 +94,13 @@ class Array:
         check(L.load().lt_array_read(self.ctx.h, self.h, out.ctypes.data_as(C.c_void_p), out.nbytes))
         return out
 
+    def write_device(self, ptr: int, nbytes: int):
+        """Copy from a dense row-major device buffer (e.g. tensor.data_ptr())."""
+        check(L.load().lt_array_write_device(self.ctx.h, self.h, C.c_void_p(ptr), nbytes))
+
+    def read_device(self, ptr: int, nbytes: int):
+        check(L.load().lt_array_read_device(self.ctx.h, self.h, C.c_void_p(ptr), nbytes))
+
     def read_box(self, lo, hi) -> np.ndarray:
         nd = len(self.shape)
         shp = tuple(int(h) - int(l) + 1 for l, h in zip(lo, hi))

@@ -1,0 +1,111 @@
+"""GPU parity of the diffusion forward launch and its chunked adjoint.
+
+Bars: forward f32 vs fp64 oracle <= 1e-5 relative (and chunked == unchunked
+bit for bit); gradients (adjoint with checkpoints + recomputation) vs the
+fp64 oracle gradient <= 1e-4 relative L2, and vs central finite differences
+of the fp64 forward (exact up to rounding: J is quadratic in u0).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth_inputs as si
+from paper_2202_05549_gb300 import _lib as L
+from paper_2202_05549_gb300 import lightning as lt
+
+pytestmark = pytest.mark.gpu
+FWD = "global [i, j] => read U[i-1:i+1, j-1:j+1], read K[i, j], write V[i, j]"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def fields(ny, nx):
+    return (si.uniform_field(si.SEED_DIFFUSION, si.STREAM_U, ny, nx),
+            si.kappa_field(si.SEED_DIFFUSION, si.STREAM_KAPPA, ny, nx))
+
+
+def test_forward_chunked_bit_exact_and_vs_fp64():
+    ny, nx, T = 300, 517, 6
+    u0, k = fields(ny, nx)
+    want = oracle.diffusion_forward(u0.astype(np.float64), k.astype(np.float64), T)
+    outs = []
+    with lt.Context() as ctx:
+        kf = ctx.kernel(lt.DIFFUSION2D, FWD, [("U", lt.F32), ("K", lt.F32), ("V", lt.F32)])
+        for dist, sb in [(lt.Dist.block(), (0, 0)), (lt.Dist.tiles((64, 128), halo=(1, 1)), (128, 64)),
+                         (lt.Dist.rows(50, halo=1), (517, 50)), (lt.Dist.tiles((64, 64)), (64, 64))]:
+            U = ctx.array(lt.F32, (ny, nx), dist)
+            V = ctx.array(lt.F32, (ny, nx), dist)
+            K = ctx.array(lt.F32, (ny, nx), dist)
+            U.write(u0)
+            K.write(k)
+            for _ in range(T):
+                kf.launch(grid=(nx, ny), block=(128, 2), superblock=sb, args=[U, K, V])
+                U, V = V, U
+            ctx.synchronize()
+            outs.append(U.read())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    assert rel(outs[0], want) < 1e-5
+
+
+@pytest.mark.parametrize("chunk,ckpt", [(0, 10), (16, 10), (24, 7)])
+def test_adjoint_64x64_vs_fp64_gradient_and_fd(chunk, ckpt):
+    torch = pytest.importorskip("torch")
+    from paper_2202_05549_gb300.autograd import DiffusionChunked
+
+    n, T = 64, 50
+    u0, k = fields(n, n)
+    u = torch.from_numpy(u0).cuda().requires_grad_(True)
+    kt = torch.from_numpy(k).cuda().requires_grad_(True)
+    sb = (chunk, chunk) if chunk else (0, 0)
+    uT = DiffusionChunked.apply(u, kt, T, ckpt, chunk, sb)
+    J = (uT.double() ** 2).sum()
+    J.backward()
+    J64, du0, dk = oracle.diffusion_grad(u0.astype(np.float64), k.astype(np.float64), T)
+    assert abs(J.item() - J64) / J64 < 1e-5
+    assert rel(u.grad.cpu().numpy(), du0) < 1e-4
+    assert rel(kt.grad.cpu().numpy(), dk) < 1e-4
+    # central finite differences of the fp64 forward
+    g = u.grad.cpu().numpy()
+    for (i, j) in [(0, 0), (31, 17), (63, 63), (5, 62)]:
+        h = 1e-3
+        up = u0.astype(np.float64).copy(); up[i, j] += h
+        dn = u0.astype(np.float64).copy(); dn[i, j] -= h
+        fd = (np.sum(oracle.diffusion_forward(up, k.astype(np.float64), T) ** 2)
+              - np.sum(oracle.diffusion_forward(dn, k.astype(np.float64), T) ** 2)) / (2 * h)
+        assert abs(g[i, j] - fd) <= 1e-4 * max(abs(fd), 1e-3)
+
+
+def test_adjoint_full_size_16384_sampled_vs_lightcone():
+    torch = pytest.importorskip("torch")
+    from paper_2202_05549_gb300.autograd import DiffusionPlan
+
+    n, T, ck, chunk = 16384, 50, 10, 4096
+    field = n * n * 4
+    with lt.Context(hbm_budget=int(26 * field * 1.1)) as ctx:
+        plan = DiffusionPlan(ctx, n, n, T, ck, lt.Dist.tiles((chunk, chunk), halo=(1, 1)), (chunk, chunk))
+        plan.K.fill(L.LT_INIT_KAPPA, seed=si.SEED_DIFFUSION, stream=si.STREAM_KAPPA)
+        plan.ck[0].fill(L.LT_INIT_UNIFORM, seed=si.SEED_DIFFUSION, stream=si.STREAM_U)
+        plan.forward()
+        uT = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        plan.ck[-1].read_device(uT.data_ptr(), field)
+        lamT = (2.0 * uT).contiguous()
+        torch.cuda.synchronize()
+        plan.lam[0].write_device(lamT.data_ptr(), field)
+        lam0 = plan.backward()
+        ii, jj = si.sample_cells(2207, n, n, 16, seams_every=chunk)
+        g_u = np.array([lam0.read_box((a, b), (a, b))[0, 0] for a, b in zip(ii, jj)])
+        g_k = np.array([plan.G.read_box((a, b), (a, b))[0, 0] for a, b in zip(ii, jj)])
+        u_T = np.array([plan.ck[-1].read_box((a, b), (a, b))[0, 0] for a, b in zip(ii, jj)])
+    wu, wdu, wdk = oracle.diffusion_lightcone(n, n, si.SEED_DIFFUSION, si.STREAM_U, si.STREAM_KAPPA, T, ii, jj)
+    assert rel(u_T, wu) < 1e-5
+    assert rel(g_u, wdu) < 1e-4
+    assert rel(g_k, wdk) < 1e-4
