@@ -35,7 +35,8 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lightning", choices=["lightning", "reference"])
-    p.add_argument("--workload", default="ooc", choices=["ooc", "incore", "gemm", "batch"])
+    p.add_argument("--workload", default="ooc", choices=["ooc", "incore", "gemm", "batch", "adjoint"])
+    p.add_argument("--adj-n", type=int, default=16384, help="grid side of the adjoint workload")
     p.add_argument("--batch-scale", type=int, default=1, help="divide the batch instance counts by this")
     p.add_argument("--gemm-n", type=int, default=65536, help="M = N = K of the GEMM workload")
     p.add_argument("--gemm-tile", type=int, default=8192, help="output tile chunk of the GEMM workload")
@@ -456,6 +457,75 @@ def run_batch(args, rank, world, local, grp):
     return res
 
 
+def run_adjoint(args, rank, world, local, grp):
+    """Gradient of J = sum u_T^2 for 50 diffusion steps on a 16384^2 grid:
+    chunked adjoint (checkpoints every 10 steps, recomputation) against the
+    plain form (torch ops, every state kept by autograd)."""
+    import torch
+
+    from paper_2202_05549_gb300.autograd import DiffusionChunked, PlainDiffusion
+
+    peaks = measured_peaks()
+    n, T, ck, chunk = args.adj_n, 50, 10, min(4096, args.adj_n)
+    dev = torch.device("cuda", local)
+    g = torch.Generator(device=dev)
+    g.manual_seed(2207)
+    u0 = torch.rand((n, n), device=dev, generator=g)
+    kap = 0.05 + 0.15 * torch.rand((n, n), device=dev, generator=g)
+
+    def ours():
+        u = u0.detach().requires_grad_(True)
+        k = kap.detach().requires_grad_(True)
+        uT = DiffusionChunked.apply(u, k, T, ck, chunk, (chunk, chunk))
+        (uT * uT).sum().backward()
+        return u.grad, k.grad
+
+    def plain():
+        u = u0.detach().requires_grad_(True)
+        k = kap.detach().requires_grad_(True)
+        uT = PlainDiffusion(u, k, T)
+        (uT * uT).sum().backward()
+        return u.grad, k.grad
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            out = fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) / steps, out
+
+    grp.barrier()
+    clk = Clocks(local)
+    t_ours, (gu, gk) = timed(ours, args.steps, args.warmup)
+    clocks = clk.stop()
+    t_plain, (pu, pk) = timed(plain, max(1, args.steps // 2), 1)
+    cells = float(n * n)
+    nbytes = cells * (12.0 * T + 12.0 * (T - T // ck) + 24.0 * T)
+    t_max = grp.max(t_ours)
+    value = grp.sum(nbytes / 1e9) / t_max
+    agree_u = float((gu - pu).norm() / pu.norm())
+    agree_k = float((gk - pk).norm() / pk.norm())
+    res = {
+        "metric": "differentiable chunked stencil: adjoint GB/s (fwd 12 B + recompute 12 B + adjoint 24 B per cell-step)",
+        "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_max * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (torch generator, uniform u0, kappa in [0.05, 0.2))",
+        "config": {"workload": f"diffusion {n}x{n}, {T} steps, checkpoints every {ck}, {chunk}^2 chunks + 1-cell halo; "
+                               "one step = forward + gradient of sum(u_T^2) via the autograd wrapper"},
+        "plain": {"ms_per_step": round(t_plain * 1e3, 2), "how": "torch ops, autograd keeps every state",
+                  "speedup_adjoint_vs_plain": round(t_plain / t_ours, 2),
+                  "rel_l2_difference_du0": agree_u, "rel_l2_difference_dkappa": agree_k},
+        "roofline": {"bound": "hbm", "achieved": round(nbytes / t_ours / 1e9, 1), "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(nbytes / t_ours / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
+                     "kernel": "diffusion_fwd_kernel + diffusion_adj_kernel (whole step, wall clock)"},
+        "clocks": clocks,
+    }
+    return res
+
+
 def cpu_baseline(args, threads=None, budget_s=15.0):
     """The oracle as it stands, on a bounded sample of the same workload."""
     import oracle
@@ -506,6 +576,9 @@ def main():
         args.no_cpu = True
     elif args.workload == "batch":
         res = run_batch(args, rank, world, local, grp)
+        args.no_cpu = True
+    elif args.workload == "adjoint":
+        res = run_adjoint(args, rank, world, local, grp)
         args.no_cpu = True
     else:
         res = run_lightning(args, rank, world, local, grp)

@@ -51,6 +51,26 @@ class DiffusionPlan:
         self.ka = ctx.kernel(lt.DIFFUSION2D_ADJ, ADJ_ANN, [("L1", lt.F32), ("K", lt.F32), ("U", lt.F32),
                                                            ("G", lt.F32), ("L0", lt.F32)])
 
+    def arrays(self):
+        return [self.K, self.G] + self.ck + self.work + self.lam
+
+    def release(self):
+        """Give the arrays and kernels back to the context."""
+        if self.K is None:
+            return
+        for a in self.arrays():
+            a.destroy()
+        self.kf.destroy()
+        self.ka.destroy()
+        self.K = None
+
+    def __del__(self):
+        try:
+            if self.K is not None and self.ctx.h:
+                self.release()
+        except Exception:
+            pass
+
     def _fwd(self, src, dst):
         self.kf.launch(grid=(self.nx, self.ny), block=(128, 2), superblock=self.sb, args=[src, self.K, dst])
 
@@ -131,6 +151,8 @@ class DiffusionChunked(torch.autograd.Function):
         dk = torch.empty_like(g)
         lam0.read_device(du0.data_ptr(), field)
         plan.G.read_device(dk.data_ptr(), field)
+        plan.release()
+        ctx.plan = None
         return du0, dk, None, None, None, None
 
 

@@ -154,6 +154,11 @@ class Kernel:
         check(L.load().lt_kernel_register(ctx.h, builtin, annotation.encode(), arr, len(self.params), C.byref(h)))
         self.h = h
 
+    def destroy(self):
+        if self.h:
+            check(L.load().lt_kernel_destroy(self.ctx.h, self.h))
+            self.h = None
+
     def _args(self, args):
         assert len(args) == len(self.params)
         a = (L.lt_arg * len(args))()
