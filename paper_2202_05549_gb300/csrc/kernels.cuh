@@ -52,33 +52,28 @@ struct CopyPiece {
     uint64_t unit_begin; // prefix sum of work units (see copy_piece_units)
 };
 
-// Work units of one copy piece: the box is linearised with the last axis
-// fastest and cut into units of LT_COPY_UNIT elements (or 16-byte vectors
-// when both sides are contiguous and aligned along the last axis).
+// Work units of one copy piece: a unit is a run of whole rows (all axes but
+// the innermost) of about LT_COPY_UNIT elements.  Within a row, when both
+// sides are contiguous along the innermost axis and equally misaligned, the
+// body moves as 16-byte vectors between a scalar head and tail.
 #define LT_COPY_UNIT 4096
-__host__ __device__ inline bool copy_piece_vec(const CopyPiece &p) {
-    int inner = p.nd - 1;
-    int64_t w = p.hi[inner] - p.lo[inner] + 1;
-    if (p.src.s[inner] != 1 || p.dst.s[inner] != 1) return false;
-    if ((w * p.esize) % 16 != 0) return false;
-    uint64_t a = p.src.base, b = p.dst.base;
-    int64_t off_s = 0, off_d = 0;
-    for (int d = 0; d < p.nd; ++d) {
-        off_s += p.lo[d] * p.src.s[d];
-        off_d += p.lo[d] * p.dst.s[d];
-        if (d < inner && ((p.src.s[d] * p.esize) % 16 != 0 || (p.dst.s[d] * p.esize) % 16 != 0)) return false;
-    }
-    a += (uint64_t)(off_s * p.esize);
-    b += (uint64_t)(off_d * p.esize);
-    return (a % 16 == 0) && (b % 16 == 0);
+__host__ __device__ inline int64_t copy_piece_width(const CopyPiece &p) {
+    return p.hi[p.nd - 1] - p.lo[p.nd - 1] + 1;
 }
-__host__ __device__ inline uint64_t copy_piece_items(const CopyPiece &p) {
-    uint64_t n = 1;
-    for (int d = 0; d < p.nd; ++d) n *= (uint64_t)(p.hi[d] - p.lo[d] + 1);
-    return copy_piece_vec(p) ? n * (uint64_t)p.esize / 16 : n;
+__host__ __device__ inline int64_t copy_piece_rows(const CopyPiece &p) {
+    int64_t r = 1;
+    for (int d = 0; d + 1 < p.nd; ++d) r *= p.hi[d] - p.lo[d] + 1;
+    return r;
+}
+__host__ __device__ inline int64_t copy_piece_rows_per_unit(const CopyPiece &p) {
+    int64_t w = copy_piece_width(p);
+    int64_t r = LT_COPY_UNIT / (w > 0 ? w : 1);
+    return r < 1 ? 1 : r;
 }
 __host__ __device__ inline uint64_t copy_piece_units(const CopyPiece &p) {
-    return (copy_piece_items(p) + LT_COPY_UNIT - 1) / LT_COPY_UNIT;
+    int64_t rpu = copy_piece_rows_per_unit(p);
+    int64_t seg = copy_piece_width(p) > LT_COPY_UNIT ? (copy_piece_width(p) + LT_COPY_UNIT - 1) / LT_COPY_UNIT : 1;
+    return (uint64_t)((copy_piece_rows(p) + rpu - 1) / rpu) * (uint64_t)seg;
 }
 
 // Reduce: dst[box] = src_0 (op) src_1 (op) ... in the listed order.

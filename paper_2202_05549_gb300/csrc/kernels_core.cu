@@ -116,64 +116,84 @@ __device__ __forceinline__ int find_piece_u(const CopyPiece *p, int n, uint64_t 
     return lo;
 }
 
-// One CTA per work unit; the piece is found by binary search.
+__device__ __forceinline__ void copy_elem(const char *s, char *d, int esize) {
+    switch (esize) {
+        case 1: *d = *s; break;
+        case 2: *(unsigned short *)d = *(const unsigned short *)s; break;
+        case 4: *(uint32_t *)d = *(const uint32_t *)s; break;
+        default: *(uint64_t *)d = *(const uint64_t *)s;
+    }
+}
+
+// One CTA per work unit (a run of rows, or a segment of one long row); the
+// piece is found by binary search.
 __global__ void __launch_bounds__(256) copy_kernel(const CopyPiece *__restrict__ pieces, int n) {
-    uint64_t u = blockIdx.x;
-    int pi = find_piece_u(pieces, n, u);
+    const uint64_t u = blockIdx.x;
+    const int pi = find_piece_u(pieces, n, u);
     const CopyPiece p = pieces[pi];
-    bool vec = copy_piece_vec(p);
-    uint64_t items = copy_piece_items(p);
-    uint64_t first = (u - p.unit_begin) * LT_COPY_UNIT;
-    uint64_t last = first + LT_COPY_UNIT < items ? first + LT_COPY_UNIT : items;
-    int inner = p.nd - 1;
-    int64_t w = p.hi[inner] - p.lo[inner] + 1;
-    int64_t e1 = p.nd == 3 ? p.hi[1] - p.lo[1] + 1 : 1;
-    if (vec) {
-        int64_t wv = w * p.esize / 16;  // vectors per row
-        for (uint64_t it = first + threadIdx.x; it < last; it += blockDim.x) {
-            int64_t row = (int64_t)(it / (uint64_t)wv), cv = (int64_t)(it % (uint64_t)wv);
+    const int inner = p.nd - 1;
+    const int64_t w = copy_piece_width(p), rows = copy_piece_rows(p);
+    const int64_t rpu = copy_piece_rows_per_unit(p);
+    const int64_t nseg = w > LT_COPY_UNIT ? (w + LT_COPY_UNIT - 1) / LT_COPY_UNIT : 1;
+    const int64_t lu = (int64_t)(u - p.unit_begin);
+    const int64_t r0 = (lu / nseg) * rpu, seg = lu % nseg;
+    const int64_t r1 = min(r0 + rpu, rows);
+    const int64_t c0 = seg * LT_COPY_UNIT, c1 = nseg > 1 ? min(c0 + LT_COPY_UNIT, w) : w;
+    const int64_t e1 = p.nd == 3 ? p.hi[1] - p.lo[1] + 1 : 1;
+    const int es = p.esize;
+    const bool contig = p.src.s[inner] == 1 && p.dst.s[inner] == 1;
+    if ((c1 - c0) * es < 512) {
+        // narrow rows: spread the unit's elements (rows x columns) over the threads
+        const uint32_t ncol = (uint32_t)(c1 - c0), nel = (uint32_t)((r1 - r0) * (c1 - c0));
+        for (uint32_t e = threadIdx.x; e < nel; e += blockDim.x) {
+            const int64_t r = r0 + e / ncol, col = p.lo[inner] + c0 + e % ncol;
             int64_t idx[3] = {0, 0, 0};
             if (p.nd == 3) {
-                idx[0] = p.lo[0] + row / e1;
-                idx[1] = p.lo[1] + row % e1;
+                idx[0] = p.lo[0] + r / e1;
+                idx[1] = p.lo[1] + r % e1;
             } else if (p.nd == 2) {
-                idx[0] = p.lo[0] + row;
+                idx[0] = p.lo[0] + r;
             }
+            idx[inner] = col;
             int64_t os = 0, od = 0;
-            for (int d = 0; d < inner; ++d) {
+            for (int d = 0; d < p.nd; ++d) {
                 os += idx[d] * p.src.s[d];
                 od += idx[d] * p.dst.s[d];
             }
-            os += p.lo[inner];
-            od += p.lo[inner];
-            const uint4 *s = (const uint4 *)(p.src.base + (uint64_t)(os * p.esize)) + cv;
-            uint4 *dd = (uint4 *)(p.dst.base + (uint64_t)(od * p.esize)) + cv;
-            *dd = __ldg(s);
+            copy_elem((const char *)(p.src.base + (uint64_t)(os * es)), (char *)(p.dst.base + (uint64_t)(od * es)),
+                      es);
         }
         return;
     }
-    for (uint64_t it = first + threadIdx.x; it < last; it += blockDim.x) {
-        int64_t row = (int64_t)(it / (uint64_t)w), col = (int64_t)(it % (uint64_t)w);
+    for (int64_t r = r0; r < r1; ++r) {
         int64_t idx[3] = {0, 0, 0};
         if (p.nd == 3) {
-            idx[0] = p.lo[0] + row / e1;
-            idx[1] = p.lo[1] + row % e1;
+            idx[0] = p.lo[0] + r / e1;
+            idx[1] = p.lo[1] + r % e1;
         } else if (p.nd == 2) {
-            idx[0] = p.lo[0] + row;
+            idx[0] = p.lo[0] + r;
         }
-        idx[inner] = p.lo[inner] + col;
         int64_t os = 0, od = 0;
-        for (int d = 0; d < p.nd; ++d) {
+        for (int d = 0; d < inner; ++d) {
             os += idx[d] * p.src.s[d];
             od += idx[d] * p.dst.s[d];
         }
-        const char *s = (const char *)(p.src.base + (uint64_t)(os * p.esize));
-        char *dd = (char *)(p.dst.base + (uint64_t)(od * p.esize));
-        switch (p.esize) {
-            case 1: *dd = *s; break;
-            case 2: *(unsigned short *)dd = *(const unsigned short *)s; break;
-            case 4: *(uint32_t *)dd = *(const uint32_t *)s; break;
-            default: *(uint64_t *)dd = *(const uint64_t *)s;
+        const int64_t col0 = p.lo[inner] + c0, ncol = c1 - c0;
+        const char *sb = (const char *)(p.src.base + (uint64_t)((os + col0 * p.src.s[inner]) * es));
+        char *db = (char *)(p.dst.base + (uint64_t)((od + col0 * p.dst.s[inner]) * es));
+        if (contig && ((uintptr_t)sb & 15) == ((uintptr_t)db & 15)) {
+            int64_t head = (int64_t)(((16 - ((uintptr_t)sb & 15)) & 15) / es);
+            if (head > ncol) head = ncol;
+            const int64_t nv = (ncol - head) * es / 16;
+            const int64_t tail0 = head + nv * 16 / es;
+            for (int64_t i = threadIdx.x; i < head; i += blockDim.x) copy_elem(sb + i * es, db + i * es, es);
+            const uint4 *sv = (const uint4 *)(sb + head * es);
+            uint4 *dv = (uint4 *)(db + head * es);
+            for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) dv[i] = __ldcg(sv + i);
+            for (int64_t i = tail0 + threadIdx.x; i < ncol; i += blockDim.x) copy_elem(sb + i * es, db + i * es, es);
+        } else {
+            const int64_t ss = p.src.s[inner] * es, ds = p.dst.s[inner] * es;
+            for (int64_t i = threadIdx.x; i < ncol; i += blockDim.x) copy_elem(sb + i * ss, db + i * ds, es);
         }
     }
 }

@@ -45,29 +45,49 @@ __device__ __forceinline__ float lap5(float c, float n, float s, float w, float 
     return __fsub_rn(__fadd_rn(__fadd_rn(__fadd_rn(n, s), w), e), __fmul_rn(4.0f, c));
 }
 
-constexpr int DT = 256;  // threads per CTA, one cell each
+constexpr int DT = 256;            // threads per CTA
+constexpr int TY = 32, TX = 128;   // cells per CTA tile
+constexpr int SP = TX + 2 + 1;     // shared row pitch (halo + bank padding)
 
-__global__ void __launch_bounds__(DT) diffusion_fwd_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+// Tiles of TY x TX cells over the box [by0, by1] x [bx0, bx1].
+__device__ __forceinline__ void tile_of(int64_t local, int64_t bx0, int64_t bx1, int64_t by0, int64_t *ty0,
+                                        int64_t *tx0) {
+    const int64_t gx = (bx1 - bx0 + TX) / TX;
+    *ty0 = by0 + (local / gx) * TY;
+    *tx0 = bx0 + (local % gx) * TX;
+}
+
+__global__ void __launch_bounds__(DT) diffusion_fwd_scalar_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    __shared__ float su[TY + 2][SP];
     const int ti = find_task_d(tasks, p.ntasks, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
     const int64_t x1 = min(t.t_hi[0], NX - 1), y1 = min(t.t_hi[1], NY - 1);
-    const int64_t w = x1 - x0 + 1;
-    const int64_t cell = (int64_t)(blockIdx.x - t.cta_begin) * DT + threadIdx.x;
-    if (w <= 0 || cell >= w * (y1 - y0 + 1)) return;
-    const int64_t i = y0 + cell / w, j = x0 + cell % w;
+    if (x1 < x0 || y1 < y0) return;
+    int64_t ty0, tx0;
+    tile_of((int64_t)(blockIdx.x - t.cta_begin), x0, x1, y0, &ty0, &tx0);
     const DView U = t.v[0], K = t.v[1], V = t.v[2];
-    float c = at2(U, i, j);
-    float n = i > 0 ? at2(U, i - 1, j) : 0.f;
-    float s = i + 1 < NY ? at2(U, i + 1, j) : 0.f;
-    float we = j > 0 ? at2(U, i, j - 1) : 0.f;
-    float e = j + 1 < NX ? at2(U, i, j + 1) : 0.f;
-    float k = at2(K, i, j);
-    ((float *)V.base)[i * V.s[0] + j * V.s[1]] = __fadd_rn(c, __fmul_rn(k, lap5(c, n, s, we, e)));
+    // U over the tile plus a one-cell ring (zero outside the domain)
+    for (int e = threadIdx.x; e < (TY + 2) * (TX + 2); e += DT) {
+        const int li = e / (TX + 2), lj = e % (TX + 2);
+        const int64_t i = ty0 - 1 + li, j = tx0 - 1 + lj;
+        su[li][lj] = (i >= 0 && i < NY && j >= 0 && j < NX && i <= y1 + 1 && j <= x1 + 1) ? at2(U, i, j) : 0.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < TY * TX; e += DT) {
+        const int li = e / TX + 1, lj = e % TX + 1;
+        const int64_t i = ty0 + li - 1, j = tx0 + lj - 1;
+        if (i > y1 || j > x1) continue;
+        const float c = su[li][lj];
+        const float l = lap5(c, su[li - 1][lj], su[li + 1][lj], su[li][lj - 1], su[li][lj + 1]);
+        ((float *)V.base)[i * V.s[0] + j * V.s[1]] = __fadd_rn(c, __fmul_rn(at2(K, i, j), l));
+    }
 }
 
-__global__ void __launch_bounds__(DT) diffusion_adj_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+__global__ void __launch_bounds__(DT) diffusion_adj_scalar_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    __shared__ float ss[TY + 2][SP];  // s = K * L1 of the superblock's own cells, 0 elsewhere
+    __shared__ float su[TY + 2][SP];  // u_t
     const int ti = find_task_d(tasks, p.ntasks, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
@@ -78,30 +98,210 @@ __global__ void __launch_bounds__(DT) diffusion_adj_kernel(const ExecTask *__res
     // its reduce region: one cell wider, clipped
     const int64_t rx0 = max(x0 - 1, (int64_t)0), ry0 = max(y0 - 1, (int64_t)0);
     const int64_t rx1 = min(x1 + 1, NX - 1), ry1 = min(y1 + 1, NY - 1);
-    const int64_t w = rx1 - rx0 + 1;
-    const int64_t cell = (int64_t)(blockIdx.x - t.cta_begin) * DT + threadIdx.x;
-    if (cell >= w * (ry1 - ry0 + 1)) return;
-    const int64_t i = ry0 + cell / w, j = rx0 + cell % w;
+    int64_t ty0, tx0;
+    tile_of((int64_t)(blockIdx.x - t.cta_begin), rx0, rx1, ry0, &ty0, &tx0);
     const DView L1 = t.v[0], K = t.v[1], U = t.v[2], G = t.v[3], L0 = t.v[4];
-    auto in_sb = [&](int64_t a, int64_t b) { return a >= y0 && a <= y1 && b >= x0 && b <= x1; };
-    auto src = [&](int64_t a, int64_t b) { return __fmul_rn(at2(K, a, b), at2(L1, a, b)); };
-    float acc = 0.f;
-    if (in_sb(i, j)) {
-        const float l1 = at2(L1, i, j);
-        acc = __fsub_rn(l1, __fmul_rn(4.0f, __fmul_rn(at2(K, i, j), l1)));
-        float c = at2(U, i, j);
-        float n = i > 0 ? at2(U, i - 1, j) : 0.f;
-        float s = i + 1 < NY ? at2(U, i + 1, j) : 0.f;
-        float we = j > 0 ? at2(U, i, j - 1) : 0.f;
-        float e = j + 1 < NX ? at2(U, i, j + 1) : 0.f;
-        float *g = (float *)G.base + i * G.s[0] + j * G.s[1];
-        *g = __fadd_rn(*g, __fmul_rn(l1, lap5(c, n, s, we, e)));
+    for (int e = threadIdx.x; e < (TY + 2) * (TX + 2); e += DT) {
+        const int li = e / (TX + 2), lj = e % (TX + 2);
+        const int64_t i = ty0 - 1 + li, j = tx0 - 1 + lj;
+        const bool sb = i >= y0 && i <= y1 && j >= x0 && j <= x1;
+        ss[li][lj] = sb ? __fmul_rn(at2(K, i, j), at2(L1, i, j)) : 0.f;
+        su[li][lj] = (sb || (i >= 0 && i < NY && j >= 0 && j < NX && i >= y0 - 1 && i <= y1 + 1 && j >= x0 - 1 &&
+                             j <= x1 + 1))
+                         ? at2(U, i, j)
+                         : 0.f;
     }
-    if (i - 1 >= 0 && in_sb(i - 1, j)) acc = __fadd_rn(acc, src(i - 1, j));
-    if (i + 1 < NY && in_sb(i + 1, j)) acc = __fadd_rn(acc, src(i + 1, j));
-    if (j - 1 >= 0 && in_sb(i, j - 1)) acc = __fadd_rn(acc, src(i, j - 1));
-    if (j + 1 < NX && in_sb(i, j + 1)) acc = __fadd_rn(acc, src(i, j + 1));
-    ((float *)L0.base)[i * L0.s[0] + j * L0.s[1]] = acc;
+    __syncthreads();
+    for (int e = threadIdx.x; e < TY * TX; e += DT) {
+        const int li = e / TX + 1, lj = e % TX + 1;
+        const int64_t i = ty0 + li - 1, j = tx0 + lj - 1;
+        if (i > ry1 || j > rx1) continue;
+        float acc = 0.f;
+        if (i >= y0 && i <= y1 && j >= x0 && j <= x1) {
+            const float l1 = at2(L1, i, j);
+            acc = __fsub_rn(l1, __fmul_rn(4.0f, ss[li][lj]));
+            const float c = su[li][lj];
+            float *g = (float *)G.base + i * G.s[0] + j * G.s[1];
+            *g = __fadd_rn(*g, __fmul_rn(l1, lap5(c, su[li - 1][lj], su[li + 1][lj], su[li][lj - 1], su[li][lj + 1])));
+        }
+        // contributions of the superblock's neighbours of (i, j): north, south, west, east
+        acc = __fadd_rn(acc, ss[li - 1][lj]);
+        acc = __fadd_rn(acc, ss[li + 1][lj]);
+        acc = __fadd_rn(acc, ss[li][lj - 1]);
+        acc = __fadd_rn(acc, ss[li][lj + 1]);
+        ((float *)L0.base)[i * L0.s[0] + j * L0.s[1]] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- vector variants
+// Tiles start on 4-aligned global columns; every view is row-major with
+// 16-byte aligned rows, so float4 groups are aligned in every chunk and
+// partial (storage is padded to 128-byte column boundaries).  Elements of a
+// group that lie outside what the annotation lets the kernel read are
+// zeroed after the load (the group itself stays inside the padded storage).
+constexpr int VQ = TX / 4;          // float4 groups per tile row
+constexpr int VP = TX + 8;          // shared pitch: 4 columns of halo room each side
+
+__device__ __forceinline__ float4 ld4v(const DView &v, int64_t i, int64_t j) {
+    return *(const float4 *)((const float *)v.base + i * v.s[0] + j);
+}
+__device__ __forceinline__ float sel(bool b, float x) { return b ? x : 0.f; }
+
+__global__ void __launch_bounds__(DT) diffusion_fwd_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    __shared__ __align__(16) float su[TY + 2][VP];
+    const int ti = find_task_d(tasks, p.ntasks, blockIdx.x);
+    const ExecTask &t = tasks[ti];
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
+    const int64_t x1 = min(t.t_hi[0], NX - 1), y1 = min(t.t_hi[1], NY - 1);
+    if (x1 < x0 || y1 < y0) return;
+    int64_t ty0, tx0;
+    tile_of((int64_t)(blockIdx.x - t.cta_begin), x0, x1, y0, &ty0, &tx0);
+    const DView U = t.v[0], K = t.v[1], V = t.v[2];
+    const int64_t cmax = min(x1 + 1, NX - 1), rmin = max(y0 - 1, (int64_t)0), rmax = min(y1 + 1, NY - 1);
+    for (int e = threadIdx.x; e < (TY + 2) * VQ; e += DT) {
+        const int li = e / VQ, q = e % VQ;
+        const int64_t i = ty0 - 1 + li, j = tx0 + 4 * q;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i >= rmin && i <= rmax && j <= cmax) {
+            v = ld4v(U, i, j);
+            v.y = sel(j + 1 <= cmax, v.y);
+            v.z = sel(j + 2 <= cmax, v.z);
+            v.w = sel(j + 3 <= cmax, v.w);
+        }
+        *(float4 *)&su[li][4 + 4 * q] = v;
+    }
+    for (int e = threadIdx.x; e < 2 * (TY + 2); e += DT) {
+        const int li = e >> 1;
+        const int64_t i = ty0 - 1 + li, j = (e & 1) ? tx0 + TX : tx0 - 1;
+        su[li][(e & 1) ? 4 + TX : 3] = (i >= rmin && i <= rmax && j >= 0 && j <= cmax) ? at2(U, i, j) : 0.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < TY * VQ; e += DT) {
+        const int li = e / VQ + 1, q = e % VQ;
+        const int64_t i = ty0 + li - 1, j = tx0 + 4 * q;
+        if (i > y1 || j > x1) continue;
+        const int c = 4 + 4 * q;
+        const float4 k4 = ld4v(K, i, j);
+        const float kk[4] = {k4.x, k4.y, k4.z, k4.w};
+        float o[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float cc = su[li][c + m];
+            o[m] = __fadd_rn(cc, __fmul_rn(kk[m], lap5(cc, su[li - 1][c + m], su[li + 1][c + m], su[li][c + m - 1],
+                                                       su[li][c + m + 1])));
+        }
+        float *dst = (float *)V.base + i * V.s[0] + j;
+        if (j + 3 <= x1) {
+            *(float4 *)dst = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+            for (int m = 0; m < 4 && j + m <= x1; ++m) dst[m] = o[m];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(DT) diffusion_adj_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    __shared__ __align__(16) float ss[TY + 2][VP];
+    __shared__ __align__(16) float su[TY + 2][VP];
+    const int ti = find_task_d(tasks, p.ntasks, blockIdx.x);
+    const ExecTask &t = tasks[ti];
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
+    const int64_t x1 = min(t.t_hi[0], NX - 1), y1 = min(t.t_hi[1], NY - 1);
+    if (x1 < x0 || y1 < y0) return;
+    const int64_t rx0 = max(x0 - 1, (int64_t)0), ry0 = max(y0 - 1, (int64_t)0);
+    const int64_t rx1 = min(x1 + 1, NX - 1), ry1 = min(y1 + 1, NY - 1);
+    const int64_t ax0 = rx0 & ~(int64_t)3;  // tiles start on 4-aligned columns
+    int64_t ty0, tx0;
+    tile_of((int64_t)(blockIdx.x - t.cta_begin), ax0, rx1, ry0, &ty0, &tx0);
+    const DView L1 = t.v[0], K = t.v[1], U = t.v[2], G = t.v[3], L0 = t.v[4];
+    for (int e = threadIdx.x; e < (TY + 2) * VQ; e += DT) {
+        const int li = e / VQ, q = e % VQ;
+        const int64_t i = ty0 - 1 + li, j = tx0 + 4 * q;
+        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f), uv = sv;
+        if (i >= y0 && i <= y1 && j + 3 >= x0 && j <= x1) {  // group meets the superblock
+            const float4 k4 = ld4v(K, i, j), l4 = ld4v(L1, i, j);
+            sv.x = sel(j >= x0 && j <= x1, __fmul_rn(k4.x, l4.x));
+            sv.y = sel(j + 1 >= x0 && j + 1 <= x1, __fmul_rn(k4.y, l4.y));
+            sv.z = sel(j + 2 >= x0 && j + 2 <= x1, __fmul_rn(k4.z, l4.z));
+            sv.w = sel(j + 3 >= x0 && j + 3 <= x1, __fmul_rn(k4.w, l4.w));
+        }
+        if (i >= ry0 && i <= ry1 && j + 3 >= rx0 && j <= rx1) {  // group meets the U read region
+            uv = ld4v(U, i, j);
+            uv.x = sel(j >= rx0 && j <= rx1, uv.x);
+            uv.y = sel(j + 1 >= rx0 && j + 1 <= rx1, uv.y);
+            uv.z = sel(j + 2 >= rx0 && j + 2 <= rx1, uv.z);
+            uv.w = sel(j + 3 >= rx0 && j + 3 <= rx1, uv.w);
+        }
+        *(float4 *)&ss[li][4 + 4 * q] = sv;
+        *(float4 *)&su[li][4 + 4 * q] = uv;
+    }
+    for (int e = threadIdx.x; e < 2 * (TY + 2); e += DT) {
+        const int li = e >> 1;
+        const int64_t i = ty0 - 1 + li, j = (e & 1) ? tx0 + TX : tx0 - 1;
+        const int c = (e & 1) ? 4 + TX : 3;
+        const bool sb = i >= y0 && i <= y1 && j >= x0 && j <= x1;
+        ss[li][c] = sb ? __fmul_rn(at2(K, i, j), at2(L1, i, j)) : 0.f;
+        su[li][c] = (i >= ry0 && i <= ry1 && j >= rx0 && j <= rx1) ? at2(U, i, j) : 0.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < TY * VQ; e += DT) {
+        const int li = e / VQ + 1, q = e % VQ;
+        const int64_t i = ty0 + li - 1, j = tx0 + 4 * q;
+        if (i > ry1 || j > rx1 || j + 3 < rx0) continue;
+        const int c = 4 + 4 * q;
+        const bool row_sb = i >= y0 && i <= y1;
+        float4 l4 = make_float4(0.f, 0.f, 0.f, 0.f), g4 = l4;
+        const bool grp_sb = row_sb && j + 3 >= x0 && j <= x1;
+        if (grp_sb) {
+            l4 = ld4v(L1, i, j);
+            g4 = ld4v(G, i, j);
+        }
+        const float l1[4] = {l4.x, l4.y, l4.z, l4.w};
+        float g[4] = {g4.x, g4.y, g4.z, g4.w};
+        float o[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const bool in = row_sb && j + m >= x0 && j + m <= x1;
+            float acc = 0.f;
+            if (in) {
+                acc = __fsub_rn(l1[m], __fmul_rn(4.0f, ss[li][c + m]));
+                const float cc = su[li][c + m];
+                g[m] = __fadd_rn(g[m], __fmul_rn(l1[m], lap5(cc, su[li - 1][c + m], su[li + 1][c + m],
+                                                              su[li][c + m - 1], su[li][c + m + 1])));
+            }
+            acc = __fadd_rn(acc, ss[li - 1][c + m]);
+            acc = __fadd_rn(acc, ss[li + 1][c + m]);
+            acc = __fadd_rn(acc, ss[li][c + m - 1]);
+            acc = __fadd_rn(acc, ss[li][c + m + 1]);
+            o[m] = acc;
+        }
+        float *dst = (float *)L0.base + i * L0.s[0] + j;
+        if (j >= rx0 && j + 3 <= rx1) {
+            *(float4 *)dst = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+            for (int m = 0; m < 4; ++m)
+                if (j + m >= rx0 && j + m <= rx1) dst[m] = o[m];
+        }
+        if (grp_sb) {
+            float *gd = (float *)G.base + i * G.s[0] + j;
+            if (j >= x0 && j + 3 <= x1) {
+                *(float4 *)gd = make_float4(g[0], g[1], g[2], g[3]);
+            } else {
+                for (int m = 0; m < 4; ++m)
+                    if (j + m >= x0 && j + m <= x1) gd[m] = g[m];
+            }
+        }
+    }
+}
+
+bool views_vec_ok(const ExecTask *t, int n, int nviews) {
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < nviews; ++a) {
+            const DView &v = t[i].v[a];
+            if (v.s[1] != 1 || (v.s[0] % 4) != 0 || (v.base % 16) != 0) return false;
+        }
+    return true;
 }
 
 }  // namespace
@@ -110,44 +310,57 @@ namespace k {
 
 uint32_t prepare_diffusion(ExecTask *t, int n, ExecParams &p) {
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    bool vec = views_vec_ok(t, n, 3);
+    for (int i = 0; i < n; ++i)
+        if (t[i].t_lo[0] % 4 != 0) vec = false;
+    p.variant = vec ? 1 : 0;
     uint32_t total = 0;
     for (int i = 0; i < n; ++i) {
         int64_t w = std::min(t[i].t_hi[0], NX - 1) - t[i].t_lo[0] + 1;
         int64_t h = std::min(t[i].t_hi[1], NY - 1) - t[i].t_lo[1] + 1;
-        uint64_t cells = (w > 0 && h > 0) ? (uint64_t)(w * h) : 0;
         t[i].cta_begin = total;
-        t[i].cta_count = (uint32_t)((cells + DT - 1) / DT);
+        t[i].cta_count = (w > 0 && h > 0) ? (uint32_t)(((w + TX - 1) / TX) * ((h + TY - 1) / TY)) : 0;
         total += t[i].cta_count;
     }
     return total;
 }
 
 cudaError_t launch_diffusion(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
-    diffusion_fwd_kernel<<<ctas, DT, 0, st>>>(dev, p);
+    if (p.variant == 1)
+        diffusion_fwd_vec_kernel<<<ctas, DT, 0, st>>>(dev, p);
+    else
+        diffusion_fwd_scalar_kernel<<<ctas, DT, 0, st>>>(dev, p);
     return cudaGetLastError();
 }
 
 uint32_t prepare_diffusion_adj(ExecTask *t, int n, ExecParams &p) {
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    const bool vec = views_vec_ok(t, n, 5);
+    p.variant = vec ? 1 : 0;
     uint32_t total = 0;
     for (int i = 0; i < n; ++i) {
         int64_t x0 = t[i].t_lo[0], y0 = t[i].t_lo[1];
         int64_t x1 = std::min(t[i].t_hi[0], NX - 1), y1 = std::min(t[i].t_hi[1], NY - 1);
-        uint64_t cells = 0;
+        uint32_t c = 0;
         if (x1 >= x0 && y1 >= y0) {
-            int64_t w = std::min(x1 + 1, NX - 1) - std::max<int64_t>(x0 - 1, 0) + 1;
+            int64_t bx0 = std::max<int64_t>(x0 - 1, 0);
+            if (vec) bx0 &= ~(int64_t)3;
+            int64_t w = std::min(x1 + 1, NX - 1) - bx0 + 1;
             int64_t h = std::min(y1 + 1, NY - 1) - std::max<int64_t>(y0 - 1, 0) + 1;
-            cells = (uint64_t)(w * h);
+            c = (uint32_t)(((w + TX - 1) / TX) * ((h + TY - 1) / TY));
         }
         t[i].cta_begin = total;
-        t[i].cta_count = (uint32_t)((cells + DT - 1) / DT);
-        total += t[i].cta_count;
+        t[i].cta_count = c;
+        total += c;
     }
     return total;
 }
 
 cudaError_t launch_diffusion_adj(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
-    diffusion_adj_kernel<<<ctas, DT, 0, st>>>(dev, p);
+    if (p.variant == 1)
+        diffusion_adj_vec_kernel<<<ctas, DT, 0, st>>>(dev, p);
+    else
+        diffusion_adj_scalar_kernel<<<ctas, DT, 0, st>>>(dev, p);
     return cudaGetLastError();
 }
 

@@ -158,6 +158,7 @@ struct BuiltinDef {
     int nd[LT_MAX_ARRAYS];
     uint32_t (*prepare)(ExecTask *, int, ExecParams &);
     cudaError_t (*launch)(const ExecTask *, uint32_t, const ExecParams &, cudaStream_t);
+    bool reduce_zero = true;  // reduce partials must start at the identity (else the kernel writes every cell)
 };
 
 const BuiltinDef kBuiltins[] = {
@@ -173,7 +174,8 @@ const BuiltinDef kBuiltins[] = {
     {LT_K_DIFFUSION2D_ADJ,
      "global [i, j] => read A0[i, j], read A1[i, j], read A2[i-1:i+1, j-1:j+1], readwrite A3[i, j], "
      "reduce(+) A4[i-1:i+1, j-1:j+1]",
-     5, {LT_F32, LT_F32, LT_F32, LT_F32, LT_F32}, {2, 2, 2, 2, 2}, k::prepare_diffusion_adj, k::launch_diffusion_adj},
+     5, {LT_F32, LT_F32, LT_F32, LT_F32, LT_F32}, {2, 2, 2, 2, 2}, k::prepare_diffusion_adj, k::launch_diffusion_adj,
+     false},
     {LT_K_GEMM_BF16, "global [i, j] => read A0[i, :], read A1[:, j], write A2[i, j]", 3, {LT_BF16, LT_BF16, LT_F32},
      {2, 2, 2}, k::prepare_gemm_bf16, k::launch_gemm_bf16},
 };
@@ -1547,12 +1549,14 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
     FenceSet red_fence;
     if (red_bytes) {
         if ((st = dev_alloc(c, red_bytes, &red_base, &red_fence))) return st;
-        op_begin(c, S_COMP, "reduce_init");
-        if ((st = op_wait(c, red_fence))) return st;
-        if (!c->dry) CK(c, cudaMemsetAsync(c->dev_base + red_base, 0, red_bytes, c->st[S_COMP]));
-        uint64_t q;
-        if ((st = op_end(c, &q))) return st;
-        red_fence = FenceSet::one(S_COMP, q);
+        if (def->reduce_zero) {
+            op_begin(c, S_COMP, "reduce_init");
+            if ((st = op_wait(c, red_fence))) return st;
+            if (!c->dry) CK(c, cudaMemsetAsync(c->dev_base + red_base, 0, red_bytes, c->st[S_COMP]));
+            uint64_t q;
+            if ((st = op_end(c, &q))) return st;
+            red_fence = FenceSet::one(S_COMP, q);
+        }
     }
 
     // process superblocks in groups: all at once when the launch fits in
@@ -1866,6 +1870,7 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
     c->cur_group = (int64_t)((nsb + gsz - 1) / gsz);
     if (red_bytes) {
         std::vector<ReducePiece> rp;
+        std::vector<CopyPiece> rcopies;
         std::vector<DView> srcs;
         FenceSet rw = red_fence;
         // per destination chunk, the (superblock, box) contributions
@@ -1935,6 +1940,20 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                                 p.nsrc++;
                             }
                         if (!p.nsrc) continue;
+                        if (p.nsrc == 1) {  // a single contribution: a plain copy
+                            CopyPiece cp{};
+                            cp.src = srcs.back();
+                            srcs.pop_back();
+                            cp.dst = view_of(c, a->g, cg, cs.off);
+                            cp.nd = a->g.nd;
+                            cp.esize = (int32_t)a->g.esize();
+                            for (int dd = 0; dd < 3; ++dd) {
+                                cp.lo[dd] = dd < a->g.nd ? cell.lo[dd] : 0;
+                                cp.hi[dd] = dd < a->g.nd ? cell.hi[dd] : 0;
+                            }
+                            rcopies.push_back(cp);
+                            continue;
+                        }
                         p.dst = view_of(c, a->g, cg, cs.off);
                         p.nd = a->g.nd;
                         p.op = red_op;
@@ -1959,16 +1978,30 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
         size_t ro1, ro2;
         if ((st = upload(c, rp.data(), rp.size() * sizeof(ReducePiece), &dp1, &ro1))) return st;
         if ((st = upload(c, srcs.data(), srcs.size() * sizeof(DView), &dp2, &ro2))) return st;
+        void *dp3;
+        size_t ro3;
+        uint64_t cunits = 0;
+        for (auto &p : rcopies) {
+            p.unit_begin = cunits;
+            cunits += copy_piece_units(p);
+        }
+        if ((st = upload(c, rcopies.data(), rcopies.size() * sizeof(CopyPiece), &dp3, &ro3))) return st;
         if (!c->dry && !rp.empty()) {
             TimeScope ts(c, CAT_COPYK);
             CK(c, k::reduce_pieces((const ReducePiece *)dp1, (const DView *)dp2, (int)rp.size(), elems,
                                    c->st[S_COMP]));
             c->stats.kernels++;
         }
+        if (!c->dry && !rcopies.empty()) {
+            TimeScope ts(c, CAT_COPYK);
+            CK(c, k::copy_pieces((const CopyPiece *)dp3, (int)rcopies.size(), cunits, c->st[S_COMP]));
+            c->stats.kernels++;
+        }
         uint64_t q;
         if ((st = op_end(c, &q))) return st;
         upload_done(c, ro1, rp.size() * sizeof(ReducePiece), q);
         upload_done(c, ro2, srcs.size() * sizeof(DView), q);
+        upload_done(c, ro3, rcopies.size() * sizeof(CopyPiece), q);
         c->stats.tasks_reduce++;
         for (auto &d : dests) {
             CState &cs = d.first->cs[(size_t)d.second];
