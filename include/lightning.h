@@ -220,7 +220,8 @@ typedef enum {
     LT_K_GEMM_BF16 = 4,      /* C[i,j] = sum_k A[i,k] B[k,j]; bf16 in, f32 accumulate/out */
     LT_K_HIST256 = 5,        /* reduce(+) H[:] of one count per u8 element */
     LT_K_DIFFUSION2D = 6,    /* u1 = u + K*(Lu), f32 */
-    LT_K_DIFFUSION2D_ADJ = 7 /* adjoint step: reduce(+) of the transposed stencil */
+    LT_K_DIFFUSION2D_ADJ = 7, /* adjoint step: reduce(+) of the transposed stencil */
+    LT_K_ROWREDUCE = 8        /* "read A[i, j], reduce(f) S[i]" (Sec. 2.3), f32, f in + * min max */
 } lt_builtin;
 
 typedef struct {

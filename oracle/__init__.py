@@ -83,6 +83,7 @@ def lib():
                 "orc_gemm_bf16_corner_f32": (C.c_int, [_i64, _i64, _i64, _i64, _i64, _u64, _u64, _u64,
                                                        C.c_double, _p]),
                 "orc_hist256": (None, [_i64, _p, _p]),
+                "orc_rowreduce_f64": (None, [_i64, _i64, _p, C.c_int, _p]),
                 "orc_diff_forward_f64": (C.c_int, [_i64, _i64, _p, _p, C.c_int, _p]),
                 "orc_diff_grad_f64": (C.c_int, [_i64, _i64, _p, _p, C.c_int, _p, _p, _p]),
                 "orc_diff_lightcone_f64": (C.c_int, [_i64, _i64, _u64, _u64, _u64, C.c_int, _i64, _p, _p,
@@ -229,6 +230,14 @@ def hist256(x: np.ndarray) -> np.ndarray:
     h = np.empty(256, np.uint32)
     lib().orc_hist256(x.size, _ptr(x), _ptr(h))
     return h
+
+
+def rowreduce(a: np.ndarray, op: str) -> np.ndarray:
+    """out[i] = a[i,0] op a[i,1] op ... (fp64, left to right); op in + * min max."""
+    a = np.ascontiguousarray(a, np.float64)
+    out = np.empty(a.shape[0], np.float64)
+    lib().orc_rowreduce_f64(a.shape[0], a.shape[1], _ptr(a), {"+": 0, "*": 1, "min": 2, "max": 3}[op], _ptr(out))
+    return out
 
 
 # ---------------------------------------------------------------- diffusion

@@ -427,6 +427,30 @@ void orc_hist256(int64_t n, const uint8_t *x, uint32_t *h) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Row reduction, the paper's third annotation example (Sec. 2.3):          */
+/*   "global [i, j] => read A[i, j], reduce(f) sum[i]",  f in {+, *, min, max} */
+/* out[i] = A[i,0] f A[i,1] f ... f A[i,nx-1], in fp64, left to right.        */
+/* op: 0 = +, 1 = *, 2 = min, 3 = max.                                        */
+/* ------------------------------------------------------------------------ */
+void orc_rowreduce_f64(int64_t ny, int64_t nx, const double *a, int op, double *out) {
+    for (int64_t i = 0; i < ny; ++i) {
+        double acc = a[i * nx];
+        for (int64_t j = 1; j < nx; ++j) {
+            double x = a[i * nx + j];
+            if (op == 0)
+                acc = acc + x;
+            else if (op == 1)
+                acc = acc * x;
+            else if (op == 2)
+                acc = x < acc ? x : acc;
+            else
+                acc = x > acc ? x : acc;
+        }
+        out[i] = acc;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Variable-coefficient diffusion and its adjoint, fp64:                    */
 /*   (L u)_ij = (((u_{i-1,j} + u_{i+1,j}) + u_{i,j-1}) + u_{i,j+1}) - 4 u_ij */
 /*   u_{t+1} = u_t + kappa (.) L u_t,   J = sum u_T^2                          */

@@ -40,6 +40,8 @@ struct ExecParams {
     uint32_t* err;                    // device error word (bounds checks)
     int32_t ntasks;
     int32_t variant;                  // kernel variant chosen by prepare_*
+    int32_t red_op;                   // operator of the reduce(f) argument (0 + 1 * 2 min 3 max)
+    int32_t pad2;
 };
 
 // Box copy (pack / unpack / replica update): copy the global box [lo, hi]
@@ -150,10 +152,14 @@ cudaError_t reduce_pieces(const ReducePiece *dev, const DView *srcs, int n, uint
 uint32_t prepare_stencil1d(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_stencil1d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p);
+uint32_t prepare_jacobi3d(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_jacobi3d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_diffusion(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_diffusion(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_diffusion_adj(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_diffusion_adj(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
+uint32_t prepare_rowreduce(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_rowreduce(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_hist256(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_hist256(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_gemm_bf16(ExecTask *t, int n, ExecParams &p);

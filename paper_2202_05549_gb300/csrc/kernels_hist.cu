@@ -82,9 +82,62 @@ __global__ void __launch_bounds__(HT) hist256_kernel(const ExecTask *__restrict_
     }
 }
 
+// Row reduction "global [i, j] => read A[i, j], reduce(f) S[i]": one warp per
+// row of the superblock; each lane folds columns lane, lane+32, ... from the
+// identity, then the warp combines lanes in a fixed shuffle tree, so the
+// partial of every row is deterministic.
+constexpr int RW = 8;  // warps (rows) per CTA
+
+__device__ __forceinline__ float rop(int op, float a, float b) {
+    switch (op) {
+        case 0: return __fadd_rn(a, b);
+        case 1: return __fmul_rn(a, b);
+        case 2: return fminf(a, b);
+        default: return fmaxf(a, b);
+    }
+}
+
+__global__ void __launch_bounds__(RW * 32) rowreduce_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    const int ti = find_task_h(tasks, p.ntasks, blockIdx.x);
+    const ExecTask &t = tasks[ti];
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    const int64_t x0 = t.t_lo[0], x1 = min(t.t_hi[0], NX - 1);
+    const int64_t y1 = min(t.t_hi[1], NY - 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = t.t_lo[1] + (int64_t)(blockIdx.x - t.cta_begin) * RW + warp;
+    if (i > y1 || x1 < x0) return;  // warp-uniform
+    const int op = p.red_op;
+    const float ident = op == 0 ? 0.0f : op == 1 ? 1.0f : op == 2 ? __int_as_float(0x7f800000) : __int_as_float(0xff800000);
+    const DView A = t.v[0], S = t.v[1];
+    const float *row = (const float *)A.base + i * A.s[0];
+    float acc = ident;
+    for (int64_t j = x0 + lane; j <= x1; j += 32) acc = rop(op, acc, row[j * A.s[1]]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc = rop(op, acc, __shfl_down_sync(0xffffffffu, acc, off));
+    if (lane == 0) ((float *)S.base)[i * S.s[0]] = acc;
+}
+
 }  // namespace
 
 namespace k {
+
+uint32_t prepare_rowreduce(ExecTask *t, int n, ExecParams &p) {
+    uint32_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        int64_t h = std::min(t[i].t_hi[1], p.shape[0][0] - 1) - t[i].t_lo[1] + 1;
+        int64_t w = std::min(t[i].t_hi[0], p.shape[0][1] - 1) - t[i].t_lo[0] + 1;
+        t[i].cta_begin = total;
+        t[i].cta_count = (h > 0 && w > 0) ? (uint32_t)((h + RW - 1) / RW) : 0;
+        total += t[i].cta_count;
+    }
+    return total;
+}
+
+cudaError_t launch_rowreduce(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
+    rowreduce_kernel<<<ctas, RW * 32, 0, st>>>(dev, p);
+    return cudaGetLastError();
+}
+
 
 uint32_t prepare_hist256(ExecTask *t, int n, ExecParams &p) {
     uint32_t total = 0;

@@ -159,6 +159,7 @@ struct BuiltinDef {
     uint32_t (*prepare)(ExecTask *, int, ExecParams &);
     cudaError_t (*launch)(const ExecTask *, uint32_t, const ExecParams &, cudaStream_t);
     bool reduce_zero = true;  // reduce partials must start at the identity (else the kernel writes every cell)
+    bool any_reduce_op = false;  // the reduce argument may use any of + * min max
 };
 
 const BuiltinDef kBuiltins[] = {
@@ -167,6 +168,8 @@ const BuiltinDef kBuiltins[] = {
      k::prepare_stencil1d, k::launch_stencil1d},
     {LT_K_JACOBI2D, "global [i, j] => read A0[i-1:i+1, j-1:j+1], write A1[i, j]", 2, {LT_F32, LT_F32}, {2, 2},
      k::prepare_jacobi2d, k::launch_jacobi2d},
+    {LT_K_JACOBI3D, "global [k, i, j] => read A0[k-1:k+1, i-1:i+1, j-1:j+1], write A1[k, i, j]", 2,
+     {LT_F32, LT_F32}, {3, 3}, k::prepare_jacobi3d, k::launch_jacobi3d},
     {LT_K_HIST256, "global i => read A0[i], reduce(+) A1[:]", 2, {LT_U8, LT_U32}, {1, 1}, k::prepare_hist256,
      k::launch_hist256},
     {LT_K_DIFFUSION2D, "global [i, j] => read A0[i-1:i+1, j-1:j+1], read A1[i, j], write A2[i, j]", 3,
@@ -176,6 +179,8 @@ const BuiltinDef kBuiltins[] = {
      "reduce(+) A4[i-1:i+1, j-1:j+1]",
      5, {LT_F32, LT_F32, LT_F32, LT_F32, LT_F32}, {2, 2, 2, 2, 2}, k::prepare_diffusion_adj, k::launch_diffusion_adj,
      false},
+    {LT_K_ROWREDUCE, "global [i, j] => read A0[i, j], reduce(+) A1[i]", 2, {LT_F32, LT_F32}, {2, 1},
+     k::prepare_rowreduce, k::launch_rowreduce, false, true},
     {LT_K_GEMM_BF16, "global [i, j] => read A0[i, :], read A1[:, j], write A2[i, j]", 3, {LT_BF16, LT_BF16, LT_F32},
      {2, 2, 2}, k::prepare_gemm_bf16, k::launch_gemm_bf16},
 };
@@ -1336,7 +1341,7 @@ lt_status lt_kernel_register(lt_ctx *c, int32_t builtin, const char *annotation,
             case MODE_READ: ok = us.mode == MODE_READ || us.mode == MODE_READWRITE; break;
             case MODE_WRITE: ok = us.mode == MODE_WRITE || us.mode == MODE_READWRITE; break;
             case MODE_READWRITE: ok = us.mode == MODE_READWRITE; break;
-            default: ok = us.mode == MODE_REDUCE && us.op == cs.op;
+            default: ok = us.mode == MODE_REDUCE && (us.op == cs.op || def->any_reduce_op);
         }
         if (!ok)
             return fail(LT_ERR_INVALID_ARG, "access mode of '" + us.array + "' does not allow what the kernel does");
@@ -1481,6 +1486,9 @@ lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const 
     ep.block[1] = (int64_t)(block.y ? block.y : 1);
     ep.block[2] = (int64_t)(block.z ? block.z : 1);
     ep.err = c->err_word;
+    for (size_t p = 0; p < parr.size(); ++p)
+        if (k->stmt_of_param[p] >= 0 && k->ann.stmts[(size_t)k->stmt_of_param[p]].mode == MODE_REDUCE)
+            ep.red_op = k->ann.stmts[(size_t)k->stmt_of_param[p]].op;
     // one launch of lookahead: the previous launch is enqueued now, knowing
     // which chunks this one overwrites without reading them
     if (c->pending) {

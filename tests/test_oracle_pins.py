@@ -340,3 +340,19 @@ def test_region_bruteforce_clips_to_domain():
                                         lambda i, j: [(i + a, j + b) for a in (-1, 0, 1) for b in (-1, 0, 1)],
                                         (4, 10))
     assert r == [(0, 3), (0, 4)]
+
+
+# ------------------------------------------------------------------ row reduction (reduce modes)
+def test_rowreduce_closed_forms_and_brute_force():
+    c = np.full((3, 7), 1.5)
+    assert np.allclose(oracle.rowreduce(c, "+"), 10.5)
+    assert np.allclose(oracle.rowreduce(c, "*"), 1.5 ** 7)
+    assert np.array_equal(oracle.rowreduce(c, "min"), [1.5] * 3)
+    a = np.array([[3.0, -1.0, 4.0, 1.0], [-5.0, 9.0, 2.0, -6.0]])
+    assert list(oracle.rowreduce(a, "+")) == [7.0, 0.0]
+    assert list(oracle.rowreduce(a, "*")) == [-12.0, 540.0]
+    assert list(oracle.rowreduce(a, "min")) == [-1.0, -6.0]
+    assert list(oracle.rowreduce(a, "max")) == [4.0, 9.0]
+    one = np.array([[2.5], [-0.5]])
+    for op in ("+", "*", "min", "max"):
+        assert list(oracle.rowreduce(one, op)) == [2.5, -0.5]
