@@ -221,7 +221,8 @@ typedef enum {
     LT_K_HIST256 = 5,        /* reduce(+) H[:] of one count per u8 element */
     LT_K_DIFFUSION2D = 6,    /* u1 = u + K*(Lu), f32 */
     LT_K_DIFFUSION2D_ADJ = 7, /* adjoint step: reduce(+) of the transposed stencil */
-    LT_K_ROWREDUCE = 8        /* "read A[i, j], reduce(f) S[i]" (Sec. 2.3), f32, f in + * min max */
+    LT_K_ROWREDUCE = 8,       /* "read A[i, j], reduce(f) S[i]" (Sec. 2.3), f32, f in + * min max */
+    LT_K_JACOBI2D_MULTI = 9   /* k Jacobi iterations per launch (value parameter k, 1..16), reads U[i-k:i+k, j-k:j+k] */
 } lt_builtin;
 
 typedef struct {

@@ -35,7 +35,7 @@ LT_FLAG_TIMING, LT_FLAG_DRYRUN, LT_FLAG_FIXED_SWEEP = 1, 2, 4
 # built-ins
 LT_K_PLAN_ONLY = 0
 LT_K_STENCIL1D, LT_K_JACOBI2D, LT_K_JACOBI3D, LT_K_GEMM_BF16, LT_K_HIST256 = 1, 2, 3, 4, 5
-LT_K_DIFFUSION2D, LT_K_DIFFUSION2D_ADJ, LT_K_ROWREDUCE = 6, 7, 8
+LT_K_DIFFUSION2D, LT_K_DIFFUSION2D_ADJ, LT_K_ROWREDUCE, LT_K_JACOBI2D_MULTI = 6, 7, 8, 9
 
 
 class lt_dist(C.Structure):

@@ -152,6 +152,8 @@ cudaError_t reduce_pieces(const ReducePiece *dev, const DView *srcs, int n, uint
 uint32_t prepare_stencil1d(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_stencil1d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p);
+uint32_t prepare_jacobi2d_multi(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_jacobi2d_multi(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_jacobi3d(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_jacobi3d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_diffusion(ExecTask *t, int n, ExecParams &p);

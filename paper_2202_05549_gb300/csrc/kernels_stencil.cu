@@ -11,6 +11,8 @@
 // bit-identical, and equal to the CPU definition.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "stencil_body.cuh"
 
@@ -137,6 +139,112 @@ cudaError_t launch_jacobi2d(const ExecTask *dev, uint32_t ctas, const ExecParams
         jacobi2d_vec_kernel<<<ctas, JWARPS * 32, 0, st>>>(dev, p);
     else
         jacobi2d_scalar_kernel<<<ctas, 256, 0, st>>>(dev, p);
+    return cudaGetLastError();
+}
+
+}  // namespace k
+}  // namespace lt
+
+// ------------------------------------------------------------------ k steps per launch
+// Temporal blocking: "global [i, j] => read U[i-k:i+k, j-k:j+k], write V[i, j]"
+// computes k Jacobi iterations in one launch.  Each CTA loads its 32 x 128
+// tile plus a k-cell ring into shared memory and updates a box that shrinks
+// by one cell per step (step s is valid on tile +/- (k-s)), so every value it
+// keeps equals the one the sequential iterations compute.  Cells outside the
+// domain stay 0 (the zero ghosts).
+namespace lt {
+namespace {
+
+constexpr int MTY = 32, MTX = 128, MT = 256;
+
+__global__ void __launch_bounds__(MT) jacobi2d_multi_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    extern __shared__ float msm[];
+    const int ti = find_task(tasks, p.ntasks, blockIdx.x);
+    const ExecTask &t = tasks[ti];
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    const int k = (int)p.i[0];
+    const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
+    const int64_t x1 = min(t.t_hi[0], NX - 1), y1 = min(t.t_hi[1], NY - 1);
+    if (x1 < x0 || y1 < y0) return;
+    const int64_t gx = (x1 - x0 + MTX) / MTX;
+    const int64_t local = blockIdx.x - t.cta_begin;
+    const int64_t ty0 = y0 + (local / gx) * MTY, tx0 = x0 + (local % gx) * MTX;
+    const int H = MTY + 2 * k, W = MTX + 2 * k;
+    float *A = msm, *B = msm + H * W;
+    // readable region: superblock +/- k, clipped to the domain
+    const int64_t rr0 = max(y0 - k, (int64_t)0), rr1 = min(y1 + k, NY - 1);
+    const int64_t rc0 = max(x0 - k, (int64_t)0), rc1 = min(x1 + k, NX - 1);
+    // local index ranges of in-domain cells (the zero ghosts lie outside them)
+    const int dr0 = (int)max((int64_t)0, -(ty0 - k)), dr1 = (int)min((int64_t)H - 1, NY - 1 - (ty0 - k));
+    const int dc0 = (int)max((int64_t)0, -(tx0 - k)), dc1 = (int)min((int64_t)W - 1, NX - 1 - (tx0 - k));
+    const DView U = t.v[0], V = t.v[1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int li = warp; li < H; li += MT / 32) {
+        const int64_t i = ty0 - k + li;
+        const bool rok = i >= rr0 && i <= rr1;
+        const float *urow = (const float *)U.base + i * U.s[0];
+        for (int lj = lane; lj < W; lj += 32) {
+            const int64_t j = tx0 - k + lj;
+            A[li * W + lj] = (rok && j >= rc0 && j <= rc1) ? urow[j * U.s[1]] : 0.f;
+            B[li * W + lj] = 0.f;
+        }
+    }
+    __syncthreads();
+    for (int s = 1; s <= k; ++s) {
+        // step s is valid on the tile +/- (k - s): local rows/cols [s, H-1-s], in the domain
+        const int r0 = max(s, dr0), r1 = min(H - 1 - s, dr1);
+        const int c0 = max(s, dc0), c1 = min(W - 1 - s, dc1);
+        for (int li = r0 + warp; li <= r1; li += MT / 32) {
+            const float *a = A + li * W;
+            float *b = B + li * W;
+            for (int lj = c0 + lane; lj <= c1; lj += 32) b[lj] = j5(a[lj], a[lj - W], a[lj + W], a[lj - 1], a[lj + 1]);
+        }
+        __syncthreads();
+        float *tmp = A;
+        A = B;
+        B = tmp;
+    }
+    for (int r = warp; r < MTY; r += MT / 32) {
+        const int64_t i = ty0 + r;
+        if (i > y1) break;
+        float *vrow = (float *)V.base + i * V.s[0];
+        const float *a = A + (k + r) * W + k;
+        for (int c = lane; c < MTX; c += 32) {
+            const int64_t j = tx0 + c;
+            if (j <= x1) vrow[j * V.s[1]] = a[c];
+        }
+    }
+}
+
+}  // namespace
+
+namespace k {
+
+uint32_t prepare_jacobi2d_multi(ExecTask *t, int n, ExecParams &p) {
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    if (p.i[0] < 1 || p.i[0] > 16) return 0xFFFFFFFFu;
+    uint32_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        int64_t w = std::min(t[i].t_hi[0], NX - 1) - t[i].t_lo[0] + 1;
+        int64_t h = std::min(t[i].t_hi[1], NY - 1) - t[i].t_lo[1] + 1;
+        t[i].cta_begin = total;
+        t[i].cta_count = (w > 0 && h > 0) ? (uint32_t)(((w + MTX - 1) / MTX) * ((h + MTY - 1) / MTY)) : 0;
+        total += t[i].cta_count;
+    }
+    return total;
+}
+
+cudaError_t launch_jacobi2d_multi(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
+    const int k = (int)p.i[0];
+    const size_t smem = 2 * (size_t)(MTY + 2 * k) * (MTX + 2 * k) * sizeof(float);
+    static size_t set = 0;
+    if (smem > 48 * 1024 && smem > set) {
+        cudaError_t e = cudaFuncSetAttribute(jacobi2d_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        set = smem;
+    }
+    jacobi2d_multi_kernel<<<ctas, MT, smem, st>>>(dev, p);
     return cudaGetLastError();
 }
 

@@ -179,11 +179,23 @@ const BuiltinDef kBuiltins[] = {
      "reduce(+) A4[i-1:i+1, j-1:j+1]",
      5, {LT_F32, LT_F32, LT_F32, LT_F32, LT_F32}, {2, 2, 2, 2, 2}, k::prepare_diffusion_adj, k::launch_diffusion_adj,
      false},
+    {LT_K_JACOBI2D_MULTI, "global [i, j] => read A0[i-{K}:i+{K}, j-{K}:j+{K}], write A1[i, j]", 2,
+     {LT_F32, LT_F32}, {2, 2}, k::prepare_jacobi2d_multi, k::launch_jacobi2d_multi},
     {LT_K_ROWREDUCE, "global [i, j] => read A0[i, j], reduce(+) A1[i]", 2, {LT_F32, LT_F32}, {2, 1},
      k::prepare_rowreduce, k::launch_rowreduce, false, true},
     {LT_K_GEMM_BF16, "global [i, j] => read A0[i, :], read A1[:, j], write A2[i, j]", 3, {LT_BF16, LT_BF16, LT_F32},
      {2, 2, 2}, k::prepare_gemm_bf16, k::launch_gemm_bf16},
 };
+
+// Canonical annotation of a built-in; "{K}" stands for the launch's first
+// integer value parameter (the step count of the multi-step stencil).
+std::string canon_text(const BuiltinDef *d, int64_t kval) {
+    std::string s = d->canon ? d->canon : "";
+    const std::string key = "{K}";
+    for (size_t pos = s.find(key); pos != std::string::npos; pos = s.find(key))
+        s.replace(pos, key.size(), std::to_string(kval));
+    return s;
+}
 
 const BuiltinDef *find_builtin(int id) {
     for (const auto &b : kBuiltins)
@@ -1287,7 +1299,7 @@ lt_status lt_kernel_register(lt_ctx *c, int32_t builtin, const char *annotation,
     std::string err;
     if (!parse_annotation(annotation, &k->ann, &err)) return fail(LT_ERR_PARSE, "annotation: " + err);
     bool plan_only = def->canon == nullptr;
-    if (!plan_only && !parse_annotation(def->canon, &k->canon, &err))
+    if (!plan_only && !parse_annotation(canon_text(def, 1), &k->canon, &err))
         return fail(LT_ERR_PARSE, "internal canonical: " + err);
     int slot = 0;
     for (int p = 0; p < nparams; ++p) {
@@ -1404,13 +1416,30 @@ static lt_status prepare_plan(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 blo
     int64_t B[3];
     for (int d = 0; d < 3; ++d) B[d] = (int64_t)(b3[d] ? b3[d] : 1);
     std::vector<int64_t> vlo, vhi;
+    Annotation canon_launch;
+    const Annotation *canon = &k->canon;
+    if (k->def->canon && std::string(k->def->canon).find("{K}") != std::string::npos) {
+        int64_t kval = 0;
+        bool found = false;
+        for (int p = 0; p < nargs && !found; ++p)
+            if (!k->params[(size_t)p].is_array && k->params[(size_t)p].dtype != LT_F32) {
+                kval = args[p].i;
+                found = true;
+            }
+        if (!found || kval < 1 || kval > 16)
+            return fail(LT_ERR_INVALID_ARG, "this built-in needs an integer step count between 1 and 16");
+        std::string err2;
+        if (!parse_annotation(canon_text(k->def, kval), &canon_launch, &err2))
+            return fail(LT_ERR_PARSE, "internal canonical: " + err2);
+        canon = &canon_launch;
+    }
     for (const auto &sb : plan->sbs) {
         if (!k->def->canon) break;
-        var_ranges(k->canon, sb.threads, B, &vlo, &vhi);
+        var_ranges(*canon, sb.threads, B, &vlo, &vhi);
         for (const auto &ap : sb.args) {
             if (ap.kind == ARG_VALUE) continue;
             int sl = k->slot_of_param[(size_t)ap.param];
-            const Stmt &cs = k->canon.stmts[(size_t)k->canon_stmt[(size_t)sl]];
+            const Stmt &cs = canon->stmts[(size_t)k->canon_stmt[(size_t)sl]];
             Box need = eval_region(cs, vlo, vhi, (*parr)[(size_t)ap.param]->g.shape);
             if (!need.empty() && !ap.region.contains(need))
                 return fail(LT_ERR_INVALID_ARG, "the annotation's region for '" +

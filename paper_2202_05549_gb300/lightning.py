@@ -19,6 +19,7 @@ STENCIL1D, JACOBI2D, JACOBI3D, GEMM_BF16, HIST256 = (L.LT_K_STENCIL1D, L.LT_K_JA
 DIFFUSION2D, DIFFUSION2D_ADJ = L.LT_K_DIFFUSION2D, L.LT_K_DIFFUSION2D_ADJ
 PLAN_ONLY = L.LT_K_PLAN_ONLY
 ROWREDUCE = L.LT_K_ROWREDUCE
+JACOBI2D_MULTI = L.LT_K_JACOBI2D_MULTI
 
 _NP = {F32: np.float32, BF16: np.uint16, U8: np.uint8, U32: np.uint32}
 

@@ -174,3 +174,49 @@ def test_out_of_core_lightcone_samples_small():
     si_, sj_ = si.sample_cells(2204, NY, NX, 512, seams_every=band)
     want = oracle.jacobi2d_lightcone(NY, NX, si.SEED_JACOBI_OOC, 0, iters, si_, sj_)
     assert np.array_equal(got[si_, sj_], want)
+
+
+MANN = "global [i, j] => read U[i-{k}:i+{k}, j-{k}:j+{k}], write V[i, j]"
+
+
+@pytest.mark.parametrize("k", [1, 2, 5])
+@pytest.mark.parametrize("dist_name", ["block", "rows_halo_k", "tiles_halo_k", "rows_halo_1_pack"])
+def test_multi_step_jacobi_bit_exact(k, dist_name):
+    ny, nx, launches = 301, 517, 3
+    u0 = si.uniform_field(si.SEED_JACOBI_INCORE, 7, ny, nx)
+    want = oracle.jacobi2d(u0, k * launches)
+    dist, sb = {"block": (lt.Dist.block(), (0, 0)),
+                "rows_halo_k": (lt.Dist.rows(64, halo=k), (nx, 64)),
+                "tiles_halo_k": (lt.Dist.tiles((64, 128), halo=(k, k)), (128, 64)),
+                "rows_halo_1_pack": (lt.Dist.rows(64, halo=1), (nx, 64))}[dist_name]
+    with lt.Context() as ctx:
+        U = ctx.array(lt.F32, (ny, nx), dist)
+        V = ctx.array(lt.F32, (ny, nx), dist)
+        U.write(u0)
+        km = ctx.kernel(lt.JACOBI2D_MULTI, MANN.format(k=k), [("U", lt.F32), ("V", lt.F32), ("k", lt.U32, False)])
+        for _ in range(launches):
+            km.launch(grid=(nx, ny), block=(128, 4), superblock=sb, args=[U, V, k])
+            U, V = V, U
+        ctx.synchronize()
+        got = U.read()
+    assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
+
+
+def test_multi_step_out_of_core_spill_bit_exact():
+    ny, nx, band, k, launches = 1024, 2048, 64, 4, 3
+    cb = (band + 2 * k) * nx * 4
+    u0 = si.uniform_field(si.SEED_JACOBI_OOC, 0, ny, nx)
+    want = oracle.jacobi2d(u0, k * launches)
+    with lt.Context(hbm_budget=6 * cb + (8 << 20), host_pool=30 * cb) as ctx:
+        U = ctx.array(lt.F32, (ny, nx), lt.Dist.rows(band, halo=k))
+        V = ctx.array(lt.F32, (ny, nx), lt.Dist.rows(band, halo=k))
+        U.fill(L.LT_INIT_UNIFORM, seed=si.SEED_JACOBI_OOC, stream=0)
+        km = ctx.kernel(lt.JACOBI2D_MULTI, MANN.format(k=k), [("U", lt.F32), ("V", lt.F32), ("k", lt.U32, False)])
+        for _ in range(launches):
+            km.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V, k])
+            U, V = V, U
+        ctx.synchronize()
+        s = ctx.stats()
+        got = U.read()
+    assert s["evictions"] > 0 and s["fetches"] > 0
+    assert np.array_equal(got, want)

@@ -360,3 +360,17 @@ def test_batch_in_dry_run_is_the_plain_sequence():
         # iteration t+1 depends on iteration t (ping-pong through U and V)
         for a, b in zip(ex[:4], ex[1:5]):
             assert a["id"] in b["deps"]
+
+
+def test_multi_step_annotation_must_cover_k_rings():
+    with dry() as ctx:
+        U = ctx.array(lt.F32, (64, 64), lt.Dist.rows(16, halo=3))
+        V = ctx.array(lt.F32, (64, 64), lt.Dist.rows(16, halo=3))
+        km = ctx.kernel(lt.JACOBI2D_MULTI, "global [i, j] => read U[i-2:i+2, j-2:j+2], write V[i, j]",
+                        [("U", lt.F32), ("V", lt.F32), ("k", lt.U32, False)])
+        km.launch(grid=(64, 64), block=(64, 4), superblock=(64, 16), args=[U, V, 2])   # k = 2: covered
+        with pytest.raises(lt.LightningError) as e:
+            km.launch(grid=(64, 64), block=(64, 4), superblock=(64, 16), args=[U, V, 3])  # k = 3: not covered
+        assert e.value.code == L.LT_ERR_INVALID_ARG
+        with pytest.raises(lt.LightningError):
+            km.launch(grid=(64, 64), block=(64, 4), superblock=(64, 16), args=[U, V, 0])   # k out of range
