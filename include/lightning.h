@@ -32,8 +32,11 @@
  *     released by the matching *_destroy call; destroying a context releases
  *     everything created in it.
  *   - A context is not thread-safe: calls on one context must not overlap.
- *   - After an LT_ERR_CUDA or LT_ERR_TIMEOUT the context is poisoned: every
- *     further call except lt_ctx_destroy returns LT_ERR_BUSY.
+ *   - After an LT_ERR_CUDA the context is poisoned: every further call
+ *     except lt_ctx_destroy returns LT_ERR_BUSY.  LT_ERR_TIMEOUT (a bounded
+ *     device-side wait expired; the kernel returned early) leaves the context
+ *     usable; the results of the work since the previous synchronize are
+ *     undefined.
  */
 #ifndef LIGHTNING_H
 #define LIGHTNING_H
@@ -288,6 +291,10 @@ typedef struct {
 #define LT_BATCH_PLAIN 1    /* issue the launches one by one */
 #define LT_BATCH_NO_GRAPH 2 /* fused kernel, launched directly (no graph capture) */
 #define LT_BATCH_RETUNE 4   /* run the autotuner again for this batch shape */
+/* Test hook: omit the first iteration's work items of every Jacobi launch
+ * with repeat >= 2, so the later items' bounded waits (2 s) expire and
+ * lt_synchronize reports LT_ERR_TIMEOUT without any fault.  Not cached. */
+#define LT_BATCH_TEST_STALL 256
 
 lt_status lt_launch_batch(lt_ctx *ctx, const lt_launch_desc *descs, int32_t n, int32_t flags);
 

@@ -83,7 +83,7 @@ class lt_launch_desc(C.Structure):
                 ("args", C.POINTER(lt_arg)), ("nargs", C.c_int32), ("repeat", C.c_int32)]
 
 
-LT_BATCH_PLAIN, LT_BATCH_NO_GRAPH, LT_BATCH_RETUNE = 1, 2, 4
+LT_BATCH_PLAIN, LT_BATCH_NO_GRAPH, LT_BATCH_RETUNE, LT_BATCH_TEST_STALL = 1, 2, 4, 256
 
 
 _vp = C.c_void_p

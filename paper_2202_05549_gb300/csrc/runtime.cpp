@@ -649,8 +649,9 @@ lt_status sync_all(lt_ctx *c) {
     CK(c, cudaMemcpy(&e, c->err_word, 4, cudaMemcpyDeviceToHost));
     if (e) {
         CK(c, cudaMemset(c->err_word, 0, 4));
-        return fail(e >= 0x6700 && e < 0x6800 ? LT_ERR_TIMEOUT : LT_ERR_DEVICE_CHECK,
-                    "a kernel recorded an error (code " + std::to_string(e) + "; 0x67xx = a bounded wait expired)");
+        return fail(e >= 0x6700 && e < 0x6900 ? LT_ERR_TIMEOUT : LT_ERR_DEVICE_CHECK,
+                    "a kernel recorded an error (code " + std::to_string(e) +
+                        "; 0x67xx / 0x68xx = a bounded wait expired and the kernel returned)");
     }
     return collect_timing(c);
 }
@@ -2068,7 +2069,7 @@ struct BatchShape {
 // `iters_cap` > 0 limits every instance to that many iterations (tuning).
 static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int hs, int iters_cap,
                          std::vector<BatchJacobi> *jac, std::vector<BatchHist> *hist, std::vector<BatchItem> *items,
-                         size_t *ncounters) {
+                         size_t *ncounters, bool stall = false) {
     jac->clear();
     hist->clear();
     items->clear();
@@ -2105,6 +2106,7 @@ static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int hs, int it
         for (size_t q = 0; q < bs.jac.size(); ++q) {
             int r = iters_cap > 0 ? std::min(iters_cap, bs.jac[q].repeat) : bs.jac[q].repeat;
             if (t >= r) continue;
+            if (stall && t == 0 && r >= 2) continue;  // test hook: iteration 1 then waits forever (bounded)
             const BatchJacobi &b = (*jac)[q];
             for (uint32_t k = 0; k < b.tiles; ++k)
                 items->push_back({(uint32_t)q, (uint32_t)t, k * (uint32_t)th,
@@ -2243,7 +2245,9 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
                                                   (uint64_t)J.repeat});
     key.push_back(~0ull);
     for (auto &H : bs.hist) key.insert(key.end(), {(uint64_t)H.x->id, H.x->cs[0].off, (uint64_t)H.h->id, H.h->cs[0].off});
-    bool use_graph = !(flags & LT_BATCH_NO_GRAPH);
+    const bool stall = (flags & LT_BATCH_TEST_STALL) != 0;
+    if (stall) key.push_back(0x57A11ull);  // never matches a real batch
+    bool use_graph = !(flags & LT_BATCH_NO_GRAPH) && !stall;
     std::pair<int64_t, int64_t> shape_key = {(int64_t)bs.jac.size(), (int64_t)bs.hist.size()};
     if (!c->batch || c->batch->key != key || (flags & LT_BATCH_RETUNE) || (use_graph && !c->batch->exec)) {
         if (c->batch) {
@@ -2260,6 +2264,7 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
         size_t ncnt = 0;
         // autotuner: time every candidate on the first iteration of the batch
         // (it writes only V and H, which the real run overwrites)
+        if (stall && !c->tuned.count(shape_key)) c->tuned[shape_key] = {32, 256 << 10};
         if (!c->tuned.count(shape_key) || (flags & LT_BATCH_RETUNE)) {
             if ((st = sync_all(c))) {
                 unpin();
@@ -2308,7 +2313,7 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
         auto tp = c->tuned[shape_key];
         auto bc = std::make_unique<BatchCache>();
         bc->key = key;
-        batch_tables(c, bs, tp.first, tp.second, 0, &jac, &hist, &items, &ncnt);
+        batch_tables(c, bs, tp.first, tp.second, 0, &jac, &hist, &items, &ncnt, stall);
         if ((st = batch_upload(c, bc.get(), jac, hist, items, ncnt))) {
             unpin();
             return st;

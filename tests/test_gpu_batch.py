@@ -98,3 +98,24 @@ def test_histogram_plain_launch_reduce_partials():
             kh.launch(grid=(n,), block=(256,), superblock=sb, args=[X, H])
             ctx.synchronize()
             assert np.array_equal(H.read(), oracle.hist256(x))
+
+
+def test_bounded_wait_expires_reports_timeout_and_context_survives():
+    # failure detection without a fault: the queue's first iteration is left
+    # out, so every later item's bounded dependency wait runs out (~2 s); the
+    # kernel records the error and returns, the host reads LT_ERR_TIMEOUT,
+    # and the same context then runs a normal batch correctly
+    with lt.Context() as ctx:
+        kj = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        u0 = si.uniform_field(2206, 9, 96, 160)
+        U = ctx.array(lt.F32, (96, 160))
+        V = ctx.array(lt.F32, (96, 160))
+        U.write(u0)
+        ctx.launch_batch([(kj, (160, 96), (128, 4), (0, 0), [U, V], 2)], L.LT_BATCH_TEST_STALL)
+        with pytest.raises(lt.LightningError) as e:
+            ctx.synchronize()
+        assert e.value.code == L.LT_ERR_TIMEOUT
+        U.write(u0)
+        ctx.launch_batch([(kj, (160, 96), (128, 4), (0, 0), [U, V], 2)])
+        ctx.synchronize()
+        assert np.array_equal(U.read(), oracle.jacobi2d(u0, 2))
