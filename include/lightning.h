@@ -60,6 +60,7 @@ typedef int32_t lt_status;
 #define LT_ERR_BUSY (-7)         /* context poisoned by an earlier error */
 #define LT_ERR_UNSUPPORTED (-8)  /* valid request this build does not do */
 #define LT_ERR_DEVICE_CHECK (-9) /* a kernel recorded a bounds violation */
+#define LT_ERR_COMPILE (-10)      /* runtime compilation of a user kernel failed */
 
 /* ---- element types (Sec. 2.2: arrays hold a primitive type) ------------- */
 typedef enum {
@@ -225,7 +226,8 @@ typedef enum {
     LT_K_DIFFUSION2D = 6,    /* u1 = u + K*(Lu), f32 */
     LT_K_DIFFUSION2D_ADJ = 7, /* adjoint step: reduce(+) of the transposed stencil */
     LT_K_ROWREDUCE = 8,       /* "read A[i, j], reduce(f) S[i]" (Sec. 2.3), f32, f in + * min max */
-    LT_K_JACOBI2D_MULTI = 9   /* k Jacobi iterations per launch (value parameter k, 1..16), reads U[i-k:i+k, j-k:j+k] */
+    LT_K_JACOBI2D_MULTI = 9,  /* k Jacobi iterations per launch (value parameter k, 1..16), reads U[i-k:i+k, j-k:j+k] */
+    LT_K_USER = 100           /* (kernels from lt_kernel_register_source) */
 } lt_builtin;
 
 typedef struct {
@@ -237,6 +239,25 @@ typedef struct {
 lt_status lt_kernel_register(lt_ctx *ctx, int32_t builtin, const char *annotation, const lt_param *params,
                              int32_t nparams, lt_kernel **out);
 lt_status lt_kernel_destroy(lt_ctx *ctx, lt_kernel *k);
+
+/* Register a kernel from CUDA source, compiled at run time (Sec. 3.5,
+ * Listings 2-3).  `source` defines
+ *     __device__ void <name>(dim3 virtBlockIdx, <one parameter per params[i]>)
+ * value parameters arrive as int64_t (integer dtypes) or double (LT_F32);
+ * array parameters as lightning::Vector<T> / Matrix<T> / Tensor<T> for 1, 2
+ * or 3 indices in the annotation, indexed with global indices (v[i],
+ * m(i, j) or m[i][j], t(k, i, j)); T is float, unsigned short (bf16 bits),
+ * unsigned char or unsigned int.  Use virtBlockIdx instead of blockIdx;
+ * blockDim and threadIdx are those of the launch.  The library generates the
+ * wrapper kernel that maps physical to virtual blocks and builds the views
+ * (the chunk offset subtracted once), compiles both with NVRTC for sm_103a
+ * (IEEE arithmetic, no FMA contraction) and loads them.  The annotation is
+ * trusted: the kernel must not touch elements outside it.  At most 5 array,
+ * 4 integer and 4 float parameters.  Errors: LT_ERR_PARSE, LT_ERR_COMPILE
+ * (the compiler log is in lt_last_error()), LT_ERR_UNSUPPORTED (no NVRTC).
+ * In LT_FLAG_DRYRUN contexts the source is compiled but not loaded. */
+lt_status lt_kernel_register_source(lt_ctx *ctx, const char *source, const char *name, const char *annotation,
+                                    const lt_param *params, int32_t nparams, lt_kernel **out);
 
 /* ---- launches (Sec. 2.1, Sec. 2.4; kernel.launch of Sec. 3.6) ------------
  * grid: number of threads along x, y, z (like launch(n, 16, ...) in the

@@ -21,6 +21,7 @@ LT_ERR_TIMEOUT = -6
 LT_ERR_BUSY = -7
 LT_ERR_UNSUPPORTED = -8
 LT_ERR_DEVICE_CHECK = -9
+LT_ERR_COMPILE = -10
 
 # dtypes
 LT_F32, LT_BF16, LT_U8, LT_U32 = 0, 1, 2, 3
@@ -34,6 +35,7 @@ LT_FLAG_TIMING, LT_FLAG_DRYRUN, LT_FLAG_FIXED_SWEEP = 1, 2, 4
  LT_INIT_U8) = range(6)
 # built-ins
 LT_K_PLAN_ONLY = 0
+LT_K_USER = 100
 LT_K_STENCIL1D, LT_K_JACOBI2D, LT_K_JACOBI3D, LT_K_GEMM_BF16, LT_K_HIST256 = 1, 2, 3, 4, 5
 LT_K_DIFFUSION2D, LT_K_DIFFUSION2D_ADJ, LT_K_ROWREDUCE, LT_K_JACOBI2D_MULTI = 6, 7, 8, 9
 
@@ -106,6 +108,8 @@ SIGNATURES = {
                                   C.POINTER(C.c_int32)]),
     "lt_kernel_register": (_st, [_vp, C.c_int32, C.c_char_p, C.POINTER(lt_param), C.c_int32, C.POINTER(_vp)]),
     "lt_kernel_destroy": (_st, [_vp, _vp]),
+    "lt_kernel_register_source": (_st, [_vp, C.c_char_p, C.c_char_p, C.c_char_p, C.POINTER(lt_param), C.c_int32,
+                                        C.POINTER(_vp)]),
     "lt_launch": (_st, [_vp, _vp, lt_dim3, lt_dim3, C.POINTER(lt_workdist), C.POINTER(lt_arg), C.c_int32]),
     "lt_synchronize": (_st, [_vp]),
     "lt_launch_batch": (_st, [_vp, C.c_void_p, C.c_int32, C.c_int32]),

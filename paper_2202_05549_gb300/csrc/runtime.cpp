@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cctype>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -29,6 +30,7 @@
 #include "core.hpp"
 #include "kernels.cuh"
 #include "lightning.h"
+#include "userkernel.hpp"
 
 using namespace lt;
 
@@ -213,6 +215,9 @@ struct lt_array {
 
 struct lt_kernel {
     const BuiltinDef *def = nullptr;
+    std::unique_ptr<BuiltinDef> own_def;     // user kernels: their own signature
+    cudaLibrary_t ulib = nullptr;            // user kernels: loaded NVRTC cubin
+    cudaKernel_t ufn = nullptr;
     Annotation ann, canon;
     std::vector<lt_param> params;
     std::vector<std::string> names;
@@ -1364,6 +1369,79 @@ lt_status lt_kernel_register(lt_ctx *c, int32_t builtin, const char *annotation,
     return LT_OK;
 }
 
+lt_status lt_kernel_register_source(lt_ctx *c, const char *source, const char *name, const char *annotation,
+                                    const lt_param *params, int32_t nparams, lt_kernel **out) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    if (!source || !name || !annotation || (!params && nparams) || !out || nparams < 0 || nparams > 13)
+        return fail(LT_ERR_INVALID_ARG, "bad source-kernel registration arguments");
+    for (const char *q = name; *q; ++q)
+        if (!(std::isalnum((unsigned char)*q) || *q == '_')) return fail(LT_ERR_INVALID_ARG, "bad kernel name");
+    auto k = std::make_unique<lt_kernel>();
+    std::string err;
+    if (!parse_annotation(annotation, &k->ann, &err)) return fail(LT_ERR_PARSE, "annotation: " + err);
+    auto def = std::make_unique<BuiltinDef>();
+    def->id = LT_K_USER;
+    def->canon = nullptr;
+    def->narr = 0;
+    def->prepare = k::prepare_user;
+    def->launch = nullptr;
+    def->reduce_zero = true;
+    std::vector<UserParam> ups;
+    int nf = 0, ni = 0;
+    for (int p = 0; p < nparams; ++p) {
+        if (!params[p].name) return fail(LT_ERR_INVALID_ARG, "parameter without a name");
+        k->params.push_back(params[p]);
+        k->names.push_back(params[p].name);
+        UserParam up;
+        up.is_array = params[p].is_array != 0;
+        up.dtype = params[p].dtype;
+        if (!up.is_array) {
+            if (params[p].dtype == LT_F32 ? ++nf > 4 : ++ni > 4)
+                return fail(LT_ERR_INVALID_ARG, "at most 4 integer and 4 float value parameters");
+            k->stmt_of_param.push_back(-1);
+            k->slot_of_param.push_back(-1);
+            ups.push_back(up);
+            continue;
+        }
+        int si = -1;
+        for (size_t s2 = 0; s2 < k->ann.stmts.size(); ++s2)
+            if (k->ann.stmts[s2].array == params[p].name) si = (int)s2;
+        if (si < 0)
+            return fail(LT_ERR_INVALID_ARG, std::string("array parameter '") + params[p].name +
+                                                "' is not named in the annotation");
+        if (def->narr >= LT_MAX_ARRAYS) return fail(LT_ERR_INVALID_ARG, "at most 5 array parameters");
+        if (dtype_size(params[p].dtype) == 0) return fail(LT_ERR_INVALID_ARG, "unknown dtype");
+        up.rank = (int)k->ann.stmts[(size_t)si].idx.size();
+        def->dtype[def->narr] = params[p].dtype;
+        def->nd[def->narr] = up.rank;
+        k->stmt_of_param.push_back(si);
+        k->slot_of_param.push_back(def->narr);
+        def->narr++;
+        ups.push_back(up);
+    }
+    for (const auto &s2 : k->ann.stmts) {
+        bool found = false;
+        for (const auto &nm : k->names)
+            if (nm == s2.array) found = true;
+        if (!found) return fail(LT_ERR_INVALID_ARG, "annotation names unknown array '" + s2.array + "'");
+    }
+    std::string src = user_wrapper_source(source, name, ups);
+    std::vector<char> cubin;
+    std::string log;
+    st = compile_user_kernel(src, &cubin, &log);
+    if (st) return fail(st, "runtime compilation failed:\n" + log);
+    if (!c->dry) {
+        CK(c, cudaLibraryLoadData(&k->ulib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
+        CK(c, cudaLibraryGetKernel(&k->ufn, k->ulib, "lt_user_wrapper"));
+    }
+    k->def = def.get();
+    k->own_def = std::move(def);
+    *out = k.get();
+    c->kernels.push_back(std::move(k));
+    return LT_OK;
+}
+
 lt_status lt_kernel_destroy(lt_ctx *c, lt_kernel *kk) {
     if (!c) return fail(LT_ERR_INVALID_ARG, "null context");
     if (c->pending && c->pending->k == kk && !c->poisoned) {
@@ -1372,6 +1450,10 @@ lt_status lt_kernel_destroy(lt_ctx *c, lt_kernel *kk) {
     }
     for (auto it = c->kernels.begin(); it != c->kernels.end(); ++it)
         if (it->get() == kk) {
+            if (kk->ulib && !c->dry) {
+                for (int s2 = 0; s2 < NSTREAM; ++s2) cudaStreamSynchronize(c->st[s2]);
+                cudaLibraryUnload(kk->ulib);
+            }
             c->kernels.erase(it);
             return LT_OK;
         }
@@ -1493,8 +1575,11 @@ lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const 
     if (st) return st;
     auto pl = std::make_unique<PendingLaunch>();
     if ((st = prepare_plan(c, k, grid, block, wd, args, nargs, &pl->plan, &pl->parr))) return st;
-    if (!k->def->launch && !c->dry)
+    if (!k->def->launch && !k->ufn && !c->dry && k->def->id != LT_K_USER)
         return fail(LT_ERR_UNSUPPORTED, "a plan-only kernel can be launched only in a dry-run context");
+    if (k->def->id == LT_K_USER &&
+        (uint64_t)(block.x ? block.x : 1) * (block.y ? block.y : 1) * (block.z ? block.z : 1) > 1024)
+        return fail(LT_ERR_INVALID_ARG, "a source kernel's block holds at most 1024 threads");
     pl->k = k;
     ExecParams &ep = pl->ep;
     const std::vector<lt_array *> &parr = pl->parr;
@@ -1788,7 +1873,14 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             if ((st = upload(c, tasks.data(), tasks.size() * sizeof(ExecTask), &dptr, &roff))) return st;
             if (!c->dry && ctas) {
                 TimeScope ts(c, CAT_EXEC);
-                CK(c, def->launch((const ExecTask *)dptr, ctas, ep, c->st[S_COMP]));
+                if (k->ufn) {
+                    const ExecTask *tp = (const ExecTask *)dptr;
+                    void *kargs[] = {(void *)&tp, (void *)&ep};
+                    dim3 blk((unsigned)ep.block[0], (unsigned)ep.block[1], (unsigned)ep.block[2]);
+                    CK(c, cudaLaunchKernel((const void *)k->ufn, dim3(ctas), blk, kargs, 0, c->st[S_COMP]));
+                } else {
+                    CK(c, def->launch((const ExecTask *)dptr, ctas, ep, c->st[S_COMP]));
+                }
                 c->stats.kernels++;
             }
             std::ostringstream ex;

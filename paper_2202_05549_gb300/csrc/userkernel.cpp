@@ -1,0 +1,209 @@
+// Runtime compilation of user kernels (Sec. 3.5 "Runtime Kernel Compilation").
+//
+// The user writes the kernel body in the paper's convention (Listing 2): a
+// __device__ function whose first parameter is the virtual block index and
+// whose array parameters are view types indexed with GLOBAL indices:
+//     __device__ void name(dim3 virtBlockIdx, <parameters in declaration order>)
+// value parameters: int64_t (integer) or double (float); arrays:
+// lightning::Vector<T> (1-D, v[i]), Matrix<T> (2-D, m(i, j) or m[i][j]) and
+// Tensor<T> (3-D, t(k, i, j)), T = float, unsigned short (bf16 bits),
+// unsigned char or unsigned int.
+//
+// Like the generated wrapper of Listing 3, the library adds a __global__
+// wrapper that turns the physical block index into the virtual one and builds
+// the views from the chunk views (base pointer with the chunk offset already
+// subtracted), then calls the user function.  The wrapper reads the same task
+// table as the built-in kernels, so one launch runs every superblock of a
+// group.  Source and wrapper are compiled by NVRTC for sm_103a and loaded
+// with cudaLibraryLoadData.  NVRTC is opened at run time, so the engine loads
+// without it; registering a source kernel then reports LT_ERR_UNSUPPORTED.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "core.hpp"
+#include "kernels.cuh"
+#include "userkernel.hpp"
+
+namespace lt {
+namespace {
+
+struct Nvrtc {
+    bool ok = false;
+    nvrtcResult (*create)(nvrtcProgram *, const char *, const char *, int, const char *const *, const char *const *);
+    nvrtcResult (*compile)(nvrtcProgram, int, const char *const *);
+    nvrtcResult (*log_size)(nvrtcProgram, size_t *);
+    nvrtcResult (*log)(nvrtcProgram, char *);
+    nvrtcResult (*cubin_size)(nvrtcProgram, size_t *);
+    nvrtcResult (*cubin)(nvrtcProgram, char *);
+    nvrtcResult (*destroy)(nvrtcProgram *);
+};
+
+Nvrtc &nvrtc() {
+    static Nvrtc n;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so"};
+        void *h = nullptr;
+        for (const char *nm : names)
+            if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) return;
+        n.create = (decltype(n.create))dlsym(h, "nvrtcCreateProgram");
+        n.compile = (decltype(n.compile))dlsym(h, "nvrtcCompileProgram");
+        n.log_size = (decltype(n.log_size))dlsym(h, "nvrtcGetProgramLogSize");
+        n.log = (decltype(n.log))dlsym(h, "nvrtcGetProgramLog");
+        n.cubin_size = (decltype(n.cubin_size))dlsym(h, "nvrtcGetCUBINSize");
+        n.cubin = (decltype(n.cubin))dlsym(h, "nvrtcGetCUBIN");
+        n.destroy = (decltype(n.destroy))dlsym(h, "nvrtcDestroyProgram");
+        n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
+    });
+    return n;
+}
+
+const char *ctype(int dtype) {
+    switch (dtype) {
+        case LT_F32: return "float";
+        case LT_BF16: return "unsigned short";
+        case LT_U8: return "unsigned char";
+        default: return "unsigned int";
+    }
+}
+
+}  // namespace
+
+std::string user_wrapper_source(const std::string &user, const std::string &name, const std::vector<UserParam> &params) {
+    std::ostringstream o;
+    o << "typedef long long int64_t;\ntypedef unsigned long long uint64_t;\ntypedef unsigned int uint32_t;\n"
+         "typedef int int32_t;\n"
+         "namespace lightning {\n"
+         "template <typename T> struct Vector {\n"
+         "  T *p; int64_t s0;\n"
+         "  __device__ T &operator[](int64_t i) const { return p[i * s0]; }\n"
+         "  __device__ T &operator()(int64_t i) const { return p[i * s0]; }\n"
+         "};\n"
+         "template <typename T> struct Matrix {\n"
+         "  T *p; int64_t s0, s1;\n"
+         "  struct Row { T *p; int64_t s1; __device__ T &operator[](int64_t j) const { return p[j * s1]; } };\n"
+         "  __device__ T &operator()(int64_t i, int64_t j) const { return p[i * s0 + j * s1]; }\n"
+         "  __device__ Row operator[](int64_t i) const { Row r; r.p = p + i * s0; r.s1 = s1; return r; }\n"
+         "};\n"
+         "template <typename T> struct Tensor {\n"
+         "  T *p; int64_t s0, s1, s2;\n"
+         "  __device__ T &operator()(int64_t k, int64_t i, int64_t j) const { return p[k * s0 + i * s1 + j * s2]; }\n"
+         "};\n"
+         "}  // namespace lightning\n"
+         "struct LtView { uint64_t base; int64_t s[3]; int64_t org[3]; int64_t hi[3]; };\n"
+         "struct LtTask { int64_t t_lo[3], t_hi[3]; LtView v["
+      << LT_MAX_ARRAYS
+      << "]; uint32_t cta_begin, cta_count; int32_t aux[4]; };\n"
+         "struct LtParams { int64_t shape["
+      << LT_MAX_ARRAYS << "][3]; int32_t nd[" << LT_MAX_ARRAYS
+      << "]; int64_t block[3]; double f[4]; int64_t i[4]; uint32_t *err;"
+         " int32_t ntasks, variant, red_op, pad2; };\n"
+         "static_assert(sizeof(LtView) == "
+      << sizeof(DView) << ", \"view layout\");\nstatic_assert(sizeof(LtTask) == " << sizeof(ExecTask)
+      << ", \"task layout\");\nstatic_assert(sizeof(LtParams) == " << sizeof(ExecParams) << ", \"params layout\");\n"
+      << "#line 1 \"user_kernel.cu\"\n"
+      << user << "\n"
+      << "extern \"C\" __global__ void lt_user_wrapper(const LtTask *__restrict__ tasks, LtParams P) {\n"
+         "  int lo = 0, hi = P.ntasks - 1;\n"
+         "  while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (tasks[mid].cta_begin <= blockIdx.x) lo = mid; else hi = mid - 1; }\n"
+         "  const LtTask &t = tasks[lo];\n"
+         "  const int64_t bx0 = t.t_lo[0] / P.block[0], by0 = t.t_lo[1] / P.block[1], bz0 = t.t_lo[2] / P.block[2];\n"
+         "  const int64_t nbx = t.t_hi[0] / P.block[0] - bx0 + 1, nby = t.t_hi[1] / P.block[1] - by0 + 1;\n"
+         "  const int64_t l = (int64_t)blockIdx.x - (int64_t)t.cta_begin;\n"
+         "  dim3 vb((unsigned)(bx0 + l % nbx), (unsigned)(by0 + (l / nbx) % nby), (unsigned)(bz0 + l / (nbx * nby)));\n";
+    int slot = 0, fi = 0, ii = 0;
+    std::ostringstream args;
+    for (size_t p = 0; p < params.size(); ++p) {
+        const UserParam &up = params[p];
+        args << ", ";
+        if (!up.is_array) {
+            if (up.dtype == LT_F32)
+                args << "P.f[" << fi++ << "]";
+            else
+                args << "P.i[" << ii++ << "]";
+            continue;
+        }
+        const char *ct = ctype(up.dtype);
+        o << "  ";
+        if (up.rank == 1)
+            o << "lightning::Vector<" << ct << "> a" << slot << "; a" << slot << ".p = (" << ct << " *)t.v[" << slot
+              << "].base; a" << slot << ".s0 = t.v[" << slot << "].s[0];\n";
+        else if (up.rank == 2)
+            o << "lightning::Matrix<" << ct << "> a" << slot << "; a" << slot << ".p = (" << ct << " *)t.v[" << slot
+              << "].base; a" << slot << ".s0 = t.v[" << slot << "].s[0]; a" << slot << ".s1 = t.v[" << slot
+              << "].s[1];\n";
+        else
+            o << "lightning::Tensor<" << ct << "> a" << slot << "; a" << slot << ".p = (" << ct << " *)t.v[" << slot
+              << "].base; a" << slot << ".s0 = t.v[" << slot << "].s[0]; a" << slot << ".s1 = t.v[" << slot
+              << "].s[1]; a" << slot << ".s2 = t.v[" << slot << "].s[2];\n";
+        args << "a" << slot;
+        slot++;
+    }
+    o << "  " << name << "(vb" << args.str() << ");\n}\n";
+    return o.str();
+}
+
+lt_status compile_user_kernel(const std::string &src, std::vector<char> *cubin, std::string *log) {
+    Nvrtc &n = nvrtc();
+    if (!n.ok) {
+        *log = "NVRTC (libnvrtc.so) could not be opened";
+        return LT_ERR_UNSUPPORTED;
+    }
+    if (const char *dump = std::getenv("LT_NVRTC_DUMP")) {  // debugging aid: the generated source
+        if (FILE *f = std::fopen(dump, "w")) {
+            std::fwrite(src.data(), 1, src.size(), f);
+            std::fclose(f);
+        }
+    }
+    nvrtcProgram prog;
+    if (n.create(&prog, src.c_str(), "lightning_user.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+        *log = "nvrtcCreateProgram failed";
+        return LT_ERR_UNSUPPORTED;
+    }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=false", "-default-device"};
+    nvrtcResult r = n.compile(prog, 4, opts);
+    size_t ls = 0;
+    n.log_size(prog, &ls);
+    std::string lg(ls, '\0');
+    if (ls) n.log(prog, &lg[0]);
+    *log = lg;
+    if (r != NVRTC_SUCCESS) {
+        n.destroy(&prog);
+        return LT_ERR_COMPILE;
+    }
+    size_t cs = 0;
+    n.cubin_size(prog, &cs);
+    cubin->resize(cs);
+    n.cubin(prog, cubin->data());
+    n.destroy(&prog);
+    return LT_OK;
+}
+
+namespace k {
+
+uint32_t prepare_user(ExecTask *t, int n, ExecParams &p) {
+    uint32_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        uint64_t nb = 1;
+        for (int d = 0; d < 3; ++d) {
+            int64_t B = p.block[d] > 0 ? p.block[d] : 1;
+            nb *= (uint64_t)(t[i].t_hi[d] / B - t[i].t_lo[d] / B + 1);
+        }
+        t[i].cta_begin = total;
+        t[i].cta_count = (uint32_t)nb;
+        total += (uint32_t)nb;
+    }
+    return total;
+}
+
+}  // namespace k
+}  // namespace lt

@@ -141,19 +141,25 @@ def _dim3(t):
 
 
 class Kernel:
-    def __init__(self, ctx: "Context", builtin: int, annotation: str, params):
+    def __init__(self, ctx: "Context", builtin: int, annotation: str, params, source: str | None = None,
+                 name: str | None = None):
         self.ctx = ctx
         self.params = []
         for p in params:
-            name, dtype = p[0], p[1]
+            pname, dtype = p[0], p[1]
             is_array = p[2] if len(p) > 2 else True
-            self.params.append((name, dtype, is_array))
+            self.params.append((pname, dtype, is_array))
         arr = (L.lt_param * len(self.params))()
         self._names = [n.encode() for n, _, _ in self.params]
         for i, (n, d, a) in enumerate(self.params):
             arr[i] = L.lt_param(self._names[i], 1 if a else 0, d)
         h = C.c_void_p()
-        check(L.load().lt_kernel_register(ctx.h, builtin, annotation.encode(), arr, len(self.params), C.byref(h)))
+        if source is not None:
+            check(L.load().lt_kernel_register_source(ctx.h, source.encode(), name.encode(), annotation.encode(), arr,
+                                                     len(self.params), C.byref(h)))
+        else:
+            check(L.load().lt_kernel_register(ctx.h, builtin, annotation.encode(), arr, len(self.params),
+                                              C.byref(h)))
         self.h = h
 
     def destroy(self):
@@ -213,6 +219,10 @@ class Context:
 
     def kernel(self, builtin, annotation, params) -> Kernel:
         return Kernel(self, builtin, annotation, params)
+
+    def kernel_from_source(self, source: str, name: str, annotation: str, params) -> Kernel:
+        """Runtime-compiled user kernel (the paper's CudaKernelDef ... compile())."""
+        return Kernel(self, L.LT_K_USER, annotation, params, source=source, name=name)
 
     def launch_batch(self, launches, flags=0):
         """launches: list of (kernel, grid, block, superblock, args, repeat)."""
