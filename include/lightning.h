@@ -362,6 +362,8 @@ typedef struct {
     uint64_t graph_replays;   /* fused batches replayed from a cached CUDA graph */
     int64_t tuned_tile_rows;  /* autotuner choice of the last fused batch */
     int64_t tuned_hist_slice;
+    uint64_t tables_resident; /* descriptor tables reused on the device without a copy */
+    uint64_t plans_reused;    /* launches whose plan came from the kernel's plan cache */
 } lt_stats;
 
 lt_status lt_stats_get(lt_ctx *ctx, lt_stats *out);

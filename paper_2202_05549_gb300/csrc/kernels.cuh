@@ -41,7 +41,7 @@ struct ExecParams {
     int32_t ntasks;
     int32_t variant;                  // kernel variant chosen by prepare_*
     int32_t red_op;                   // operator of the reduce(f) argument (0 + 1 * 2 min 3 max)
-    int32_t pad2;
+    int32_t uniform_ctas;             // if > 0: task i owns CTAs [i * uniform_ctas, (i + 1) * uniform_ctas)
 };
 
 // Box copy (pack / unpack / replica update): copy the global box [lo, hi]

@@ -21,21 +21,10 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "task_lookup.cuh"
 
 namespace lt {
 namespace {
-
-__device__ __forceinline__ int find_task_d(const ExecTask *t, int n, uint32_t cta) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (t[mid].cta_begin <= cta)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
 
 __device__ __forceinline__ float at2(const DView &v, int64_t i, int64_t j) {
     return ((const float *)v.base)[i * v.s[0] + j * v.s[1]];
@@ -50,23 +39,24 @@ constexpr int TY = 32, TX = 128;   // cells per CTA tile
 constexpr int SP = TX + 2 + 1;     // shared row pitch (halo + bank padding)
 
 // Tiles of TY x TX cells over the box [by0, by1] x [bx0, bx1].
-__device__ __forceinline__ void tile_of(int64_t local, int64_t bx0, int64_t bx1, int64_t by0, int64_t *ty0,
+// (32-bit split: a 64-bit division costs registers and latency in every CTA)
+__device__ __forceinline__ void tile_of(uint32_t local, int64_t bx0, int64_t bx1, int64_t by0, int64_t *ty0,
                                         int64_t *tx0) {
-    const int64_t gx = (bx1 - bx0 + TX) / TX;
-    *ty0 = by0 + (local / gx) * TY;
-    *tx0 = bx0 + (local % gx) * TX;
+    const uint32_t gx = (uint32_t)((bx1 - bx0 + TX) / TX);
+    *ty0 = by0 + (int64_t)(local / gx) * TY;
+    *tx0 = bx0 + (int64_t)(local % gx) * TX;
 }
 
 __global__ void __launch_bounds__(DT) diffusion_fwd_scalar_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     __shared__ float su[TY + 2][SP];
-    const int ti = find_task_d(tasks, p.ntasks, blockIdx.x);
+    const int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
     const int64_t x1 = min(t.t_hi[0], NX - 1), y1 = min(t.t_hi[1], NY - 1);
     if (x1 < x0 || y1 < y0) return;
     int64_t ty0, tx0;
-    tile_of((int64_t)(blockIdx.x - t.cta_begin), x0, x1, y0, &ty0, &tx0);
+    tile_of(blockIdx.x - t.cta_begin, x0, x1, y0, &ty0, &tx0);
     const DView U = t.v[0], K = t.v[1], V = t.v[2];
     // U over the tile plus a one-cell ring (zero outside the domain)
     for (int e = threadIdx.x; e < (TY + 2) * (TX + 2); e += DT) {
@@ -88,7 +78,7 @@ __global__ void __launch_bounds__(DT) diffusion_fwd_scalar_kernel(const ExecTask
 __global__ void __launch_bounds__(DT) diffusion_adj_scalar_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     __shared__ float ss[TY + 2][SP];  // s = K * L1 of the superblock's own cells, 0 elsewhere
     __shared__ float su[TY + 2][SP];  // u_t
-    const int ti = find_task_d(tasks, p.ntasks, blockIdx.x);
+    const int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     // the superblock's cells (thread box clipped to the domain)
@@ -99,7 +89,7 @@ __global__ void __launch_bounds__(DT) diffusion_adj_scalar_kernel(const ExecTask
     const int64_t rx0 = max(x0 - 1, (int64_t)0), ry0 = max(y0 - 1, (int64_t)0);
     const int64_t rx1 = min(x1 + 1, NX - 1), ry1 = min(y1 + 1, NY - 1);
     int64_t ty0, tx0;
-    tile_of((int64_t)(blockIdx.x - t.cta_begin), rx0, rx1, ry0, &ty0, &tx0);
+    tile_of(blockIdx.x - t.cta_begin, rx0, rx1, ry0, &ty0, &tx0);
     const DView L1 = t.v[0], K = t.v[1], U = t.v[2], G = t.v[3], L0 = t.v[4];
     for (int e = threadIdx.x; e < (TY + 2) * (TX + 2); e += DT) {
         const int li = e / (TX + 2), lj = e % (TX + 2);
@@ -149,14 +139,14 @@ __device__ __forceinline__ float sel(bool b, float x) { return b ? x : 0.f; }
 
 __global__ void __launch_bounds__(DT) diffusion_fwd_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     __shared__ __align__(16) float su[TY + 2][VP];
-    const int ti = find_task_d(tasks, p.ntasks, blockIdx.x);
+    const int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
     const int64_t x1 = min(t.t_hi[0], NX - 1), y1 = min(t.t_hi[1], NY - 1);
     if (x1 < x0 || y1 < y0) return;
     int64_t ty0, tx0;
-    tile_of((int64_t)(blockIdx.x - t.cta_begin), x0, x1, y0, &ty0, &tx0);
+    tile_of(blockIdx.x - t.cta_begin, x0, x1, y0, &ty0, &tx0);
     const DView U = t.v[0], K = t.v[1], V = t.v[2];
     const int64_t cmax = min(x1 + 1, NX - 1), rmin = max(y0 - 1, (int64_t)0), rmax = min(y1 + 1, NY - 1);
     for (int e = threadIdx.x; e < (TY + 2) * VQ; e += DT) {
@@ -203,7 +193,7 @@ __global__ void __launch_bounds__(DT) diffusion_fwd_vec_kernel(const ExecTask *_
 __global__ void __launch_bounds__(DT) diffusion_adj_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     __shared__ __align__(16) float ss[TY + 2][VP];
     __shared__ __align__(16) float su[TY + 2][VP];
-    const int ti = find_task_d(tasks, p.ntasks, blockIdx.x);
+    const int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
@@ -213,7 +203,7 @@ __global__ void __launch_bounds__(DT) diffusion_adj_vec_kernel(const ExecTask *_
     const int64_t rx1 = min(x1 + 1, NX - 1), ry1 = min(y1 + 1, NY - 1);
     const int64_t ax0 = rx0 & ~(int64_t)3;  // tiles start on 4-aligned columns
     int64_t ty0, tx0;
-    tile_of((int64_t)(blockIdx.x - t.cta_begin), ax0, rx1, ry0, &ty0, &tx0);
+    tile_of(blockIdx.x - t.cta_begin, ax0, rx1, ry0, &ty0, &tx0);
     const DView L1 = t.v[0], K = t.v[1], U = t.v[2], G = t.v[3], L0 = t.v[4];
     for (int e = threadIdx.x; e < (TY + 2) * VQ; e += DT) {
         const int li = e / VQ, q = e % VQ;

@@ -10,24 +10,13 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "task_lookup.cuh"
 
 namespace lt {
 namespace {
 
 constexpr int HT = 256;                  // threads per CTA
 constexpr int64_t HCHUNK = 64 * 1024;    // bytes of X per CTA
-
-__device__ __forceinline__ int find_task_h(const ExecTask *t, int n, uint32_t cta) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (t[mid].cta_begin <= cta)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
 
 __device__ __forceinline__ void count4(uint32_t w, uint32_t *h) {
     atomicAdd(&h[w & 255u], 1u);
@@ -40,7 +29,7 @@ __global__ void __launch_bounds__(HT) hist256_kernel(const ExecTask *__restrict_
     __shared__ uint32_t sh[HT / 32][256];
     for (int i = threadIdx.x; i < (HT / 32) * 256; i += HT) (&sh[0][0])[i] = 0;
     __syncthreads();
-    const int ti = find_task_h(tasks, p.ntasks, blockIdx.x);
+    const int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t n = p.shape[0][0];
     const int64_t lo = t.t_lo[0] + (int64_t)(blockIdx.x - t.cta_begin) * HCHUNK;
@@ -98,7 +87,7 @@ __device__ __forceinline__ float rop(int op, float a, float b) {
 }
 
 __global__ void __launch_bounds__(RW * 32) rowreduce_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
-    const int ti = find_task_h(tasks, p.ntasks, blockIdx.x);
+    const int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const int64_t x0 = t.t_lo[0], x1 = min(t.t_hi[0], NX - 1);

@@ -14,22 +14,11 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "task_lookup.cuh"
 #include "stencil_body.cuh"
 
 namespace lt {
 namespace {
-
-__device__ __forceinline__ int find_task(const ExecTask *t, int n, uint32_t cta) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (t[mid].cta_begin <= cta)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
 
 // ------------------------------------------------------------------ 1-D example
 __device__ __forceinline__ void stencil1d_body(int64_t i, int64_t n, const DView &out, const DView &in) {
@@ -42,7 +31,7 @@ __device__ __forceinline__ void stencil1d_body(int64_t i, int64_t n, const DView
 }
 
 __global__ void __launch_bounds__(256) stencil1d_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
-    int ti = find_task(tasks, p.ntasks, blockIdx.x);
+    int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     int64_t n = p.shape[0][0];
     int64_t i = t.t_lo[0] + (int64_t)(blockIdx.x - t.cta_begin) * blockDim.x + threadIdx.x;
@@ -52,30 +41,36 @@ __global__ void __launch_bounds__(256) stencil1d_kernel(const ExecTask *__restri
 
 // ------------------------------------------------------------------ 2-D Jacobi
 constexpr int JWARPS = 4;    // warps per CTA, side by side along x
+constexpr int JV = 8;        // rows per warp strip of the single-step kernel
 
 // Vector variant: every lane owns 4 adjacent columns of a 128-column strip and
-// sweeps JR rows (jacobi_strip in stencil_body.cuh).
+// sweeps R rows (jacobi_strip in stencil_body.cuh).  R = 8 keeps the kernel
+// near 72 registers (7 CTAs of 128 threads per SM); the two halo rows each
+// strip re-reads come from L2.  The CTA index is split with 32-bit
+// arithmetic: a 64-bit division here costs registers and prologue latency in
+// every CTA.
+template <int R>
 __global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
-    int ti = find_task(tasks, p.ntasks, blockIdx.x);
+    int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
     const int64_t xe = min(t.t_hi[0], NX - 1), ye = min(t.t_hi[1], NY - 1);  // last output column / row
-    const int64_t width = t.t_hi[0] - x0 + 1;
-    const int64_t gx = (width + JWARPS * JCOLS - 1) / (JWARPS * JCOLS);
-    const int64_t local = blockIdx.x - t.cta_begin;
-    const int64_t tx = local % gx, ty = local / gx;
+    const uint32_t width = (uint32_t)(t.t_hi[0] - x0 + 1);
+    const uint32_t gx = (width + JWARPS * JCOLS - 1) / (JWARPS * JCOLS);
+    const uint32_t local = blockIdx.x - t.cta_begin;
+    const uint32_t tx = local % gx, ty = local / gx;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t js = x0 + (tx * JWARPS + warp) * JCOLS;  // first column of this warp's strip
-    const int64_t r0 = y0 + ty * JR;
+    const int64_t js = x0 + (int64_t)(tx * JWARPS + warp) * JCOLS;  // first column of this warp's strip
+    const int64_t r0 = y0 + (int64_t)ty * R;
     if (js > xe || r0 > ye) return;  // warp-uniform: nothing to write
-    jacobi_strip<false>((const float *)t.v[0].base, t.v[0].s[0], (float *)t.v[1].base, t.v[1].s[0], NY, NX, js, r0,
-                        xe, ye, lane);
+    jacobi_strip<false, R>((const float *)t.v[0].base, t.v[0].s[0], (float *)t.v[1].base, t.v[1].s[0], NY, NX, js,
+                           r0, xe, ye, lane);
 }
 
 // Scalar variant for unaligned tasks: one thread per output cell.
 __global__ void __launch_bounds__(256) jacobi2d_scalar_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
-    int ti = find_task(tasks, p.ntasks, blockIdx.x);
+    int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const int64_t width = t.t_hi[0] - t.t_lo[0] + 1;
@@ -121,11 +116,12 @@ uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p) {
         for (int a = 0; a < 2; ++a)
             if (t[i].v[a].s[1] != 1 || (t[i].v[a].s[0] % 4) != 0 || (t[i].v[a].base % 16) != 0) vec = false;
     }
+    // variant 1: strips of JV rows (vector); 0: one thread per cell (scalar)
     p.variant = vec ? 1 : 0;
     uint32_t total = 0;
     for (int i = 0; i < n; ++i) {
         int64_t w = t[i].t_hi[0] - t[i].t_lo[0] + 1, h = t[i].t_hi[1] - t[i].t_lo[1] + 1;
-        uint64_t c = vec ? (uint64_t)((w + JWARPS * JCOLS - 1) / (JWARPS * JCOLS)) * (uint64_t)((h + JR - 1) / JR)
+        uint64_t c = vec ? (uint64_t)((w + JWARPS * JCOLS - 1) / (JWARPS * JCOLS)) * (uint64_t)((h + JV - 1) / JV)
                          : (uint64_t)((w * h + 255) / 256);
         t[i].cta_begin = total;
         t[i].cta_count = (uint32_t)c;
@@ -136,7 +132,7 @@ uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p) {
 
 cudaError_t launch_jacobi2d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
     if (p.variant == 1)
-        jacobi2d_vec_kernel<<<ctas, JWARPS * 32, 0, st>>>(dev, p);
+        jacobi2d_vec_kernel<JV><<<ctas, JWARPS * 32, 0, st>>>(dev, p);
     else
         jacobi2d_scalar_kernel<<<ctas, 256, 0, st>>>(dev, p);
     return cudaGetLastError();
@@ -159,16 +155,16 @@ constexpr int MTY = 32, MTX = 128, MT = 256;
 
 __global__ void __launch_bounds__(MT) jacobi2d_multi_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     extern __shared__ float msm[];
-    const int ti = find_task(tasks, p.ntasks, blockIdx.x);
+    const int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const int k = (int)p.i[0];
     const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
     const int64_t x1 = min(t.t_hi[0], NX - 1), y1 = min(t.t_hi[1], NY - 1);
     if (x1 < x0 || y1 < y0) return;
-    const int64_t gx = (x1 - x0 + MTX) / MTX;
-    const int64_t local = blockIdx.x - t.cta_begin;
-    const int64_t ty0 = y0 + (local / gx) * MTY, tx0 = x0 + (local % gx) * MTX;
+    const uint32_t gx = (uint32_t)((x1 - x0 + MTX) / MTX);
+    const uint32_t local = blockIdx.x - t.cta_begin;
+    const int64_t ty0 = y0 + (int64_t)(local / gx) * MTY, tx0 = x0 + (int64_t)(local % gx) * MTX;
     const int H = MTY + 2 * k, W = MTX + 2 * k;
     float *A = msm, *B = msm + H * W;
     // readable region: superblock +/- k, clipped to the domain

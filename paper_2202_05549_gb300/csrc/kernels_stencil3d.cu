@@ -10,6 +10,7 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "task_lookup.cuh"
 
 namespace lt {
 namespace {
@@ -20,18 +21,6 @@ constexpr int SKR = 32;           // planes per CTA (k run)
 constexpr int SQ = SX / 4;        // float4 groups per tile row
 constexpr int SPITCH = SX + 8;    // shared pitch, 4 cells of room each side
 constexpr int GPT = SY * SQ / ST; // float4 groups per thread (2)
-
-__device__ __forceinline__ int find_task3(const ExecTask *t, int n, uint32_t cta) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (t[mid].cta_begin <= cta)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
 
 __device__ __forceinline__ float j7(float c, float zm, float zp, float ym, float yp, float xm, float xp) {
     float a = __fadd_rn(c, zm);
@@ -67,17 +56,17 @@ __device__ __forceinline__ const float *row3(const DView &v, int64_t k, int64_t 
 
 __global__ void __launch_bounds__(ST) jacobi3d_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     __shared__ __align__(16) float pl[SY + 2][SPITCH];
-    const int ti = find_task3(tasks, p.ntasks, blockIdx.x);
+    const int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     Geo3 g;
     if (!geo3(t, p, &g)) return;
-    const int64_t gx = (g.x1 - g.x0 + SX) / SX, gy = (g.y1 - g.y0 + SY) / SY;
-    int64_t local = blockIdx.x - t.cta_begin;
-    const int64_t tx0 = g.x0 + (local % gx) * SX;
+    const uint32_t gx = (uint32_t)((g.x1 - g.x0 + SX) / SX), gy = (uint32_t)((g.y1 - g.y0 + SY) / SY);
+    uint32_t local = blockIdx.x - t.cta_begin;  // 32-bit split: no 64-bit division in the prologue
+    const int64_t tx0 = g.x0 + (int64_t)(local % gx) * SX;
     local /= gx;
-    const int64_t ty0 = g.y0 + (local % gy) * SY;
+    const int64_t ty0 = g.y0 + (int64_t)(local % gy) * SY;
     local /= gy;
-    const int64_t kz0 = g.z0 + local * SKR, kz1 = min(kz0 + SKR - 1, g.z1);
+    const int64_t kz0 = g.z0 + (int64_t)local * SKR, kz1 = min(kz0 + SKR - 1, g.z1);
     const DView U = t.v[0], V = t.v[1];
     // readable box (the annotation's region, clipped)
     const int64_t cmin = max(g.x0 - 1, (int64_t)0), cmax = min(g.x1 + 1, g.NX - 1);
@@ -143,7 +132,7 @@ __global__ void __launch_bounds__(ST) jacobi3d_vec_kernel(const ExecTask *__rest
 }
 
 __global__ void __launch_bounds__(ST) jacobi3d_scalar_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
-    const int ti = find_task3(tasks, p.ntasks, blockIdx.x);
+    const int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     Geo3 g;
     if (!geo3(t, p, &g)) return;

@@ -213,7 +213,24 @@ struct lt_array {
     int64_t id = 0;
 };
 
+// A launch plan and what follows from the plan alone.  Launches of the same
+// shape (kernel, grid, block, superblock, step count, and array arguments of
+// the same geometry with the same aliasing) share one, so an iterative loop
+// that swaps its arrays plans once.
+struct PlanBundle {
+    LaunchPlan plan;
+    std::vector<std::pair<int, int64_t>> dead;  // (parameter, chunk) the launch overwrites without reading
+};
+
+struct CachedPlan {
+    std::vector<int64_t> key;
+    std::shared_ptr<const PlanBundle> b;
+    uint64_t last_use = 0;
+};
+
 struct lt_kernel {
+    std::vector<CachedPlan> plans;  // most recently used shapes (at most PLAN_CACHE)
+    uint64_t plan_tick = 0;
     const BuiltinDef *def = nullptr;
     std::unique_ptr<BuiltinDef> own_def;     // user kernels: their own signature
     cudaLibrary_t ulib = nullptr;            // user kernels: loaded NVRTC cubin
@@ -234,7 +251,7 @@ struct TimedOp {
 // A planned launch waiting for the next one (one launch of lookahead).
 struct PendingLaunch {
     lt_kernel *k = nullptr;
-    LaunchPlan plan;
+    std::shared_ptr<const PlanBundle> b;
     std::vector<lt_array *> parr;
     ExecParams ep{};
 };
@@ -272,6 +289,14 @@ struct lt_ctx {
     char *up_host = nullptr, *up_dev = nullptr;
     size_t up_cap = 0, up_head = 0;
     std::deque<UploadUse> up_inflight;
+    // resident descriptor tables (after the ring in both allocations)
+    struct TableSlot {
+        std::vector<char> bytes;  // host copy of the slot's contents (empty: free)
+        uint64_t last_use = 0;
+        cudaEvent_t staged = nullptr;  // recorded after the copy that filled the slot
+    };
+    std::vector<TableSlot> tslots;
+    uint64_t tslot_tick = 0;
     uint32_t *err_word = nullptr;  // device error word
     std::vector<std::unique_ptr<lt_array>> arrays;
     std::vector<std::unique_ptr<lt_kernel>> kernels;
@@ -598,9 +623,57 @@ lt_status ensure_dev(lt_ctx *c, lt_array *a, int64_t ci, bool need_data) {
 }
 
 // Upload a descriptor table for the next compute-stream kernel.
+// Descriptor tables that repeat (iterative launches over resident chunks
+// plan the same tasks, views and copy pieces every time) stay on the device:
+// a table whose bytes equal a resident slot is used in place, with no
+// host-to-device copy.  Every kernel that reads a table runs on the compute
+// stream, as does the copy that refills a slot, so stream order keeps a
+// slot's earlier readers ahead of its new contents; the slot's event keeps
+// its pinned staging bytes until that copy has run.
+constexpr int TSLOTS = 32;
+constexpr size_t TSLOT_BYTES = (size_t)64 << 10;
+constexpr size_t NO_RING = ~(size_t)0;  // ring offset of a table served by a resident slot
+
+lt_status upload_resident(lt_ctx *c, const void *src, size_t n, void **dev_ptr, bool *done) {
+    *done = false;
+    if (n == 0 || n > TSLOT_BYTES || c->tslots.empty()) return LT_OK;
+    int lru = 0;
+    for (int i = 0; i < (int)c->tslots.size(); ++i) {
+        auto &t = c->tslots[(size_t)i];
+        if (t.bytes.size() == n && std::memcmp(t.bytes.data(), src, n) == 0) {
+            t.last_use = ++c->tslot_tick;
+            *dev_ptr = c->up_dev + c->up_cap + (size_t)i * TSLOT_BYTES;
+            *done = true;
+            c->stats.tables_resident++;
+            return LT_OK;
+        }
+        if (t.last_use < c->tslots[(size_t)lru].last_use) lru = i;
+    }
+    auto &t = c->tslots[(size_t)lru];
+    char *h = c->up_host + c->up_cap + (size_t)lru * TSLOT_BYTES;
+    char *d = c->up_dev + c->up_cap + (size_t)lru * TSLOT_BYTES;
+    if (!t.bytes.empty()) CK(c, cudaEventSynchronize(t.staged));  // its last copy has read the staging bytes
+    t.bytes.assign((const char *)src, (const char *)src + n);
+    std::memcpy(h, src, n);
+    CK(c, cudaMemcpyAsync(d, h, n, cudaMemcpyHostToDevice, c->st[S_COMP]));
+    CK(c, cudaEventRecord(t.staged, c->st[S_COMP]));
+    t.last_use = ++c->tslot_tick;
+    *dev_ptr = d;
+    *done = true;
+    return LT_OK;
+}
+
 lt_status upload(lt_ctx *c, const void *src, size_t n, void **dev_ptr, size_t *ring_off) {
     if (c->dry) {
         *dev_ptr = nullptr;
+        *ring_off = NO_RING;
+        return LT_OK;
+    }
+    bool done = false;
+    lt_status rs = upload_resident(c, src, n, dev_ptr, &done);
+    if (rs) return rs;
+    if (done) {
+        *ring_off = NO_RING;
         return LT_OK;
     }
     size_t sz = align_up(n ? n : 1, 256);
@@ -625,7 +698,7 @@ lt_status upload(lt_ctx *c, const void *src, size_t n, void **dev_ptr, size_t *r
 }
 
 void upload_done(lt_ctx *c, size_t off, size_t n, uint64_t seq) {
-    if (c->dry) return;
+    if (c->dry || off == NO_RING) return;
     c->up_inflight.push_back({off, off + align_up(n ? n : 1, 256), seq});
 }
 
@@ -645,6 +718,17 @@ lt_kernel *find_kernel(lt_ctx *c, const lt_kernel *k) {
     for (auto &p : c->kernels)
         if (p.get() == k) return p.get();
     return nullptr;
+}
+
+// The CTA count shared by every task when task i owns CTAs [i*n, (i+1)*n),
+// else 0.  Kernels then find their task by one division (task_of).
+int32_t uniform_cta_count(const std::vector<ExecTask> &tasks) {
+    if (tasks.empty()) return 0;
+    const uint32_t n = tasks[0].cta_count;
+    if (n == 0 || n > (uint32_t)INT32_MAX) return 0;
+    for (size_t i = 0; i < tasks.size(); ++i)
+        if (tasks[i].cta_count != n || (uint64_t)tasks[i].cta_begin != (uint64_t)i * n) return 0;
+    return (int32_t)n;
 }
 
 lt_status sync_all(lt_ctx *c) {
@@ -862,9 +946,20 @@ std::vector<std::pair<lt_array *, int64_t>> dead_chunks(const LaunchPlan &plan, 
     return out;
 }
 
+// The same, as (parameter, chunk): parameter = the first one naming the array.
+std::vector<std::pair<int, int64_t>> dead_by_param(const LaunchPlan &plan, const std::vector<lt_array *> &parr) {
+    std::vector<std::pair<int, int64_t>> out;
+    for (auto &d : dead_chunks(plan, parr)) {
+        int p = 0;
+        while (parr[(size_t)p] != d.first) ++p;
+        out.push_back({p, d.second});
+    }
+    return out;
+}
+
 // Mark the chunks this launch overwrites unread (no fetch on first touch).
-void mark_dead(lt_ctx *c, const LaunchPlan &plan, const std::vector<lt_array *> &parr) {
-    for (auto &d : dead_chunks(plan, parr)) d.first->cs[(size_t)d.second].dead_launch = c->launch_id;
+void mark_dead(lt_ctx *c, const PlanBundle &b, const std::vector<lt_array *> &parr) {
+    for (auto &d : b.dead) parr[(size_t)d.first]->cs[(size_t)d.second].dead_launch = c->launch_id;
 }
 
 }  // namespace
@@ -924,8 +1019,10 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     }
     c->host.init(cfg->host_pool_bytes, c->host_base);
     c->up_cap = (size_t)32 << 20;
-    CK(cp, cudaHostAlloc((void **)&c->up_host, c->up_cap, cudaHostAllocDefault));
-    CK(cp, cudaMalloc((void **)&c->up_dev, c->up_cap));
+    CK(cp, cudaHostAlloc((void **)&c->up_host, c->up_cap + TSLOTS * TSLOT_BYTES, cudaHostAllocDefault));
+    CK(cp, cudaMalloc((void **)&c->up_dev, c->up_cap + TSLOTS * TSLOT_BYTES));
+    c->tslots.resize(TSLOTS);
+    for (auto &t : c->tslots) CK(cp, cudaEventCreateWithFlags(&t.staged, cudaEventDisableTiming));
     CK(cp, cudaMalloc((void **)&c->err_word, 16));
     CK(cp, cudaMemset(c->err_word, 0, 16));
     *out = c.release();
@@ -955,6 +1052,8 @@ lt_status lt_ctx_destroy(lt_ctx *c) {
         if (c->batch && c->batch->exec) cudaGraphExecDestroy(c->batch->exec);
         if (c->dev_base) cudaFree(c->dev_base);
         if (c->host_base) cudaFreeHost(c->host_base);
+        for (auto &t : c->tslots)
+            if (t.staged) cudaEventDestroy(t.staged);
         if (c->up_host) cudaFreeHost(c->up_host);
         if (c->up_dev) cudaFree(c->up_dev);
         if (c->err_word) cudaFree(c->err_word);
@@ -1460,8 +1559,11 @@ lt_status lt_kernel_destroy(lt_ctx *c, lt_kernel *kk) {
     return fail(LT_ERR_INVALID_ARG, "unknown kernel");
 }
 
+constexpr size_t PLAN_CACHE = 8;
+
 static lt_status prepare_plan(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const lt_workdist *wd,
-                              const lt_arg *args, int32_t nargs, LaunchPlan *plan, std::vector<lt_array *> *parr) {
+                              const lt_arg *args, int32_t nargs, std::shared_ptr<const PlanBundle> *out,
+                              std::vector<lt_array *> *parr) {
     if (!k || !find_kernel(c, k)) return fail(LT_ERR_INVALID_ARG, "unknown kernel");
     if (nargs != (int32_t)k->params.size() || (nargs && !args))
         return fail(LT_ERR_INVALID_ARG, "argument count does not match the kernel's parameters");
@@ -1493,16 +1595,9 @@ static lt_status prepare_plan(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 blo
     int64_t sb3[3] = {0, 0, 0};
     if (wd)
         for (int d = 0; d < 3; ++d) sb3[d] = wd->superblock[d];
-    std::string err;
-    if (!plan_launch(k->ann, k->stmt_of_param, pa, g3, b3, sb3, plan, &err)) return fail(LT_ERR_INVALID_ARG, err);
-    // the annotation must contain every access the built-in makes
-    int64_t B[3];
-    for (int d = 0; d < 3; ++d) B[d] = (int64_t)(b3[d] ? b3[d] : 1);
-    std::vector<int64_t> vlo, vhi;
-    Annotation canon_launch;
-    const Annotation *canon = &k->canon;
-    if (k->def->canon && std::string(k->def->canon).find("{K}") != std::string::npos) {
-        int64_t kval = 0;
+    const bool has_k = k->def->canon && std::strstr(k->def->canon, "{K}") != nullptr;
+    int64_t kval = 0;
+    if (has_k) {
         bool found = false;
         for (int p = 0; p < nargs && !found; ++p)
             if (!k->params[(size_t)p].is_array && k->params[(size_t)p].dtype != LT_F32) {
@@ -1511,6 +1606,45 @@ static lt_status prepare_plan(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 blo
             }
         if (!found || kval < 1 || kval > 16)
             return fail(LT_ERR_INVALID_ARG, "this built-in needs an integer step count between 1 and 16");
+    }
+    // plan cache: everything the plan depends on
+    std::vector<int64_t> key = {(int64_t)g3[0], (int64_t)g3[1], (int64_t)g3[2], (int64_t)b3[0], (int64_t)b3[1],
+                                (int64_t)b3[2], sb3[0], sb3[1], sb3[2], kval, nargs};
+    for (int p = 0; p < nargs; ++p) {
+        const lt_array *a = (*parr)[(size_t)p];
+        if (!a) {
+            key.push_back(-1);
+            continue;
+        }
+        int alias = p;
+        for (int q = 0; q < p; ++q)
+            if ((*parr)[(size_t)q] == a) {
+                alias = q;
+                break;
+            }
+        const ArrayGeom &g = a->g;
+        key.insert(key.end(), {(int64_t)alias, (int64_t)g.dtype, (int64_t)g.nd, g.shape[0], g.shape[1], g.shape[2],
+                               (int64_t)g.dist.kind, (int64_t)g.dist.order, g.dist.chunk[0], g.dist.chunk[1],
+                               g.dist.chunk[2], g.dist.halo[0], g.dist.halo[1], g.dist.halo[2]});
+    }
+    for (auto &e : k->plans)
+        if (e.key == key) {
+            e.last_use = ++k->plan_tick;
+            *out = e.b;
+            c->stats.plans_reused++;
+            return LT_OK;
+        }
+    auto bundle = std::make_shared<PlanBundle>();
+    LaunchPlan *plan = &bundle->plan;
+    std::string err;
+    if (!plan_launch(k->ann, k->stmt_of_param, pa, g3, b3, sb3, plan, &err)) return fail(LT_ERR_INVALID_ARG, err);
+    // the annotation must contain every access the built-in makes
+    int64_t B[3];
+    for (int d = 0; d < 3; ++d) B[d] = (int64_t)(b3[d] ? b3[d] : 1);
+    std::vector<int64_t> vlo, vhi;
+    Annotation canon_launch;
+    const Annotation *canon = &k->canon;
+    if (has_k) {
         std::string err2;
         if (!parse_annotation(canon_text(k->def, kval), &canon_launch, &err2))
             return fail(LT_ERR_PARSE, "internal canonical: " + err2);
@@ -1530,6 +1664,19 @@ static lt_status prepare_plan(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 blo
                                                     "' does not contain what the kernel accesses");
         }
     }
+    bundle->dead = dead_by_param(*plan, *parr);
+    if (k->plans.size() >= PLAN_CACHE) {
+        size_t lru = 0;
+        for (size_t i = 1; i < k->plans.size(); ++i)
+            if (k->plans[i].last_use < k->plans[lru].last_use) lru = i;
+        k->plans.erase(k->plans.begin() + (std::ptrdiff_t)lru);
+    }
+    CachedPlan ce;
+    ce.key = std::move(key);
+    ce.b = bundle;
+    ce.last_use = ++k->plan_tick;
+    k->plans.push_back(std::move(ce));
+    *out = std::move(bundle);
     return LT_OK;
 }
 
@@ -1537,10 +1684,10 @@ lt_status lt_plan_explain(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, 
                           const lt_arg *args, int32_t nargs, char *buf, size_t cap, size_t *needed) {
     lt_status st = check_ctx(c);
     if (st) return st;
-    LaunchPlan plan;
+    std::shared_ptr<const PlanBundle> b;
     std::vector<lt_array *> parr;
-    if ((st = prepare_plan(c, k, grid, block, wd, args, nargs, &plan, &parr))) return st;
-    std::string js = plan_to_json(plan);
+    if ((st = prepare_plan(c, k, grid, block, wd, args, nargs, &b, &parr))) return st;
+    std::string js = plan_to_json(b->plan);
     if (needed) *needed = js.size() + 1;
     if (buf && cap) {
         size_t n = std::min(cap - 1, js.size());
@@ -1574,7 +1721,7 @@ lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const 
     lt_status st = check_ctx(c);
     if (st) return st;
     auto pl = std::make_unique<PendingLaunch>();
-    if ((st = prepare_plan(c, k, grid, block, wd, args, nargs, &pl->plan, &pl->parr))) return st;
+    if ((st = prepare_plan(c, k, grid, block, wd, args, nargs, &pl->b, &pl->parr))) return st;
     if (!k->def->launch && !k->ufn && !c->dry && k->def->id != LT_K_USER)
         return fail(LT_ERR_UNSUPPORTED, "a plan-only kernel can be launched only in a dry-run context");
     if (k->def->id == LT_K_USER &&
@@ -1607,7 +1754,8 @@ lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const 
     // one launch of lookahead: the previous launch is enqueued now, knowing
     // which chunks this one overwrites without reading them
     if (c->pending) {
-        auto nd = dead_chunks(pl->plan, pl->parr);
+        std::vector<std::pair<lt_array *, int64_t>> nd;
+        for (auto &d : pl->b->dead) nd.push_back({pl->parr[(size_t)d.first], d.second});
         std::unique_ptr<PendingLaunch> prev = std::move(c->pending);
         c->pending = std::move(pl);
         return emit_launch(c, *prev, &nd);
@@ -1620,12 +1768,12 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                              const std::vector<std::pair<lt_array *, int64_t>> *next_dead) {
     lt_status st = LT_OK;
     lt_kernel *k = pl.k;
-    const LaunchPlan &plan = pl.plan;
+    const LaunchPlan &plan = pl.b->plan;
     const std::vector<lt_array *> &parr = pl.parr;
     ExecParams &ep = pl.ep;
     ++c->launch_id;
     c->stats.launches++;
-    mark_dead(c, plan, parr);
+    mark_dead(c, *pl.b, parr);
     if (next_dead)
         for (auto &d : *next_dead) d.first->cs[(size_t)d.second].next_dead_launch = c->launch_id;
     const BuiltinDef *def = k->def;
@@ -1862,7 +2010,9 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             op_begin(c, S_COMP, "execute");
             if ((st = op_wait(c, ex_wait))) return st;
             ep.ntasks = (int32_t)tasks.size();
+            ep.uniform_ctas = 0;
             uint32_t ctas = def->prepare ? def->prepare(tasks.data(), (int)tasks.size(), ep) : 0;
+            if (ctas != 0xFFFFFFFFu) ep.uniform_ctas = uniform_cta_count(tasks);
             if (ctas == 0xFFFFFFFFu)
                 return fail(LT_ERR_UNSUPPORTED, "this built-in cannot run these chunks (code " +
                                                     std::to_string(ep.variant) +
@@ -1883,11 +2033,15 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 }
                 c->stats.kernels++;
             }
-            std::ostringstream ex;
-            ex << ",\"superblocks\":[";
-            for (size_t oi = g0; oi < g1; ++oi) ex << (oi > g0 ? "," : "") << plan.sbs[order[oi]].index;
-            ex << "]";
-            if ((st = op_end(c, &exq, ex.str()))) return st;
+            std::string extra;
+            if (c->log_on) {
+                std::ostringstream ex;
+                ex << ",\"superblocks\":[";
+                for (size_t oi = g0; oi < g1; ++oi) ex << (oi > g0 ? "," : "") << plan.sbs[order[oi]].index;
+                ex << "]";
+                extra = ex.str();
+            }
+            if ((st = op_end(c, &exq, extra))) return st;
             upload_done(c, roff, tasks.size() * sizeof(ExecTask), exq);
             c->stats.tasks_execute += tasks.size();
             for (auto &u : uses) {
@@ -2302,9 +2456,9 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
     if (!fused) return batch_plain(c, d, n);
     // the plain form validates annotations per launch; the fused form checks them once
     for (int32_t i = 0; i < n; ++i) {
-        LaunchPlan plan;
+        std::shared_ptr<const PlanBundle> b;
         std::vector<lt_array *> parr;
-        if ((st = prepare_plan(c, d[i].kernel, d[i].grid, d[i].block, &d[i].wd, d[i].args, d[i].nargs, &plan, &parr)))
+        if ((st = prepare_plan(c, d[i].kernel, d[i].grid, d[i].block, &d[i].wd, d[i].args, d[i].nargs, &b, &parr)))
             return st;
     }
     if ((st = flush_pending(c))) return st;

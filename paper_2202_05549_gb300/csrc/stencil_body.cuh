@@ -33,30 +33,30 @@ __device__ __forceinline__ float ld1(const float *p) {
     return *p;
 }
 
-// One warp computes output rows r0 .. min(r0+JR-1, ye) of the 128-column
+// One warp computes output rows r0 .. min(r0+R-1, ye) of the 128-column
 // strip starting at column js (js <= xe, js % 4 == 0), reading U (row
 // stride su) and writing V (row stride sv); both are views indexed with
-// global indices whose rows are 16-byte aligned.  All JR+2 input rows are
+// global indices whose rows are 16-byte aligned.  All R+2 input rows are
 // loaded before any arithmetic; horizontal neighbours come from the
 // adjacent lanes.  L2ONLY loads bypass L1 (data written by other SMs in the
 // same kernel).  Columns read: up to min(xe+1, NX-1), in 4-aligned groups.
-template <bool L2ONLY>
+template <bool L2ONLY, int R = JR>
 __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float *vb, int64_t sv, int64_t NY,
                                              int64_t NX, int64_t js, int64_t r0, int64_t xe, int64_t ye, int lane) {
     const int64_t j0 = js + lane * 4;
-    const int64_t rlast = min(r0 + JR - 1, ye);
+    const int64_t rlast = min(r0 + R - 1, ye);
     const int64_t cmax = min(xe + 1, NX - 1);  // last column that may be read
     const bool ld = j0 <= cmax;
-    float4 row[JR + 2];
-    float wl[JR], er[JR];
+    float4 row[R + 2];
+    float wl[R], er[R];
 #pragma unroll
-    for (int k = 0; k < JR + 2; ++k) {
+    for (int k = 0; k < R + 2; ++k) {
         int64_t r = r0 - 1 + k;
         row[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ld && r >= 0 && r < NY && r <= rlast + 1) row[k] = ld4<L2ONLY>(ub + r * su + j0);
     }
 #pragma unroll
-    for (int k = 0; k < JR; ++k) {
+    for (int k = 0; k < R; ++k) {
         int64_t r = r0 + k;
         wl[k] = 0.f;
         er[k] = 0.f;
@@ -67,13 +67,13 @@ __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float 
     }
     // columns of this lane that lie outside the domain read as 0
 #pragma unroll
-    for (int k = 0; k < JR + 2; ++k) {
+    for (int k = 0; k < R + 2; ++k) {
         if (j0 + 1 > NX - 1) row[k].y = 0.f;
         if (j0 + 2 > NX - 1) row[k].z = 0.f;
         if (j0 + 3 > NX - 1) row[k].w = 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < JR; ++k) {
+    for (int k = 0; k < R; ++k) {
         int64_t r = r0 + k;
         const float4 up = row[k], mid = row[k + 1], dn = row[k + 2];
         float w_in = __shfl_up_sync(0xffffffffu, mid.w, 1);

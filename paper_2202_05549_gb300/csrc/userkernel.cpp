@@ -106,7 +106,7 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
          "struct LtParams { int64_t shape["
       << LT_MAX_ARRAYS << "][3]; int32_t nd[" << LT_MAX_ARRAYS
       << "]; int64_t block[3]; double f[4]; int64_t i[4]; uint32_t *err;"
-         " int32_t ntasks, variant, red_op, pad2; };\n"
+         " int32_t ntasks, variant, red_op, uniform_ctas; };\n"
          "static_assert(sizeof(LtView) == "
       << sizeof(DView) << ", \"view layout\");\nstatic_assert(sizeof(LtTask) == " << sizeof(ExecTask)
       << ", \"task layout\");\nstatic_assert(sizeof(LtParams) == " << sizeof(ExecParams) << ", \"params layout\");\n"
@@ -114,7 +114,8 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
       << user << "\n"
       << "extern \"C\" __global__ void lt_user_wrapper(const LtTask *__restrict__ tasks, LtParams P) {\n"
          "  int lo = 0, hi = P.ntasks - 1;\n"
-         "  while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (tasks[mid].cta_begin <= blockIdx.x) lo = mid; else hi = mid - 1; }\n"
+         "  if (P.uniform_ctas > 0) lo = (int)(blockIdx.x / (unsigned)P.uniform_ctas);\n"
+         "  else while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (tasks[mid].cta_begin <= blockIdx.x) lo = mid; else hi = mid - 1; }\n"
          "  const LtTask &t = tasks[lo];\n"
          "  const int64_t bx0 = t.t_lo[0] / P.block[0], by0 = t.t_lo[1] / P.block[1], bz0 = t.t_lo[2] / P.block[2];\n"
          "  const int64_t nbx = t.t_hi[0] / P.block[0] - bx0 + 1, nby = t.t_hi[1] / P.block[1] - by0 + 1;\n"
