@@ -150,6 +150,7 @@ struct CState {
     int64_t next_dead_launch = -1;  // launch after which the next launch overwrites it unread
     int64_t last_use_launch = -1;   // launch and group of its last use in that launch
     int64_t last_use_group = -1;
+    int64_t last_write_launch = -1;  // last launch that wrote it
 };
 
 struct BuiltinDef {
@@ -473,15 +474,51 @@ DView view_of(lt_ctx *c, const ArrayGeom &g, const ChunkGeom &cg, size_t off) {
 lt_status evict(lt_ctx *c, lt_array *a, int64_t ci);
 
 // Pick the least-recently-used unpinned resident chunk.
+// Can chunk state s be evicted without writing it back?  Its contents are
+// overwritten unread in this launch (not yet touched by it), or in the next
+// launch and this launch has used it for the last time.
+bool droppable(const lt_ctx *c, const CState &s) {
+    if (s.dead_launch == c->launch_id) return true;
+    return s.next_dead_launch == c->launch_id &&
+           (s.last_use_launch != c->launch_id || s.last_use_group < c->cur_group);
+}
+
+// Victim for eviction, in this order:
+//   0. a droppable chunk (no transfer), least recently used first;
+//   1. a chunk this launch does not use again and did not write, then one it
+//      wrote (its output is the likely input of the next launch), least
+//      recently used first within each;
+//   2. a chunk this launch still needs: the one it needs last (the planner
+//      knows each chunk's last group in the launch; a chunk that the launch
+//      uses once is needed exactly then, so this is Belady's choice).
+// Plain LRU writes back bands the launch has just written while dead bands
+// hold their memory, and in a launch over more data than fits it evicts the
+// inputs it has not read yet (their last use was the previous launch) only to
+// fetch them again.
 bool pick_victim(lt_ctx *c, lt_array **va, int64_t *vc) {
-    uint64_t best = UINT64_MAX;
+    int best_cls = 4;
+    uint64_t best_key = 0;
     *va = nullptr;
     for (auto &ap : c->arrays) {
         lt_array *a = ap.get();
         for (size_t i = 0; i < a->cs.size(); ++i) {
             const CState &s = a->cs[i];
-            if (s.loc == LOC_DEV && s.pin == 0 && s.lru < best) {
-                best = s.lru;
+            if (s.loc != LOC_DEV || s.pin != 0) continue;
+            int cls;
+            uint64_t key;  // smaller is the better victim within a class
+            if (droppable(c, s)) {
+                cls = 0;
+                key = s.lru;
+            } else if (s.last_use_launch != c->launch_id || s.last_use_group < c->cur_group) {
+                cls = s.last_write_launch == c->launch_id ? 2 : 1;
+                key = s.lru;
+            } else {
+                cls = 3;
+                key = UINT64_MAX - (uint64_t)s.last_use_group;
+            }
+            if (cls < best_cls || (cls == best_cls && key < best_key)) {
+                best_cls = cls;
+                best_key = key;
                 *va = a;
                 *vc = (int64_t)i;
             }
@@ -506,9 +543,7 @@ lt_status dev_alloc(lt_ctx *c, size_t bytes, size_t *off, FenceSet *f) {
 lt_status evict(lt_ctx *c, lt_array *a, int64_t ci) {
     CState &s = a->cs[(size_t)ci];
     const ChunkGeom &cg = a->g.chunks[(size_t)ci];
-    bool next_dead = s.next_dead_launch == c->launch_id &&
-                     (s.last_use_launch != c->launch_id || s.last_use_group < c->cur_group);
-    if (s.dead_launch == c->launch_id || next_dead) {
+    if (droppable(c, s)) {
         // contents are overwritten unread in this launch, or in the next one
         // after their last use here: drop them instead of writing them back
         FenceSet f = s.busy;
@@ -1877,7 +1912,10 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 for (auto &pc : ap.replicas) add_use(a, pc.chunk, ap.kind == ARG_DIRECT);
             }
         }
-        for (auto &u : uses) u.a->cs[(size_t)u.chunk].pin++;
+        for (auto &u : uses) {
+            u.a->cs[(size_t)u.chunk].pin++;
+            if (u.write) u.a->cs[(size_t)u.chunk].last_write_launch = c->launch_id;
+        }
         for (auto &u : uses) {
             // a chunk whose region is only partly written must keep its data
             st = ensure_dev(c, u.a, u.chunk, true);

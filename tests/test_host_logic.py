@@ -291,8 +291,9 @@ def test_alternating_sweep_reuses_resident_chunks():
     ny, nx, band = 1024, 256, 64
     cb = (band + 2) * nx * 4
     res = {}
+    # 16 bands per array: the live data (one array) exceeds the 10-chunk budget
     for flags in (0, L.LT_FLAG_FIXED_SWEEP):
-        with dry(budget=20 * cb, host=40 * cb, flags=flags) as ctx:
+        with dry(budget=10 * cb, host=40 * cb, flags=flags) as ctx:
             U, V, k = _jacobi_ctx(ctx, ny, nx, lt.Dist.rows(band, halo=1))
             U.fill(L.LT_INIT_UNIFORM, seed=3)
             ctx.reset_stats()
@@ -374,3 +375,71 @@ def test_multi_step_annotation_must_cover_k_rings():
         assert e.value.code == L.LT_ERR_INVALID_ARG
         with pytest.raises(lt.LightningError):
             km.launch(grid=(64, 64), block=(64, 4), superblock=(64, 16), args=[U, V, 0])   # k out of range
+
+
+def test_plan_cache_reuses_plans_of_the_same_shape_only():
+    # the plan depends on grid, block, superblock and the arrays' geometry
+    # and aliasing, not on which arrays of that geometry are passed
+    with dry() as ctx:
+        U, V, k = _jacobi_ctx(ctx, 96, 128, lt.Dist.tiles((32, 64), halo=(1, 1)))
+        W = ctx.array(lt.F32, (96, 128), lt.Dist.rows(32, halo=1))
+        launch = dict(grid=(128, 96), block=(64, 4), superblock=(64, 32))
+        plan_uv = k.explain(args=[U, V], **launch)
+        ctx.reset_stats()
+        k.launch(args=[U, V], **launch)
+        k.launch(args=[V, U], **launch)                 # swapped arrays: same plan
+        assert ctx.stats()["plans_reused"] == 2          # both launches hit the cached plan
+        assert k.explain(args=[V, U], **launch) == plan_uv
+        ctx.reset_stats()
+        k.launch(args=[U, W], **launch)                 # other geometry for V
+        k.launch(grid=(128, 96), block=(64, 4), superblock=(64, 16), args=[U, V])  # other superblock
+        assert ctx.stats()["plans_reused"] == 0
+        plan_uw = k.explain(args=[U, W], **launch)
+        assert plan_uw != plan_uv
+        ctx.synchronize()
+
+
+def test_plan_cache_tells_aliased_arguments_apart():
+    # passing one array twice is a different plan input (the dead-data analysis
+    # differs), so it must not reuse the plan of two distinct arrays
+    with dry() as ctx:
+        A = ctx.array(lt.F32, (64,), lt.Dist.rows(16, halo=1))
+        B = ctx.array(lt.F32, (64,), lt.Dist.rows(16, halo=1))
+        k = ctx.kernel(lt.STENCIL1D, "global i => read input[i-1:i+1], write output[i]",
+                       [("n", lt.U32, False), ("output", lt.F32), ("input", lt.F32)])
+        ctx.reset_stats()
+        k.launch(grid=(64,), block=(16,), superblock=(16,), args=[64, B, A])
+        k.launch(grid=(64,), block=(16,), superblock=(16,), args=[64, A, A])
+        assert ctx.stats()["plans_reused"] == 0
+        k.launch(grid=(64,), block=(16,), superblock=(16,), args=[64, A, B])
+        assert ctx.stats()["plans_reused"] == 1
+        ctx.synchronize()
+
+
+def test_eviction_prefers_dead_and_finished_chunks():
+    # Two arrays of 16 bands, 20 chunk slots: one array (the live data of an
+    # iterative U -> V -> U loop) fits.  With the one-launch lookahead every
+    # band a launch has read is dead (the next launch overwrites it), so the
+    # steady state moves nothing over the host link.  The last launch, flushed
+    # without a successor, must write back what does not fit, but it never
+    # evicts an input it has yet to read (no fetches).
+    ny, nx, band = 1024, 256, 64
+    cb = (band + 2) * nx * 4
+    with dry(budget=20 * cb, host=40 * cb) as ctx:
+        U, V, k = _jacobi_ctx(ctx, ny, nx, lt.Dist.rows(band, halo=1))
+        U.fill(L.LT_INIT_UNIFORM, seed=3)
+        ctx.synchronize()
+        ctx.log_enable()
+        for it in range(8):
+            k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V])
+            U, V = V, U
+        ctx.synchronize()
+        log = ctx.log()
+        launches = sorted({t["launch"] for t in log if t["kind"] == "execute"})
+        assert len(launches) == 8
+        last = launches[-1]
+        moved = [(t["launch"], t["kind"]) for t in log if t["kind"] in ("fetch", "evict")]
+        assert all(l == last for l, _ in moved), moved          # nothing in the steady state
+        assert not any(kind == "fetch" for _, kind in moved)   # the flush only writes back
+        # both arrays are live after the flush: 32 chunks in 20 slots, so exactly 12 go to host
+        assert sum(1 for _, kind in moved if kind == "evict") == 32 - 20
