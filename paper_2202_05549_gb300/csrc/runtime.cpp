@@ -82,61 +82,77 @@ struct FenceSet {
     }
 };
 
-// Pool of one pre-allocated region; best-fit with coalescing.  Each free
-// block remembers the fences of the operations that last used its memory.
+// Pool of one pre-allocated region; best-fit, coalescing on demand.  Each
+// free block remembers the fences of the operations that last used its memory
+// and when it was released.  Freed blocks stay separate, each with its own
+// fences, and among equally good fits the block released longest ago is
+// reused first: the copy that freed the newest block is likely still running,
+// and reusing its memory would order the next copy behind it (for instance a
+// device-to-host eviction behind the host-to-device fetch that just released
+// a host block, which serialises the two directions of the link).  Only when
+// no single free block is large enough are adjacent blocks merged (and their
+// fences with them).
 struct Arena {
+    struct Free {
+        size_t size;
+        FenceSet f;
+        uint64_t tick;
+    };
     size_t cap = 0;
     char *base = nullptr;
-    std::map<size_t, std::pair<size_t, FenceSet>> free_;
+    std::map<size_t, Free> free_;
     size_t used = 0, peak = 0;
+    uint64_t tick = 0;
 
     void init(size_t c, char *b) {
         cap = c / ALIGN * ALIGN;
         base = b;
         free_.clear();
-        if (cap) free_[0] = {cap, FenceSet()};
+        if (cap) free_[0] = {cap, FenceSet(), 0};
         used = peak = 0;
     }
-    bool alloc(size_t sz, size_t *off, FenceSet *f) {
-        sz = size_class(sz);
+    bool take(size_t sz, size_t *off, FenceSet *f) {
         auto best = free_.end();
-        for (auto it = free_.begin(); it != free_.end(); ++it)
-            if (it->second.first >= sz && (best == free_.end() || it->second.first < best->second.first)) best = it;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second.size < sz) continue;
+            if (best == free_.end() || it->second.size < best->second.size ||
+                (it->second.size == best->second.size && it->second.tick < best->second.tick))
+                best = it;
+        }
         if (best == free_.end()) return false;
         *off = best->first;
-        *f = best->second.second;
-        size_t rem = best->second.first - sz;
-        FenceSet keep = best->second.second;
+        *f = best->second.f;
+        size_t rem = best->second.size - sz;
+        Free keep = best->second;
         free_.erase(best);
-        if (rem) free_[*off + sz] = {rem, keep};
+        if (rem) free_[*off + sz] = {rem, keep.f, keep.tick};
         used += sz;
         peak = std::max(peak, used);
         return true;
     }
+    void coalesce() {
+        for (auto it = free_.begin(); it != free_.end();) {
+            auto nx = std::next(it);
+            if (nx != free_.end() && it->first + it->second.size == nx->first) {
+                it->second.size += nx->second.size;
+                it->second.f.merge(nx->second.f);
+                it->second.tick = std::max(it->second.tick, nx->second.tick);
+                free_.erase(nx);
+            } else {
+                it = nx;
+            }
+        }
+    }
+    bool alloc(size_t sz, size_t *off, FenceSet *f) {
+        sz = size_class(sz);
+        if (take(sz, off, f)) return true;
+        coalesce();
+        return take(sz, off, f);
+    }
     void release(size_t off, size_t sz, const FenceSet &f) {
         sz = size_class(sz);
         used -= sz;
-        FenceSet fs = f;
-        auto it = free_.lower_bound(off);
-        if (it != free_.end() && it->first == off + sz) {
-            sz += it->second.first;
-            fs.merge(it->second.second);
-            it = free_.erase(it);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second.first == off) {
-                pv->second.first += sz;
-                pv->second.second.merge(fs);
-                return;
-            }
-        }
-        free_[off] = {sz, fs};
-    }
-    size_t largest_free() const {
-        size_t m = 0;
-        for (auto &kv : free_) m = std::max(m, kv.second.first);
-        return m;
+        free_[off] = {sz, f, ++tick};
     }
 };
 
@@ -527,14 +543,18 @@ bool pick_victim(lt_ctx *c, lt_array **va, int64_t *vc) {
     return *va != nullptr;
 }
 
-lt_status dev_alloc(lt_ctx *c, size_t bytes, size_t *off, FenceSet *f) {
+// soft: report a full budget as LT_ERR_OOM_DEVICE without recording an error
+// (a prefetch that does not fit is skipped, not failed)
+lt_status dev_alloc(lt_ctx *c, size_t bytes, size_t *off, FenceSet *f, bool soft = false) {
     for (;;) {
         if (c->dev.alloc(bytes, off, f)) return LT_OK;
         lt_array *va;
         int64_t vc;
-        if (!pick_victim(c, &va, &vc))
+        if (!pick_victim(c, &va, &vc)) {
+            if (soft) return LT_ERR_OOM_DEVICE;
             return fail(LT_ERR_OOM_DEVICE, "HBM budget too small: no evictable chunk left for a request of " +
                                                std::to_string(bytes) + " bytes");
+        }
         lt_status st = evict(c, va, vc);
         if (st) return st;
     }
@@ -590,19 +610,22 @@ lt_status evict(lt_ctx *c, lt_array *a, int64_t ci) {
 
 // Materialise chunk ci of a in device memory.  need_data: its current
 // contents must be preserved (fetched from host, or zero if never written).
-lt_status ensure_dev(lt_ctx *c, lt_array *a, int64_t ci, bool need_data) {
+lt_status ensure_dev(lt_ctx *c, lt_array *a, int64_t ci, bool need_data, bool soft = false) {
     CState &s = a->cs[(size_t)ci];
     const ChunkGeom &cg = a->g.chunks[(size_t)ci];
     s.lru = ++c->clock;
-    if (s.dead_launch == c->launch_id) need_data = false;
-    s.dead_launch = -1;  // first touch in this launch done
-    if (s.loc == LOC_DEV) return LT_OK;
+    if (s.loc == LOC_DEV) {
+        s.dead_launch = -1;  // first touch in this launch done
+        return LT_OK;
+    }
     s.pin++;
     size_t off;
     FenceSet bf;
-    lt_status st = dev_alloc(c, cg.bytes, &off, &bf);
+    lt_status st = dev_alloc(c, cg.bytes, &off, &bf, soft);
     s.pin--;
     if (st) return st;
+    if (s.dead_launch == c->launch_id) need_data = false;
+    s.dead_launch = -1;  // first touch in this launch done
     if (s.loc == LOC_HOST) {
         if (need_data) {
             op_begin(c, S_H2D, "fetch");
@@ -1886,9 +1909,8 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 for (auto &pc : ap.replicas) mark(pc.chunk);
             }
     }
-    c->cur_group = 0;
-    for (size_t g0 = 0; g0 < nsb; g0 += gsz, ++c->cur_group) {
-        size_t g1 = std::min(nsb, g0 + gsz);
+    // the chunks the superblocks [g0, g1) of this launch use
+    auto collect_uses = [&](size_t g0, size_t g1) {
         std::vector<ArgUse> uses;
         auto add_use = [&](lt_array *a, int64_t ci, bool w) {
             for (auto &u : uses)
@@ -1912,10 +1934,29 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 for (auto &pc : ap.replicas) add_use(a, pc.chunk, ap.kind == ARG_DIRECT);
             }
         }
+        return uses;
+    };
+    // Streaming: the next group's chunks are fetched (or allocated) while
+    // this group runs, so host-to-device copies overlap its kernels and the
+    // evictions that make room; `ahead` keeps them pinned until their group.
+    // Pinning them early also takes them out of the eviction choices, which
+    // costs more transfers than the overlap saves when the budget holds only
+    // a few groups (measured: with 3 groups' worth it lost 4 %, with 6 it
+    // gained 2 %), so it runs ahead only with at least 4 groups' worth.
+    std::vector<ArgUse> ahead;
+    auto unpin_ahead = [&]() {
+        for (auto &u : ahead) u.a->cs[(size_t)u.chunk].pin--;
+        ahead.clear();
+    };
+    c->cur_group = 0;
+    for (size_t g0 = 0; g0 < nsb; g0 += gsz, ++c->cur_group) {
+        size_t g1 = std::min(nsb, g0 + gsz);
+        std::vector<ArgUse> uses = collect_uses(g0, g1);
         for (auto &u : uses) {
             u.a->cs[(size_t)u.chunk].pin++;
             if (u.write) u.a->cs[(size_t)u.chunk].last_write_launch = c->launch_id;
         }
+        unpin_ahead();  // now pinned as this group's uses
         for (auto &u : uses) {
             // a chunk whose region is only partly written must keep its data
             st = ensure_dev(c, u.a, u.chunk, true);
@@ -1923,6 +1964,22 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 for (auto &v : uses) v.a->cs[(size_t)v.chunk].pin--;
                 return st;
             }
+        }
+        size_t group_bytes = 0;
+        for (auto &u : uses) group_bytes += align_up(u.a->g.chunks[(size_t)u.chunk].bytes, ALIGN);
+        if (!batched && g1 < nsb && c->dev.cap >= 4 * group_bytes) {
+            ahead = collect_uses(g1, std::min(nsb, g1 + gsz));
+            for (auto &u : ahead) u.a->cs[(size_t)u.chunk].pin++;
+            for (auto &u : ahead) {
+                st = ensure_dev(c, u.a, u.chunk, true, /*soft=*/true);
+                if (st == LT_ERR_OOM_DEVICE) break;  // no room to run ahead: fetch when the group starts
+                if (st) {
+                    unpin_ahead();
+                    for (auto &v : uses) v.a->cs[(size_t)v.chunk].pin--;
+                    return st;
+                }
+            }
+            st = LT_OK;
         }
         // temporaries for pack / temp-write
         std::vector<TempAlloc> temps;
