@@ -202,6 +202,24 @@ def link_peaks(local):
     return out
 
 
+def kernel_traffic(kernel, units):
+    """DRAM bytes of one launch of `kernel` processing `units` cells, scaled
+    from an ncu capture (profiles/traffic.json), or None when the kernel's
+    sources have changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, "paper_2202_05549_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None
+    return rec["dram_bytes_per_cell"] * units
+
+
 # ------------------------------------------------------------------ workloads
 def plan_ooc(args, world):
     """HBM budget and host pool for the out-of-core grid on this machine."""
@@ -320,7 +338,8 @@ def run_lightning(args, rank, world, local, grp):
                    "l2": "inputs larger than L2 (129 MB)" if args.workload == "ooc"
                    else "working set 128 MiB ~ L2 size; not flushed"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                     "frac": round(achieved / peaks["hbm_gbs"], 4),
+                     "traffic": None if tb > 1 else kernel_traffic("jacobi2d_vec_kernel", cells_per_launch),
                      "kernel": "jacobi2d_multi_kernel" if tb > 1 else "jacobi2d_vec_kernel", "launch_ms": round(ex_ms, 4),
                      "bytes_per_launch": 8.0 * cells_per_launch, "peak_source": peaks["source"]},
         "host_link": {"bytes_h2d_per_step": st["bytes_h2d"] / args.steps,
