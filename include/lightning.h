@@ -413,6 +413,17 @@ lt_status lt_debug_log(lt_ctx *ctx, char *buf, size_t cap, size_t *needed);
 lt_status lt_jacobi2d_packed_noalloc(const float *U, float *V, int64_t ny, int64_t nx, int64_t ld_u, int64_t ld_v,
                                      int64_t tile_rows, int64_t tile_cols, void *stream);
 
+/* ---- self-test of the stencils' constant divisions (no paper counterpart) --
+ * The Jacobi built-ins divide their sums by 5 (2-D) and 7 (3-D) with a
+ * correctly rounded three-instruction sequence (Markstein's correction step)
+ * instead of a full IEEE division.  This call runs that sequence on `device`
+ * for all 2^32 float bit patterns and counts the inputs where it differs
+ * from the IEEE quotient (any two NaNs count as equal) into *mismatches
+ * (0 expected).  divisor: 5 or 7.  Synchronous; allocates 8 bytes of device
+ * memory for the count.  Errors: LT_ERR_INVALID_ARG (other divisor, null
+ * output), LT_ERR_CUDA (a CUDA call failed). */
+lt_status lt_selftest_div_const(int32_t device, int32_t divisor, uint64_t *mismatches);
+
 #ifdef __cplusplus
 }
 #endif

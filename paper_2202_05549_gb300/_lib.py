@@ -124,6 +124,7 @@ SIGNATURES = {
     "lt_debug_log": (_st, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "lt_jacobi2d_packed_noalloc": (_st, [_vp, _vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
                                          C.c_int64, _vp]),
+    "lt_selftest_div_const": (_st, [C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]),
 }
 
 _lib = None

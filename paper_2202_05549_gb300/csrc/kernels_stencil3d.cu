@@ -1,7 +1,8 @@
 // 3-D 7-point Jacobi built-in:
 //   "global [k, i, j] => read U[k-1:k+1, i-1:i+1, j-1:j+1], write V[k, i, j]"
 //   V = ((((((U + U[k-1]) + U[k+1]) + U[i-1]) + U[i+1]) + U[j-1]) + U[j+1]) / 7
-// zero outside the domain, __fadd_rn / __fdiv_rn in that fixed order.
+// zero outside the domain, __fadd_rn in that fixed order, then a correctly
+// rounded division by 7 (div_const_rn).
 // Each CTA owns a 16 x 128 (i, j) tile and sweeps a run of planes along k:
 // the current plane is staged in shared memory (with a one-cell ring) for
 // the i and j neighbours, the planes above and below stay in registers.
@@ -9,6 +10,7 @@
 
 #include <algorithm>
 
+#include "div_const.cuh"
 #include "kernels.cuh"
 #include "task_lookup.cuh"
 
@@ -29,7 +31,7 @@ __device__ __forceinline__ float j7(float c, float zm, float zp, float ym, float
     a = __fadd_rn(a, yp);
     a = __fadd_rn(a, xm);
     a = __fadd_rn(a, xp);
-    return __fdiv_rn(a, 7.0f);
+    return div_const_rn<7>(a);
 }
 
 struct Geo3 {

@@ -1,12 +1,15 @@
 // Device bodies shared by the stencil kernels (single launches and the
 // batched persistent kernel).
 //   V[i,j] = ((((U[i,j] + U[i-1,j]) + U[i+1,j]) + U[i,j-1]) + U[i,j+1]) / 5,
-// zero outside the NY x NX domain, __fadd_rn / __fdiv_rn (no contraction).
+// zero outside the NY x NX domain, __fadd_rn in that order and a correctly
+// rounded division (no contraction).
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include <cstdint>
+
+#include "div_const.cuh"
 
 namespace lt {
 
@@ -18,7 +21,7 @@ __device__ __forceinline__ float j5(float c, float n, float s, float w, float e)
     acc = __fadd_rn(acc, s);
     acc = __fadd_rn(acc, w);
     acc = __fadd_rn(acc, e);
-    return __fdiv_rn(acc, 5.0f);
+    return div_const_rn<5>(acc);
 }
 
 template <bool L2ONLY>

@@ -206,6 +206,46 @@ def test_multi_step_jacobi_bit_exact(k, dist_name):
     assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
 
 
+@pytest.mark.parametrize("k", [3, 10, 16])
+@pytest.mark.parametrize("dist_name", ["block", "rows_halo_k"])
+def test_multi_step_tall_grid_bit_exact(k, dist_name):
+    # more rows than one warp segment (512) and columns that end mid-window
+    ny, nx, launches = 1500, 700, 3
+    u0 = si.uniform_field(si.SEED_JACOBI_INCORE, 8, ny, nx)
+    want = oracle.jacobi2d(u0, k * launches)
+    dist, sb = {"block": (lt.Dist.block(), (0, 0)),
+                "rows_halo_k": (lt.Dist.rows(400, halo=k), (nx, 400))}[dist_name]
+    with lt.Context() as ctx:
+        U = ctx.array(lt.F32, (ny, nx), dist)
+        V = ctx.array(lt.F32, (ny, nx), dist)
+        U.write(u0)
+        km = ctx.kernel(lt.JACOBI2D_MULTI, MANN.format(k=k), [("U", lt.F32), ("V", lt.F32), ("k", lt.U32, False)])
+        for _ in range(launches):
+            km.launch(grid=(nx, ny), block=(128, 4), superblock=sb, args=[U, V, k])
+            U, V = V, U
+        ctx.synchronize()
+        got = U.read()
+    assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
+
+
+def test_multi_step_unaligned_superblocks_bit_exact():
+    # superblocks that start at columns not divisible by 4 take the shared-memory variant
+    ny, nx, k, launches = 200, 390, 3, 2
+    u0 = si.uniform_field(si.SEED_JACOBI_INCORE, 9, ny, nx)
+    want = oracle.jacobi2d(u0, k * launches)
+    with lt.Context() as ctx:
+        U = ctx.array(lt.F32, (ny, nx), lt.Dist.block())
+        V = ctx.array(lt.F32, (ny, nx), lt.Dist.block())
+        U.write(u0)
+        km = ctx.kernel(lt.JACOBI2D_MULTI, MANN.format(k=k), [("U", lt.F32), ("V", lt.F32), ("k", lt.U32, False)])
+        for _ in range(launches):
+            km.launch(grid=(nx, ny), block=(2, 2), superblock=(130, 66), args=[U, V, k])
+            U, V = V, U
+        ctx.synchronize()
+        got = U.read()
+    assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
+
+
 def test_multi_step_out_of_core_spill_bit_exact():
     ny, nx, band, k, launches = 1024, 2048, 64, 4, 3
     cb = (band + 2 * k) * nx * 4
