@@ -76,6 +76,8 @@ def lib():
                 "orc_jacobi2d_f64_ring": (C.c_int, [_i64, _i64, _p, C.c_int, C.c_int]),
                 "orc_jacobi2d_f32_lightcone": (C.c_int, [_i64, _i64, _u64, _u64, C.c_int, _i64, _p, _p, _p]),
                 "orc_jacobi3d_f32": (C.c_int, [_i64, _i64, _i64, _p, _p, C.c_int]),
+                "orc_kmeans_assign": (None, [_i64, _i64, _p, _p, _p, _p]),
+                "orc_kmeans_update": (None, [_i64, _p, _p, _p]),
                 "orc_jacobi3d_f64": (C.c_int, [_i64, _i64, _i64, _p, C.c_int]),
                 "orc_gemm_f64": (None, [_i64, _i64, _i64, _p, _p, _p]),
                 "orc_gemm_sample_f64": (C.c_int, [_i64, _i64, _i64, _u64, _u64, _u64, C.c_double,
@@ -273,6 +275,27 @@ def diffusion_lightcone(NY, NX, seed, stream_u, stream_k, T, si, sj):
 
 
 # ---------------------------------------------------------------- planner
+def kmeans_assign(x: np.ndarray, c: np.ndarray):
+    """One K-Means assignment (Sec. 4 K-Means benchmark): x (n, 4) f32 records,
+    c (k, 4) f32 centres -> (s (k, 5) fp64 feature sums and counts, labels (n,))."""
+    x = np.ascontiguousarray(x, np.float32)
+    c = np.ascontiguousarray(c, np.float32)
+    n, k = x.shape[0], c.shape[0]
+    s = np.zeros((k, 5), np.float64)
+    lab = np.zeros(n, np.int32)
+    lib().orc_kmeans_assign(n, k, _ptr(x), _ptr(c), _ptr(s), _ptr(lab))
+    return s, lab
+
+
+def kmeans_update(s: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """New centres from the sums and counts of kmeans_assign (empty clusters keep theirs)."""
+    s = np.ascontiguousarray(s, np.float64)
+    c = np.ascontiguousarray(c, np.float32)
+    out = np.empty_like(c)
+    lib().orc_kmeans_update(c.shape[0], _ptr(s), _ptr(c), _ptr(out))
+    return out
+
+
 def access_region_bruteforce(thread_box, accesses, shape):
     """Access region of one superblock for one array, by enumeration.
 

@@ -562,3 +562,45 @@ int orc_diff_lightcone_f64(int64_t NY, int64_t NX, uint64_t seed, uint64_t strea
     }
     return failed ? -1 : 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* K-Means (Lloyd's algorithm), as the K-Means benchmark of Sec. 4 runs it:  */
+/* n records of 4 f32 features (record i = x[4i .. 4i+3]) and k centres      */
+/* (c[4j .. 4j+3]).  The paper computes the centres on the GPU with a        */
+/* reduction; one iteration is                                               */
+/*  assignment: every record joins its nearest centre by squared Euclidean   */
+/*   distance in f32: with d_f = x_f - c_f, dist = fma(d3, d3, fma(d2, d2,   */
+/*   fma(d1, d1, d0 * d0))) (each operation rounded once), ties going to     */
+/*   the lowest centre index;                                                */
+/*  reduction: per centre the fp64 sums of its records' features and their  */
+/*   count, s[5j .. 5j+3] and s[5j+4];                                       */
+/*  update: centre j becomes f32(sum / count) (fp64 division, then rounded   */
+/*   to f32), or keeps its value when no record chose it.                    */
+/* ------------------------------------------------------------------------ */
+void orc_kmeans_assign(int64_t n, int64_t k, const float *x, const float *c, double *s, int32_t *label) {
+    memset(s, 0, (size_t)(5 * k) * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        const float *r = x + 4 * i;
+        int64_t best = 0;
+        float bd = 0.0f;
+        for (int64_t j = 0; j < k; ++j) {
+            const float *m = c + 4 * j;
+            float d0 = r[0] - m[0], d1 = r[1] - m[1], d2 = r[2] - m[2], d3 = r[3] - m[3];
+            float d = fmaf(d3, d3, fmaf(d2, d2, fmaf(d1, d1, d0 * d0)));
+            if (j == 0 || d < bd) {
+                bd = d;
+                best = j;
+            }
+        }
+        for (int f = 0; f < 4; ++f) s[5 * best + f] += (double)r[f];
+        s[5 * best + 4] += 1.0;
+        if (label) label[i] = (int32_t)best;
+    }
+}
+
+void orc_kmeans_update(int64_t k, const double *s, const float *c, float *c_new) {
+    for (int64_t j = 0; j < k; ++j) {
+        double cnt = s[5 * j + 4];
+        for (int f = 0; f < 4; ++f) c_new[4 * j + f] = cnt > 0.0 ? (float)(s[5 * j + f] / cnt) : c[4 * j + f];
+    }
+}

@@ -356,3 +356,71 @@ def test_rowreduce_closed_forms_and_brute_force():
     one = np.array([[2.5], [-0.5]])
     for op in ("+", "*", "min", "max"):
         assert list(oracle.rowreduce(one, op)) == [2.5, -0.5]
+
+
+# ------------------------------------------------------------------ K-Means
+def test_kmeans_constructed_clusters_exact_means():
+    # three well separated centres; every record is its centre plus an offset
+    # that is a multiple of 2^-10 below 0.1, so the labels are known by
+    # construction and the new centres are exact rational means rounded to f32
+    rng = np.random.default_rng(11)
+    true_c = np.array([[1, 1, 1, 1], [5, 1, 1, 1], [1, 5, 5, 1]], np.float32)
+    n = 300
+    lab_true = rng.integers(0, 3, n)
+    off = rng.integers(-100, 101, (n, 4)) / 1024.0
+    x = (true_c[lab_true] + off).astype(np.float32)
+    start = true_c + np.float32(0.25)
+    s, lab = oracle.kmeans_assign(x, start)
+    assert np.array_equal(lab, lab_true)
+    for j in range(3):
+        members = x[lab_true == j].astype(np.float64)
+        assert s[j, 4] == len(members)
+        for f in range(4):
+            exact = sum(Fraction(float(v)) for v in members[:, f])
+            assert Fraction(s[j, f]) == exact                     # fp64 sums of 2^-10 multiples are exact
+    c1 = oracle.kmeans_update(s, start)
+    for j in range(3):
+        members = x[lab_true == j]
+        for f in range(4):
+            mean = sum(Fraction(float(v)) for v in members[:, f]) / len(members)
+            assert c1[j, f] == np.float32(float(mean))
+
+
+def test_kmeans_ties_go_to_the_lowest_centre():
+    x = np.zeros((1, 4), np.float32)
+    c = np.array([[2, 0, 0, 0], [-1, 0, 0, 0], [1, 0, 0, 0]], np.float32)  # centres 1 and 2 equidistant
+    s, lab = oracle.kmeans_assign(x, c)
+    assert lab[0] == 1 and s[1, 4] == 1 and s[0, 4] == 0 and s[2, 4] == 0
+
+
+def test_kmeans_invariants_and_optimal_assignment():
+    # uniform features (multiples of 2^-24 in [0, 1)): counts add up to n, the
+    # sums are conserved exactly, and each record's centre is nearest in fp64
+    # up to f32 rounding of the distances
+    n, k = 5000, 40
+    x = si.uniform_field(2209, 0, n, 4)
+    c = x[:k].copy()
+    s, lab = oracle.kmeans_assign(x, c)
+    assert s[:, 4].sum() == n and np.array_equal(np.bincount(lab, minlength=k), s[:, 4].astype(np.int64))
+    for f in range(4):
+        assert math.fsum(s[:, f]) == math.fsum(x[:, f].astype(np.float64))
+    d = ((x.astype(np.float64)[:, None, :] - c.astype(np.float64)[None, :, :]) ** 2).sum(axis=2)
+    chosen = d[np.arange(n), lab]
+    assert np.all(chosen <= d.min(axis=1) * (1 + 4 * 2.0**-23) + 1e-12)
+
+
+def test_kmeans_lloyd_objective_never_increases_and_empty_cluster_keeps_centre():
+    n, k = 4000, 12
+    x = si.uniform_field(2209, 1, n, 4)
+    c = x[:k].copy()
+    c[-1] = 50.0  # no record comes near this centre
+    prev = math.inf
+    for _ in range(6):
+        s, lab = oracle.kmeans_assign(x, c)
+        obj = float(((x.astype(np.float64) - c.astype(np.float64)[lab]) ** 2).sum())
+        assert obj <= prev * (1 + 1e-6)
+        prev = obj
+        assert s[k - 1, 4] == 0
+        c_new = oracle.kmeans_update(s, c)
+        assert np.array_equal(c_new[k - 1], c[k - 1])
+        c = c_new
