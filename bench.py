@@ -35,7 +35,11 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lightning", choices=["lightning", "reference"])
-    p.add_argument("--workload", default="ooc", choices=["ooc", "incore", "gemm", "batch", "adjoint"])
+    p.add_argument("--workload", default="ooc", choices=["ooc", "incore", "gemm", "batch", "adjoint", "jacobi3d", "kmeans"])
+    p.add_argument("--records", type=int, default=1_000_000_000, help="records of the kmeans workload")
+    p.add_argument("--clusters", type=int, default=40, help="centres of the kmeans workload")
+    p.add_argument("--n3", type=int, default=1024, help="side of the cubic grid of the jacobi3d workload")
+    p.add_argument("--slab", type=int, default=128, help="planes per z-slab chunk of the jacobi3d workload")
     p.add_argument("--adj-n", type=int, default=16384, help="grid side of the adjoint workload")
     p.add_argument("--batch-scale", type=int, default=1, help="divide the batch instance counts by this")
     p.add_argument("--gemm-n", type=int, default=65536, help="M = N = K of the GEMM workload")
@@ -44,7 +48,8 @@ def parse():
     p.add_argument("--cols", type=int, default=131072, help="grid columns (ooc)")
     p.add_argument("--band", type=int, default=8192)
     p.add_argument("--hbm-gib", type=float, default=0.0,
-                   help="cap the HBM budget (GiB); below one array's size the launches stream every step")
+                   help="cap the HBM budget (GiB): out-of-core, below one array the launches stream every step; "
+                        "the other workloads take it as their pool size")
     p.add_argument("--tb", type=int, default=1, help="Jacobi iterations per launch (temporal blocking, halo = tb)")
     p.add_argument("--iters", type=int, default=0,
                    help="Jacobi iterations per step (one run of the workload; default 20 out-of-core, 10 in-core)")
@@ -202,6 +207,13 @@ def link_peaks(local):
     return out
 
 
+def hbm_cap(args):
+    """HBM pool of the in-HBM workloads: --hbm-gib if given (small pools let
+    ncu's kernel replay save and restore device memory), else 0 = the library
+    default, 90 % of free HBM."""
+    return int(args.hbm_gib * 2**30) if args.hbm_gib > 0 else 0
+
+
 def kernel_traffic(kernel, units):
     """DRAM bytes of one launch of `kernel` processing `units` cells, scaled
     from an ncu capture (profiles/traffic.json), or None when the kernel's
@@ -269,7 +281,7 @@ def run_lightning(args, rank, world, local, grp):
     else:
         ny = nx = 4096
         pl = dict(budget=0, host=0, chunk_bytes=None, data_bytes=2 * ny * nx * 4)
-        ctx = lt.Context(device=local, flags=L.LT_FLAG_TIMING)
+        ctx = lt.Context(device=local, hbm_budget=hbm_cap(args), flags=L.LT_FLAG_TIMING)
         sb = (1024, 1024)
         band = 1024
         seed = si.SEED_JACOBI_INCORE
@@ -379,6 +391,170 @@ def run_lightning(args, rank, world, local, grp):
     return res
 
 
+def run_jacobi3d(args, rank, world, local, grp):
+    """3-D 7-point Jacobi over z-slab chunks with a one-plane halo (in HBM)."""
+    from paper_2202_05549_gb300 import _lib as L
+    from paper_2202_05549_gb300 import lightning as lt
+
+    peaks = measured_peaks()
+    n, slab = args.n3, args.slab
+    iters = args.iters or 10
+    ctx = lt.Context(device=local, hbm_budget=hbm_cap(args), flags=L.LT_FLAG_TIMING)
+    dist = lt.Dist.rows(slab, halo=1)
+    U = ctx.array(lt.F32, (n, n, n), dist)
+    V = ctx.array(lt.F32, (n, n, n), dist)
+    U.fill(L.LT_INIT_UNIFORM, seed=2208, stream=0)
+    ann = "global [k, i, j] => read U[k-1:k+1, i-1:i+1, j-1:j+1], write V[k, i, j]"
+    k = ctx.kernel(lt.JACOBI3D, ann, [("U", lt.F32), ("V", lt.F32)])
+    bufs = [U, V]
+
+    def step():
+        for _ in range(iters):
+            k.launch(grid=(n, n, n), block=(128, 4, 1), superblock=(n, n, slab), args=[bufs[0], bufs[1]])
+            bufs.reverse()
+        ctx.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    ctx.reset_stats()
+    grp.barrier()
+    clk = Clocks(local)
+    ctx.timer_start()
+    for _ in range(args.steps):
+        step()
+    ms = ctx.timer_stop()
+    clocks = clk.stop()
+    ctx.synchronize()
+    st = ctx.stats()
+    cells = n * n * n * iters
+    t_max = grp.max(ms / 1e3)
+    value = grp.sum(8.0 * cells * args.steps / 1e9) / t_max
+    n_ex = max(1, st["n_execute_kernels"])
+    ex_ms = st["ms_execute"] / n_ex
+    per_launch = 8.0 * cells * args.steps / n_ex
+    achieved = per_launch / (ex_ms / 1e3) / 1e9
+    res = {
+        "metric": "annotated-launch GB/s (8 B per cell-update) vs HBM roofline",
+        "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_max * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64 uniform[0,1))",
+        "config": {"workload": f"3-D 7-point Jacobi f32 {n}^3, {slab}-plane z-slabs + 1-plane halo, "
+                               f"{iters} iterations per step", "grid": [n, n, n], "iterations_per_step": iters,
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (129 MB)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": kernel_traffic("jacobi3d_vec_kernel", per_launch / 8.0),
+                     "kernel": "jacobi3d_vec_kernel", "launch_ms": round(ex_ms, 4), "bytes_per_launch": per_launch,
+                     "peak_source": peaks["source"]},
+        "copy_kernels_ms_per_step": round(st["ms_copy_kernels"] / args.steps, 3),
+        "gpu_launches": st["kernels"],
+        "clocks": clocks,
+    }
+    if not args.no_e2e:
+        ctx.reset_stats()
+        t0 = time.perf_counter()
+        nstep = max(1, args.steps // 2)
+        for _ in range(nstep):
+            step()
+            plane = bufs[0].read_box((n // 2, 0, 0), (n // 2, n - 1, n - 1))
+        t1 = time.perf_counter()
+        e2e = grp.sum(8.0 * cells * nstep / 1e9) / grp.max(t1 - t0)
+        res["e2e"] = {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                      "d2h_bytes_per_step": int(plane.nbytes),
+                      "how": "public Python API, wall clock; per step: the step's launches, a synchronize and a "
+                             "host read of the middle plane of its result"}
+    ctx.close()
+    return res
+
+
+def fp32_peak_tflops(sm_mhz=None):
+    """FP32 FMA peak from unit counts and clocks: 152 SMs x 128 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
+def run_kmeans(args, rank, world, local, grp):
+    """K-Means (the Sec. 4 benchmark): n records of 4 f32 features, k centres,
+    25M records per chunk; a step is 5 Lloyd iterations (assignment with a
+    reduce(+) of per-centre sums and counts, then the centre update)."""
+    from paper_2202_05549_gb300 import _lib as L
+    from paper_2202_05549_gb300 import lightning as lt
+
+    n, k = args.records, args.clusters
+    iters = args.iters or 5
+    per_chunk = 25_000_000
+    ctx = lt.Context(device=local, hbm_budget=hbm_cap(args), flags=L.LT_FLAG_TIMING)
+    X = ctx.array(lt.F32, (4 * n,), lt.Dist.rows(4 * per_chunk))
+    C = ctx.array(lt.F32, (4 * k,), lt.Dist.block())
+    C2 = ctx.array(lt.F32, (4 * k,), lt.Dist.block())
+    S = ctx.array(lt.F64, (5 * k,), lt.Dist.block())
+    X.fill(L.LT_INIT_UNIFORM, seed=2209, stream=0)
+    C.write(X.read_box((0,), (4 * k - 1,)))  # the first k records start as centres
+    ka = ctx.kernel(lt.KMEANS_ASSIGN, "global i => read X[4*i:4*i+3], read C[:], reduce(+) S[:]",
+                    [("X", lt.F32), ("C", lt.F32), ("S", lt.F64), ("k", lt.U32, False)])
+    ku = ctx.kernel(lt.KMEANS_UPDATE, "global j => read S[5*j:5*j+4], read C[4*j:4*j+3], write C2[4*j:4*j+3]",
+                    [("S", lt.F64), ("C", lt.F32), ("C2", lt.F32)])
+    cen = [C, C2]
+
+    def step():
+        for _ in range(iters):
+            ka.launch(grid=(n,), block=(256,), superblock=(per_chunk,), args=[X, cen[0], S, k])
+            ku.launch(grid=(k,), block=(64,), superblock=(0,), args=[S, cen[0], cen[1]])
+            cen.reverse()
+        ctx.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    ctx.reset_stats()
+    grp.barrier()
+    clk = Clocks(local)
+    ctx.timer_start()
+    for _ in range(args.steps):
+        step()
+    ms = ctx.timer_stop()
+    clocks = clk.stop()
+    ctx.synchronize()
+    st = ctx.stats()
+    t_max = grp.max(ms / 1e3)
+    rec_it = float(n) * iters * args.steps
+    value = grp.sum(16.0 * rec_it / 1e9) / t_max
+    # dominant kernel: the assignment (one execute kernel per launch); the
+    # update kernels take a few microseconds and are counted with it
+    assign_launches = iters * args.steps
+    flops = 11.0 * k * n  # per assignment: 4 sub + 1 mul + 3 fma per centre and record
+    assign_ms = st["ms_execute"] / assign_launches  # the update kernels are a few microseconds
+    peak = fp32_peak_tflops(clocks.get("sm_mhz"))
+    achieved = flops / (assign_ms / 1e3) / 1e12
+    res = {
+        "metric": "K-Means GB/s (16 B per record per iteration) vs FP32 ALU roofline",
+        "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_max * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (fp64 sums)", "data": "synthetic (seeded SplitMix64 uniform[0,1))",
+        "config": {"workload": f"K-Means {n} records x 4 features, k={k}, {per_chunk} records per chunk, "
+                               f"{iters} iterations per step", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (129 MB)"},
+        "roofline": {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "kernel": "kmeans_assign_kernel",
+                     "launch_ms": round(assign_ms, 4), "flops_per_launch": flops,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x median SM clock (derived)",
+                     "hbm_GBs_of_assignment": round(16.0 * n / (assign_ms / 1e3) / 1e9, 1)},
+        "gpu_launches": st["kernels"],
+        "clocks": clocks,
+    }
+    if not args.no_e2e:
+        ctx.reset_stats()
+        t0 = time.perf_counter()
+        nstep = max(1, args.steps // 2)
+        for _ in range(nstep):
+            step()
+            centres = cen[0].read()
+        t1 = time.perf_counter()
+        res["e2e"] = {"value": round(grp.sum(16.0 * n * iters * nstep / 1e9) / grp.max(t1 - t0), 2), "unit": "GB/s",
+                      "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(centres.nbytes),
+                      "how": "public Python API, wall clock; per step: the iterations, a synchronize and a host "
+                             "read of the centres"}
+    ctx.close()
+    return res
+
+
 def run_gemm(args, rank, world, local, grp):
     from paper_2202_05549_gb300 import _lib as L
     from paper_2202_05549_gb300 import lightning as lt
@@ -386,7 +562,7 @@ def run_gemm(args, rank, world, local, grp):
 
     peaks = measured_peaks()
     n, t = args.gemm_n, args.gemm_tile
-    ctx = lt.Context(device=local, flags=L.LT_FLAG_TIMING)
+    ctx = lt.Context(device=local, hbm_budget=hbm_cap(args), flags=L.LT_FLAG_TIMING)
     A = ctx.array(lt.BF16, (n, n), lt.Dist.rows(t))
     B = ctx.array(lt.BF16, (n, n), lt.Dist.cols(t, order=L.LT_ORDER_COL))
     Cm = ctx.array(lt.F32, (n, n), lt.Dist.tiles((t, t)))
@@ -447,7 +623,7 @@ def run_batch(args, rank, world, local, grp):
     r = si.BatchRecipe()
     sides = r.sides()[: r.n_jacobi // args.batch_scale]
     lens = r.hist_lengths()[: r.n_hist // args.batch_scale]
-    ctx = lt.Context(device=local, flags=L.LT_FLAG_TIMING)
+    ctx = lt.Context(device=local, hbm_budget=hbm_cap(args), flags=L.LT_FLAG_TIMING)
     kj = ctx.kernel(lt.JACOBI2D, "global [i, j] => read U[i-1:i+1, j-1:j+1], write V[i, j]",
                     [("U", lt.F32), ("V", lt.F32)])
     kh = ctx.kernel(lt.HIST256, "global i => read X[i], reduce(+) H[:]", [("X", lt.U8), ("H", lt.U32)])
@@ -584,6 +760,35 @@ def cpu_baseline(args, threads=None, budget_s=15.0):
     if threads:
         oracle.set_threads(threads)
     cores = oracle.max_threads()
+    if args.workload == "kmeans":
+        nrec, kc = 1_000_000, args.clusters
+        x = oracle.gen_uniform_f32(2209, 0, 0, 4 * nrec).reshape(nrec, 4)
+        c = x[:kc].copy()
+        t0 = time.perf_counter()
+        done = 0
+        while True:
+            s_, _ = oracle.kmeans_assign(x, c)
+            c = oracle.kmeans_update(s_, c)
+            done += nrec
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+        return {"value": round(16.0 * done / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                "sample": f"{nrec} records, k={kc}, one Lloyd iteration per call (single-threaded C), "
+                          f"repeated for ~{budget_s:.0f}s"}
+    if args.workload == "jacobi3d":
+        nz, ny3, nx3 = 64, 512, 512
+        u3 = si.uniform_field(2208, 0, nz * ny3, nx3).reshape(nz, ny3, nx3)
+        t0 = time.perf_counter()
+        done = 0
+        while True:
+            oracle.jacobi3d(u3, 2)
+            done += nz * ny3 * nx3 * 2
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+        return {"value": round(8.0 * done / dt / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                "sample": f"{nz}x{ny3}x{nx3} block, 2 iterations per call, repeated for ~{budget_s:.0f}s"}
     nx = args.cols if args.workload == "ooc" else 4096
     rows = 256 if args.workload == "ooc" else 4096
     iters = 2
@@ -631,6 +836,10 @@ def main():
     elif args.workload == "adjoint":
         res = run_adjoint(args, rank, world, local, grp)
         args.no_cpu = True
+    elif args.workload == "jacobi3d":
+        res = run_jacobi3d(args, rank, world, local, grp)
+    elif args.workload == "kmeans":
+        res = run_kmeans(args, rank, world, local, grp)
     else:
         res = run_lightning(args, rank, world, local, grp)
     grp.barrier()

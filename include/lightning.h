@@ -67,7 +67,8 @@ typedef enum {
     LT_F32 = 0,
     LT_BF16 = 1,
     LT_U8 = 2,
-    LT_U32 = 3
+    LT_U32 = 3,
+    LT_F64 = 4
 } lt_dtype;
 
 /* ---- distributions (Sec. 2.2; StencilDist / row-wise / column-wise /
@@ -227,6 +228,11 @@ typedef enum {
     LT_K_DIFFUSION2D_ADJ = 7, /* adjoint step: reduce(+) of the transposed stencil */
     LT_K_ROWREDUCE = 8,       /* "read A[i, j], reduce(f) S[i]" (Sec. 2.3), f32, f in + * min max */
     LT_K_JACOBI2D_MULTI = 9,  /* k Jacobi iterations per launch (value parameter k, 1..16), reads U[i-k:i+k, j-k:j+k] */
+    LT_K_KMEANS_ASSIGN = 10,  /* K-Means (Sec. 4): X (f32, 4 features per record, flat), C (f32, k x 4, flat),
+                               * reduce(+) S (f64, k x 5: feature sums and count per centre); value parameter
+                               * k (1..64); "global i => read X[4*i:4*i+3], read C[:], reduce(+) S[:]" */
+    LT_K_KMEANS_UPDATE = 11,  /* new centres: C2[4j+f] = f32(S[5j+f] / S[5j+4]), or C[4j+f] when the count
+                               * is 0; "global j => read S[5*j:5*j+4], read C[4*j:4*j+3], write C2[4*j:4*j+3]" */
     LT_K_USER = 100           /* (kernels from lt_kernel_register_source) */
 } lt_builtin;
 

@@ -24,7 +24,7 @@ LT_ERR_DEVICE_CHECK = -9
 LT_ERR_COMPILE = -10
 
 # dtypes
-LT_F32, LT_BF16, LT_U8, LT_U32 = 0, 1, 2, 3
+LT_F32, LT_BF16, LT_U8, LT_U32, LT_F64 = 0, 1, 2, 3, 4
 # distributions
 LT_DIST_BLOCK, LT_DIST_ROWS, LT_DIST_COLS, LT_DIST_TILES = 0, 1, 2, 3
 LT_ORDER_ROW, LT_ORDER_COL = 0, 1
@@ -38,6 +38,7 @@ LT_K_PLAN_ONLY = 0
 LT_K_USER = 100
 LT_K_STENCIL1D, LT_K_JACOBI2D, LT_K_JACOBI3D, LT_K_GEMM_BF16, LT_K_HIST256 = 1, 2, 3, 4, 5
 LT_K_DIFFUSION2D, LT_K_DIFFUSION2D_ADJ, LT_K_ROWREDUCE, LT_K_JACOBI2D_MULTI = 6, 7, 8, 9
+LT_K_KMEANS_ASSIGN, LT_K_KMEANS_UPDATE = 10, 11
 
 
 class lt_dist(C.Structure):

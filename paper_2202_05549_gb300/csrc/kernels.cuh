@@ -162,6 +162,10 @@ uint32_t prepare_diffusion_adj(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_diffusion_adj(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_rowreduce(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_rowreduce(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
+uint32_t prepare_kmeans_assign(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_kmeans_assign(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
+uint32_t prepare_kmeans_update(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_kmeans_update(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_hist256(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_hist256(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_gemm_bf16(ExecTask *t, int n, ExecParams &p);

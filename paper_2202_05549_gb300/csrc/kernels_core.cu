@@ -95,6 +95,10 @@ __global__ void fill_kernel(FillDesc d) {
                     ((unsigned char *)d.dst.base)[addr_el] = v;
                     break;
                 }
+                case 4: {  // f64
+                    ((double *)d.dst.base)[addr_el] = d.kind == 1 ? d.value : 0.0;
+                    break;
+                }
                 default: {  // u32
                     uint32_t v = d.kind == 1 ? (uint32_t)d.value : 0u;
                     ((uint32_t *)d.dst.base)[addr_el] = v;
@@ -255,6 +259,8 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ReducePiece *__restri
             reduce_one<uint32_t>(p, srcs, idx);
         else if (p.dtype == 2)
             reduce_one<unsigned char>(p, srcs, idx);
+        else if (p.dtype == 4)
+            reduce_one<double>(p, srcs, idx);
     }
 }
 

@@ -1,0 +1,231 @@
+// K-Means built-ins: one Lloyd iteration of the K-Means benchmark of Sec. 4,
+// with the centre computation on the GPU through a reduction.
+//   KMEANS_ASSIGN  "global i => read A0[4*i:4*i+3], read A1[:], reduce(+) A2[:]"
+//     record i (features X[4i .. 4i+3], f32) joins the nearest of the k
+//     centres C[4j .. 4j+3]: squared distance in f32 as
+//     fma(d3, d3, fma(d2, d2, fma(d1, d1, d0*d0))), d_f = x_f - c_f, ties to
+//     the lowest j; its features and a count of 1 are added into
+//     S[5j .. 5j+4] (fp64).
+//   KMEANS_UPDATE  "global j => read A0[5*j:5*j+4], read A1[4*j:4*j+3], write A2[4*j:4*j+3]"
+//     centre j becomes f32(S[5j+f] / S[5j+4]) (fp64 division), or keeps
+//     C[4j+f] when its count is zero.
+// Each warp of the assignment accumulates into its own totals in shared
+// memory; the CTA then adds them to the superblock's reduce(+) partial with
+// fp64 atomics.  A feature that is a multiple of 2^-24 in [0, 1) (the seeded
+// uniform inputs) is the integer m = x * 2^24 < 2^24 scaled, and a warp's 256
+// records sum such integers exactly in 32 bits: those go through integer
+// shared-memory atomics, with no fp64 arithmetic per record (fp64 runs at a
+// small fraction of the fp32 rate on this GPU).  Other features take fp64
+// atomics.  Every addition is exact when all features are such multiples and
+// a centre collects fewer than 2^29 records (its sums are then integers times
+// 2^-24 below 2^53), so the result does not depend on the order of the
+// additions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "task_lookup.cuh"
+
+namespace lt {
+namespace {
+
+constexpr int KT = 256;    // threads per CTA
+constexpr int KRPT = 8;    // records per thread and round (a warp's 32-bit totals stay exact)
+constexpr int KROUNDS = 8; // rounds per CTA; the warps' totals fold into 64-bit CTA totals after each
+constexpr int KMAX = 64;   // most centres
+
+// Is x a multiple of 2^-24 in [0, 1)?  Then *m = x * 2^24 exactly.
+__device__ __forceinline__ bool fixed24(float x, uint32_t *m) {
+    const float t = __fmul_rn(x, 16777216.0f);  // exact: a power-of-two scale
+    *m = __float2uint_rz(t);
+    return x >= 0.0f && x < 1.0f && __uint2float_rn(*m) == t;
+}
+
+__device__ __forceinline__ int nearest(const float4 *cs, int k, float4 x) {
+    int best = 0;
+    float bd = 0.f;
+    for (int j = 0; j < k; ++j) {
+        const float4 c = cs[j];
+        const float d0 = __fsub_rn(x.x, c.x), d1 = __fsub_rn(x.y, c.y);
+        const float d2 = __fsub_rn(x.z, c.z), d3 = __fsub_rn(x.w, c.w);
+        const float d = __fmaf_rn(d3, d3, __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0))));
+        if (j == 0 || d < bd) {
+            bd = d;
+            best = j;
+        }
+    }
+    return best;
+}
+
+__global__ void __launch_bounds__(KT) kmeans_assign_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    __shared__ float4 cs[KMAX];
+    __shared__ uint32_t iacc[KT / 32][KMAX * 5];  // a warp's fixed-point sums (2^-24 units) and counts
+    __shared__ unsigned long long tot[KMAX * 5];  // the CTA's
+    __shared__ double dacc[KT / 32][KMAX * 4];    // features that are not such multiples
+    __shared__ int slow;
+    const int ti = task_of(tasks, p, blockIdx.x);
+    const ExecTask &t = tasks[ti];
+    const int k = (int)p.i[0];
+    const int64_t n = p.shape[0][0] / 4;
+    const int64_t i0 = t.t_lo[0], i1 = min(t.t_hi[0], n - 1);
+    const DView X = t.v[0], Cv = t.v[1], S = t.v[2];
+    for (int e = threadIdx.x; e < k; e += KT) {
+        const float *c = (const float *)Cv.base;
+        cs[e] = make_float4(c[(4 * e) * Cv.s[0]], c[(4 * e + 1) * Cv.s[0]], c[(4 * e + 2) * Cv.s[0]],
+                            c[(4 * e + 3) * Cv.s[0]]);
+    }
+    for (int e = threadIdx.x; e < (KT / 32) * KMAX * 5; e += KT) (&iacc[0][0])[e] = 0u;
+    for (int e = threadIdx.x; e < (KT / 32) * KMAX * 4; e += KT) (&dacc[0][0])[e] = 0.0;
+    for (int e = threadIdx.x; e < KMAX * 5; e += KT) tot[e] = 0ull;
+    if (threadIdx.x == 0) slow = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    const float *xb = (const float *)X.base;
+    const bool vec = p.variant == 1;
+    auto load = [&](int64_t r) {
+        if (vec) return *(const float4 *)(xb + 4 * r);
+        return make_float4(xb[(4 * r) * X.s[0]], xb[(4 * r + 1) * X.s[0]], xb[(4 * r + 2) * X.s[0]],
+                           xb[(4 * r + 3) * X.s[0]]);
+    };
+    auto add = [&](int best, float4 x) {
+        uint32_t m0, m1, m2, m3;
+        const bool ok0 = fixed24(x.x, &m0), ok1 = fixed24(x.y, &m1), ok2 = fixed24(x.z, &m2), ok3 = fixed24(x.w, &m3);
+        uint32_t *ia = &iacc[warp][best * 5];
+        double *da = &dacc[warp][best * 4];
+        if (!(ok0 && ok1 && ok2 && ok3)) slow = 1;
+        if (ok0) atomicAdd(ia + 0, m0); else atomicAdd(da + 0, (double)x.x);
+        if (ok1) atomicAdd(ia + 1, m1); else atomicAdd(da + 1, (double)x.y);
+        if (ok2) atomicAdd(ia + 2, m2); else atomicAdd(da + 2, (double)x.z);
+        if (ok3) atomicAdd(ia + 3, m3); else atomicAdd(da + 3, (double)x.w);
+        atomicAdd(ia + 4, 1u);
+    };
+    const int64_t cta_base = i0 + (int64_t)(blockIdx.x - t.cta_begin) * (KT * KRPT * KROUNDS);
+    for (int round = 0; round < KROUNDS; ++round) {
+        const int64_t base = cta_base + (int64_t)round * (KT * KRPT);
+        if (base > i1) break;  // uniform across the CTA
+        // two records per thread at a time: one centre read from shared memory serves both
+#pragma unroll 1
+        for (int q = 0; q < KRPT; q += 2) {
+            const int64_t ra = base + q * KT + threadIdx.x, rb = ra + KT;
+            if (ra > i1) break;
+            const float4 xa = load(ra);
+            if (rb <= i1) {
+                const float4 xq = load(rb);
+                int ba = 0, bb = 0;
+                float da = 0.f, db = 0.f;
+                for (int j = 0; j < k; ++j) {
+                    const float4 c = cs[j];
+                    float e0 = __fsub_rn(xa.x, c.x), e1 = __fsub_rn(xa.y, c.y);
+                    float e2 = __fsub_rn(xa.z, c.z), e3 = __fsub_rn(xa.w, c.w);
+                    const float d = __fmaf_rn(e3, e3, __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0))));
+                    e0 = __fsub_rn(xq.x, c.x), e1 = __fsub_rn(xq.y, c.y);
+                    e2 = __fsub_rn(xq.z, c.z), e3 = __fsub_rn(xq.w, c.w);
+                    const float dq = __fmaf_rn(e3, e3, __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0))));
+                    if (j == 0 || d < da) {
+                        da = d;
+                        ba = j;
+                    }
+                    if (j == 0 || dq < db) {
+                        db = dq;
+                        bb = j;
+                    }
+                }
+                add(ba, xa);
+                add(bb, xq);
+            } else {
+                add(nearest(cs, k, xa), xa);
+            }
+        }
+        __syncthreads();
+        // a warp's totals of one round stay below 256 * 2^24 = 2^32; fold them into the CTA's
+        for (int e = threadIdx.x; e < k * 5; e += KT) {
+            unsigned long long v = 0ull;
+#pragma unroll
+            for (int w = 0; w < KT / 32; ++w) {
+                v += iacc[w][e];
+                iacc[w][e] = 0u;
+            }
+            tot[e] += v;
+        }
+        __syncthreads();
+    }
+    double *sb = (double *)S.base;
+    for (int e = threadIdx.x; e < k * 5; e += KT) {
+        const int j = e / 5, f = e % 5;
+        double v = (double)tot[e];  // exact below 2^53
+        if (f < 4) {
+            v *= 0x1p-24;
+            if (slow)
+                for (int w = 0; w < KT / 32; ++w) v += dacc[w][j * 4 + f];
+        }
+        if (v != 0.0) atomicAdd(sb + e * S.s[0], v);
+    }
+}
+
+__global__ void __launch_bounds__(128) kmeans_update_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    const int ti = task_of(tasks, p, blockIdx.x);
+    const ExecTask &t = tasks[ti];
+    const int64_t kc = p.shape[1][0] / 4;
+    const int64_t j = t.t_lo[0] + (int64_t)(blockIdx.x - t.cta_begin) * 128 + threadIdx.x;
+    if (j > t.t_hi[0] || j >= kc) return;
+    const DView S = t.v[0], Cv = t.v[1], Cn = t.v[2];
+    const double *s = (const double *)S.base;
+    const double cnt = s[(5 * j + 4) * S.s[0]];
+    for (int f = 0; f < 4; ++f) {
+        const float old = ((const float *)Cv.base)[(4 * j + f) * Cv.s[0]];
+        ((float *)Cn.base)[(4 * j + f) * Cn.s[0]] =
+            cnt > 0.0 ? __double2float_rn(__ddiv_rn(s[(5 * j + f) * S.s[0]], cnt)) : old;
+    }
+}
+
+}  // namespace
+
+namespace k {
+
+uint32_t prepare_kmeans_assign(ExecTask *t, int n, ExecParams &p) {
+    const int64_t k = p.i[0];
+    if (k < 1 || k > KMAX || p.shape[0][0] % 4 != 0 || p.shape[1][0] != 4 * k || p.shape[2][0] != 5 * k)
+        return 0xFFFFFFFFu;
+    const int64_t nrec = p.shape[0][0] / 4;
+    bool vec = true;
+    for (int i = 0; i < n && vec; ++i)
+        if (t[i].v[0].s[0] != 1 || t[i].v[0].base % 16 != 0) vec = false;
+    p.variant = vec ? 1 : 0;
+    uint32_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const int64_t cnt = std::min(t[i].t_hi[0], nrec - 1) - t[i].t_lo[0] + 1;
+        t[i].cta_begin = total;
+        t[i].cta_count = cnt > 0 ? (uint32_t)((cnt + KT * KRPT * KROUNDS - 1) / (KT * KRPT * KROUNDS)) : 0;
+        total += t[i].cta_count;
+    }
+    return total;
+}
+
+cudaError_t launch_kmeans_assign(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
+    kmeans_assign_kernel<<<ctas, KT, 0, st>>>(dev, p);
+    return cudaGetLastError();
+}
+
+uint32_t prepare_kmeans_update(ExecTask *t, int n, ExecParams &p) {
+    if (p.shape[0][0] % 5 != 0 || p.shape[1][0] % 4 != 0 || p.shape[0][0] / 5 != p.shape[1][0] / 4 ||
+        p.shape[2][0] != p.shape[1][0])
+        return 0xFFFFFFFFu;
+    const int64_t kc = p.shape[1][0] / 4;
+    uint32_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const int64_t cnt = std::min(t[i].t_hi[0], kc - 1) - t[i].t_lo[0] + 1;
+        t[i].cta_begin = total;
+        t[i].cta_count = cnt > 0 ? (uint32_t)((cnt + 127) / 128) : 0;
+        total += t[i].cta_count;
+    }
+    return total;
+}
+
+cudaError_t launch_kmeans_update(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
+    kmeans_update_kernel<<<ctas, 128, 0, st>>>(dev, p);
+    return cudaGetLastError();
+}
+
+}  // namespace k
+}  // namespace lt

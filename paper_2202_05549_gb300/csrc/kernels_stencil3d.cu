@@ -3,9 +3,8 @@
 //   V = ((((((U + U[k-1]) + U[k+1]) + U[i-1]) + U[i+1]) + U[j-1]) + U[j+1]) / 7
 // zero outside the domain, __fadd_rn in that fixed order, then a correctly
 // rounded division by 7 (div_const_rn).
-// Each CTA owns a 16 x 128 (i, j) tile and sweeps a run of planes along k:
-// the current plane is staged in shared memory (with a one-cell ring) for
-// the i and j neighbours, the planes above and below stay in registers.
+// The vector kernel computes register strips of one plane (below); the
+// scalar kernel takes tasks whose rows are not 16-byte aligned.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,12 +16,7 @@
 namespace lt {
 namespace {
 
-constexpr int ST = 256;           // threads per CTA
-constexpr int SY = 16, SX = 128;  // (i, j) tile
-constexpr int SKR = 32;           // planes per CTA (k run)
-constexpr int SQ = SX / 4;        // float4 groups per tile row
-constexpr int SPITCH = SX + 8;    // shared pitch, 4 cells of room each side
-constexpr int GPT = SY * SQ / ST; // float4 groups per thread (2)
+constexpr int ST = 256;  // threads per CTA of the scalar kernel
 
 __device__ __forceinline__ float j7(float c, float zm, float zp, float ym, float yp, float xm, float xp) {
     float a = __fadd_rn(c, zm);
@@ -56,80 +50,95 @@ __device__ __forceinline__ const float *row3(const DView &v, int64_t k, int64_t 
     return (const float *)v.base + k * v.s[0] + i * v.s[1];
 }
 
-__global__ void __launch_bounds__(ST) jacobi3d_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
-    __shared__ __align__(16) float pl[SY + 2][SPITCH];
+// Vector kernel: each warp computes J3R rows x 128 columns (4 per lane) of
+// one plane k.  It loads everything first (planes k-1 and k+1 over its rows,
+// plane k over its rows and the one above and below, and the column outside
+// the strip for lanes 0 and 31), then computes: no shared memory, no
+// barriers, and 3*J3R+2 independent 16-byte loads per lane in flight, as in
+// the 2-D kernel.  The neighbouring planes a warp reads are re-read by the
+// warps of planes k-1 and k+1; CTAs are ordered plane by plane (j fastest,
+// then i, then k), so those reads come from L2.
+constexpr int J3R = 8;   // output rows per warp
+constexpr int J3W = 4;   // warps per CTA, side by side along j
+
+__global__ void __launch_bounds__(J3W * 32) jacobi3d_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     const int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     Geo3 g;
     if (!geo3(t, p, &g)) return;
-    const uint32_t gx = (uint32_t)((g.x1 - g.x0 + SX) / SX), gy = (uint32_t)((g.y1 - g.y0 + SY) / SY);
+    const uint32_t gx = (uint32_t)((g.x1 - g.x0 + J3W * 128) / (J3W * 128));
+    const uint32_t gy = (uint32_t)((g.y1 - g.y0 + J3R) / J3R);
     uint32_t local = blockIdx.x - t.cta_begin;  // 32-bit split: no 64-bit division in the prologue
-    const int64_t tx0 = g.x0 + (int64_t)(local % gx) * SX;
+    const uint32_t tx = local % gx;
     local /= gx;
-    const int64_t ty0 = g.y0 + (int64_t)(local % gy) * SY;
-    local /= gy;
-    const int64_t kz0 = g.z0 + (int64_t)local * SKR, kz1 = min(kz0 + SKR - 1, g.z1);
+    const int64_t r0 = g.y0 + (int64_t)(local % gy) * J3R;
+    const int64_t k = g.z0 + (int64_t)(local / gy);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t js = g.x0 + (int64_t)(tx * J3W + warp) * 128;
+    if (js > g.x1 || r0 > g.y1) return;  // warp-uniform
+    const int64_t j0 = js + 4 * lane;
     const DView U = t.v[0], V = t.v[1];
     // readable box (the annotation's region, clipped)
     const int64_t cmin = max(g.x0 - 1, (int64_t)0), cmax = min(g.x1 + 1, g.NX - 1);
     const int64_t rmin = max(g.y0 - 1, (int64_t)0), rmax = min(g.y1 + 1, g.NY - 1);
-    const int64_t zmax = min(g.z1 + 1, g.NZ - 1);
-    auto load4 = [&](int64_t k, int64_t i, int64_t j) {
+    const int64_t zmin = max(g.z0 - 1, (int64_t)0), zmax = min(g.z1 + 1, g.NZ - 1);
+    const bool ldc = j0 <= cmax;
+    // guarded loads only; the columns past cmax are cleared after every load
+    // is in flight (clearing right after each load would wait for it)
+    auto ld4 = [&](int64_t kk, int64_t i) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k >= 0 && k <= zmax && k >= g.z0 - 1 && i >= rmin && i <= rmax && j <= cmax) {
-            v = *(const float4 *)(row3(U, k, i) + j);
-            if (j + 1 > cmax) v.y = 0.f;
-            if (j + 2 > cmax) v.z = 0.f;
-            if (j + 3 > cmax) v.w = 0.f;
-        }
+        if (ldc && kk >= zmin && kk <= zmax && i >= rmin && i <= rmax) v = *(const float4 *)(row3(U, kk, i) + j0);
         return v;
     };
-    float4 prev[GPT], cur[GPT];
+    auto clip = [&](float4 &v) {
+        if (j0 + 1 > cmax) v.y = 0.f;
+        if (j0 + 2 > cmax) v.z = 0.f;
+        if (j0 + 3 > cmax) v.w = 0.f;
+    };
+    // the column left of the strip (lane 0) or right of it (lane 31)
+    const int64_t jx = lane == 0 ? j0 - 1 : j0 + 4;
+    const bool ldx = (lane == 0 || lane == 31) && jx >= cmin && jx <= cmax && k >= zmin && k <= zmax;
+    float4 zm[J3R], zp[J3R], pc[J3R + 2];
+    float xo[J3R];
 #pragma unroll
-    for (int q = 0; q < GPT; ++q) {
-        const int e = threadIdx.x + q * ST, li = e / SQ, c = e % SQ;
-        prev[q] = load4(kz0 - 1, ty0 + li, tx0 + 4 * c);
-        cur[q] = load4(kz0, ty0 + li, tx0 + 4 * c);
+    for (int m = 0; m < J3R + 2; ++m) pc[m] = ld4(k, r0 - 1 + m);
+#pragma unroll
+    for (int m = 0; m < J3R; ++m) {
+        zm[m] = ld4(k - 1, r0 + m);
+        zp[m] = ld4(k + 1, r0 + m);
+        const int64_t i = r0 + m;
+        xo[m] = (ldx && i >= rmin && i <= rmax) ? row3(U, k, i)[jx] : 0.f;
     }
-    for (int64_t k = kz0; k <= kz1; ++k) {
-        // stage plane k with its ring
-        for (int e = threadIdx.x; e < (SY + 2) * SQ; e += ST) {
-            const int li = e / SQ, c = e % SQ;
-            *(float4 *)&pl[li][4 + 4 * c] = load4(k, ty0 - 1 + li, tx0 + 4 * c);
-        }
-        for (int e = threadIdx.x; e < 2 * (SY + 2); e += ST) {
-            const int li = e >> 1;
-            const int64_t i = ty0 - 1 + li, j = (e & 1) ? tx0 + SX : tx0 - 1;
-            float v = 0.f;
-            if (i >= rmin && i <= rmax && j >= cmin && j <= cmax) v = row3(U, k, i)[j];
-            pl[li][(e & 1) ? 4 + SX : 3] = v;
-        }
-        __syncthreads();
 #pragma unroll
-        for (int q = 0; q < GPT; ++q) {
-            const int e = threadIdx.x + q * ST, li = e / SQ + 1, c = e % SQ;
-            const int64_t i = ty0 + li - 1, j = tx0 + 4 * c;
-            const float4 nx = load4(k + 1, i, j);
-            if (i <= g.y1 && j <= g.x1) {
-                const int cc = 4 + 4 * c;
-                const float zm[4] = {prev[q].x, prev[q].y, prev[q].z, prev[q].w};
-                const float zp[4] = {nx.x, nx.y, nx.z, nx.w};
-                float o[4];
+    for (int m = 0; m < J3R + 2; ++m) clip(pc[m]);
 #pragma unroll
-                for (int m = 0; m < 4; ++m)
-                    o[m] = j7(pl[li][cc + m], zm[m], zp[m], pl[li - 1][cc + m], pl[li + 1][cc + m], pl[li][cc + m - 1],
-                              pl[li][cc + m + 1]);
-                float *dst = (float *)V.base + k * V.s[0] + i * V.s[1] + j;
-                if (j + 3 <= g.x1) {
-                    *(float4 *)dst = make_float4(o[0], o[1], o[2], o[3]);
-                } else {
-                    for (int m = 0; m < 4 && j + m <= g.x1; ++m) dst[m] = o[m];
-                }
-            }
-            prev[q] = cur[q];
-            cur[q] = nx;
+    for (int m = 0; m < J3R; ++m) {
+        clip(zm[m]);
+        clip(zp[m]);
+    }
+    float *vb = (float *)V.base;
+#pragma unroll
+    for (int m = 0; m < J3R; ++m) {
+        const float4 mid = pc[m + 1], up = pc[m], dn = pc[m + 2], lo = zm[m], hi = zp[m];
+        const float w_in = __shfl_up_sync(0xffffffffu, mid.w, 1);
+        const float e_in = __shfl_down_sync(0xffffffffu, mid.x, 1);
+        const float w = lane == 0 ? xo[m] : w_in;
+        const float e = lane == 31 ? xo[m] : e_in;
+        const int64_t i = r0 + m;
+        if (i > g.y1 || j0 > g.x1) continue;
+        float4 o;
+        o.x = j7(mid.x, lo.x, hi.x, up.x, dn.x, w, mid.y);
+        o.y = j7(mid.y, lo.y, hi.y, up.y, dn.y, mid.x, mid.z);
+        o.z = j7(mid.z, lo.z, hi.z, up.z, dn.z, mid.y, mid.w);
+        o.w = j7(mid.w, lo.w, hi.w, up.w, dn.w, mid.z, e);
+        float *dst = vb + k * V.s[0] + i * V.s[1] + j0;
+        if (j0 + 3 <= g.x1) {
+            *(float4 *)dst = o;
+        } else {
+            dst[0] = o.x;
+            if (j0 + 1 <= g.x1) dst[1] = o.y;
+            if (j0 + 2 <= g.x1) dst[2] = o.z;
         }
-        __syncthreads();
     }
 }
 
@@ -174,7 +183,7 @@ uint32_t prepare_jacobi3d(ExecTask *t, int n, ExecParams &p) {
         int64_t d = std::min(t[i].t_hi[2], NZ - 1) - t[i].t_lo[2] + 1;
         uint64_t c = 0;
         if (w > 0 && h > 0 && d > 0)
-            c = vec ? (uint64_t)((w + SX - 1) / SX) * (uint64_t)((h + SY - 1) / SY) * (uint64_t)((d + SKR - 1) / SKR)
+            c = vec ? (uint64_t)((w + J3W * 128 - 1) / (J3W * 128)) * (uint64_t)((h + J3R - 1) / J3R) * (uint64_t)d
                     : (uint64_t)((w * h * d + ST - 1) / ST);
         t[i].cta_begin = total;
         t[i].cta_count = (uint32_t)c;
@@ -185,7 +194,7 @@ uint32_t prepare_jacobi3d(ExecTask *t, int n, ExecParams &p) {
 
 cudaError_t launch_jacobi3d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
     if (p.variant == 1)
-        jacobi3d_vec_kernel<<<ctas, ST, 0, st>>>(dev, p);
+        jacobi3d_vec_kernel<<<ctas, J3W * 32, 0, st>>>(dev, p);
     else
         jacobi3d_scalar_kernel<<<ctas, ST, 0, st>>>(dev, p);
     return cudaGetLastError();

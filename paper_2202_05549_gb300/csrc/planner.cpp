@@ -509,6 +509,7 @@ size_t dtype_size(int dtype) {
         case LT_BF16: return 2;
         case LT_U8: return 1;
         case LT_U32: return 4;
+        case LT_F64: return 8;
         default: return 0;
     }
 }

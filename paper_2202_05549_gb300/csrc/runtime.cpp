@@ -202,6 +202,10 @@ const BuiltinDef kBuiltins[] = {
      {LT_F32, LT_F32}, {2, 2}, k::prepare_jacobi2d_multi, k::launch_jacobi2d_multi},
     {LT_K_ROWREDUCE, "global [i, j] => read A0[i, j], reduce(+) A1[i]", 2, {LT_F32, LT_F32}, {2, 1},
      k::prepare_rowreduce, k::launch_rowreduce, false, true},
+    {LT_K_KMEANS_ASSIGN, "global i => read A0[4*i:4*i+3], read A1[:], reduce(+) A2[:]", 3, {LT_F32, LT_F32, LT_F64},
+     {1, 1, 1}, k::prepare_kmeans_assign, k::launch_kmeans_assign},
+    {LT_K_KMEANS_UPDATE, "global i => read A0[5*i:5*i+4], read A1[4*i:4*i+3], write A2[4*i:4*i+3]", 3,
+     {LT_F64, LT_F32, LT_F32}, {1, 1, 1}, k::prepare_kmeans_update, k::launch_kmeans_update},
     {LT_K_GEMM_BF16, "global [i, j] => read A0[i, :], read A1[:, j], write A2[i, j]", 3, {LT_BF16, LT_BF16, LT_F32},
      {2, 2, 2}, k::prepare_gemm_bf16, k::launch_gemm_bf16},
 };

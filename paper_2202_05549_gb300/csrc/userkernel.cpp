@@ -6,7 +6,7 @@
 //     __device__ void name(dim3 virtBlockIdx, <parameters in declaration order>)
 // value parameters: int64_t (integer) or double (float); arrays:
 // lightning::Vector<T> (1-D, v[i]), Matrix<T> (2-D, m(i, j) or m[i][j]) and
-// Tensor<T> (3-D, t(k, i, j)), T = float, unsigned short (bf16 bits),
+// Tensor<T> (3-D, t(k, i, j)), T = float, double, unsigned short (bf16 bits),
 // unsigned char or unsigned int.
 //
 // Like the generated wrapper of Listing 3, the library adds a __global__
@@ -72,6 +72,7 @@ const char *ctype(int dtype) {
         case LT_F32: return "float";
         case LT_BF16: return "unsigned short";
         case LT_U8: return "unsigned char";
+        case LT_F64: return "double";
         default: return "unsigned int";
     }
 }

@@ -13,15 +13,17 @@ import numpy as np
 
 from . import _lib as L
 
-F32, BF16, U8, U32 = L.LT_F32, L.LT_BF16, L.LT_U8, L.LT_U32
+F32, BF16, U8, U32, F64 = L.LT_F32, L.LT_BF16, L.LT_U8, L.LT_U32, L.LT_F64
 STENCIL1D, JACOBI2D, JACOBI3D, GEMM_BF16, HIST256 = (L.LT_K_STENCIL1D, L.LT_K_JACOBI2D, L.LT_K_JACOBI3D,
                                                      L.LT_K_GEMM_BF16, L.LT_K_HIST256)
 DIFFUSION2D, DIFFUSION2D_ADJ = L.LT_K_DIFFUSION2D, L.LT_K_DIFFUSION2D_ADJ
 PLAN_ONLY = L.LT_K_PLAN_ONLY
 ROWREDUCE = L.LT_K_ROWREDUCE
 JACOBI2D_MULTI = L.LT_K_JACOBI2D_MULTI
+KMEANS_ASSIGN = L.LT_K_KMEANS_ASSIGN
+KMEANS_UPDATE = L.LT_K_KMEANS_UPDATE
 
-_NP = {F32: np.float32, BF16: np.uint16, U8: np.uint8, U32: np.uint32}
+_NP = {F32: np.float32, BF16: np.uint16, U8: np.uint8, U32: np.uint32, F64: np.float64}
 
 
 class LightningError(RuntimeError):
