@@ -351,7 +351,8 @@ def run_lightning(args, rank, world, local, grp):
                    else "working set 128 MiB ~ L2 size; not flushed"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": round(achieved / peaks["hbm_gbs"], 4),
-                     "traffic": None if tb > 1 else kernel_traffic("jacobi2d_vec_kernel", cells_per_launch),
+                     "traffic": kernel_traffic("jacobi2d_multi_kernel" if tb > 1 else "jacobi2d_vec_kernel",
+                                               cells_per_launch / tb),
                      "kernel": "jacobi2d_multi_kernel" if tb > 1 else "jacobi2d_vec_kernel", "launch_ms": round(ex_ms, 4),
                      "bytes_per_launch": 8.0 * cells_per_launch, "peak_source": peaks["source"]},
         "host_link": {"bytes_h2d_per_step": st["bytes_h2d"] / args.steps,
@@ -532,7 +533,8 @@ def run_kmeans(args, rank, world, local, grp):
                                f"{iters} iterations per step", "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (129 MB)"},
         "roofline": {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "kernel": "kmeans_assign_kernel",
+                     "frac": round(achieved / peak, 4), "traffic": kernel_traffic("kmeans_assign_kernel", n),
+                     "kernel": "kmeans_assign_kernel",
                      "launch_ms": round(assign_ms, 4), "flops_per_launch": flops,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x median SM clock (derived)",
                      "hbm_GBs_of_assignment": round(16.0 * n / (assign_ms / 1e3) / 1e9, 1)},
