@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--tb", type=int, default=1, help="Jacobi iterations per launch (temporal blocking, halo = tb)")
     p.add_argument("--iters", type=int, default=0,
                    help="Jacobi iterations per step (one run of the workload; default 20 out-of-core, 10 in-core)")
+    p.add_argument("--user-kernel", action="store_true",
+                   help="stencil workloads: run a Jacobi body compiled at run time (NVRTC) instead of the built-in")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -207,6 +209,22 @@ def link_peaks(local):
     return out
 
 
+# A Jacobi body as a user would write it for runtime compilation (Sec. 3.5):
+# one thread per cell, the same sum order and division as the built-in.
+USER_JACOBI = r"""
+__device__ void jacobi(dim3 vb, int64_t ny, int64_t nx, lightning::Matrix<float> U, lightning::Matrix<float> V) {
+    const int64_t i = (int64_t)vb.y * blockDim.y + threadIdx.y, j = (int64_t)vb.x * blockDim.x + threadIdx.x;
+    if (i >= ny || j >= nx) return;
+    float a = U(i, j);
+    a = a + (i > 0 ? U(i - 1, j) : 0.0f);
+    a = a + (i + 1 < ny ? U(i + 1, j) : 0.0f);
+    a = a + (j > 0 ? U(i, j - 1) : 0.0f);
+    a = a + (j + 1 < nx ? U(i, j + 1) : 0.0f);
+    V(i, j) = a / 5.0f;
+}
+"""
+
+
 def hbm_cap(args):
     """HBM pool of the in-HBM workloads: --hbm-gib if given (small pools let
     ncu's kernel replay save and restore device memory), else 0 = the library
@@ -291,8 +309,12 @@ def run_lightning(args, rank, world, local, grp):
     U = ctx.array(lt.F32, (ny, nx), dist)
     V = ctx.array(lt.F32, (ny, nx), dist)
     U.fill(L.LT_INIT_UNIFORM, seed=seed, stream=0)
+    user = args.user_kernel and tb == 1
     if tb > 1:
         k = ctx.kernel(lt.JACOBI2D_MULTI, ann, [("U", lt.F32), ("V", lt.F32), ("k", lt.U32, False)])
+    elif user:
+        k = ctx.kernel_from_source(USER_JACOBI, "jacobi", ann, [("ny", lt.U32, False), ("nx", lt.U32, False),
+                                                                  ("U", lt.F32), ("V", lt.F32)])
     else:
         k = ctx.kernel(lt.JACOBI2D, ann, [("U", lt.F32), ("V", lt.F32)])
     bufs = [U, V]
@@ -308,7 +330,10 @@ def run_lightning(args, rank, world, local, grp):
     def step():
         extra = [tb] if tb > 1 else []
         for _ in range(launches):
-            k.launch(grid=(nx, ny), block=(128, 4), superblock=sb, args=[bufs[0], bufs[1]] + extra)
+            if user:
+                k.launch(grid=(nx, ny), block=(128, 4), superblock=sb, args=[ny, nx, bufs[0], bufs[1]])
+            else:
+                k.launch(grid=(nx, ny), block=(128, 4), superblock=sb, args=[bufs[0], bufs[1]] + extra)
             bufs.reverse()
         ctx.synchronize()
 
@@ -343,7 +368,8 @@ def run_lightning(args, rank, world, local, grp):
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_max * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64 uniform[0,1))",
-        "config": {"workload": workload, "grid": [ny, nx], "iterations_per_step": iters,
+        "config": {"workload": workload + (" (Jacobi body compiled at run time)" if user else ""),
+                   "grid": [ny, nx], "iterations_per_step": iters,
                    "launches_per_step": launches, "iterations_per_launch": tb,
                    "hbm_budget_bytes": pl["budget"], "host_pool_bytes": pl["host"],
                    "data_bytes": pl["data_bytes"], "parallelism": f"replicas x{world}",
@@ -351,9 +377,10 @@ def run_lightning(args, rank, world, local, grp):
                    else "working set 128 MiB ~ L2 size; not flushed"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": round(achieved / peaks["hbm_gbs"], 4),
-                     "traffic": kernel_traffic("jacobi2d_multi_kernel" if tb > 1 else "jacobi2d_vec_kernel",
-                                               cells_per_launch / tb),
-                     "kernel": "jacobi2d_multi_kernel" if tb > 1 else "jacobi2d_vec_kernel", "launch_ms": round(ex_ms, 4),
+                     "traffic": None if user else kernel_traffic(
+                         "jacobi2d_multi_kernel" if tb > 1 else "jacobi2d_vec_kernel", cells_per_launch / tb),
+                     "kernel": ("jacobi2d_multi_kernel" if tb > 1 else
+                                "lt_user_wrapper (NVRTC)" if user else "jacobi2d_vec_kernel"), "launch_ms": round(ex_ms, 4),
                      "bytes_per_launch": 8.0 * cells_per_launch, "peak_source": peaks["source"]},
         "host_link": {"bytes_h2d_per_step": st["bytes_h2d"] / args.steps,
                       "bytes_d2h_per_step": st["bytes_d2h"] / args.steps,

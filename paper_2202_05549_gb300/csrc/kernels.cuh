@@ -27,7 +27,7 @@ struct ExecTask {
     DView v[LT_MAX_ARRAYS];       // views, in array-parameter order
     uint32_t cta_begin;           // first CTA (or work tile) of this task in the launch
     uint32_t cta_count;
-    int32_t aux[4];               // kernel-specific per-task values set by prepare_*
+    int32_t aux[6];               // kernel-specific per-task values set by prepare_*
 };
 
 // Per-launch constants of an Execute kernel.

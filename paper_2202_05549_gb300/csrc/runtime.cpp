@@ -2113,10 +2113,12 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             uint32_t ctas = def->prepare ? def->prepare(tasks.data(), (int)tasks.size(), ep) : 0;
             if (ctas != 0xFFFFFFFFu) ep.uniform_ctas = uniform_cta_count(tasks);
             if (ctas == 0xFFFFFFFFu)
-                return fail(LT_ERR_UNSUPPORTED, "this built-in cannot run these chunks (code " +
-                                                    std::to_string(ep.variant) +
-                                                    "; the GEMM needs A row-major and B column-major chunks, at "
-                                                    "most 15 distinct chunks of each per launch)");
+                return fail(LT_ERR_UNSUPPORTED,
+                            "this kernel cannot run this launch (code " + std::to_string(ep.variant) +
+                                "): the GEMM needs A row-major and B column-major chunks, at most 15 distinct "
+                                "chunks of each per launch; the multi-step stencil 1 <= k <= 16; K-Means "
+                                "1 <= k <= 64 and arrays of 4k / 5k elements; a source kernel virtual block "
+                                "indices below 2^32");
             void *dptr;
             size_t roff;
             if ((st = upload(c, tasks.data(), tasks.size() * sizeof(ExecTask), &dptr, &roff))) return st;

@@ -103,7 +103,7 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
          "struct LtView { uint64_t base; int64_t s[3]; int64_t org[3]; int64_t hi[3]; };\n"
          "struct LtTask { int64_t t_lo[3], t_hi[3]; LtView v["
       << LT_MAX_ARRAYS
-      << "]; uint32_t cta_begin, cta_count; int32_t aux[4]; };\n"
+      << "]; uint32_t cta_begin, cta_count; uint32_t aux[6]; };\n"
          "struct LtParams { int64_t shape["
       << LT_MAX_ARRAYS << "][3]; int32_t nd[" << LT_MAX_ARRAYS
       << "]; int64_t block[3]; double f[4]; int64_t i[4]; uint32_t *err;"
@@ -118,10 +118,9 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
          "  if (P.uniform_ctas > 0) lo = (int)(blockIdx.x / (unsigned)P.uniform_ctas);\n"
          "  else while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (tasks[mid].cta_begin <= blockIdx.x) lo = mid; else hi = mid - 1; }\n"
          "  const LtTask &t = tasks[lo];\n"
-         "  const int64_t bx0 = t.t_lo[0] / P.block[0], by0 = t.t_lo[1] / P.block[1], bz0 = t.t_lo[2] / P.block[2];\n"
-         "  const int64_t nbx = t.t_hi[0] / P.block[0] - bx0 + 1, nby = t.t_hi[1] / P.block[1] - by0 + 1;\n"
-         "  const int64_t l = (int64_t)blockIdx.x - (int64_t)t.cta_begin;\n"
-         "  dim3 vb((unsigned)(bx0 + l % nbx), (unsigned)(by0 + (l / nbx) % nby), (unsigned)(bz0 + l / (nbx * nby)));\n";
+         "  // first virtual block and the task's extent in blocks along x and y (set by the host)\n"
+         "  const unsigned l = blockIdx.x - t.cta_begin, q = l / t.aux[3];\n"
+         "  dim3 vb(t.aux[0] + (l - q * t.aux[3]), t.aux[1] + q % t.aux[4], t.aux[2] + q / t.aux[4]);\n";
     int slot = 0, fi = 0, ii = 0;
     std::ostringstream args;
     for (size_t p = 0; p < params.size(); ++p) {
@@ -192,19 +191,31 @@ lt_status compile_user_kernel(const std::string &src, std::vector<char> *cubin, 
 
 namespace k {
 
+// One CTA per virtual block of each task.  aux[0..2] = the task's first
+// virtual block, aux[3], aux[4] = its extent in blocks along x and y, so the
+// wrapper maps its CTA with two 32-bit divisions.  Virtual block indices are
+// dim3 components: every value must fit 32 bits (else the launch is refused).
 uint32_t prepare_user(ExecTask *t, int n, ExecParams &p) {
-    uint32_t total = 0;
+    uint64_t total = 0;
     for (int i = 0; i < n; ++i) {
         uint64_t nb = 1;
+        int64_t first[3], ext[3];
         for (int d = 0; d < 3; ++d) {
-            int64_t B = p.block[d] > 0 ? p.block[d] : 1;
-            nb *= (uint64_t)(t[i].t_hi[d] / B - t[i].t_lo[d] / B + 1);
+            const int64_t B = p.block[d] > 0 ? p.block[d] : 1;
+            first[d] = t[i].t_lo[d] / B;
+            ext[d] = t[i].t_hi[d] / B - first[d] + 1;
+            if (t[i].t_hi[d] / B > 0xFFFFFFFFll) return 0xFFFFFFFFu;
+            nb *= (uint64_t)ext[d];
         }
-        t[i].cta_begin = total;
+        for (int d = 0; d < 3; ++d) t[i].aux[d] = (int32_t)(uint32_t)first[d];
+        t[i].aux[3] = (int32_t)(uint32_t)ext[0];
+        t[i].aux[4] = (int32_t)(uint32_t)ext[1];
+        t[i].cta_begin = (uint32_t)total;
         t[i].cta_count = (uint32_t)nb;
-        total += (uint32_t)nb;
+        total += nb;
+        if (total >= 0xFFFFFFFFull) return 0xFFFFFFFFu;
     }
-    return total;
+    return (uint32_t)total;
 }
 
 }  // namespace k
