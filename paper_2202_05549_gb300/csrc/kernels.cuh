@@ -138,6 +138,7 @@ struct BatchParams {
 namespace k {
 
 int batch_threads();
+int batch_ctas_per_sm();  // resident CTAs of the persistent batch kernel per SM
 cudaError_t launch_batch(const BatchParams &p, int ctas, cudaStream_t st);
 cudaError_t launch_batch_zero_hist(const BatchHist *hist, int n, cudaStream_t st);
 

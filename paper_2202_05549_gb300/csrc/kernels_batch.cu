@@ -21,6 +21,8 @@ namespace lt {
 namespace {
 
 constexpr int BT = 256;  // threads per CTA (8 warps)
+constexpr int BR = 8;    // rows per warp strip of a Jacobi tile
+constexpr int BOCC = 3;  // CTAs per SM the kernel is built for (registers capped to fit)
 constexpr unsigned long long BWAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long btimer() {
@@ -35,7 +37,7 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     return v;
 }
 
-__global__ void __launch_bounds__(BT, 1) batch_kernel(BatchParams P) {
+__global__ void __launch_bounds__(BT, BOCC) batch_kernel(BatchParams P) {
     __shared__ uint32_t s_item;
     __shared__ int s_stop;
     __shared__ uint32_t sh[BT / 32][256];
@@ -73,10 +75,10 @@ __global__ void __launch_bounds__(BT, 1) batch_kernel(BatchParams P) {
             const int64_t ss = even ? J.su : J.sv, sd = even ? J.sv : J.su;
             const int64_t ny = J.ny, nx = J.nx;
             const int64_t ye = min((int64_t)(w.row0 + w.nrows) - 1, ny - 1);
-            const int64_t sx = (nx + JCOLS - 1) / JCOLS, sy = ((int64_t)w.nrows + JR - 1) / JR;
-            for (int64_t s = warp; s < sx * sy; s += BT / 32) {
-                const int64_t js = (s % sx) * JCOLS, r0 = w.row0 + (s / sx) * JR;
-                if (r0 <= ye) jacobi_strip<true>(src, ss, dst, sd, ny, nx, js, r0, nx - 1, ye, lane);
+            const uint32_t sx = (uint32_t)((nx + JCOLS - 1) / JCOLS), sy = (w.nrows + BR - 1) / BR;
+            for (uint32_t s = warp; s < sx * sy; s += BT / 32) {  // 32-bit: tiles are small
+                const int64_t js = (int64_t)(s % sx) * JCOLS, r0 = (int64_t)w.row0 + (int64_t)(s / sx) * BR;
+                if (r0 <= ye) jacobi_strip<true, BR>(src, ss, dst, sd, ny, nx, js, r0, nx - 1, ye, lane);
             }
             __threadfence();
             __syncthreads();
@@ -129,6 +131,12 @@ __global__ void batch_zero_hist_kernel(const BatchHist *__restrict__ hist, int n
 namespace k {
 
 int batch_threads() { return BT; }
+
+int batch_ctas_per_sm() {
+    int n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel, BT, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
 
 cudaError_t launch_batch_zero_hist(const BatchHist *hist, int n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;

@@ -2635,7 +2635,7 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
                         return st;
                     }
                     tc.bp.hist_slice = hs;
-                    tc.ctas = sms;
+                    tc.ctas = sms * k::batch_ctas_per_sm();
                     CK(c, cudaEventRecord(e0, c->st[S_COMP]));
                     CK(c, batch_enqueue(c, tc, c->st[S_COMP]));
                     CK(c, cudaEventRecord(e1, c->st[S_COMP]));
@@ -2666,7 +2666,7 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
             return st;
         }
         bc->bp.hist_slice = tp.second;
-        bc->ctas = sms;
+        bc->ctas = sms * k::batch_ctas_per_sm();
         if (use_graph) {
             cudaGraph_t graph = nullptr;
             CK(c, cudaStreamBeginCapture(c->st[S_COMP], cudaStreamCaptureModeThreadLocal));
