@@ -58,7 +58,7 @@ struct CopyPiece {
 // the innermost) of about LT_COPY_UNIT elements.  Within a row, when both
 // sides are contiguous along the innermost axis and equally misaligned, the
 // body moves as 16-byte vectors between a scalar head and tail.
-#define LT_COPY_UNIT 4096
+#define LT_COPY_UNIT 16384
 __host__ __device__ inline int64_t copy_piece_width(const CopyPiece &p) {
     return p.hi[p.nd - 1] - p.lo[p.nd - 1] + 1;
 }

@@ -129,12 +129,13 @@ __device__ __forceinline__ void copy_elem(const char *s, char *d, int esize) {
     }
 }
 
-// One CTA per work unit (a run of rows, or a segment of one long row); the
-// piece is found by binary search.
-__global__ void __launch_bounds__(256) copy_kernel(const CopyPiece *__restrict__ pieces, int n) {
+// One CTA per work unit (a run of rows, or a segment of one long row, of
+// about LT_COPY_UNIT elements); the piece is found by binary search and read
+// in place (no local copy of the record).
+__global__ void __launch_bounds__(256, 3) copy_kernel(const CopyPiece *__restrict__ pieces, int n) {
     const uint64_t u = blockIdx.x;
     const int pi = find_piece_u(pieces, n, u);
-    const CopyPiece p = pieces[pi];
+    const CopyPiece &p = pieces[pi];
     const int inner = p.nd - 1;
     const int64_t w = copy_piece_width(p), rows = copy_piece_rows(p);
     const int64_t rpu = copy_piece_rows_per_unit(p);
@@ -193,7 +194,20 @@ __global__ void __launch_bounds__(256) copy_kernel(const CopyPiece *__restrict__
             for (int64_t i = threadIdx.x; i < head; i += blockDim.x) copy_elem(sb + i * es, db + i * es, es);
             const uint4 *sv = (const uint4 *)(sb + head * es);
             uint4 *dv = (uint4 *)(db + head * es);
-            for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) dv[i] = __ldcg(sv + i);
+            // four 16-byte loads in flight per thread before their stores
+            for (int64_t b = 0; b < nv; b += 4 * (int64_t)blockDim.x) {
+                uint4 v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int64_t i = b + k * (int64_t)blockDim.x + threadIdx.x;
+                    if (i < nv) v[k] = __ldcg(sv + i);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int64_t i = b + k * (int64_t)blockDim.x + threadIdx.x;
+                    if (i < nv) dv[i] = v[k];
+                }
+            }
             for (int64_t i = tail0 + threadIdx.x; i < ncol; i += blockDim.x) copy_elem(sb + i * es, db + i * es, es);
         } else {
             const int64_t ss = p.src.s[inner] * es, ds = p.dst.s[inner] * es;

@@ -137,6 +137,13 @@ __device__ __forceinline__ float4 ld4v(const DView &v, int64_t i, int64_t j) {
 }
 __device__ __forceinline__ float sel(bool b, float x) { return b ? x : 0.f; }
 
+// Both vector kernels issue every load of a thread (its staging groups, its
+// ring cells and the groups its compute phase needs) before using any, then
+// mask, stage and compute: no load waits behind another.
+constexpr int NS = ((TY + 2) * VQ + DT - 1) / DT;  // staging groups per thread (last one partial)
+constexpr int NC = TY * VQ / DT;                   // compute groups per thread
+static_assert(TY * VQ % DT == 0, "compute groups divide evenly");
+
 __global__ void __launch_bounds__(DT) diffusion_fwd_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     __shared__ __align__(16) float su[TY + 2][VP];
     const int ti = task_of(tasks, p, blockIdx.x);
@@ -149,31 +156,48 @@ __global__ void __launch_bounds__(DT) diffusion_fwd_vec_kernel(const ExecTask *_
     tile_of(blockIdx.x - t.cta_begin, x0, x1, y0, &ty0, &tx0);
     const DView U = t.v[0], K = t.v[1], V = t.v[2];
     const int64_t cmax = min(x1 + 1, NX - 1), rmin = max(y0 - 1, (int64_t)0), rmax = min(y1 + 1, NY - 1);
-    for (int e = threadIdx.x; e < (TY + 2) * VQ; e += DT) {
+    float4 uv[NS], kv[NC];
+#pragma unroll
+    for (int s2 = 0; s2 < NS; ++s2) {
+        const int e = threadIdx.x + s2 * DT;
         const int li = e / VQ, q = e % VQ;
         const int64_t i = ty0 - 1 + li, j = tx0 + 4 * q;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i >= rmin && i <= rmax && j <= cmax) {
-            v = ld4v(U, i, j);
-            v.y = sel(j + 1 <= cmax, v.y);
-            v.z = sel(j + 2 <= cmax, v.z);
-            v.w = sel(j + 3 <= cmax, v.w);
-        }
+        uv[s2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < (TY + 2) * VQ && i >= rmin && i <= rmax && j <= cmax) uv[s2] = ld4v(U, i, j);
+    }
+#pragma unroll
+    for (int c2 = 0; c2 < NC; ++c2) {
+        const int e = threadIdx.x + c2 * DT;
+        const int64_t i = ty0 + e / VQ, j = tx0 + 4 * (e % VQ);
+        kv[c2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i <= y1 && j <= x1) kv[c2] = ld4v(K, i, j);
+    }
+    float ring = 0.f;
+    const int re = threadIdx.x;
+    const int64_t ri = ty0 - 1 + (re >> 1), rj = (re & 1) ? tx0 + TX : tx0 - 1;
+    if (re < 2 * (TY + 2) && ri >= rmin && ri <= rmax && rj >= 0 && rj <= cmax) ring = at2(U, ri, rj);
+#pragma unroll
+    for (int s2 = 0; s2 < NS; ++s2) {
+        const int e = threadIdx.x + s2 * DT;
+        if (e >= (TY + 2) * VQ) break;
+        const int li = e / VQ, q = e % VQ;
+        const int64_t j = tx0 + 4 * q;
+        float4 v = uv[s2];
+        v.y = sel(j + 1 <= cmax, v.y);
+        v.z = sel(j + 2 <= cmax, v.z);
+        v.w = sel(j + 3 <= cmax, v.w);
         *(float4 *)&su[li][4 + 4 * q] = v;
     }
-    for (int e = threadIdx.x; e < 2 * (TY + 2); e += DT) {
-        const int li = e >> 1;
-        const int64_t i = ty0 - 1 + li, j = (e & 1) ? tx0 + TX : tx0 - 1;
-        su[li][(e & 1) ? 4 + TX : 3] = (i >= rmin && i <= rmax && j >= 0 && j <= cmax) ? at2(U, i, j) : 0.f;
-    }
+    if (re < 2 * (TY + 2)) su[re >> 1][(re & 1) ? 4 + TX : 3] = ring;
     __syncthreads();
-    for (int e = threadIdx.x; e < TY * VQ; e += DT) {
+#pragma unroll
+    for (int c2 = 0; c2 < NC; ++c2) {
+        const int e = threadIdx.x + c2 * DT;
         const int li = e / VQ + 1, q = e % VQ;
         const int64_t i = ty0 + li - 1, j = tx0 + 4 * q;
         if (i > y1 || j > x1) continue;
         const int c = 4 + 4 * q;
-        const float4 k4 = ld4v(K, i, j);
-        const float kk[4] = {k4.x, k4.y, k4.z, k4.w};
+        const float kk[4] = {kv[c2].x, kv[c2].y, kv[c2].z, kv[c2].w};
         float o[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
@@ -190,7 +214,7 @@ __global__ void __launch_bounds__(DT) diffusion_fwd_vec_kernel(const ExecTask *_
     }
 }
 
-__global__ void __launch_bounds__(DT) diffusion_adj_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+__global__ void __launch_bounds__(DT, 2) diffusion_adj_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     __shared__ __align__(16) float ss[TY + 2][VP];
     __shared__ __align__(16) float su[TY + 2][VP];
     const int ti = task_of(tasks, p, blockIdx.x);
@@ -205,50 +229,79 @@ __global__ void __launch_bounds__(DT) diffusion_adj_vec_kernel(const ExecTask *_
     int64_t ty0, tx0;
     tile_of(blockIdx.x - t.cta_begin, ax0, rx1, ry0, &ty0, &tx0);
     const DView L1 = t.v[0], K = t.v[1], U = t.v[2], G = t.v[3], L0 = t.v[4];
-    for (int e = threadIdx.x; e < (TY + 2) * VQ; e += DT) {
+    // staging: s = K * L1 over the superblock's own cells (0 elsewhere), u over the U read region
+    float4 kv[NS], lv[NS], uv[NS], l1c[NC], gc[NC];  // gc: loaded after the barrier, before the compute
+#pragma unroll
+    for (int s2 = 0; s2 < NS; ++s2) {
+        const int e = threadIdx.x + s2 * DT;
         const int li = e / VQ, q = e % VQ;
         const int64_t i = ty0 - 1 + li, j = tx0 + 4 * q;
-        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f), uv = sv;
-        if (i >= y0 && i <= y1 && j + 3 >= x0 && j <= x1) {  // group meets the superblock
-            const float4 k4 = ld4v(K, i, j), l4 = ld4v(L1, i, j);
-            sv.x = sel(j >= x0 && j <= x1, __fmul_rn(k4.x, l4.x));
-            sv.y = sel(j + 1 >= x0 && j + 1 <= x1, __fmul_rn(k4.y, l4.y));
-            sv.z = sel(j + 2 >= x0 && j + 2 <= x1, __fmul_rn(k4.z, l4.z));
-            sv.w = sel(j + 3 >= x0 && j + 3 <= x1, __fmul_rn(k4.w, l4.w));
+        kv[s2] = lv[s2] = uv[s2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < (TY + 2) * VQ) {
+            if (i >= y0 && i <= y1 && j + 3 >= x0 && j <= x1) {  // group meets the superblock
+                kv[s2] = ld4v(K, i, j);
+                lv[s2] = ld4v(L1, i, j);
+            }
+            if (i >= ry0 && i <= ry1 && j + 3 >= rx0 && j <= rx1) uv[s2] = ld4v(U, i, j);  // meets U's region
         }
-        if (i >= ry0 && i <= ry1 && j + 3 >= rx0 && j <= rx1) {  // group meets the U read region
-            uv = ld4v(U, i, j);
-            uv.x = sel(j >= rx0 && j <= rx1, uv.x);
-            uv.y = sel(j + 1 >= rx0 && j + 1 <= rx1, uv.y);
-            uv.z = sel(j + 2 >= rx0 && j + 2 <= rx1, uv.z);
-            uv.w = sel(j + 3 >= rx0 && j + 3 <= rx1, uv.w);
-        }
-        *(float4 *)&ss[li][4 + 4 * q] = sv;
-        *(float4 *)&su[li][4 + 4 * q] = uv;
     }
-    for (int e = threadIdx.x; e < 2 * (TY + 2); e += DT) {
-        const int li = e >> 1;
-        const int64_t i = ty0 - 1 + li, j = (e & 1) ? tx0 + TX : tx0 - 1;
-        const int c = (e & 1) ? 4 + TX : 3;
-        const bool sb = i >= y0 && i <= y1 && j >= x0 && j <= x1;
-        ss[li][c] = sb ? __fmul_rn(at2(K, i, j), at2(L1, i, j)) : 0.f;
-        su[li][c] = (i >= ry0 && i <= ry1 && j >= rx0 && j <= rx1) ? at2(U, i, j) : 0.f;
+#pragma unroll
+    for (int c2 = 0; c2 < NC; ++c2) {
+        const int e = threadIdx.x + c2 * DT;
+        const int64_t i = ty0 + e / VQ, j = tx0 + 4 * (e % VQ);
+        l1c[c2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i >= y0 && i <= y1 && j + 3 >= x0 && j <= x1) l1c[c2] = ld4v(L1, i, j);
+    }
+    float rs = 0.f, ru = 0.f;
+    const int re = threadIdx.x;
+    const int64_t ri = ty0 - 1 + (re >> 1), rj = (re & 1) ? tx0 + TX : tx0 - 1;
+    if (re < 2 * (TY + 2)) {
+        if (ri >= y0 && ri <= y1 && rj >= x0 && rj <= x1) rs = __fmul_rn(at2(K, ri, rj), at2(L1, ri, rj));
+        if (ri >= ry0 && ri <= ry1 && rj >= rx0 && rj <= rx1) ru = at2(U, ri, rj);
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < NS; ++s2) {
+        const int e = threadIdx.x + s2 * DT;
+        if (e >= (TY + 2) * VQ) break;
+        const int li = e / VQ, q = e % VQ;
+        const int64_t i = ty0 - 1 + li, j = tx0 + 4 * q;
+        const bool rsb = i >= y0 && i <= y1;
+        float4 sv, uu = uv[s2];
+        sv.x = sel(rsb && j >= x0 && j <= x1, __fmul_rn(kv[s2].x, lv[s2].x));
+        sv.y = sel(rsb && j + 1 >= x0 && j + 1 <= x1, __fmul_rn(kv[s2].y, lv[s2].y));
+        sv.z = sel(rsb && j + 2 >= x0 && j + 2 <= x1, __fmul_rn(kv[s2].z, lv[s2].z));
+        sv.w = sel(rsb && j + 3 >= x0 && j + 3 <= x1, __fmul_rn(kv[s2].w, lv[s2].w));
+        uu.x = sel(j >= rx0 && j <= rx1, uu.x);
+        uu.y = sel(j + 1 >= rx0 && j + 1 <= rx1, uu.y);
+        uu.z = sel(j + 2 >= rx0 && j + 2 <= rx1, uu.z);
+        uu.w = sel(j + 3 >= rx0 && j + 3 <= rx1, uu.w);
+        *(float4 *)&ss[li][4 + 4 * q] = sv;
+        *(float4 *)&su[li][4 + 4 * q] = uu;
+    }
+    if (re < 2 * (TY + 2)) {
+        const int c = (re & 1) ? 4 + TX : 3;
+        ss[re >> 1][c] = rs;
+        su[re >> 1][c] = ru;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < TY * VQ; e += DT) {
+#pragma unroll
+    for (int c2 = 0; c2 < NC; ++c2) {
+        const int e = threadIdx.x + c2 * DT;
+        const int64_t i = ty0 + e / VQ, j = tx0 + 4 * (e % VQ);
+        gc[c2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i >= y0 && i <= y1 && j + 3 >= x0 && j <= x1) gc[c2] = ld4v(G, i, j);
+    }
+#pragma unroll
+    for (int c2 = 0; c2 < NC; ++c2) {
+        const int e = threadIdx.x + c2 * DT;
         const int li = e / VQ + 1, q = e % VQ;
         const int64_t i = ty0 + li - 1, j = tx0 + 4 * q;
         if (i > ry1 || j > rx1 || j + 3 < rx0) continue;
         const int c = 4 + 4 * q;
         const bool row_sb = i >= y0 && i <= y1;
-        float4 l4 = make_float4(0.f, 0.f, 0.f, 0.f), g4 = l4;
         const bool grp_sb = row_sb && j + 3 >= x0 && j <= x1;
-        if (grp_sb) {
-            l4 = ld4v(L1, i, j);
-            g4 = ld4v(G, i, j);
-        }
-        const float l1[4] = {l4.x, l4.y, l4.z, l4.w};
-        float g[4] = {g4.x, g4.y, g4.z, g4.w};
+        const float l1[4] = {l1c[c2].x, l1c[c2].y, l1c[c2].z, l1c[c2].w};
+        float g[4] = {gc[c2].x, gc[c2].y, gc[c2].z, gc[c2].w};
         float o[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
