@@ -370,6 +370,7 @@ typedef struct {
     int64_t tuned_hist_slice;
     uint64_t tables_resident; /* descriptor tables reused on the device without a copy */
     uint64_t plans_reused;    /* launches whose plan came from the kernel's plan cache */
+    uint64_t reduce_inplace;  /* reduce partials accumulated in their destination chunk (no copy) */
 } lt_stats;
 
 lt_status lt_stats_get(lt_ctx *ctx, lt_stats *out);

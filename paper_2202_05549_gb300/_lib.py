@@ -79,7 +79,7 @@ class lt_stats(C.Structure):
         ("n_copy_kernels", C.c_uint64), ("ms_h2d", C.c_double), ("ms_d2h", C.c_double), ("ms_fill", C.c_double),
         ("batches_fused", C.c_uint64), ("batches_plain", C.c_uint64), ("graph_replays", C.c_uint64),
         ("tuned_tile_rows", C.c_int64), ("tuned_hist_slice", C.c_int64), ("tables_resident", C.c_uint64),
-        ("plans_reused", C.c_uint64)]
+        ("plans_reused", C.c_uint64), ("reduce_inplace", C.c_uint64)]
 
 
 class lt_launch_desc(C.Structure):

@@ -1866,31 +1866,76 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
     bool rev = !(c->cfg.flags & LT_FLAG_FIXED_SWEEP) && (c->launch_id & 1);
     for (size_t i = 0; i < nsb; ++i) order[i] = rev ? nsb - 1 - i : i;
 
-    // reduce partials: one block for the whole launch
+    // reduce partials.  A superblock whose reduce region is exactly the box
+    // of a chunk of the destination array (an array no other argument of the
+    // launch names; a chunk no earlier superblock took) accumulates in that
+    // chunk itself: the cells only it contributes to are then final where
+    // they lie, and the combine touches the shared ones only.  The other
+    // partials share one temporary block.
     std::vector<std::vector<ChunkGeom>> red_geom(nsb);
     std::vector<std::vector<size_t>> red_off(nsb);
+    std::vector<std::vector<int64_t>> red_chunk(nsb);  // chunk holding the partial, -1 = temporary
+    std::vector<std::pair<lt_array *, int64_t>> red_inplace;
     size_t red_bytes = 0;
     for (size_t s = 0; s < nsb; ++s)
         for (const auto &ap : plan.sbs[s].args)
             if (ap.kind == ARG_REDUCE) {
-                ChunkGeom g = temp_geometry(parr[(size_t)ap.param]->g, ap.region);
+                lt_array *a = parr[(size_t)ap.param];
+                int64_t ic = -1;
+                if (std::count(parr.begin(), parr.end(), a) == 1)
+                    for (const auto &pc : ap.pieces) {
+                        const Box &cb = a->g.chunks[(size_t)pc.chunk].box;
+                        if (cb.contains(ap.region) && ap.region.contains(cb) &&
+                            std::find(red_inplace.begin(), red_inplace.end(), std::make_pair(a, pc.chunk)) ==
+                                red_inplace.end()) {
+                            ic = pc.chunk;
+                            break;
+                        }
+                    }
+                red_chunk[s].push_back(ic);
+                if (ic >= 0) {
+                    c->stats.reduce_inplace++;
+                    red_inplace.push_back({a, ic});
+                    red_geom[s].push_back(a->g.chunks[(size_t)ic]);
+                    red_off[s].push_back(0);
+                    continue;
+                }
+                ChunkGeom g = temp_geometry(a->g, ap.region);
                 red_geom[s].push_back(g);
                 red_off[s].push_back(red_bytes);
                 red_bytes += align_up(g.bytes, 256);
             }
     size_t red_base = 0;
     FenceSet red_fence;
-    if (red_bytes) {
-        if ((st = dev_alloc(c, red_bytes, &red_base, &red_fence))) return st;
-        if (def->reduce_zero) {
-            op_begin(c, S_COMP, "reduce_init");
-            if ((st = op_wait(c, red_fence))) return st;
-            if (!c->dry) CK(c, cudaMemsetAsync(c->dev_base + red_base, 0, red_bytes, c->st[S_COMP]));
-            uint64_t q;
-            if ((st = op_end(c, &q))) return st;
-            red_fence = FenceSet::one(S_COMP, q);
-        }
+    const bool any_red = red_bytes || !red_inplace.empty();
+    if (red_bytes && (st = dev_alloc(c, red_bytes, &red_base, &red_fence))) return st;
+    for (auto &ip : red_inplace) ip.first->cs[(size_t)ip.second].pin++;
+    for (auto &ip : red_inplace) {
+        // the launch overwrites the chunk's region: its old contents are not needed
+        if ((st = ensure_dev(c, ip.first, ip.second, false))) return st;
+        CState &cs = ip.first->cs[(size_t)ip.second];
+        red_fence.merge(cs.ready);
+        red_fence.merge(cs.busy);
     }
+    if (any_red && def->reduce_zero) {
+        op_begin(c, S_COMP, "reduce_init");
+        if ((st = op_wait(c, red_fence))) return st;
+        if (!c->dry) {
+            if (red_bytes) CK(c, cudaMemsetAsync(c->dev_base + red_base, 0, red_bytes, c->st[S_COMP]));
+            for (auto &ip : red_inplace)
+                CK(c, cudaMemsetAsync(c->dev_base + ip.first->cs[(size_t)ip.second].off, 0,
+                                      ip.first->g.chunks[(size_t)ip.second].bytes, c->st[S_COMP]));
+        }
+        uint64_t q;
+        if ((st = op_end(c, &q))) return st;
+        red_fence = FenceSet::one(S_COMP, q);
+    }
+    // the view of superblock s's ri-th reduce partial
+    auto red_view = [&](size_t s, size_t ri, lt_array *a) {
+        const int64_t ic = red_chunk[s][ri];
+        if (ic >= 0) return view_of(c, a->g, a->g.chunks[(size_t)ic], a->cs[(size_t)ic].off);
+        return view_of(c, a->g, red_geom[s][ri], red_base + red_off[s][ri]);
+    };
 
     // process superblocks in groups: all at once when the launch fits in
     // the HBM budget, else one at a time (streaming through host memory)
@@ -2098,7 +2143,7 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                     const TempAlloc &tm = temps[(size_t)temp_of[oi - g0][ai]];
                     t.v[sl] = view_of(c, a->g, tm.geom, tm.off);
                 } else if (ap.kind == ARG_REDUCE) {
-                    t.v[sl] = view_of(c, a->g, red_geom[s][ri], red_base + red_off[s][ri]);
+                    t.v[sl] = red_view(s, ri, a);
                     ri++;
                 }
             }
@@ -2253,11 +2298,25 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
 
     // --- reduce: combine the per-superblock partials in superblock order
     c->cur_group = (int64_t)((nsb + gsz - 1) / gsz);
-    if (red_bytes) {
+    if (any_red) {
         std::vector<ReducePiece> rp;
         std::vector<CopyPiece> rcopies;
         std::vector<DView> srcs;
         FenceSet rw = red_fence;
+        // With partials in place, a cell several superblocks share is reduced
+        // into scratch first and copied to its chunks after: no kernel writes
+        // a cell another piece may still read.
+        const bool two_phase = !red_inplace.empty();
+        struct ScratchPiece {
+            size_t rp;  // reduce piece writing the scratch block
+            lt_array *a;
+            int64_t chunk;
+            Box box;
+            ChunkGeom geom;
+            size_t off;
+        };
+        std::vector<ScratchPiece> scratch;
+        size_t scratch_bytes = 0;
         // per destination chunk, the (superblock, box) contributions
         struct Contrib {
             size_t sb, ri;
@@ -2318,13 +2377,18 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                         }
                         ReducePiece p{};
                         p.src_begin = (uint32_t)srcs.size();
+                        const Contrib *only = nullptr;
                         for (const auto &cb : cl)
                             if (cb.box.contains(cell)) {
-                                srcs.push_back(
-                                    view_of(c, a->g, red_geom[cb.sb][cb.ri], red_base + red_off[cb.sb][cb.ri]));
+                                srcs.push_back(red_view(cb.sb, cb.ri, a));
                                 p.nsrc++;
+                                only = &cb;
                             }
                         if (!p.nsrc) continue;
+                        if (p.nsrc == 1 && red_chunk[only->sb][only->ri] == d.second) {
+                            srcs.pop_back();  // the partial lies in this chunk already
+                            continue;
+                        }
                         if (p.nsrc == 1) {  // a single contribution: a plain copy
                             CopyPiece cp{};
                             cp.src = srcs.back();
@@ -2347,8 +2411,39 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                             p.lo[dd] = dd < a->g.nd ? cell.lo[dd] : 0;
                             p.hi[dd] = dd < a->g.nd ? cell.hi[dd] : 0;
                         }
+                        if (two_phase) {
+                            ScratchPiece sp;
+                            sp.rp = rp.size();
+                            sp.a = a;
+                            sp.chunk = d.second;
+                            sp.box = cell;
+                            sp.geom = temp_geometry(a->g, cell);
+                            sp.off = scratch_bytes;
+                            scratch_bytes += align_up(sp.geom.bytes, 256);
+                            scratch.push_back(sp);
+                        }
                         rp.push_back(p);
                     }
+        }
+        size_t scratch_base = 0;
+        if (scratch_bytes) {
+            FenceSet sf;
+            if ((st = dev_alloc(c, scratch_bytes, &scratch_base, &sf))) return st;
+            rw.merge(sf);
+            for (auto &sp : scratch) {  // reduce into scratch, then copy the scratch block to the chunk
+                const DView sv = view_of(c, sp.a->g, sp.geom, scratch_base + sp.off);
+                rp[sp.rp].dst = sv;
+                CopyPiece cp{};
+                cp.src = sv;
+                cp.dst = view_of(c, sp.a->g, sp.a->g.chunks[(size_t)sp.chunk], sp.a->cs[(size_t)sp.chunk].off);
+                cp.nd = sp.a->g.nd;
+                cp.esize = (int32_t)sp.a->g.esize();
+                for (int dd = 0; dd < 3; ++dd) {
+                    cp.lo[dd] = dd < sp.a->g.nd ? sp.box.lo[dd] : 0;
+                    cp.hi[dd] = dd < sp.a->g.nd ? sp.box.hi[dd] : 0;
+                }
+                rcopies.push_back(cp);
+            }
         }
         uint64_t elems = 0;
         for (auto &p : rp) {
@@ -2394,7 +2489,14 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             cs.busy.add(S_COMP, q);
             cs.pin--;
         }
-        c->dev.release(red_base, red_bytes, FenceSet::one(S_COMP, q));
+        for (auto &ip : red_inplace) {
+            CState &cs = ip.first->cs[(size_t)ip.second];
+            cs.ready = FenceSet::one(S_COMP, q);
+            cs.busy.add(S_COMP, q);
+            cs.pin--;
+        }
+        if (red_bytes) c->dev.release(red_base, red_bytes, FenceSet::one(S_COMP, q));
+        if (scratch_bytes) c->dev.release(scratch_base, scratch_bytes, FenceSet::one(S_COMP, q));
     }
     return LT_OK;
 }

@@ -443,3 +443,28 @@ def test_eviction_prefers_dead_and_finished_chunks():
         assert not any(kind == "fetch" for _, kind in moved)   # the flush only writes back
         # both arrays are live after the flush: 32 chunks in 20 slots, so exactly 12 go to host
         assert sum(1 for _, kind in moved if kind == "evict") == 32 - 20
+
+
+def test_reduce_partials_in_place_when_regions_are_chunk_boxes():
+    # the adjoint's reduce(+) over a superblock and its ring equals the box of
+    # the superblock's own chunk (tiles with a one-cell halo): every partial
+    # accumulates in its chunk; a reduce into one small array takes only the
+    # first superblock's partial in place
+    n, t = 256, 64
+    with dry() as ctx:
+        dist = lt.Dist.tiles((t, t), halo=(1, 1))
+        arrs = [ctx.array(lt.F32, (n, n), dist) for _ in range(5)]
+        ka = ctx.kernel(lt.DIFFUSION2D_ADJ, "global [i, j] => read L1[i, j], read K[i, j], read U[i-1:i+1, j-1:j+1], "
+                        "readwrite G[i, j], reduce(+) L0[i-1:i+1, j-1:j+1]",
+                        [("L1", lt.F32), ("K", lt.F32), ("U", lt.F32), ("G", lt.F32), ("L0", lt.F32)])
+        ctx.reset_stats()
+        ka.launch(grid=(n, n), block=(64, 2), superblock=(t, t), args=arrs)
+        ctx.synchronize()
+        assert ctx.stats()["reduce_inplace"] == (n // t) ** 2
+        x = ctx.array(lt.U8, (10_000,), lt.Dist.rows(2_500))
+        h = ctx.array(lt.U32, (256,), lt.Dist.block())
+        kh = ctx.kernel(lt.HIST256, "global i => read X[i], reduce(+) H[:]", [("X", lt.U8), ("H", lt.U32)])
+        ctx.reset_stats()
+        kh.launch(grid=(10_000,), block=(256,), superblock=(2_500,), args=[x, h])
+        ctx.synchronize()
+        assert ctx.stats()["reduce_inplace"] == 1
