@@ -119,3 +119,43 @@ def test_bounded_wait_expires_reports_timeout_and_context_survives():
         ctx.launch_batch([(kj, (160, 96), (128, 4), (0, 0), [U, V], 2)])
         ctx.synchronize()
         assert np.array_equal(U.read(), oracle.jacobi2d(u0, 2))
+
+
+def test_batch_full_size_sampled_vs_oracle():
+    # the batched configuration at full size, as bench.py builds it: 4096
+    # Jacobi instances (sides log-uniform 64..4096, 8 iterations) and 1024
+    # histograms (lengths log-uniform 1e4..1e7), one fused batch; 8 instances
+    # across the size range and every histogram against the oracle
+    r = si.BatchRecipe()
+    sides, lens = [int(x) for x in r.sides()], [int(x) for x in r.hist_lengths()]
+    with lt.Context() as ctx:
+        kj = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        kh = ctx.kernel(lt.HIST256, HANN, [("X", lt.U8), ("H", lt.U32)])
+        launches, Us, Hs = [], [], []
+        for q, s_ in enumerate(sides):
+            U = ctx.array(lt.F32, (s_, s_))
+            V = ctx.array(lt.F32, (s_, s_))
+            U.fill(L.LT_INIT_UNIFORM, seed=si.SEED_BATCH, stream=si.STREAM_BATCH_JACOBI0 + q)
+            launches.append((kj, (s_, s_), (128, 4), (0, 0), [U, V], r.iters))
+            Us.append(U)
+        for h, n in enumerate(lens):
+            X = ctx.array(lt.U8, (n,))
+            H = ctx.array(lt.U32, (256,))
+            X.fill(L.LT_INIT_U8, seed=si.SEED_BATCH, stream=si.STREAM_BATCH_HIST0 + h)
+            launches.append((kh, (n,), (256,), (0,), [X, H], 1))
+            Hs.append(H)
+        ctx.launch_batch(launches, 0)
+        ctx.synchronize()
+        assert ctx.stats()["batches_fused"] == 1
+        order = sorted(range(len(sides)), key=lambda q: sides[q])
+        pick = sorted({order[0], order[-1]} | {order[len(order) * f // 6] for f in range(1, 6)} | {1})
+        got_u = {q: Us[q].read() for q in pick}
+        got_h = [H.read() for H in Hs]
+    assert r.iters % 2 == 0  # the newest state is back in U
+    for q in pick:
+        s_ = sides[q]
+        u0 = oracle.gen_uniform_f32(si.SEED_BATCH, si.STREAM_BATCH_JACOBI0 + q, 0, s_ * s_).reshape(s_, s_)
+        assert np.array_equal(got_u[q], oracle.jacobi2d(u0, r.iters)), f"instance {q} ({s_}^2) differs"
+    for h, n in enumerate(lens):
+        x = oracle.gen_u8(si.SEED_BATCH, si.STREAM_BATCH_HIST0 + h, 0, n)
+        assert np.array_equal(got_h[h], oracle.hist256(x)), f"histogram {h} differs"

@@ -180,6 +180,33 @@ def test_out_of_core_lightcone_samples_small():
     assert np.array_equal(got[si_, sj_], want)
 
 
+def test_out_of_core_full_size_lightcone_samples():
+    # the out-of-core configuration at full size, as bench.py runs it: 262144 x
+    # 131072 f32 (128 GiB per buffer), 8192-row bands + 1-row halo, the HBM
+    # budget and pinned host pool bench.py sizes, one run of 20 iterations;
+    # 4096 cells (edges and band seams included) against the oracle's light cone
+    import types
+
+    import bench
+    NY, NX, band, iters = 262144, 131072, 8192, 20
+    pl = bench.plan_ooc(types.SimpleNamespace(rows=NY, cols=NX, band=band, tb=1, hbm_gib=0.0), 1)
+    si_, sj_ = si.sample_cells(2204, NY, NX, 4096, seams_every=band)
+    with lt.Context(hbm_budget=pl["budget"], host_pool=pl["host"]) as ctx:
+        U = ctx.array(lt.F32, (NY, NX), lt.Dist.rows(band, halo=1))
+        V = ctx.array(lt.F32, (NY, NX), lt.Dist.rows(band, halo=1))
+        U.fill(L.LT_INIT_UNIFORM, seed=si.SEED_JACOBI_OOC, stream=0)
+        k = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=(NX, NY), block=(128, 4), superblock=(NX, band), args=[U, V])
+            U, V = V, U
+        ctx.synchronize()
+        s = ctx.stats()
+        got = np.array([U.read_box((i, j), (i, j))[0, 0] for i, j in zip(si_, sj_)], np.float32)
+    assert s["evictions"] > 0  # the run does not fit: the synchronize writes back what does not
+    want = oracle.jacobi2d_lightcone(NY, NX, si.SEED_JACOBI_OOC, 0, iters, si_, sj_)
+    assert np.array_equal(got, want), f"{np.sum(got != want)} of {len(want)} sampled cells differ"
+
+
 MANN = "global [i, j] => read U[i-{k}:i+{k}, j-{k}:j+{k}], write V[i, j]"
 
 
