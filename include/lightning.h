@@ -142,6 +142,19 @@ const char *lt_last_error(void);
  * Its contents start as zero (chunks materialise lazily). */
 lt_status lt_array_create(lt_ctx *ctx, lt_dtype dtype, int32_t ndim, const int64_t shape[3],
                           const lt_dist *dist, lt_array **out);
+
+/* Zero-copy import of caller-owned DEVICE memory (for instance a CUDA
+ * tensor) as a one-chunk array (no paper counterpart; the paper's arrays are
+ * always library-owned).  ptr: device address of element 0; strides:
+ * element strides per axis, the innermost 1.  The library reads and writes
+ * that memory in place; it never moves, evicts or frees it.  The caller's
+ * pending work on the memory must be complete before this call, and after
+ * lt_synchronize the memory holds the results of every launch so far.
+ * lt_array_destroy returns once no queued work uses the memory; the caller
+ * may free it then.  Errors: LT_ERR_INVALID_ARG (null pointer, bad ndim,
+ * non-positive strides, innermost stride not 1). */
+lt_status lt_array_wrap_device(lt_ctx *ctx, lt_dtype dtype, int32_t ndim, const int64_t shape[3],
+                               const int64_t strides[3], void *ptr, lt_array **out);
 lt_status lt_array_destroy(lt_ctx *ctx, lt_array *arr);
 
 /* Copy the whole array from / to a dense row-major host buffer of exactly

@@ -98,6 +98,8 @@ SIGNATURES = {
     "lt_last_error": (C.c_char_p, []),
     "lt_array_create": (_st, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(lt_dist),
                               C.POINTER(_vp)]),
+    "lt_array_wrap_device": (_st, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp,
+                                   C.POINTER(_vp)]),
     "lt_array_destroy": (_st, [_vp, _vp]),
     "lt_array_write": (_st, [_vp, _vp, _vp, C.c_size_t]),
     "lt_array_read": (_st, [_vp, _vp, _vp, C.c_size_t]),

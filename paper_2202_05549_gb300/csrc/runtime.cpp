@@ -158,7 +158,8 @@ struct Arena {
 
 struct CState {
     int loc = LOC_NONE;
-    size_t off = 0;
+    size_t off = 0;     // offset from the device pool's base (external chunks: their address, minus that base)
+    bool ext = false;   // storage owned by the caller (lt_array_wrap_device): always resident, never freed
     FenceSet ready, busy;
     uint64_t lru = 0;
     int pin = 0;
@@ -474,9 +475,14 @@ lt_status collect_timing(lt_ctx *c) {
 }
 
 // ---------------------------------------------------------------- views
+// Device address of pool offset `off`.  Unsigned arithmetic, so offsets of
+// external chunks (their address minus the pool base, modulo 2^64) come back
+// exactly.
+char *dptr(const lt_ctx *c, uint64_t off) { return (char *)(uintptr_t)((uint64_t)(uintptr_t)c->dev_base + off); }
+
 DView view_of(lt_ctx *c, const ArrayGeom &g, const ChunkGeom &cg, size_t off) {
     DView v;
-    uint64_t p = (uint64_t)(uintptr_t)(c->dev_base + off);
+    uint64_t p = (uint64_t)(uintptr_t)dptr(c, off);
     int64_t o = 0;
     for (int d = 0; d < 3; ++d) {
         v.s[d] = d < g.nd ? cg.stride[d] : 0;
@@ -591,7 +597,7 @@ lt_status evict(lt_ctx *c, lt_array *a, int64_t ci) {
     if (st) return st;
     if (!c->dry) {
         TimeScope ts(c, CAT_D2H);
-        CK(c, cudaMemcpyAsync(c->host_base + hoff, c->dev_base + s.off, cg.bytes, cudaMemcpyDeviceToHost,
+        CK(c, cudaMemcpyAsync(c->host_base + hoff, dptr(c, s.off), cg.bytes, cudaMemcpyDeviceToHost,
                               c->st[S_D2H]));
     }
     uint64_t q;
@@ -639,7 +645,7 @@ lt_status ensure_dev(lt_ctx *c, lt_array *a, int64_t ci, bool need_data, bool so
             if (st) return st;
             if (!c->dry) {
                 TimeScope ts(c, CAT_H2D);
-                CK(c, cudaMemcpyAsync(c->dev_base + off, c->host_base + s.off, cg.bytes, cudaMemcpyHostToDevice,
+                CK(c, cudaMemcpyAsync(dptr(c, off), c->host_base + s.off, cg.bytes, cudaMemcpyHostToDevice,
                                       c->st[S_H2D]));
             }
             uint64_t q;
@@ -668,7 +674,7 @@ lt_status ensure_dev(lt_ctx *c, lt_array *a, int64_t ci, bool need_data, bool so
             op_begin(c, S_COMP, "zero");
             st = op_wait(c, bf);
             if (st) return st;
-            if (!c->dry) CK(c, cudaMemsetAsync(c->dev_base + off, 0, cg.bytes, c->st[S_COMP]));
+            if (!c->dry) CK(c, cudaMemsetAsync(dptr(c, off), 0, cg.bytes, c->st[S_COMP]));
             uint64_t q;
             st = op_end(c, &q);
             if (st) return st;
@@ -818,7 +824,7 @@ lt_status xfer_chunk(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *h
     size_t es = g.esize();
     int64_t gs[3] = {1, 1, 1};
     for (int d = g.nd - 2; d >= 0; --d) gs[d] = gs[d + 1] * g.shape[d + 1];
-    char *dev = c->dev_base + s.off;
+    char *dev = dptr(c, s.off);
     auto dev_addr = [&](int64_t i0, int64_t i1, int64_t i2) {
         int64_t idx[3] = {i0, i1, i2};
         int64_t o = 0;
@@ -1142,6 +1148,39 @@ lt_status lt_array_create(lt_ctx *c, lt_dtype dtype, int32_t ndim, const int64_t
     return LT_OK;
 }
 
+lt_status lt_array_wrap_device(lt_ctx *c, lt_dtype dtype, int32_t ndim, const int64_t shape[3],
+                               const int64_t strides[3], void *ptr, lt_array **out) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    if (!shape || !strides || !out || (!ptr && !c->dry)) return fail(LT_ERR_INVALID_ARG, "null argument");
+    if (ndim < 1 || ndim > 3) return fail(LT_ERR_INVALID_ARG, "ndim must be 1, 2 or 3");
+    if (strides[ndim - 1] != 1) return fail(LT_ERR_INVALID_ARG, "the innermost stride must be 1");
+    lt_dist whole{};
+    whole.kind = LT_DIST_BLOCK;
+    auto a = std::make_unique<lt_array>();
+    std::string err;
+    if (!make_geometry((int)dtype, ndim, shape, whole, &a->g, &err)) return fail(LT_ERR_INVALID_ARG, err);
+    ChunkGeom &cg = a->g.chunks[0];
+    int64_t span = 1;  // elements from the first to one past the last
+    for (int d = 0; d < ndim; ++d) {
+        if (strides[d] < 1) return fail(LT_ERR_INVALID_ARG, "strides must be positive");
+        cg.s_origin[d] = 0;
+        cg.stride[d] = strides[d];
+        span += (shape[d] - 1) * strides[d];
+    }
+    cg.bytes = (size_t)span * a->g.esize();
+    a->cs.resize(1);
+    CState &cs = a->cs[0];
+    cs.loc = LOC_DEV;
+    cs.ext = true;
+    cs.pin = 1;  // never a victim
+    cs.off = (size_t)((uint64_t)(uintptr_t)ptr - (uint64_t)(uintptr_t)c->dev_base);
+    a->id = c->next_array_id++;
+    *out = a.get();
+    c->arrays.push_back(std::move(a));
+    return LT_OK;
+}
+
 lt_status lt_array_destroy(lt_ctx *c, lt_array *arr) {
     lt_status st = check_ctx(c);
     if (st) return st;
@@ -1152,6 +1191,12 @@ lt_status lt_array_destroy(lt_ctx *c, lt_array *arr) {
         CState &s = a->cs[i];
         FenceSet f = s.busy;
         f.merge(s.ready);
+        if (s.ext) {  // the caller's memory: return once no queued work uses it
+            for (int t = 0; t < NSTREAM; ++t)
+                if ((st = host_wait(c, t, f.q[t]))) return st;
+            s.loc = LOC_NONE;
+            continue;
+        }
         if (s.loc == LOC_DEV) c->dev.release(s.off, a->g.chunks[i].bytes, f);
         if (s.loc == LOC_HOST) c->host.release(s.off, a->g.chunks[i].bytes, f);
         s.loc = LOC_NONE;
@@ -1343,7 +1388,7 @@ lt_status lt_array_read_box(lt_ctx *c, lt_array *arr, const int64_t lo[3], const
                 char *dst = (char *)host + ho * (int64_t)es;
                 int64_t cstride = cg.stride[inner];
                 if (s.loc == LOC_DEV) {
-                    const char *src = c->dev_base + s.off + co * (int64_t)es;
+                    const char *src = dptr(c, s.off + co * (int64_t)es);
                     if (cstride == 1)
                         CK(c, cudaMemcpyAsync(dst, src, (size_t)w * es, cudaMemcpyDeviceToHost, c->st[S_COMP]));
                     else
@@ -1921,9 +1966,9 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
         op_begin(c, S_COMP, "reduce_init");
         if ((st = op_wait(c, red_fence))) return st;
         if (!c->dry) {
-            if (red_bytes) CK(c, cudaMemsetAsync(c->dev_base + red_base, 0, red_bytes, c->st[S_COMP]));
+            if (red_bytes) CK(c, cudaMemsetAsync(dptr(c, red_base), 0, red_bytes, c->st[S_COMP]));
             for (auto &ip : red_inplace)
-                CK(c, cudaMemsetAsync(c->dev_base + ip.first->cs[(size_t)ip.second].off, 0,
+                CK(c, cudaMemsetAsync(dptr(c, ip.first->cs[(size_t)ip.second].off), 0,
                                       ip.first->g.chunks[(size_t)ip.second].bytes, c->st[S_COMP]));
         }
         uint64_t q;
@@ -2529,8 +2574,8 @@ static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int hs, int it
         const ArrayGeom &g = J.u->g;
         const ChunkGeom &cu = g.chunks[0], &cv = J.v->g.chunks[0];
         BatchJacobi b{};
-        b.u = (uint64_t)(uintptr_t)(c->dev_base + J.u->cs[0].off);
-        b.v = (uint64_t)(uintptr_t)(c->dev_base + J.v->cs[0].off);
+        b.u = (uint64_t)(uintptr_t)(dptr(c, J.u->cs[0].off));
+        b.v = (uint64_t)(uintptr_t)(dptr(c, J.v->cs[0].off));
         b.su = cu.stride[0];
         b.sv = cv.stride[0];
         b.ny = g.shape[0];
@@ -2544,9 +2589,9 @@ static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int hs, int it
     }
     for (size_t h = 0; h < bs.hist.size(); ++h) {
         BatchHist b{};
-        b.x = (uint64_t)(uintptr_t)(c->dev_base + bs.hist[h].x->cs[0].off);
+        b.x = (uint64_t)(uintptr_t)(dptr(c, bs.hist[h].x->cs[0].off));
         b.len = bs.hist[h].x->g.shape[0];
-        b.h = (uint64_t)(uintptr_t)(c->dev_base + bs.hist[h].h->cs[0].off);
+        b.h = (uint64_t)(uintptr_t)(dptr(c, bs.hist[h].h->cs[0].off));
         hist->push_back(b);
         int64_t ns = (b.len + hs - 1) / hs;
         for (int64_t k = 0; k < ns; ++k) items->push_back({(1u << 30) | (uint32_t)h, 0u, (uint32_t)k, 0u});
@@ -2577,7 +2622,7 @@ static lt_status batch_upload(lt_ctx *c, BatchCache *bc, const std::vector<Batch
     if (st) return st;
     bc->bytes = total;
     if ((st = sync_all(c))) return st;  // the block's previous users are done
-    char *base = c->dev_base + bc->off;
+    char *base = dptr(c, bc->off);
     if (!jac.empty()) CK(c, cudaMemcpy(base + o_jac, jac.data(), jac.size() * sizeof(BatchJacobi), cudaMemcpyHostToDevice));
     if (!hist.empty()) CK(c, cudaMemcpy(base + o_hist, hist.data(), hist.size() * sizeof(BatchHist), cudaMemcpyHostToDevice));
     if (!items.empty())
@@ -2600,7 +2645,7 @@ static lt_status batch_upload(lt_ctx *c, BatchCache *bc, const std::vector<Batch
 
 // The work of one run on stream st: zero counters and histograms, run the queue.
 static cudaError_t batch_enqueue(lt_ctx *c, const BatchCache &bc, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(c->dev_base + bc.off + bc.counters_off, 0, bc.counters_bytes, st);
+    cudaError_t e = cudaMemsetAsync(dptr(c, bc.off + bc.counters_off), 0, bc.counters_bytes, st);
     if (e == cudaSuccess) e = k::launch_batch_zero_hist(bc.dev_hist, bc.nhist, st);
     if (e == cudaSuccess && bc.bp.nitems) e = k::launch_batch(bc.bp, bc.ctas, st);
     return e;

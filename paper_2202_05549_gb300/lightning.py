@@ -74,14 +74,22 @@ class Dist:
 
 
 class Array:
-    def __init__(self, ctx: "Context", dtype: int, shape, dist: Dist):
+    def __init__(self, ctx: "Context", dtype: int, shape, dist: Dist | None, wrap=None):
+        """wrap: (device pointer, element strides, owner) for a zero-copy
+        import of caller memory (lt_array_wrap_device); owner is kept alive."""
         self.ctx = ctx
         self.dtype = dtype
         self.shape = tuple(int(s) for s in shape)
         sh = (C.c_int64 * 3)(*(list(self.shape) + [1] * (3 - len(self.shape))))
-        d = dist.c()
         h = C.c_void_p()
-        check(L.load().lt_array_create(ctx.h, dtype, len(self.shape), sh, C.byref(d), C.byref(h)))
+        self._owner = None
+        if wrap is not None:
+            ptr, strides, self._owner = wrap
+            st = (C.c_int64 * 3)(*(list(strides) + [1] * (3 - len(strides))))
+            check(L.load().lt_array_wrap_device(ctx.h, dtype, len(self.shape), sh, st, C.c_void_p(ptr), C.byref(h)))
+        else:
+            d = dist.c()
+            check(L.load().lt_array_create(ctx.h, dtype, len(self.shape), sh, C.byref(d), C.byref(h)))
         self.h = h
 
     @property
@@ -221,6 +229,18 @@ class Context:
 
     def kernel(self, builtin, annotation, params) -> Kernel:
         return Kernel(self, builtin, annotation, params)
+
+    def wrap(self, tensor) -> Array:
+        """Zero-copy array over a CUDA tensor's memory (one chunk, never moved
+        or freed by the library).  The tensor's pending work is waited for
+        first; the tensor holds every launch's results after synchronize()."""
+        import torch
+        dt = {torch.float32: F32, torch.float64: F64, torch.uint8: U8, torch.bfloat16: BF16, torch.int32: U32}
+        if not tensor.is_cuda or tensor.dtype not in dt:
+            raise ValueError("wrap needs a CUDA tensor of float32, float64, uint8, bfloat16 or int32")
+        torch.cuda.current_stream(tensor.device).synchronize()
+        return Array(self, dt[tensor.dtype], tuple(tensor.shape), None,
+                     wrap=(tensor.data_ptr(), tuple(tensor.stride()), tensor))
 
     def kernel_from_source(self, source: str, name: str, annotation: str, params) -> Kernel:
         """Runtime-compiled user kernel (the paper's CudaKernelDef ... compile())."""

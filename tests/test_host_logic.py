@@ -468,3 +468,29 @@ def test_reduce_partials_in_place_when_regions_are_chunk_boxes():
         kh.launch(grid=(10_000,), block=(256,), superblock=(2_500,), args=[x, h])
         ctx.synchronize()
         assert ctx.stats()["reduce_inplace"] == 1
+
+
+def test_wrapped_device_memory_is_never_moved():
+    # a wrapped array's one chunk is the caller's memory: always resident,
+    # never evicted (even under a budget that forces the other array to
+    # spill), never freed by the library; launches use it directly
+    ny, nx = 512, 256
+    cb = (64 + 2) * nx * 4
+    with dry(budget=6 * cb, host=40 * cb) as ctx:
+        fake = 0x7F0000000000  # dry run: never dereferenced
+        U = lt.Array(ctx, lt.F32, (ny, nx), None, wrap=(fake, (nx, 1), None))
+        V = ctx.array(lt.F32, (ny, nx), lt.Dist.rows(64, halo=1))
+        k = ctx.kernel(lt.JACOBI2D, "global [i, j] => read U[i-1:i+1, j-1:j+1], write V[i, j]",
+                       [("U", lt.F32), ("V", lt.F32)])
+        plan = k.explain(grid=(nx, ny), block=(128, 4), superblock=(nx, 64), args=[U, V])
+        assert all(sb["args"][0]["kind"] == "direct" for sb in plan["superblocks"])
+        ctx.log_enable()
+        for _ in range(3):
+            k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, 64), args=[U, V])
+        ctx.synchronize()
+        u_id = [t for t in ctx.log() if t["kind"] == "execute"]
+        assert u_id
+        assert not any(t["kind"] in ("evict", "fetch") and t.get("array") == 1 for t in ctx.log())
+        U.destroy()
+        with pytest.raises(lt.LightningError):
+            lt.Array(ctx, lt.F32, (4, 4), None, wrap=(fake, (1, 4), None))  # innermost stride must be 1
