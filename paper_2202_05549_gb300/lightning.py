@@ -101,8 +101,12 @@ class Array:
         assert a.shape == self.shape, (a.shape, self.shape)
         check(L.load().lt_array_write(self.ctx.h, self.h, a.ctypes.data_as(C.c_void_p), a.nbytes))
 
-    def read(self) -> np.ndarray:
-        out = np.empty(self.shape, dtype=_NP[self.dtype])
+    def read(self, out: np.ndarray | None = None) -> np.ndarray:
+        """The whole array, into `out` if given (C-contiguous, this shape and
+        dtype; a pinned buffer makes the copy a direct DMA)."""
+        if out is None:
+            out = np.empty(self.shape, dtype=_NP[self.dtype])
+        assert out.shape == self.shape and out.dtype == _NP[self.dtype] and out.flags.c_contiguous
         check(L.load().lt_array_read(self.ctx.h, self.h, out.ctypes.data_as(C.c_void_p), out.nbytes))
         return out
 
