@@ -266,7 +266,7 @@ def plan_ooc(args, world):
     dev_slots = max(2 * nb - host_slots + 3, 6)  # a band task pins 4 chunks
     if args.hbm_gib > 0:
         dev_slots = max(int(args.hbm_gib * 2**30) // chunk_c, 6)
-        host_slots = 2 * nb - dev_slots + 3
+        host_slots = max(2 * nb - dev_slots + 3, 0)
         if host_slots * chunk_c > 0.6 * avail:
             raise SystemExit(f"--hbm-gib {args.hbm_gib}: the rest of the data does not fit in pinned host memory")
     budget = dev_slots * chunk_c + (64 << 20)
