@@ -398,8 +398,10 @@ lt_status lt_plan_explain(lt_ctx *ctx, lt_kernel *k, lt_dim3 grid, lt_dim3 block
                           const lt_arg *args, int32_t nargs, char *buf, size_t cap, size_t *needed);
 
 /* JSON log of the tasks enqueued since the last reset: kind, superblock,
- * chunks, predecessor task ids, memory actions (fetch / evict / dead).
- * Kept only while `enable` is 1 (lt_debug_log_enable), for tests. */
+ * chunks, predecessor task ids, memory actions (fetch / evict / dead);
+ * execute tasks add the kernel variant the built-in chose for the launch
+ * ("variant") and the CTA count.  Kept only while `enable` is 1
+ * (lt_debug_log_enable), for tests. */
 lt_status lt_debug_log_enable(lt_ctx *ctx, int32_t enable);
 lt_status lt_debug_log(lt_ctx *ctx, char *buf, size_t cap, size_t *needed);
 

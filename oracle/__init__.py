@@ -15,7 +15,7 @@ Functions and the passages they follow:
   stands in for HotSpot (Sec. 4.2), f32, zero ghosts, fixed sum order.
 * ``jacobi2d_ring_f64`` -- the same update in fp64 with arbitrary fixed or
   periodic ghost rings, used only to pin the definition.
-* ``jacobi3d`` -- 3-D 7-point variant.
+* ``jacobi3d`` / ``jacobi3d_lightcone`` -- 3-D 7-point variant.
 * ``gemm_f64`` / ``gemm_sample`` -- C = A B (Sec. 4.2 "GEMM") in fp64.
 * ``hist256`` -- the reduce(+) access mode (Sec. 2.3) as a 256-bin count.
 * ``diffusion_*`` -- variable-coefficient diffusion, its loss and its
@@ -188,6 +188,27 @@ def jacobi3d(u: np.ndarray, iters: int) -> np.ndarray:
     u = np.ascontiguousarray(u, np.float32)
     out = np.empty_like(u)
     _check(lib().orc_jacobi3d_f32(*u.shape, _ptr(u), _ptr(out), iters), "jacobi3d")
+    return out
+
+
+def jacobi3d_lightcone(shape, seed, stream, iters, sk, si, sj) -> np.ndarray:
+    """Cells (sk, si, sj) of ``iters`` 3-D Jacobi steps from the seeded
+    uniform field of ``shape``, each from its light cone alone: a cell after
+    n steps depends only on initial cells within n steps along every axis, so
+    the box [p - n, p + n] (clipped to the domain, where the zero ghosts are
+    the true ones) run through ``jacobi3d`` gives it exactly; the wrong zeros
+    beyond the box's inner faces move one cell per step and never reach p."""
+    import synth_inputs as si_mod
+
+    NZ, NY, NX = shape
+    out = np.empty(len(sk), np.float32)
+    for n, (k, i, j) in enumerate(zip(sk, si, sj)):
+        lo = [max(0, int(c) - iters) for c in (k, i, j)]
+        hi = [min(e - 1, int(c) + iters) for c, e in zip((k, i, j), shape)]
+        kk, ii, jj = np.meshgrid(*[np.arange(a, b + 1, dtype=np.uint64) for a, b in zip(lo, hi)], indexing="ij")
+        idx = (kk * np.uint64(NY) + ii) * np.uint64(NX) + jj
+        box = si_mod.gen_uniform_f32(seed, stream, idx.ravel()).reshape(kk.shape)
+        out[n] = jacobi3d(box, iters)[int(k) - lo[0], int(i) - lo[1], int(j) - lo[2]]
     return out
 
 

@@ -2229,7 +2229,7 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 std::ostringstream ex;
                 ex << ",\"superblocks\":[";
                 for (size_t oi = g0; oi < g1; ++oi) ex << (oi > g0 ? "," : "") << plan.sbs[order[oi]].index;
-                ex << "]";
+                ex << "],\"variant\":" << ep.variant << ",\"ctas\":" << ctas;
                 extra = ex.str();
             }
             if ((st = op_end(c, &exq, extra))) return st;

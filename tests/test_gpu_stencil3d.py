@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import synth_inputs as si
+from paper_2202_05549_gb300 import _lib as L
 from paper_2202_05549_gb300 import lightning as lt
 
 pytestmark = pytest.mark.gpu
@@ -23,32 +24,115 @@ def field3(nz, ny, nx, stream=0):
     return si.gen_uniform_f32(2203, 20 + stream, idx).reshape(nz, ny, nx)
 
 
+# distribution, block, superblock (x, y, z; rounded up to whole blocks), and
+# the kernel variant the launch takes: 2 = TMA plane ring (every superblock's
+# columns start 16-byte aligned), 0 = scalar (some do not)
 DISTS = {
-    "block": (lt.Dist.block(), (0, 0, 0)),
-    "tiles_halo": (lt.Dist.tiles((16, 24, 64), halo=(1, 1, 1)), (64, 24, 16)),
-    "tiles_nohalo": (lt.Dist.tiles((16, 24, 64)), (64, 24, 16)),
-    "zbands_halo": (lt.Dist.rows(10, halo=1), (0, 0, 10)),
-    "odd_sb": (lt.Dist.tiles((13, 30, 70), halo=(1, 1, 1)), (35, 15, 13)),
+    "block": (lt.Dist.block(), (64, 4, 1), (0, 0, 0), 2),
+    "tiles_halo": (lt.Dist.tiles((16, 24, 64), halo=(1, 1, 1)), (64, 4, 1), (64, 24, 16), 2),
+    "tiles_nohalo": (lt.Dist.tiles((16, 24, 64)), (64, 4, 1), (64, 24, 16), 2),
+    "zbands_halo": (lt.Dist.rows(10, halo=1), (64, 4, 1), (0, 0, 10), 2),
+    "odd_sb_rounded": (lt.Dist.tiles((13, 30, 70), halo=(1, 1, 1)), (64, 4, 1), (35, 15, 13), 2),
+    "odd_sb": (lt.Dist.tiles((13, 30, 70), halo=(1, 1, 1)), (5, 3, 1), (35, 15, 13), 0),
 }
+
+
+def variants(ctx):
+    return {t["variant"] for t in ctx.log() if t["kind"] == "execute"}
 
 
 @pytest.mark.parametrize("name", sorted(DISTS))
 def test_jacobi3d_bit_exact(name):
+    # 37 x 50 x 133: ragged against the staged kernel's 32-plane units,
+    # 32-row and 128-column tiles (the last column tile is 5 wide)
     nz, ny, nx, iters = 37, 50, 133, 3
     u0 = field3(nz, ny, nx)
     want = oracle.jacobi3d(u0, iters)
-    dist, sb = DISTS[name]
+    dist, block, sb, variant = DISTS[name]
     with lt.Context() as ctx:
+        ctx.log_enable()
         U = ctx.array(lt.F32, (nz, ny, nx), dist)
         V = ctx.array(lt.F32, (nz, ny, nx), dist)
         U.write(u0)
         k = ctx.kernel(lt.JACOBI3D, ANN, [("U", lt.F32), ("V", lt.F32)])
         for _ in range(iters):
-            k.launch(grid=(nx, ny, nz), block=(64, 4, 1), superblock=sb, args=[U, V])
+            k.launch(grid=(nx, ny, nz), block=block, superblock=sb, args=[U, V])
             U, V = V, U
         ctx.synchronize()
         got = U.read()
+        ran = variants(ctx)
     assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
+    assert ran == {variant}
+
+
+def test_jacobi3d_many_chunks_take_the_register_kernel():
+    # 512 chunks in one launch: more than the staged kernel's tensor maps, so
+    # the register-strip kernel runs
+    shape = (8, 64, 256)
+    u0 = field3(*shape, stream=3)
+    with lt.Context() as ctx:
+        ctx.log_enable()
+        dist = lt.Dist.tiles((1, 8, 32), halo=(1, 1, 1))
+        U = ctx.array(lt.F32, shape, dist)
+        V = ctx.array(lt.F32, shape, dist)
+        U.write(u0)
+        k = ctx.kernel(lt.JACOBI3D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        for _ in range(2):
+            k.launch(grid=shape[::-1], block=(32, 4, 1), superblock=(32, 8, 1), args=[U, V])
+            U, V = V, U
+        ctx.synchronize()
+        assert np.array_equal(U.read(), oracle.jacobi3d(u0, 2))
+        assert variants(ctx) == {1}
+
+
+def test_jacobi3d_units_outnumber_ctas():
+    # 40 x 300 x 1000 in 8-plane slabs: 5 tasks x 8 x 10 tiles x 1 unit = 400
+    # units, more than the resident CTAs, so CTAs stream several units and the
+    # plane ring carries loads across unit boundaries
+    shape = (40, 300, 1000)
+    u0 = field3(*shape, stream=4)
+    with lt.Context() as ctx:
+        ctx.log_enable()
+        U = ctx.array(lt.F32, shape, lt.Dist.rows(8, halo=1))
+        V = ctx.array(lt.F32, shape, lt.Dist.rows(8, halo=1))
+        U.write(u0)
+        k = ctx.kernel(lt.JACOBI3D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        for _ in range(3):
+            k.launch(grid=shape[::-1], block=(128, 4, 1), superblock=(1000, 300, 8), args=[U, V])
+            U, V = V, U
+        ctx.synchronize()
+        assert np.array_equal(U.read(), oracle.jacobi3d(u0, 3))
+        assert variants(ctx) == {2}
+
+
+def test_jacobi3d_full_size_lightcone_samples():
+    # the configuration bench.py times: 1024^3 f32 in 128-plane z-slabs with
+    # a 1-plane halo, one run of 10 iterations; 192 cells (corners, faces,
+    # slab seams, unit and tile seams) against the oracle's light cone
+    n, slab, iters = 1024, 128, 10
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 0), (n - 1, 0, n - 1), (n // 2, 0, n // 2),
+           (n // 2, n - 1, 5), (7, 9, n - 1), (n - 1, 300, 0)]
+    for z in (slab - 1, slab, 31, 32, 3 * slab - 1, 3 * slab):
+        for y, x in ((31, 127), (32, 128), (500, 511), (0, 640), (n - 1, 129)):
+            pts.append((z, y, x))
+    r = si.gen_u64(2208, 79, np.arange(3 * 154, dtype=np.uint64))
+    pts += [(int(r[3 * m] % np.uint64(n)), int(r[3 * m + 1] % np.uint64(n)), int(r[3 * m + 2] % np.uint64(n)))
+            for m in range(192 - len(pts))]
+    sk, si_, sj = (np.array(c, np.int64) for c in zip(*pts))
+    with lt.Context() as ctx:
+        ctx.log_enable()
+        U = ctx.array(lt.F32, (n, n, n), lt.Dist.rows(slab, halo=1))
+        V = ctx.array(lt.F32, (n, n, n), lt.Dist.rows(slab, halo=1))
+        U.fill(L.LT_INIT_UNIFORM, seed=2208, stream=0)
+        k = ctx.kernel(lt.JACOBI3D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=(n, n, n), block=(128, 4, 1), superblock=(n, n, slab), args=[U, V])
+            U, V = V, U
+        ctx.synchronize()
+        assert variants(ctx) == {2}
+        got = np.array([U.read_box((a, b, c), (a, b, c))[0, 0, 0] for a, b, c in pts], np.float32)
+    want = oracle.jacobi3d_lightcone((n, n, n), 2208, 0, iters, sk, si_, sj)
+    assert np.array_equal(got, want), f"{np.sum(got != want)} of {len(want)} sampled cells differ"
 
 
 def test_jacobi3d_degenerate_and_larger():

@@ -190,6 +190,15 @@ def test_jacobi_lightcone_equals_full_run():
     assert np.array_equal(got.reshape(NY, NX), full)
 
 
+def test_jacobi3d_lightcone_equals_full_run():
+    shape, T = (9, 11, 13), 3
+    idx = np.arange(9 * 11 * 13, dtype=np.uint64)
+    full = oracle.jacobi3d(si.gen_uniform_f32(2208, 0, idx).reshape(shape), T)
+    kk, ii, jj = np.meshgrid(*[np.arange(e) for e in shape], indexing="ij")
+    got = oracle.jacobi3d_lightcone(shape, 2208, 0, T, kk.ravel(), ii.ravel(), jj.ravel())
+    assert np.array_equal(got.reshape(shape), full)
+
+
 def test_jacobi3d_sine_mode_closed_form_and_f32():
     nz, ny, nx, T = 5, 7, 9, 6
     z = np.arange(nz)[:, None, None]
