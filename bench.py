@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--rows", type=int, default=262144, help="grid rows (ooc)")
     p.add_argument("--cols", type=int, default=131072, help="grid columns (ooc)")
     p.add_argument("--band", type=int, default=8192)
+    p.add_argument("--no-staged", action="store_true",
+                   help="stencil built-ins use their register kernels instead of the TMA-staged ones")
     p.add_argument("--hbm-gib", type=float, default=0.0,
                    help="cap the HBM budget (GiB): out-of-core, below one array the launches stream every step; "
                         "the other workloads take it as their pool size")
@@ -225,6 +227,13 @@ __device__ void jacobi(dim3 vb, int64_t ny, int64_t nx, lightning::Matrix<float>
 """
 
 
+def ctx_flags(args):
+    """Context flags of the timed runs: per-kernel CUDA events, and the
+    register stencil kernels when --no-staged asks for them."""
+    from paper_2202_05549_gb300 import _lib as L
+    return L.LT_FLAG_TIMING | (L.LT_FLAG_NO_STAGED if args.no_staged else 0)
+
+
 def hbm_cap(args):
     """HBM pool of the in-HBM workloads: --hbm-gib if given (small pools let
     ncu's kernel replay save and restore device memory), else 0 = the library
@@ -234,8 +243,9 @@ def hbm_cap(args):
 
 def kernel_traffic(kernel, units):
     """DRAM bytes of one launch of `kernel` processing `units` cells, scaled
-    from an ncu capture (profiles/traffic.json), or None when the kernel's
-    sources have changed since the counters were taken."""
+    from an ncu capture (profiles/traffic.json; a key may name a workload
+    after '@' when its traffic differs, e.g. an L2-sized grid), or None when
+    the kernel's sources have changed since the counters were taken."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
@@ -290,7 +300,7 @@ def run_lightning(args, rank, world, local, grp):
     if args.workload == "ooc":
         pl = plan_ooc(args, world)
         ny, nx, band = pl["ny"], pl["nx"], pl["band"]
-        ctx = lt.Context(device=local, hbm_budget=pl["budget"], host_pool=pl["host"], flags=L.LT_FLAG_TIMING)
+        ctx = lt.Context(device=local, hbm_budget=pl["budget"], host_pool=pl["host"], flags=ctx_flags(args))
         dist = lt.Dist.rows(band, halo=tb)
         sb = (nx, band)
         seed = si.SEED_JACOBI_OOC
@@ -299,7 +309,7 @@ def run_lightning(args, rank, world, local, grp):
     else:
         ny = nx = 4096
         pl = dict(budget=0, host=0, chunk_bytes=None, data_bytes=2 * ny * nx * 4)
-        ctx = lt.Context(device=local, hbm_budget=hbm_cap(args), flags=L.LT_FLAG_TIMING)
+        ctx = lt.Context(device=local, hbm_budget=hbm_cap(args), flags=ctx_flags(args))
         sb = (1024, 1024)
         band = 1024
         seed = si.SEED_JACOBI_INCORE
@@ -337,9 +347,21 @@ def run_lightning(args, rank, world, local, grp):
             bufs.reverse()
         ctx.synchronize()
 
+    ctx.log_enable()
     for _ in range(args.warmup):
         step()
     ctx.synchronize()
+    # which of the built-in's kernels the launches took
+    variant = max((t.get("variant", 0) for t in ctx.log() if t["kind"] == "execute"), default=0)
+    ctx.log_enable(False)
+    if tb > 1:
+        kname = "jacobi2d_multi_kernel"
+    elif user:
+        kname = "lt_user_wrapper (NVRTC)"
+    else:
+        kname = {2: "jacobi2d_tma_kernel", 1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
+    # DRAM traffic records: the in-core grid keeps part of its working set in L2
+    tkey = kname + ("@incore4096" if args.workload != "ooc" and tb == 1 else "")
     ctx.reset_stats()
     grp.barrier()
     clk = Clocks(local)
@@ -377,10 +399,8 @@ def run_lightning(args, rank, world, local, grp):
                    else "working set 128 MiB ~ L2 size; not flushed"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": round(achieved / peaks["hbm_gbs"], 4),
-                     "traffic": None if user else kernel_traffic(
-                         "jacobi2d_multi_kernel" if tb > 1 else "jacobi2d_vec_kernel", cells_per_launch / tb),
-                     "kernel": ("jacobi2d_multi_kernel" if tb > 1 else
-                                "lt_user_wrapper (NVRTC)" if user else "jacobi2d_vec_kernel"), "launch_ms": round(ex_ms, 4),
+                     "traffic": None if user else kernel_traffic(tkey, cells_per_launch / tb),
+                     "kernel": kname, "launch_ms": round(ex_ms, 4),
                      "bytes_per_launch": 8.0 * cells_per_launch, "peak_source": peaks["source"]},
         "host_link": {"bytes_h2d_per_step": st["bytes_h2d"] / args.steps,
                       "bytes_d2h_per_step": st["bytes_d2h"] / args.steps,
@@ -449,7 +469,7 @@ def run_jacobi3d(args, rank, world, local, grp):
     peaks = measured_peaks()
     n, slab = args.n3, args.slab
     iters = args.iters or 10
-    ctx = lt.Context(device=local, hbm_budget=hbm_cap(args), flags=L.LT_FLAG_TIMING)
+    ctx = lt.Context(device=local, hbm_budget=hbm_cap(args), flags=ctx_flags(args))
     dist = lt.Dist.rows(slab, halo=1)
     U = ctx.array(lt.F32, (n, n, n), dist)
     V = ctx.array(lt.F32, (n, n, n), dist)
@@ -651,9 +671,21 @@ def run_gemm(args, rank, world, local, grp):
     def step():
         k.launch(grid=(n, n), block=(256, 1), superblock=(t, t), args=[A, B, Cm])
 
+    ctx.log_enable()
     for _ in range(args.warmup):
         step()
     ctx.synchronize()
+    # which of the built-in's kernels the launches took
+    variant = max((t.get("variant", 0) for t in ctx.log() if t["kind"] == "execute"), default=0)
+    ctx.log_enable(False)
+    if tb > 1:
+        kname = "jacobi2d_multi_kernel"
+    elif user:
+        kname = "lt_user_wrapper (NVRTC)"
+    else:
+        kname = {2: "jacobi2d_tma_kernel", 1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
+    # DRAM traffic records: the in-core grid keeps part of its working set in L2
+    tkey = kname + ("@incore4096" if args.workload != "ooc" and tb == 1 else "")
     ctx.reset_stats()
     grp.barrier()
     clk = Clocks(local)

@@ -110,10 +110,13 @@ typedef struct {
  *   computed; lt_array_read/write/fill only update bookkeeping), for tests of
  *   the host logic; LT_FLAG_FIXED_SWEEP visits superblocks in index order
  *   every launch (default: the order alternates between launches, so the
- *   chunks used last are reused first). */
+ *   chunks used last are reused first); LT_FLAG_NO_STAGED makes the stencil
+ *   built-ins use their register kernels instead of the TMA-staged ones (same
+ *   results; for comparing the two). */
 #define LT_FLAG_TIMING 1
 #define LT_FLAG_DRYRUN 2
 #define LT_FLAG_FIXED_SWEEP 4
+#define LT_FLAG_NO_STAGED 8
 
 typedef struct {
     size_t hbm_budget_bytes;
@@ -384,6 +387,7 @@ typedef struct {
     uint64_t tables_resident; /* descriptor tables reused on the device without a copy */
     uint64_t plans_reused;    /* launches whose plan came from the kernel's plan cache */
     uint64_t reduce_inplace;  /* reduce partials accumulated in their destination chunk (no copy) */
+    uint64_t bytes_replica_wt; /* halo-replica bytes the Execute kernels wrote themselves (no copy step) */
 } lt_stats;
 
 lt_status lt_stats_get(lt_ctx *ctx, lt_stats *out);

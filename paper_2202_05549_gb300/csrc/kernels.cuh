@@ -21,6 +21,19 @@ struct DView {
 
 #define LT_MAX_ARRAYS 5
 
+// A halo copy that an Execute kernel keeps current itself: the cells of the
+// box [lo, hi] (global indices, axis 0 slowest), which task `task` writes,
+// are also computed by extra CTAs of the same kernel, from that task's input
+// views, and stored to `dst`, the view of another chunk whose halo holds a
+// copy of them.  This replaces the copy step after the kernel.
+struct ReplicaTarget {
+    DView dst;
+    int64_t lo[3], hi[3];
+    uint64_t cell_begin;  // prefix sum of the box volumes over the launch's replicas
+    int32_t task;
+    int32_t pad;
+};
+
 // One Execute task: a superblock's thread box and its argument views.
 struct ExecTask {
     int64_t t_lo[3], t_hi[3];     // thread box (x, y, z), inclusive
@@ -42,6 +55,12 @@ struct ExecParams {
     int32_t variant;                  // kernel variant chosen by prepare_*
     int32_t red_op;                   // operator of the reduce(f) argument (0 + 1 * 2 min 3 max)
     int32_t uniform_ctas;             // if > 0: task i owns CTAs [i * uniform_ctas, (i + 1) * uniform_ctas)
+    const ReplicaTarget *reps;        // write-through replicas of the launch (null if none) ...
+    uint64_t rep_cells;               // ... their cells in total, computed by CTAs main_ctas .. of the grid
+    uint32_t nreps;
+    uint32_t main_ctas;               // CTAs of the tasks (the grid's first CTAs)
+    int32_t no_staged;                // 1: prepare_* picks no TMA-staged kernel (context flag)
+    int32_t pad;
 };
 
 // Box copy (pack / unpack / replica update): copy the global box [lo, hi]

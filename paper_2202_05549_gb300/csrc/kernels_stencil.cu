@@ -52,6 +52,10 @@ constexpr int JV = 8;        // rows per warp strip of the single-step kernel
 // every CTA.
 template <int R>
 __global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    if (blockIdx.x >= p.main_ctas) {  // write-through replica CTAs
+        jacobi_replica_cell(tasks, p, (uint64_t)(blockIdx.x - p.main_ctas) * blockDim.x + threadIdx.x);
+        return;
+    }
     int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
@@ -71,6 +75,10 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTas
 
 // Scalar variant for unaligned tasks: one thread per output cell.
 __global__ void __launch_bounds__(256) jacobi2d_scalar_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
+    if (blockIdx.x >= p.main_ctas) {  // write-through replica CTAs
+        jacobi_replica_cell(tasks, p, (uint64_t)(blockIdx.x - p.main_ctas) * blockDim.x + threadIdx.x);
+        return;
+    }
     int ti = task_of(tasks, p, blockIdx.x);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
@@ -131,11 +139,17 @@ uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p) {
     return total;
 }
 
+// The grid is the tasks' CTAs followed by the write-through replica CTAs
+// (one thread per replica cell).
 cudaError_t launch_jacobi2d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
+    const uint32_t threads = p.variant == 1 ? JWARPS * 32 : 256;
+    const uint64_t extra = (p.rep_cells + threads - 1) / threads;
+    if ((uint64_t)p.main_ctas + extra > 0x7FFFFFFFull || p.main_ctas != ctas) return cudaErrorInvalidValue;
+    const uint32_t grid = ctas + (uint32_t)extra;
     if (p.variant == 1)
-        jacobi2d_vec_kernel<JV><<<ctas, JWARPS * 32, 0, st>>>(dev, p);
+        jacobi2d_vec_kernel<JV><<<grid, threads, 0, st>>>(dev, p);
     else
-        jacobi2d_scalar_kernel<<<ctas, 256, 0, st>>>(dev, p);
+        jacobi2d_scalar_kernel<<<grid, threads, 0, st>>>(dev, p);
     return cudaGetLastError();
 }
 

@@ -462,7 +462,7 @@ uint32_t prepare_jacobi3d(ExecTask *t, int n, ExecParams &p) {
             if (t[i].v[a].s[2] != 1 || t[i].v[a].s[1] % 4 != 0 || t[i].v[a].s[0] % 4 != 0 ||
                 t[i].v[a].base % 16 != 0)
                 vec = false;
-    if (vec) {
+    if (vec && !p.no_staged) {
         const uint32_t ctas = prepare_jacobi3d_tma(t, n, p);
         if (ctas) {
             p.variant = 2;

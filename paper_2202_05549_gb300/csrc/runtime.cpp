@@ -180,6 +180,7 @@ struct BuiltinDef {
     cudaError_t (*launch)(const ExecTask *, uint32_t, const ExecParams &, cudaStream_t);
     bool reduce_zero = true;  // reduce partials must start at the identity (else the kernel writes every cell)
     bool any_reduce_op = false;  // the reduce argument may use any of + * min max
+    int write_through = -1;      // array slot whose halo replicas the kernel writes itself (ExecTask.rep_*)
 };
 
 const BuiltinDef kBuiltins[] = {
@@ -187,7 +188,7 @@ const BuiltinDef kBuiltins[] = {
     {LT_K_STENCIL1D, "global i => write A0[i], read A1[i-1:i+1]", 2, {LT_F32, LT_F32}, {1, 1},
      k::prepare_stencil1d, k::launch_stencil1d},
     {LT_K_JACOBI2D, "global [i, j] => read A0[i-1:i+1, j-1:j+1], write A1[i, j]", 2, {LT_F32, LT_F32}, {2, 2},
-     k::prepare_jacobi2d, k::launch_jacobi2d},
+     k::prepare_jacobi2d, k::launch_jacobi2d, true, false, 1},
     {LT_K_JACOBI3D, "global [k, i, j] => read A0[k-1:k+1, i-1:i+1, j-1:j+1], write A1[k, i, j]", 2,
      {LT_F32, LT_F32}, {3, 3}, k::prepare_jacobi3d, k::launch_jacobi3d},
     {LT_K_HIST256, "global i => read A0[i], reduce(+) A1[:]", 2, {LT_U8, LT_U32}, {1, 1}, k::prepare_hist256,
@@ -298,6 +299,7 @@ struct UploadUse {
 struct lt_ctx {
     lt_config cfg{};
     bool dry = false;
+    bool no_staged = false;  // LT_FLAG_NO_STAGED
     bool poisoned = false;
     cudaStream_t st[NSTREAM] = {nullptr, nullptr, nullptr};
     uint64_t seq[NSTREAM] = {0, 0, 0};
@@ -1043,6 +1045,7 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     auto c = std::make_unique<lt_ctx>();
     c->cfg = *cfg;
     c->dry = (cfg->flags & LT_FLAG_DRYRUN) != 0;
+    c->no_staged = (cfg->flags & LT_FLAG_NO_STAGED) != 0;
     for (int s = 0; s < NSTREAM; ++s) {
         c->ev[s].assign(RING, nullptr);
         c->evseq[s].assign(RING, 0);
@@ -1855,6 +1858,7 @@ lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const 
     ep.block[1] = (int64_t)(block.y ? block.y : 1);
     ep.block[2] = (int64_t)(block.z ? block.z : 1);
     ep.err = c->err_word;
+    ep.no_staged = c->no_staged ? 1 : 0;
     for (size_t p = 0; p < parr.size(); ++p)
         if (k->stmt_of_param[p] >= 0 && k->ann.stmts[(size_t)k->stmt_of_param[p]].mode == MODE_REDUCE)
             ep.red_op = k->ann.stmts[(size_t)k->stmt_of_param[p]].op;
@@ -2161,7 +2165,20 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 }
         }
         // --- execute (all superblocks of the group in one kernel)
+        // A kernel that keeps halo replicas itself (write_through) writes the
+        // replicas of a write-only argument no other parameter aliases; its
+        // tasks carry the replica boxes and no copy step follows for them.
+        auto writes_through = [&](const ArgPlan &ap, int sl) {
+            if (k->ufn || def->write_through < 0 || sl != def->write_through) return false;
+            if (ap.kind != ARG_DIRECT || ap.mode != MODE_WRITE || ap.replicas.empty()) return false;
+            for (size_t j = 0; j < parr.size(); ++j)
+                if ((int)j != ap.param && parr[j] == parr[(size_t)ap.param]) return false;
+            return true;
+        };
         std::vector<ExecTask> tasks;
+        std::vector<ReplicaTarget> reps;
+        uint64_t rep_cells = 0;
+        std::vector<CState *> wt_chunks;  // replica chunks the execute kernel writes
         FenceSet ex_wait = temp_fences;
         ex_wait.merge(temp_ready);
         ex_wait.merge(red_fence);
@@ -2184,6 +2201,25 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                     t.v[sl] = view_of(c, a->g, a->g.chunks[(size_t)ap.chunk], cs.off);
                     ex_wait.merge(cs.ready);
                     if (ap.mode != MODE_READ) ex_wait.merge(cs.busy);
+                    if (writes_through(ap, sl)) {
+                        for (const auto &pc : ap.replicas) {
+                            CState &dcs = a->cs[(size_t)pc.chunk];
+                            ReplicaTarget r{};
+                            r.dst = view_of(c, a->g, a->g.chunks[(size_t)pc.chunk], dcs.off);
+                            for (int d = 0; d < 3; ++d) {
+                                r.lo[d] = d < a->g.nd ? pc.box.lo[d] : 0;
+                                r.hi[d] = d < a->g.nd ? pc.box.hi[d] : 0;
+                            }
+                            r.task = (int32_t)tasks.size();
+                            r.cell_begin = rep_cells;
+                            rep_cells += (uint64_t)pc.box.volume();
+                            reps.push_back(r);
+                            ex_wait.merge(dcs.ready);
+                            ex_wait.merge(dcs.busy);
+                            wt_chunks.push_back(&dcs);
+                            c->stats.bytes_replica_wt += (uint64_t)pc.box.volume() * a->g.esize();
+                        }
+                    }
                 } else if (ap.kind == ARG_PACK || ap.kind == ARG_TEMPW) {
                     const TempAlloc &tm = temps[(size_t)temp_of[oi - g0][ai]];
                     t.v[sl] = view_of(c, a->g, tm.geom, tm.off);
@@ -2209,9 +2245,18 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                                 "chunks of each per launch; the multi-step stencil 1 <= k <= 16; K-Means "
                                 "1 <= k <= 64 and arrays of 4k / 5k elements; a source kernel virtual block "
                                 "indices below 2^32");
+            // one table: the tasks, then their replica targets
+            const size_t tbytes = tasks.size() * sizeof(ExecTask), rbytes = reps.size() * sizeof(ReplicaTarget);
+            std::vector<char> table(tbytes + rbytes);
+            std::memcpy(table.data(), tasks.data(), tbytes);
+            if (rbytes) std::memcpy(table.data() + tbytes, reps.data(), rbytes);
             void *dptr;
             size_t roff;
-            if ((st = upload(c, tasks.data(), tasks.size() * sizeof(ExecTask), &dptr, &roff))) return st;
+            if ((st = upload(c, table.data(), table.size(), &dptr, &roff))) return st;
+            ep.reps = (rbytes && dptr) ? (const ReplicaTarget *)((const char *)dptr + tbytes) : nullptr;
+            ep.nreps = (uint32_t)reps.size();
+            ep.rep_cells = ep.reps ? rep_cells : 0;
+            ep.main_ctas = ctas;
             if (!c->dry && ctas) {
                 TimeScope ts(c, CAT_EXEC);
                 if (k->ufn) {
@@ -2229,11 +2274,15 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 std::ostringstream ex;
                 ex << ",\"superblocks\":[";
                 for (size_t oi = g0; oi < g1; ++oi) ex << (oi > g0 ? "," : "") << plan.sbs[order[oi]].index;
-                ex << "],\"variant\":" << ep.variant << ",\"ctas\":" << ctas;
+                ex << "],\"variant\":" << ep.variant << ",\"ctas\":" << ctas << ",\"replicas\":" << reps.size();
                 extra = ex.str();
             }
             if ((st = op_end(c, &exq, extra))) return st;
-            upload_done(c, roff, tasks.size() * sizeof(ExecTask), exq);
+            upload_done(c, roff, table.size(), exq);
+            for (CState *d : wt_chunks) {
+                d->ready = FenceSet::one(S_COMP, exq);
+                d->busy.add(S_COMP, exq);
+            }
             c->stats.tasks_execute += tasks.size();
             for (auto &u : uses) {
                 CState &cs = u.a->cs[(size_t)u.chunk];
@@ -2256,7 +2305,8 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             for (size_t ai = 0; ai < sb.args.size(); ++ai) {
                 const auto &ap = sb.args[ai];
                 lt_array *a = ap.param >= 0 && ap.kind != ARG_VALUE ? parr[(size_t)ap.param] : nullptr;
-                if (ap.kind == ARG_DIRECT && ap.mode != MODE_READ) {
+                if (ap.kind == ARG_DIRECT && ap.mode != MODE_READ &&
+                    !writes_through(ap, k->slot_of_param[(size_t)ap.param])) {
                     for (const auto &pc : ap.replicas) {
                         CopyPiece cp{};
                         cp.src = view_of(c, a->g, a->g.chunks[(size_t)ap.chunk], a->cs[(size_t)ap.chunk].off);
@@ -2318,7 +2368,8 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 for (const auto &ap : plan.sbs[order[oi]].args) {
                     if (ap.kind == ARG_VALUE) continue;
                     lt_array *a = parr[(size_t)ap.param];
-                    if (ap.kind == ARG_DIRECT && ap.mode != MODE_READ) {
+                    if (ap.kind == ARG_DIRECT && ap.mode != MODE_READ &&
+                        !writes_through(ap, k->slot_of_param[(size_t)ap.param])) {
                         a->cs[(size_t)ap.chunk].busy.add(S_COMP, outq);
                         for (const auto &pc : ap.replicas) {
                             CState &d = a->cs[(size_t)pc.chunk];

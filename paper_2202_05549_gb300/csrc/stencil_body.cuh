@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "div_const.cuh"
+#include "kernels.cuh"
 
 namespace lt {
 
@@ -98,6 +99,35 @@ __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float 
             if (j0 + 2 <= xe) dst[2] = o.z;
         }
     }
+}
+
+// Write-through replicas (ExecParams.reps): thread `cell` of the CTAs that
+// follow the tasks' CTAs computes one replica cell from the input view of the
+// task that owns it, with the same operations as that task, and stores it to
+// the replica's view.
+__device__ __forceinline__ void jacobi_replica_cell(const ExecTask *tasks, const ExecParams &p, uint64_t cell) {
+    if (cell >= p.rep_cells) return;
+    int lo = 0, hi = (int)p.nreps - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.reps[mid].cell_begin <= cell)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const ReplicaTarget &r = p.reps[lo];
+    const uint64_t l = cell - r.cell_begin, w = (uint64_t)(r.hi[1] - r.lo[1] + 1);
+    const int64_t i = r.lo[0] + (int64_t)(l / w), j = r.lo[1] + (int64_t)(l % w);
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    const DView U = tasks[r.task].v[0];
+    const float *u = (const float *)U.base;
+    auto at = [&](int64_t a, int64_t b) { return u[a * U.s[0] + b * U.s[1]]; };
+    const float c = at(i, j);
+    const float n = i > 0 ? at(i - 1, j) : 0.f;
+    const float s = i + 1 < NY ? at(i + 1, j) : 0.f;
+    const float wv = j > 0 ? at(i, j - 1) : 0.f;
+    const float e = j + 1 < NX ? at(i, j + 1) : 0.f;
+    ((float *)r.dst.base)[i * r.dst.s[0] + j * r.dst.s[1]] = j5(c, n, s, wv, e);
 }
 
 }  // namespace lt

@@ -22,6 +22,12 @@ def _built():
     __graft_entry__.build()
 
 
+def variants(ctx):
+    """Kernel variants the Execute tasks logged since logging was enabled:
+    1 register strips, 0 scalar."""
+    return {t["variant"] for t in ctx.log() if t["kind"] == "execute"}
+
+
 def run_jacobi(ctx, u0, dist, iters, block=(128, 4), superblock=(0, 0), fill_seed=None):
     ny, nx = u0.shape
     U = ctx.array(lt.F32, (ny, nx), dist)
@@ -101,17 +107,46 @@ def test_jacobi_all_distributions_bit_exact(name, sbshape):
     want = oracle.jacobi2d(u0, iters)
     block = (32, 4) if sbshape == (96, 32) else (128, 4)
     with lt.Context() as ctx:
+        ctx.log_enable()
         got = run_jacobi(ctx, u0, DISTS[name], iters, block=block, superblock=sbshape)
+        ran = variants(ctx)
     assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
+    assert ran == {1}  # every superblock starts on a multiple of 4 columns
 
 
 def test_jacobi_degenerate_shapes():
     with lt.Context() as ctx:
+        ctx.log_enable()
         for (ny, nx) in [(1, 1), (1, 7), (9, 1), (2, 3), (5, 129)]:
             u0 = si.uniform_field(2203, 5, ny, nx)
             for dist in (lt.Dist.block(), lt.Dist.tiles((2, 2), halo=(1, 1)), lt.Dist.tiles((1, 2))):
                 got = run_jacobi(ctx, u0, dist, 3, block=(1, 1), superblock=(2, 2))
                 assert np.array_equal(got, oracle.jacobi2d(u0, 3)), (ny, nx)
+        # superblocks two columns wide: single-superblock launches take the
+        # strip kernel, the others the scalar one
+        assert variants(ctx) == {0, 1}
+
+
+@pytest.mark.parametrize("block", [(64, 4), (1, 4)])
+def test_jacobi_write_through_replicas_many_chunks(block):
+    # 8 x 16 = 128 chunks with 1-cell halos: every launch writes ~900
+    # replica boxes (edges and corners) from the replica CTAs appended to the
+    # strip kernel's grid (block (64, 4)) or the scalar kernel's ((1, 4): odd
+    # superblock columns)
+    ny, nx = 256, 1024
+    u0 = si.uniform_field(2203, 13, ny, nx)
+    sb = (64, 32) if block[0] == 64 else (63, 32)
+    with lt.Context() as ctx:
+        ctx.log_enable()
+        got = run_jacobi(ctx, u0, lt.Dist.tiles((32, 64), halo=(1, 1)), 3, block=block, superblock=sb)
+        ran = variants(ctx)
+        st = ctx.stats()
+        unpacks = [t for t in ctx.log() if t["kind"] == "unpack"]
+    assert np.array_equal(got, oracle.jacobi2d(u0, 3))
+    assert ran == ({1} if block[0] == 64 else {0})
+    assert st["bytes_replica_wt"] > 0
+    if block[0] == 64:
+        assert not unpacks  # superblocks equal the chunks: every write is direct
 
 
 def test_jacobi_grid_larger_than_array_and_superblock_order():

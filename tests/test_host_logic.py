@@ -246,13 +246,34 @@ def test_dependencies_between_successive_launches():
         log = ctx.log()
         ex = [t for t in log if t["kind"] == "execute"]
         un = [t for t in log if t["kind"] == "unpack"]
-        assert len(ex) == 2 and len(un) == 2
+        # the Jacobi kernel writes the halo replicas of its output itself: no copy step
+        assert len(ex) == 2 and not un
+        assert ex[0]["replicas"] == 6 and ex[1]["replicas"] == 6  # 4 bands: 3 seams x 2 sides
         l1, l2 = ex[0]["launch"], ex[1]["launch"]
         assert l2 > l1
-        # launch 2 must wait for launch 1's writes of V (execute + replica copies)
-        assert un[0]["id"] in ex[1]["deps"] or ex[0]["id"] in ex[1]["deps"]
-        # its write of U (read by launch 1) must come after launch 1's reads
-        assert ex[0]["id"] in ex[1]["deps"] or un[0]["id"] in ex[1]["deps"]
+        # launch 2 must wait for launch 1's writes of V (its outputs and replicas)
+        # and its write of U (read by launch 1) must come after launch 1's reads
+        assert ex[0]["id"] in ex[1]["deps"]
+        s = ctx.stats()
+        assert s["bytes_replica_wt"] == 2 * 6 * 64 * 4
+
+
+def test_replica_copies_remain_for_kernels_that_do_not_write_through():
+    # the multi-step stencil keeps the copy step for its k-row halo replicas
+    with dry(flags=L.LT_FLAG_FIXED_SWEEP) as ctx:
+        dist = lt.Dist.rows(16, halo=2)
+        U = ctx.array(lt.F32, (64, 64), dist)
+        V = ctx.array(lt.F32, (64, 64), dist)
+        U.fill(L.LT_INIT_UNIFORM, seed=1)
+        km = ctx.kernel(lt.JACOBI2D_MULTI, "global [i, j] => read U[i-2:i+2, j-2:j+2], write V[i, j]",
+                        [("U", lt.F32), ("V", lt.F32), ("k", lt.U32, False)])
+        ctx.log_enable()
+        km.launch(grid=(64, 64), block=(64, 4), superblock=(64, 16), args=[U, V, 2])
+        log = ctx.log()
+        ex = [t for t in log if t["kind"] == "execute"]
+        un = [t for t in log if t["kind"] == "unpack"]
+        assert len(ex) == 1 and ex[0]["replicas"] == 0 and len(un) == 1
+        assert un[0]["id"] > ex[0]["id"] and ex[0]["id"] in un[0]["deps"]
 
 
 def test_write_only_chunks_are_not_fetched_and_spill_roundtrip():
