@@ -56,9 +56,9 @@ struct ExecParams {
     int32_t red_op;                   // operator of the reduce(f) argument (0 + 1 * 2 min 3 max)
     int32_t uniform_ctas;             // if > 0: task i owns CTAs [i * uniform_ctas, (i + 1) * uniform_ctas)
     const ReplicaTarget *reps;        // write-through replicas of the launch (null if none) ...
-    uint64_t rep_cells;               // ... their cells in total, computed by CTAs main_ctas .. of the grid
+    uint64_t rep_cells;               // ... their cells in total, one thread each in the grid's first CTAs
     uint32_t nreps;
-    uint32_t main_ctas;               // CTAs of the tasks (the grid's first CTAs)
+    uint32_t rep_ctas;                // CTAs before the tasks' CTAs (set by the launch from rep_cells)
     int32_t no_staged;                // 1: prepare_* picks no TMA-staged kernel (context flag)
     int32_t pad;
 };

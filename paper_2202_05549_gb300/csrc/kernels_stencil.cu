@@ -52,18 +52,19 @@ constexpr int JV = 8;        // rows per warp strip of the single-step kernel
 // every CTA.
 template <int R>
 __global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
-    if (blockIdx.x >= p.main_ctas) {  // write-through replica CTAs
-        jacobi_replica_cell(tasks, p, (uint64_t)(blockIdx.x - p.main_ctas) * blockDim.x + threadIdx.x);
+    if (blockIdx.x < p.rep_ctas) {  // write-through replica CTAs come first: their latency overlaps the strips
+        jacobi_replica_cell(tasks, p, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
         return;
     }
-    int ti = task_of(tasks, p, blockIdx.x);
+    const uint32_t cta = blockIdx.x - p.rep_ctas;
+    int ti = task_of(tasks, p, cta);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
     const int64_t xe = min(t.t_hi[0], NX - 1), ye = min(t.t_hi[1], NY - 1);  // last output column / row
     const uint32_t width = (uint32_t)(t.t_hi[0] - x0 + 1);
     const uint32_t gx = (width + JWARPS * JCOLS - 1) / (JWARPS * JCOLS);
-    const uint32_t local = blockIdx.x - t.cta_begin;
+    const uint32_t local = cta - t.cta_begin;
     const uint32_t tx = local % gx, ty = local / gx;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t js = x0 + (int64_t)(tx * JWARPS + warp) * JCOLS;  // first column of this warp's strip
@@ -75,15 +76,16 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTas
 
 // Scalar variant for unaligned tasks: one thread per output cell.
 __global__ void __launch_bounds__(256) jacobi2d_scalar_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
-    if (blockIdx.x >= p.main_ctas) {  // write-through replica CTAs
-        jacobi_replica_cell(tasks, p, (uint64_t)(blockIdx.x - p.main_ctas) * blockDim.x + threadIdx.x);
+    if (blockIdx.x < p.rep_ctas) {  // write-through replica CTAs
+        jacobi_replica_cell(tasks, p, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
         return;
     }
-    int ti = task_of(tasks, p, blockIdx.x);
+    const uint32_t cta = blockIdx.x - p.rep_ctas;
+    int ti = task_of(tasks, p, cta);
     const ExecTask &t = tasks[ti];
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const int64_t width = t.t_hi[0] - t.t_lo[0] + 1;
-    const int64_t cell = (int64_t)(blockIdx.x - t.cta_begin) * blockDim.x + threadIdx.x;
+    const int64_t cell = (int64_t)(cta - t.cta_begin) * blockDim.x + threadIdx.x;
     const int64_t j = t.t_lo[0] + cell % width, i = t.t_lo[1] + cell / width;
     if (i > t.t_hi[1] || i >= NY || j >= NX) return;
     const DView U = t.v[0], V = t.v[1];
@@ -139,17 +141,19 @@ uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p) {
     return total;
 }
 
-// The grid is the tasks' CTAs followed by the write-through replica CTAs
-// (one thread per replica cell).
+// The grid is the write-through replica CTAs (one thread per replica cell)
+// followed by the tasks' CTAs.
 cudaError_t launch_jacobi2d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
     const uint32_t threads = p.variant == 1 ? JWARPS * 32 : 256;
     const uint64_t extra = (p.rep_cells + threads - 1) / threads;
-    if ((uint64_t)p.main_ctas + extra > 0x7FFFFFFFull || p.main_ctas != ctas) return cudaErrorInvalidValue;
+    if ((uint64_t)ctas + extra > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    ExecParams q = p;
+    q.rep_ctas = (uint32_t)extra;
     const uint32_t grid = ctas + (uint32_t)extra;
     if (p.variant == 1)
-        jacobi2d_vec_kernel<JV><<<grid, threads, 0, st>>>(dev, p);
+        jacobi2d_vec_kernel<JV><<<grid, threads, 0, st>>>(dev, q);
     else
-        jacobi2d_scalar_kernel<<<grid, threads, 0, st>>>(dev, p);
+        jacobi2d_scalar_kernel<<<grid, threads, 0, st>>>(dev, q);
     return cudaGetLastError();
 }
 

@@ -136,7 +136,6 @@ extern "C" lt_status lt_jacobi2d_packed_noalloc(const float *U, float *V, int64_
         }
         ep.ntasks = (int32_t)tasks.size();
         uint32_t ctas = k::prepare_jacobi2d(tasks.data(), (int)tasks.size(), ep);
-        ep.main_ctas = ctas;  // no write-through replicas: the grid is the tasks' CTAs
         size_t pbytes = packs.size() * sizeof(CopyPiece);
         size_t tbytes = tasks.size() * sizeof(ExecTask);
         std::vector<unsigned char> host(up(pbytes, 256) + tbytes);

@@ -2256,7 +2256,6 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             ep.reps = (rbytes && dptr) ? (const ReplicaTarget *)((const char *)dptr + tbytes) : nullptr;
             ep.nreps = (uint32_t)reps.size();
             ep.rep_cells = ep.reps ? rep_cells : 0;
-            ep.main_ctas = ctas;
             if (!c->dry && ctas) {
                 TimeScope ts(c, CAT_EXEC);
                 if (k->ufn) {

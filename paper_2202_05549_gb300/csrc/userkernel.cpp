@@ -108,7 +108,7 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
       << LT_MAX_ARRAYS << "][3]; int32_t nd[" << LT_MAX_ARRAYS
       << "]; int64_t block[3]; double f[4]; int64_t i[4]; uint32_t *err;"
          " int32_t ntasks, variant, red_op, uniform_ctas; const void *reps; uint64_t rep_cells;"
-         " uint32_t nreps, main_ctas; int32_t no_staged, pad; };\n"
+         " uint32_t nreps, rep_ctas; int32_t no_staged, pad; };\n"
          "static_assert(sizeof(LtView) == "
       << sizeof(DView) << ", \"view layout\");\nstatic_assert(sizeof(LtTask) == " << sizeof(ExecTask)
       << ", \"task layout\");\nstatic_assert(sizeof(LtParams) == " << sizeof(ExecParams) << ", \"params layout\");\n"
