@@ -362,6 +362,10 @@ def run_lightning(args, rank, world, local, grp):
         kname = {2: "jacobi2d_tma_kernel", 1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
     # DRAM traffic records: the in-core grid keeps part of its working set in L2
     tkey = kname + ("@incore4096" if args.workload != "ooc" and tb == 1 else "")
+    # the timed steps run without per-operation CUDA events (a few
+    # microseconds of GPU time each, 12 % of an in-core launch); the kernel
+    # durations for the roofline come from a second, instrumented pass
+    ctx.op_timing(False)
     ctx.reset_stats()
     grp.barrier()
     clk = Clocks(local)
@@ -370,7 +374,13 @@ def run_lightning(args, rank, world, local, grp):
         step()
     ms = ctx.timer_stop()
     clocks = clk.stop()
-    ctx.synchronize()  # collects the per-kernel event timings (outside the timed region)
+    ctx.synchronize()
+    st_run = ctx.stats()
+    ctx.op_timing(True)
+    ctx.reset_stats()
+    for _ in range(max(1, min(args.steps, 3))):
+        step()
+    ctx.synchronize()  # collects the per-kernel event timings
     st = ctx.stats()
     cells = ny * nx * iters  # cell-updates per step
     t_s = ms / 1e3
@@ -380,11 +390,12 @@ def run_lightning(args, rank, world, local, grp):
     # dominant kernel: the Jacobi execute kernel
     n_ex = max(1, st["n_execute_kernels"])
     ex_ms = st["ms_execute"] / n_ex
-    cells_per_launch = cells * args.steps / n_ex
+    cells_per_launch = cells * max(1, min(args.steps, 3)) / n_ex
     achieved = 8.0 * cells_per_launch / (ex_ms / 1e3) / 1e9
-    link_bytes = st["bytes_h2d"] + st["bytes_d2h"]
-    t_link_floor = max(st["bytes_h2d"] / (links["h2d"] * 1e9), st["bytes_d2h"] / (links["d2h"] * 1e9),
+    link_bytes = st_run["bytes_h2d"] + st_run["bytes_d2h"]
+    t_link_floor = max(st_run["bytes_h2d"] / (links["h2d"] * 1e9), st_run["bytes_d2h"] / (links["d2h"] * 1e9),
                        link_bytes / (links["bidir"] * 1e9))
+    n_inst = max(1, min(args.steps, 3))  # steps of the instrumented pass
     res = {
         "metric": "annotated-launch GB/s (8 B per cell-update) vs HBM / host-link roofline",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -402,17 +413,18 @@ def run_lightning(args, rank, world, local, grp):
                      "traffic": None if user else kernel_traffic(tkey, cells_per_launch / tb),
                      "kernel": kname, "launch_ms": round(ex_ms, 4),
                      "bytes_per_launch": 8.0 * cells_per_launch, "peak_source": peaks["source"]},
-        "host_link": {"bytes_h2d_per_step": st["bytes_h2d"] / args.steps,
-                      "bytes_d2h_per_step": st["bytes_d2h"] / args.steps,
+        "host_link": {"bytes_h2d_per_step": st_run["bytes_h2d"] / args.steps,
+                      "bytes_d2h_per_step": st_run["bytes_d2h"] / args.steps,
                       "achieved_GBs": round(link_bytes / t_s / 1e9, 1),
                       "measured_peak_GBs": {k2: round(v, 1) for k2, v in links.items()},
                       "frac_of_link_roofline": round(t_link_floor / t_s, 4) if link_bytes else None,
-                      "exec_ms_total": round(st["ms_execute"], 2), "h2d_ms_total": round(st["ms_h2d"], 2),
-                      "d2h_ms_total": round(st["ms_d2h"], 2)},
-        "gpu_launches": st["kernels"],
+                      "instrumented_ms_per_step": {"execute": round(st["ms_execute"] / n_inst, 2),
+                                                   "h2d": round(st["ms_h2d"] / n_inst, 2),
+                                                   "d2h": round(st["ms_d2h"] / n_inst, 2)}},
+        "gpu_launches": st_run["kernels"],
         "clocks": clocks,
-        "stats": {k2: st[k2] for k2 in ("fetches", "evictions", "dead_skips", "tasks_execute", "tasks_copy",
-                                        "hbm_peak")},
+        "stats": {k2: st_run[k2] for k2 in ("fetches", "evictions", "dead_skips", "tasks_execute", "tasks_copy",
+                                            "hbm_peak", "bytes_replica_wt")},
     }
     if not args.no_e2e:
         # end to end through the public API.  In-core: every step uploads its
@@ -420,6 +432,7 @@ def run_lightning(args, rank, world, local, grp):
         # back.  Out-of-core: the 128 GiB input cannot sit in host memory beside
         # the pinned pool, so every step runs the workload (streaming whatever
         # the budget forces through the pool) and reads a row of its result.
+        ctx.op_timing(False)
         ctx.synchronize()
         ctx.reset_stats()
         incore = args.workload != "ooc"

@@ -353,6 +353,12 @@ lt_status lt_synchronize(lt_ctx *ctx);
 lt_status lt_timer_start(lt_ctx *ctx);
 lt_status lt_timer_stop(lt_ctx *ctx, double *ms);
 
+/* Turns the per-operation CUDA events of LT_FLAG_TIMING on (1) or off (0)
+ * for the operations enqueued from now on (the pending launch is enqueued
+ * first).  The events cost a few microseconds of GPU time per operation, so
+ * a caller can time a run with them off and measure kernels with them on. */
+lt_status lt_op_timing(lt_ctx *ctx, int32_t on);
+
 /* ---- statistics and plan inspection -------------------------------------- */
 typedef struct {
     uint64_t launches;        /* lt_launch calls */

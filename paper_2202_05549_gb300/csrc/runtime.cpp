@@ -2925,6 +2925,17 @@ lt_status lt_synchronize(lt_ctx *c) {
     return sync_all(c);
 }
 
+lt_status lt_op_timing(lt_ctx *c, int32_t on) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    if ((st = flush_pending(c))) return st;
+    if (on)
+        c->cfg.flags |= LT_FLAG_TIMING;
+    else
+        c->cfg.flags &= ~(int32_t)LT_FLAG_TIMING;
+    return LT_OK;
+}
+
 lt_status lt_timer_start(lt_ctx *c) {
     lt_status st = check_ctx(c);
     if (st) return st;

@@ -278,6 +278,9 @@ class Context:
         check(L.load().lt_timer_stop(self.h, C.byref(ms)))
         return ms.value
 
+    def op_timing(self, on: bool = True):
+        check(L.load().lt_op_timing(self.h, 1 if on else 0))
+
     def stats(self) -> dict:
         s = L.lt_stats()
         check(L.load().lt_stats_get(self.h, C.byref(s)))
