@@ -407,7 +407,8 @@ def run_lightning(args, rank, world, local, grp):
                    "hbm_budget_bytes": pl["budget"], "host_pool_bytes": pl["host"],
                    "data_bytes": pl["data_bytes"], "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (129 MB)" if args.workload == "ooc"
-                   else "working set 128 MiB ~ L2 size; not flushed"},
+                   else "inputs larger than L2: two arrays of 16 chunks, 140.7 MB with halos and row padding, "
+                        "against 129 MB of L2; not flushed (part of each launch's input is still in L2)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": round(achieved / peaks["hbm_gbs"], 4),
                      "traffic": None if user else kernel_traffic(tkey, cells_per_launch / tb),
