@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--rows", type=int, default=262144, help="grid rows (ooc)")
     p.add_argument("--cols", type=int, default=131072, help="grid columns (ooc)")
     p.add_argument("--band", type=int, default=8192)
+    p.add_argument("--keep-stale", action="store_true",
+                   help="stencil runs: do not discard the stale ping-pong buffer before the closing synchronize")
     p.add_argument("--no-staged", action="store_true",
                    help="stencil built-ins use their register kernels instead of the TMA-staged ones")
     p.add_argument("--hbm-gib", type=float, default=0.0,
@@ -345,6 +347,10 @@ def run_lightning(args, rank, world, local, grp):
             else:
                 k.launch(grid=(nx, ny), block=(128, 4), superblock=sb, args=[bufs[0], bufs[1]] + extra)
             bufs.reverse()
+        if not args.keep_stale:
+            # the input of the last launch is stale once the result is in the
+            # other buffer: dropped instead of written back (lt_array_discard)
+            bufs[1].discard()
         ctx.synchronize()
 
     ctx.log_enable()
@@ -404,6 +410,8 @@ def run_lightning(args, rank, world, local, grp):
         "config": {"workload": workload + (" (Jacobi body compiled at run time)" if user else ""),
                    "grid": [ny, nx], "iterations_per_step": iters,
                    "launches_per_step": launches, "iterations_per_launch": tb,
+                   "stale_buffer": "written back at the closing synchronize" if args.keep_stale else
+                   "discarded before the closing synchronize (lt_array_discard): the run needs only its result",
                    "hbm_budget_bytes": pl["budget"], "host_pool_bytes": pl["host"],
                    "data_bytes": pl["data_bytes"], "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (129 MB)" if args.workload == "ooc"

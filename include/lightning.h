@@ -160,6 +160,18 @@ lt_status lt_array_wrap_device(lt_ctx *ctx, lt_dtype dtype, int32_t ndim, const 
                                const int64_t strides[3], void *ptr, lt_array **out);
 lt_status lt_array_destroy(lt_ctx *ctx, lt_array *arr);
 
+/* Declare that the array's current contents will not be read again (for
+ * instance the stale buffer of a ping-pong pair once the result is in the
+ * other).  Its chunks are then dropped instead of written back when memory
+ * is needed: once the launch that is still pending, if any, has finished
+ * with each of them.  Reading the array before writing it again gives
+ * unspecified values; any write (launch, lt_array_write, lt_array_fill)
+ * makes the written chunks live again.  No counterpart in the paper: its
+ * runtime learns that data is dead only from a later launch that overwrites
+ * it (one launch of lookahead here), so a run's last launch must write back
+ * an input it will never read again.  Errors: LT_ERR_INVALID_ARG. */
+lt_status lt_array_discard(lt_ctx *ctx, lt_array *arr);
+
 /* Copy the whole array from / to a dense row-major host buffer of exactly
  * `bytes` bytes.  Synchronous: waits for all earlier work; the buffer is
  * borrowed only during the call. */

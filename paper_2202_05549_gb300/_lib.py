@@ -120,6 +120,7 @@ SIGNATURES = {
     "lt_timer_start": (_st, [_vp]),
     "lt_timer_stop": (_st, [_vp, C.POINTER(C.c_double)]),
     "lt_op_timing": (_st, [_vp, C.c_int32]),
+    "lt_array_discard": (_st, [_vp, _vp]),
     "lt_stats_get": (_st, [_vp, C.POINTER(lt_stats)]),
     "lt_stats_reset": (_st, [_vp]),
     "lt_plan_explain": (_st, [_vp, _vp, lt_dim3, lt_dim3, C.POINTER(lt_workdist), C.POINTER(lt_arg), C.c_int32,

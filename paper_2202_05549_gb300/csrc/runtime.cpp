@@ -168,6 +168,7 @@ struct CState {
     int64_t last_use_launch = -1;   // launch and group of its last use in that launch
     int64_t last_use_group = -1;
     int64_t last_write_launch = -1;  // last launch that wrote it
+    bool discarded = false;          // contents declared dead (lt_array_discard) and not written since
 };
 
 struct BuiltinDef {
@@ -507,6 +508,7 @@ lt_status evict(lt_ctx *c, lt_array *a, int64_t ci);
 // launch and this launch has used it for the last time.
 bool droppable(const lt_ctx *c, const CState &s) {
     if (s.dead_launch == c->launch_id) return true;
+    if (s.discarded) return s.last_use_launch != c->launch_id || s.last_use_group < c->cur_group;
     return s.next_dead_launch == c->launch_id &&
            (s.last_use_launch != c->launch_id || s.last_use_group < c->cur_group);
 }
@@ -1227,7 +1229,10 @@ lt_status lt_array_write(lt_ctx *c, lt_array *arr, const void *host, size_t byte
     if (bytes != array_bytes(a)) return fail(LT_ERR_INVALID_ARG, "buffer size does not match the array");
     if ((st = sync_all(c))) return st;
     ++c->launch_id;
-    for (size_t ci = 0; ci < a->cs.size(); ++ci) a->cs[ci].dead_launch = c->launch_id;
+    for (size_t ci = 0; ci < a->cs.size(); ++ci) {
+            a->cs[ci].dead_launch = c->launch_id;
+            a->cs[ci].discarded = false;
+        }
     for (size_t ci = 0; ci < a->cs.size(); ++ci) {
         CState &s = a->cs[ci];
         if (s.loc == LOC_HOST && !c->dry) {
@@ -1305,7 +1310,10 @@ static lt_status array_copy_device(lt_ctx *c, lt_array *arr, void *dev, size_t b
     if ((st = sync_all(c))) return st;
     if (to_array) {
         ++c->launch_id;
-        for (size_t ci = 0; ci < a->cs.size(); ++ci) a->cs[ci].dead_launch = c->launch_id;
+        for (size_t ci = 0; ci < a->cs.size(); ++ci) {
+            a->cs[ci].dead_launch = c->launch_id;
+            a->cs[ci].discarded = false;
+        }
     }
     for (size_t ci = 0; ci < a->cs.size(); ++ci) {
         CState &s = a->cs[ci];
@@ -1423,7 +1431,10 @@ lt_status lt_array_fill(lt_ctx *c, lt_array *arr, const lt_init *init) {
     if (!ok) return fail(LT_ERR_INVALID_ARG, "fill kind does not match the array dtype");
     ++c->launch_id;
     c->stats.launches++;
-    for (size_t ci = 0; ci < a->cs.size(); ++ci) a->cs[ci].dead_launch = c->launch_id;
+    for (size_t ci = 0; ci < a->cs.size(); ++ci) {
+            a->cs[ci].dead_launch = c->launch_id;
+            a->cs[ci].discarded = false;
+        }
     uint64_t key;
     {
         uint64_t s0 = init->seed ^ (init->stream << 32);
@@ -2052,7 +2063,10 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
         std::vector<ArgUse> uses = collect_uses(g0, g1);
         for (auto &u : uses) {
             u.a->cs[(size_t)u.chunk].pin++;
-            if (u.write) u.a->cs[(size_t)u.chunk].last_write_launch = c->launch_id;
+            if (u.write) {
+                u.a->cs[(size_t)u.chunk].last_write_launch = c->launch_id;
+                u.a->cs[(size_t)u.chunk].discarded = false;
+            }
         }
         unpin_ahead();  // now pinned as this group's uses
         for (auto &u : uses) {
@@ -2768,11 +2782,13 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
         uses.push_back({J.u, true});
         uses.push_back({J.v, true});
         J.v->cs[0].dead_launch = c->launch_id;
+        J.v->cs[0].discarded = false;
     }
     for (auto &H : bs.hist) {
         uses.push_back({H.x, false});
         uses.push_back({H.h, true});
         H.h->cs[0].dead_launch = c->launch_id;
+        H.h->cs[0].discarded = false;
     }
     for (auto &u : uses) u.first->cs[0].pin++;
     auto unpin = [&]() {
@@ -2923,6 +2939,18 @@ lt_status lt_synchronize(lt_ctx *c) {
     if (st) return st;
     if ((st = flush_pending(c))) return st;
     return sync_all(c);
+}
+
+lt_status lt_array_discard(lt_ctx *c, lt_array *arr) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    lt_array *a = find_array(c, arr);
+    if (!a) return fail(LT_ERR_INVALID_ARG, "unknown array");
+    // No flush: the pending launch (if any) still reads the array; its chunks
+    // become droppable as that launch finishes with each of them.
+    for (auto &s : a->cs)
+        if (!s.ext) s.discarded = true;
+    return LT_OK;
 }
 
 lt_status lt_op_timing(lt_ctx *c, int32_t on) {

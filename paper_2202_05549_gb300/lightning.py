@@ -101,6 +101,11 @@ class Array:
         assert a.shape == self.shape, (a.shape, self.shape)
         check(L.load().lt_array_write(self.ctx.h, self.h, a.ctypes.data_as(C.c_void_p), a.nbytes))
 
+    def discard(self):
+        """Declare the contents dead: dropped instead of written back when
+        memory is needed (lt_array_discard)."""
+        check(L.load().lt_array_discard(self.ctx.h, self.h))
+
     def read(self, out: np.ndarray | None = None) -> np.ndarray:
         """The whole array, into `out` if given (C-contiguous, this shape and
         dtype; a pinned buffer makes the copy a direct DMA)."""

@@ -215,6 +215,34 @@ def test_out_of_core_lightcone_samples_small():
     assert np.array_equal(got[si_, sj_], want)
 
 
+def test_discard_of_the_stale_buffer_keeps_results_exact():
+    # out of core (budget 5 bands of 16 + 16): runs of 3 iterations, each
+    # ending with the stale ping-pong buffer discarded before the synchronize;
+    # the result stays bit-exact and the closing write-back shrinks
+    ny, nx, band = 2048, 2048, 128
+    cb = (band + 2) * nx * 4
+    u0 = si.uniform_field(si.SEED_JACOBI_OOC, 3, ny, nx)
+    d2h = []
+    for discard in (False, True):
+        with lt.Context(hbm_budget=5 * cb + (1 << 20), host_pool=40 * cb) as ctx:
+            U = ctx.array(lt.F32, (ny, nx), lt.Dist.rows(band, halo=1))
+            V = ctx.array(lt.F32, (ny, nx), lt.Dist.rows(band, halo=1))
+            U.write(u0)
+            k = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+            ctx.synchronize()
+            ctx.reset_stats()
+            for run in range(2):
+                for _ in range(3):
+                    k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V])
+                    U, V = V, U
+                if discard:
+                    V.discard()
+                ctx.synchronize()
+                assert np.array_equal(U.read(), oracle.jacobi2d(u0, 3 * (run + 1))), (discard, run)
+            d2h.append(ctx.stats()["bytes_d2h"])
+    assert d2h[1] < d2h[0]
+
+
 def test_out_of_core_full_size_lightcone_samples():
     # the out-of-core configuration at full size, as bench.py runs it: 262144 x
     # 131072 f32 (128 GiB per buffer), 8192-row bands + 1-row halo, the HBM

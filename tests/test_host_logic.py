@@ -236,6 +236,70 @@ def _jacobi_ctx(ctx, ny, nx, dist):
     return U, V, k
 
 
+def _ooc_run(discard):
+    # 8 row bands of 64 x 1024 f32 per array; the HBM budget holds 6 bands,
+    # so both arrays cannot stay resident: 4 launches, then a synchronize
+    ny, nx, band = 512, 1024, 64
+    cb = (band + 2) * nx * 4
+    with dry(budget=6 * cb + 4096, host=16 * cb) as ctx:
+        U, V, k = _jacobi_ctx(ctx, ny, nx, lt.Dist.rows(band, halo=1))
+        U.fill(L.LT_INIT_UNIFORM, seed=3)
+        ctx.synchronize()
+        ctx.reset_stats()
+        for _ in range(4):
+            k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V])
+            U, V = V, U
+        if discard:
+            V.discard()  # the last launch's input: stale once U holds the result
+        ctx.synchronize()
+        s = ctx.stats()
+        # the result is still complete: one more launch reads it and
+        # overwrites the discarded array
+        k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V])
+        ctx.synchronize()
+        return s
+
+
+def test_discarded_array_is_dropped_not_written_back():
+    keep, drop = _ooc_run(False), _ooc_run(True)
+    # without the discard the last launch writes back the input bands it
+    # evicts to make room for its output; with it they are dropped
+    assert drop["bytes_d2h"] < keep["bytes_d2h"]
+    assert drop["dead_skips"] > keep["dead_skips"]
+    assert drop["bytes_h2d"] == keep["bytes_h2d"]  # the launches read the same inputs
+
+
+def test_discard_waits_for_the_pending_launch_and_writes_revive():
+    # the pending launch still reads the discarded array: its chunks may be
+    # dropped only after that launch has used them, and a fill makes them live
+    ny, nx, band = 512, 1024, 64
+    cb = (band + 2) * nx * 4
+    with dry(budget=6 * cb + 4096, host=16 * cb, flags=L.LT_FLAG_FIXED_SWEEP) as ctx:
+        U, V, k = _jacobi_ctx(ctx, ny, nx, lt.Dist.rows(band, halo=1))
+        U.fill(L.LT_INIT_UNIFORM, seed=3)
+        on_host = ctx.stats()["evictions"]  # U bands the fill moved to host memory
+        ctx.reset_stats()
+        ctx.log_enable()
+        k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V])
+        U.discard()
+        ctx.synchronize()
+        log = ctx.log()
+        ex = [t for t in log if t["kind"] == "execute"]
+        assert len(ex) == 8  # one band per group: every band of U was read
+        # U is the context's first array (id 1).  The budget is too small for
+        # the launch itself, so bands it still needs are written back and
+        # fetched again; a band past its last use is dropped, never written back
+        ev = [t for t in log if t["kind"] == "evict" and t.get("array") == 1]
+        fe = [t for t in log if t["kind"] == "fetch" and t.get("array") == 1]
+        assert on_host > 0 and len(fe) >= on_host
+        for t in ev:
+            assert any(f["chunk"] == t["chunk"] and f["id"] > t["id"] for f in fe), t
+        assert ctx.stats()["dead_skips"] > 0
+        U.fill(L.LT_INIT_UNIFORM, seed=4)
+        k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[U, V])
+        ctx.synchronize()
+
+
 def test_dependencies_between_successive_launches():
     with dry(flags=L.LT_FLAG_FIXED_SWEEP) as ctx:
         U, V, k = _jacobi_ctx(ctx, 64, 64, lt.Dist.rows(16, halo=1))
