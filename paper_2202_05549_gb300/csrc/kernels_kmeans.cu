@@ -42,15 +42,21 @@ __device__ __forceinline__ bool fixed24(float x, uint32_t *m) {
     return x >= 0.0f && x < 1.0f && __uint2float_rn(*m) == t;
 }
 
+// Squared distance in the fixed order of the definition.
+__device__ __forceinline__ float dist2(float4 x, float4 c) {
+    const float d0 = __fsub_rn(x.x, c.x), d1 = __fsub_rn(x.y, c.y);
+    const float d2 = __fsub_rn(x.z, c.z), d3 = __fsub_rn(x.w, c.w);
+    return __fmaf_rn(d3, d3, __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0))));
+}
+
+// Nearest centre, ties to the lowest index (centre 0 taken first, then a
+// strictly smaller distance wins).
 __device__ __forceinline__ int nearest(const float4 *cs, int k, float4 x) {
     int best = 0;
-    float bd = 0.f;
-    for (int j = 0; j < k; ++j) {
-        const float4 c = cs[j];
-        const float d0 = __fsub_rn(x.x, c.x), d1 = __fsub_rn(x.y, c.y);
-        const float d2 = __fsub_rn(x.z, c.z), d3 = __fsub_rn(x.w, c.w);
-        const float d = __fmaf_rn(d3, d3, __fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0))));
-        if (j == 0 || d < bd) {
+    float bd = dist2(x, cs[0]);
+    for (int j = 1; j < k; ++j) {
+        const float d = dist2(x, cs[j]);
+        if (d < bd) {
             bd = d;
             best = j;
         }
@@ -113,20 +119,16 @@ __global__ void __launch_bounds__(KT) kmeans_assign_kernel(const ExecTask *__res
             if (rb <= i1) {
                 const float4 xq = load(rb);
                 int ba = 0, bb = 0;
-                float da = 0.f, db = 0.f;
-                for (int j = 0; j < k; ++j) {
+                float da = dist2(xa, cs[0]), db = dist2(xq, cs[0]);
+#pragma unroll 4
+                for (int j = 1; j < k; ++j) {
                     const float4 c = cs[j];
-                    float e0 = __fsub_rn(xa.x, c.x), e1 = __fsub_rn(xa.y, c.y);
-                    float e2 = __fsub_rn(xa.z, c.z), e3 = __fsub_rn(xa.w, c.w);
-                    const float d = __fmaf_rn(e3, e3, __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0))));
-                    e0 = __fsub_rn(xq.x, c.x), e1 = __fsub_rn(xq.y, c.y);
-                    e2 = __fsub_rn(xq.z, c.z), e3 = __fsub_rn(xq.w, c.w);
-                    const float dq = __fmaf_rn(e3, e3, __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0))));
-                    if (j == 0 || d < da) {
+                    const float d = dist2(xa, c), dq = dist2(xq, c);
+                    if (d < da) {
                         da = d;
                         ba = j;
                     }
-                    if (j == 0 || dq < db) {
+                    if (dq < db) {
                         db = dq;
                         bb = j;
                     }
