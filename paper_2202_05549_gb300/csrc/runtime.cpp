@@ -1969,7 +1969,10 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
     FenceSet red_fence;
     const bool any_red = red_bytes || !red_inplace.empty();
     if (red_bytes && (st = dev_alloc(c, red_bytes, &red_base, &red_fence))) return st;
-    for (auto &ip : red_inplace) ip.first->cs[(size_t)ip.second].pin++;
+    for (auto &ip : red_inplace) {
+        ip.first->cs[(size_t)ip.second].pin++;
+        ip.first->cs[(size_t)ip.second].discarded = false;  // the launch writes its partial there
+    }
     for (auto &ip : red_inplace) {
         // the launch overwrites the chunk's region: its old contents are not needed
         if ((st = ensure_dev(c, ip.first, ip.second, false))) return st;
@@ -2449,7 +2452,10 @@ static lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             }
         }
         std::vector<std::pair<lt_array *, int64_t>> dests = dest_order;
-        for (auto &d : dests) d.first->cs[(size_t)d.second].pin++;
+        for (auto &d : dests) {
+            d.first->cs[(size_t)d.second].pin++;
+            d.first->cs[(size_t)d.second].discarded = false;  // the reduce writes it
+        }
         for (auto &d : dests) {
             if ((st = ensure_dev(c, d.first, d.second, true))) {
                 for (auto &e : dests) e.first->cs[(size_t)e.second].pin--;
@@ -2782,6 +2788,7 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
         uses.push_back({J.u, true});
         uses.push_back({J.v, true});
         J.v->cs[0].dead_launch = c->launch_id;
+        J.u->cs[0].discarded = false;  // both buffers of an instance are written (ping-pong)
         J.v->cs[0].discarded = false;
     }
     for (auto &H : bs.hist) {
