@@ -579,3 +579,35 @@ def test_wrapped_device_memory_is_never_moved():
         U.destroy()
         with pytest.raises(lt.LightningError):
             lt.Array(ctx, lt.F32, (4, 4), None, wrap=(fake, (1, 4), None))  # innermost stride must be 1
+
+
+def _reduce_then_pressure(discard):
+    ny, nx = 256, 1024
+    cb = 64 * nx * 4
+    with dry(budget=5 * cb, host=16 * cb) as ctx:
+        A = ctx.array(lt.F32, (ny, nx), lt.Dist.rows(64))
+        B = ctx.array(lt.F32, (ny, nx), lt.Dist.rows(64))
+        S = ctx.array(lt.F32, (ny,), lt.Dist.block())
+        T = ctx.array(lt.F32, (ny,), lt.Dist.block())
+        A.fill(L.LT_INIT_UNIFORM, seed=1)
+        S.fill(L.LT_INIT_ZERO)
+        if discard:
+            S.discard()
+        k = ctx.kernel(lt.ROWREDUCE, "global [i, j] => read A[i, j], reduce(+) sum[i]",
+                       [("A", lt.F32), ("sum", lt.F32)])
+        k.launch(grid=(nx, ny), block=(32, 8), superblock=(nx, 64), args=[A, S])
+        ctx.synchronize()
+        B.fill(L.LT_INIT_UNIFORM, seed=2)  # needs every slot: A and S must leave HBM
+        k.launch(grid=(nx, ny), block=(32, 8), superblock=(nx, 64), args=[B, T])
+        ctx.synchronize()
+        return ctx.stats()
+
+
+def test_reduce_into_a_discarded_array_makes_it_live():
+    # S is discarded, then a launch reduces into it: from then on it is live,
+    # so memory pressure treats it exactly as if it had never been discarded
+    # (written back, not dropped)
+    a, b = _reduce_then_pressure(False), _reduce_then_pressure(True)
+    for key in ("evictions", "dead_skips", "bytes_d2h", "fetches"):
+        assert a[key] == b[key], key
+    assert a["evictions"] > 0
