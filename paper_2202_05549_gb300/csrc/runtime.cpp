@@ -1837,6 +1837,22 @@ static lt_status flush_pending(lt_ctx *c) {
     return emit_launch(c, *p, nullptr);
 }
 
+// Does the launch use only chunks already in device memory, with no
+// temporaries (packs, temp writes, reduce partials)?
+static bool runs_in_place(const lt_ctx *c, const PendingLaunch &pl) {
+    if (c->dry) return false;  // dry runs keep the lookahead, whose decisions the tests inspect
+    for (const auto &sb : pl.b->plan.sbs)
+        for (const auto &ap : sb.args) {
+            if (ap.kind == ARG_VALUE || ap.kind == ARG_NONE) continue;
+            if (ap.kind != ARG_DIRECT) return false;
+            const lt_array *a = pl.parr[(size_t)ap.param];
+            if (a->cs[(size_t)ap.chunk].loc != LOC_DEV) return false;
+            for (const auto &pc : ap.replicas)
+                if (a->cs[(size_t)pc.chunk].loc != LOC_DEV) return false;
+        }
+    return true;
+}
+
 lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const lt_workdist *wd, const lt_arg *args,
                     int32_t nargs) {
     lt_status st = check_ctx(c);
@@ -1879,9 +1895,13 @@ lt_status lt_launch(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const 
         std::vector<std::pair<lt_array *, int64_t>> nd;
         for (auto &d : pl->b->dead) nd.push_back({pl->parr[(size_t)d.first], d.second});
         std::unique_ptr<PendingLaunch> prev = std::move(c->pending);
-        c->pending = std::move(pl);
-        return emit_launch(c, *prev, &nd);
+        if ((st = emit_launch(c, *prev, &nd))) return st;
     }
+    // A launch that touches only resident chunks and needs no temporaries
+    // will evict nothing, so the next launch's plan cannot change what it
+    // does: it is enqueued at once instead of waiting for that plan, and the
+    // GPU does not idle while the host plans the next launch.
+    if (runs_in_place(c, *pl)) return emit_launch(c, *pl, nullptr);
     c->pending = std::move(pl);
     return LT_OK;
 }
