@@ -338,6 +338,131 @@ __global__ void __launch_bounds__(DT, 2) diffusion_adj_vec_kernel(const ExecTask
     }
 }
 
+// Staged adjoint: the same tile and arithmetic as diffusion_adj_vec_kernel,
+// but every input group goes global -> shared with cp.async (16 bytes,
+// cached in L2 only) instead of through registers, so a CTA holds few
+// registers and three CTAs fit on an SM with all their loads in flight.
+// Shared tiles (TY+2 rows x VP columns; group q of a row, global columns
+// tx0+4q .. tx0+4q+3, sits at shared columns 4+4q, q = -1 .. VQ covering the
+// ring columns 3 and 4+TX): K (then s = K*L1 in place), L1, u_t and G.
+// A group is copied when it meets the region its array may be read in (the
+// same test as the register kernel, so the copied bytes lie in the chunk's
+// padded rows); otherwise the copy zero-fills it.  Columns of a copied group
+// that lie outside the region are cleared in shared memory before use.
+constexpr int AQ = VQ + 2;                    // groups per staged row, ring groups included
+constexpr int ATILE = (TY + 2) * VP;          // floats per staged tile
+constexpr int ASMEM = 4 * ATILE * 4;          // dynamic shared memory of the kernel
+constexpr int AT = DT;                        // threads per CTA
+constexpr int ACTA = 3;                       // CTAs per SM the kernel is built for
+
+__device__ __forceinline__ void cp16(float *dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(AT, ACTA) diffusion_adj_async_kernel(const ExecTask *__restrict__ tasks,
+                                                                      ExecParams p) {
+    extern __shared__ __align__(16) float asmem[];
+    float *sK = asmem, *sL = asmem + ATILE, *sU = asmem + 2 * ATILE, *sG = asmem + 3 * ATILE;
+    const int ti = task_of(tasks, p, blockIdx.x);
+    const ExecTask &t = tasks[ti];
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    const int64_t x0 = t.t_lo[0], y0 = t.t_lo[1];
+    const int64_t x1 = min(t.t_hi[0], NX - 1), y1 = min(t.t_hi[1], NY - 1);
+    if (x1 < x0 || y1 < y0) return;
+    const int64_t rx0 = max(x0 - 1, (int64_t)0), ry0 = max(y0 - 1, (int64_t)0);
+    const int64_t rx1 = min(x1 + 1, NX - 1), ry1 = min(y1 + 1, NY - 1);
+    const int64_t ax0 = rx0 & ~(int64_t)3;  // tiles start on 4-aligned columns
+    int64_t ty0, tx0;
+    tile_of(blockIdx.x - t.cta_begin, ax0, rx1, ry0, &ty0, &tx0);
+    const DView L1 = t.v[0], K = t.v[1], U = t.v[2], G = t.v[3], L0 = t.v[4];
+    const void *nowhere = p.err;  // source of zero-filling copies (nothing is read)
+    for (int e = threadIdx.x; e < (TY + 2) * AQ; e += AT) {
+        const int li = e / AQ, qq = e % AQ - 1;
+        const int64_t i = ty0 - 1 + li, j = tx0 + 4 * qq;
+        const int o = li * VP + 4 + 4 * qq;
+        const bool sb = i >= y0 && i <= y1 && j + 3 >= x0 && j <= x1;       // meets the superblock
+        const bool ur = i >= ry0 && i <= ry1 && j + 3 >= rx0 && j <= rx1;   // meets U's region
+        cp16(sK + o, sb ? (const void *)((const float *)K.base + i * K.s[0] + j) : nowhere, sb);
+        cp16(sL + o, sb ? (const void *)((const float *)L1.base + i * L1.s[0] + j) : nowhere, sb);
+        cp16(sU + o, ur ? (const void *)((const float *)U.base + i * U.s[0] + j) : nowhere, ur);
+        if (li >= 1 && li <= TY)
+            cp16(sG + o, sb ? (const void *)((const float *)G.base + i * G.s[0] + j) : nowhere, sb);
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    // s = K * L1 on the superblock's cells, 0 elsewhere; u_t outside its region is 0
+    for (int e = threadIdx.x; e < (TY + 2) * AQ; e += AT) {
+        const int li = e / AQ, qq = e % AQ - 1;
+        const int64_t i = ty0 - 1 + li, j = tx0 + 4 * qq;
+        const int o = li * VP + 4 + 4 * qq;
+        const bool rsb = i >= y0 && i <= y1;
+        float4 k4 = *(float4 *)(sK + o);
+        const float4 l4 = *(const float4 *)(sL + o);
+        k4.x = sel(rsb && j >= x0 && j <= x1, __fmul_rn(k4.x, l4.x));
+        k4.y = sel(rsb && j + 1 >= x0 && j + 1 <= x1, __fmul_rn(k4.y, l4.y));
+        k4.z = sel(rsb && j + 2 >= x0 && j + 2 <= x1, __fmul_rn(k4.z, l4.z));
+        k4.w = sel(rsb && j + 3 >= x0 && j + 3 <= x1, __fmul_rn(k4.w, l4.w));
+        *(float4 *)(sK + o) = k4;
+        if (j < rx0 || j + 3 > rx1) {
+            float4 u4 = *(float4 *)(sU + o);
+            u4.x = sel(j >= rx0 && j <= rx1, u4.x);
+            u4.y = sel(j + 1 >= rx0 && j + 1 <= rx1, u4.y);
+            u4.z = sel(j + 2 >= rx0 && j + 2 <= rx1, u4.z);
+            u4.w = sel(j + 3 >= rx0 && j + 3 <= rx1, u4.w);
+            *(float4 *)(sU + o) = u4;
+        }
+    }
+    __syncthreads();
+    auto ss = [&](int li, int c) { return sK[li * VP + c]; };
+    auto su = [&](int li, int c) { return sU[li * VP + c]; };
+    for (int e = threadIdx.x; e < TY * VQ; e += AT) {
+        const int li = e / VQ + 1, q = e % VQ;
+        const int64_t i = ty0 + li - 1, j = tx0 + 4 * q;
+        if (i > ry1 || j > rx1 || j + 3 < rx0) continue;
+        const int c = 4 + 4 * q;
+        const bool row_sb = i >= y0 && i <= y1;
+        const bool grp_sb = row_sb && j + 3 >= x0 && j <= x1;
+        const float4 l14 = *(const float4 *)(sL + li * VP + c), g4 = *(const float4 *)(sG + li * VP + c);
+        const float l1[4] = {l14.x, l14.y, l14.z, l14.w};
+        float g[4] = {g4.x, g4.y, g4.z, g4.w};
+        float o[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const bool in = row_sb && j + m >= x0 && j + m <= x1;
+            float acc = 0.f;
+            if (in) {
+                acc = __fsub_rn(l1[m], __fmul_rn(4.0f, ss(li, c + m)));
+                const float cc = su(li, c + m);
+                g[m] = __fadd_rn(g[m], __fmul_rn(l1[m], lap5(cc, su(li - 1, c + m), su(li + 1, c + m),
+                                                              su(li, c + m - 1), su(li, c + m + 1))));
+            }
+            acc = __fadd_rn(acc, ss(li - 1, c + m));
+            acc = __fadd_rn(acc, ss(li + 1, c + m));
+            acc = __fadd_rn(acc, ss(li, c + m - 1));
+            acc = __fadd_rn(acc, ss(li, c + m + 1));
+            o[m] = acc;
+        }
+        float *dst = (float *)L0.base + i * L0.s[0] + j;
+        if (j >= rx0 && j + 3 <= rx1) {
+            *(float4 *)dst = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+            for (int m = 0; m < 4; ++m)
+                if (j + m >= rx0 && j + m <= rx1) dst[m] = o[m];
+        }
+        if (grp_sb) {
+            float *gd = (float *)G.base + i * G.s[0] + j;
+            if (j >= x0 && j + 3 <= x1) {
+                *(float4 *)gd = make_float4(g[0], g[1], g[2], g[3]);
+            } else {
+                for (int m = 0; m < 4; ++m)
+                    if (j + m >= x0 && j + m <= x1) gd[m] = g[m];
+            }
+        }
+    }
+}
+
 bool views_vec_ok(const ExecTask *t, int n, int nviews) {
     for (int i = 0; i < n; ++i)
         for (int a = 0; a < nviews; ++a) {
@@ -379,7 +504,8 @@ cudaError_t launch_diffusion(const ExecTask *dev, uint32_t ctas, const ExecParam
 uint32_t prepare_diffusion_adj(ExecTask *t, int n, ExecParams &p) {
     const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
     const bool vec = views_vec_ok(t, n, 5);
-    p.variant = vec ? 1 : 0;
+    // variant 2: staged through shared memory with cp.async; 1: registers; 0: scalar
+    p.variant = vec ? (p.no_staged ? 1 : 2) : 0;
     uint32_t total = 0;
     for (int i = 0; i < n; ++i) {
         int64_t x0 = t[i].t_lo[0], y0 = t[i].t_lo[1];
@@ -400,6 +526,17 @@ uint32_t prepare_diffusion_adj(ExecTask *t, int n, ExecParams &p) {
 }
 
 cudaError_t launch_diffusion_adj(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
+    if (p.variant == 2) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(diffusion_adj_async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 ASMEM);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        diffusion_adj_async_kernel<<<ctas, AT, ASMEM, st>>>(dev, p);
+        return cudaGetLastError();
+    }
     if (p.variant == 1)
         diffusion_adj_vec_kernel<<<ctas, DT, 0, st>>>(dev, p);
     else

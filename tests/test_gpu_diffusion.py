@@ -109,3 +109,36 @@ def test_adjoint_full_size_16384_sampled_vs_lightcone():
     assert rel(u_T, wu) < 1e-5
     assert rel(g_u, wdu) < 1e-4
     assert rel(g_k, wdk) < 1e-4
+
+
+@pytest.mark.parametrize("dist_name", ["tiles_halo", "block"])
+def test_adjoint_staged_and_register_kernels_agree_bit_for_bit(dist_name):
+    # the adjoint launch through the cp.async-staged kernel (default) and the
+    # register kernel (LT_FLAG_NO_STAGED): same operations, same results;
+    # 300 x 520 is ragged against the 32 x 128 tiles and the 4-column groups
+    torch = pytest.importorskip("torch")
+    from paper_2202_05549_gb300.autograd import DiffusionPlan
+
+    ny, nx, T, ck = 300, 520, 6, 3
+    dist, sb = {"tiles_halo": (lt.Dist.tiles((100, 256), halo=(1, 1)), (256, 100)),
+                "block": (lt.Dist.block(), (0, 0))}[dist_name]
+    u0, k = fields(ny, nx)
+    out = []
+    for flags in (0, L.LT_FLAG_NO_STAGED):
+        with lt.Context(flags=flags) as ctx:
+            ctx.log_enable()
+            plan = DiffusionPlan(ctx, ny, nx, T, ck, dist, sb)
+            plan.K.write(k)
+            plan.ck[0].write(u0)
+            plan.forward()
+            uT = plan.ck[-1].read()
+            plan.lam[0].write((2.0 * uT).astype(np.float32))
+            lam0 = plan.backward()
+            ctx.synchronize()
+            variants = {t["variant"] for t in ctx.log() if t["kind"] == "execute"}
+            out.append((lam0.read(), plan.G.read(), variants))
+    assert 2 in out[0][2] and 2 not in out[1][2]
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    _, du0, dk = oracle.diffusion_grad(u0.astype(np.float64), k.astype(np.float64), T)
+    assert rel(out[0][0], du0) < 1e-4 and rel(out[0][1], dk) < 1e-4
