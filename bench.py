@@ -365,7 +365,7 @@ def run_lightning(args, rank, world, local, grp):
     elif user:
         kname = "lt_user_wrapper (NVRTC)"
     else:
-        kname = {2: "jacobi2d_tma_kernel", 1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
+        kname = {1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
     # DRAM traffic records: the in-core grid keeps part of its working set in L2
     tkey = kname + ("@incore4096" if args.workload != "ooc" and tb == 1 else "")
     # the timed steps run without per-operation CUDA events (a few
@@ -720,7 +720,7 @@ def run_gemm(args, rank, world, local, grp):
     elif user:
         kname = "lt_user_wrapper (NVRTC)"
     else:
-        kname = {2: "jacobi2d_tma_kernel", 1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
+        kname = {1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
     # DRAM traffic records: the in-core grid keeps part of its working set in L2
     tkey = kname + ("@incore4096" if args.workload != "ooc" and tb == 1 else "")
     ctx.reset_stats()

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 
+#include "async_copy.cuh"
 #include "kernels.cuh"
 #include "task_lookup.cuh"
 
@@ -355,12 +356,6 @@ constexpr int ASMEM = 4 * ATILE * 4;          // dynamic shared memory of the ke
 constexpr int AT = DT;                        // threads per CTA
 constexpr int ACTA = 3;                       // CTAs per SM the kernel is built for
 
-__device__ __forceinline__ void cp16(float *dst, const void *src, bool valid) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src), "r"(valid ? 16 : 0)
-                 : "memory");
-}
-
 __global__ void __launch_bounds__(AT, ACTA) diffusion_adj_async_kernel(const ExecTask *__restrict__ tasks,
                                                                       ExecParams p) {
     extern __shared__ __align__(16) float asmem[];
@@ -384,13 +379,13 @@ __global__ void __launch_bounds__(AT, ACTA) diffusion_adj_async_kernel(const Exe
         const int o = li * VP + 4 + 4 * qq;
         const bool sb = i >= y0 && i <= y1 && j + 3 >= x0 && j <= x1;       // meets the superblock
         const bool ur = i >= ry0 && i <= ry1 && j + 3 >= rx0 && j <= rx1;   // meets U's region
-        cp16(sK + o, sb ? (const void *)((const float *)K.base + i * K.s[0] + j) : nowhere, sb);
-        cp16(sL + o, sb ? (const void *)((const float *)L1.base + i * L1.s[0] + j) : nowhere, sb);
-        cp16(sU + o, ur ? (const void *)((const float *)U.base + i * U.s[0] + j) : nowhere, ur);
+        cp_async16(sK + o, sb ? (const void *)((const float *)K.base + i * K.s[0] + j) : nowhere, sb);
+        cp_async16(sL + o, sb ? (const void *)((const float *)L1.base + i * L1.s[0] + j) : nowhere, sb);
+        cp_async16(sU + o, ur ? (const void *)((const float *)U.base + i * U.s[0] + j) : nowhere, ur);
         if (li >= 1 && li <= TY)
-            cp16(sG + o, sb ? (const void *)((const float *)G.base + i * G.s[0] + j) : nowhere, sb);
+            cp_async16(sG + o, sb ? (const void *)((const float *)G.base + i * G.s[0] + j) : nowhere, sb);
     }
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    cp_async_wait_all();
     __syncthreads();
     // s = K * L1 on the superblock's cells, 0 elsewhere; u_t outside its region is 0
     for (int e = threadIdx.x; e < (TY + 2) * AQ; e += AT) {
