@@ -708,21 +708,9 @@ def run_gemm(args, rank, world, local, grp):
     def step():
         k.launch(grid=(n, n), block=(256, 1), superblock=(t, t), args=[A, B, Cm])
 
-    ctx.log_enable()
     for _ in range(args.warmup):
         step()
     ctx.synchronize()
-    # which of the built-in's kernels the launches took
-    variant = max((t.get("variant", 0) for t in ctx.log() if t["kind"] == "execute"), default=0)
-    ctx.log_enable(False)
-    if tb > 1:
-        kname = "jacobi2d_multi_kernel"
-    elif user:
-        kname = "lt_user_wrapper (NVRTC)"
-    else:
-        kname = {1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
-    # DRAM traffic records: the in-core grid keeps part of its working set in L2
-    tkey = kname + ("@incore4096" if args.workload != "ooc" and tb == 1 else "")
     ctx.reset_stats()
     grp.barrier()
     clk = Clocks(local)
