@@ -30,12 +30,20 @@
 namespace lt {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, UMMA_K = 16;
+// Tile BM x BN: MH M-halves of UM = 128 rows (one tcgen05.mma each, both
+// reading the same B stage), so a stage's B bytes serve MH MMAs.  The
+// accumulators of a tile take MH x BN TMEM columns; NACC tiles fit in the
+// 512 columns (NACC = 2 lets the epilogue of one tile overlap the next).
+constexpr int MH = 2, UM = 128;
+constexpr int BM = MH * UM, BN = 256, BK = 64, UMMA_K = 16;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
 constexpr int THREADS = 192;
 constexpr int TMEM_COLS = 512;
+constexpr int NACC = TMEM_COLS / (MH * BN);
+static_assert(NACC >= 1 && STAGES >= 2, "tile shape does not fit TMEM or shared memory");
 constexpr int MAX_MAPS = 15;
 constexpr int GROUP_M = 16;  // tile raster: 16 M-tiles share each B panel
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
@@ -131,9 +139,9 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 }
 
 // Instruction descriptor, kind::f16: f32 accumulator, bf16 A and B, both
-// K-major, N = 256, M = 128.
+// K-major, N = BN = 256, M = UM = 128.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+                           ((uint32_t)(UM >> 4) << 24);
 
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
     asm volatile(
@@ -208,8 +216,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_bf16_kernel(const ExecTask *_
     uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
     uint64_t *acc_full = empty + STAGES;
-    uint64_t *acc_empty = acc_full + 2;
-    uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
+    uint64_t *acc_empty = acc_full + NACC;
+    uint32_t *tmem_slot = (uint32_t *)(acc_empty + NACC);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -218,7 +226,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_bf16_kernel(const ExecTask *_
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 128);
         }
@@ -288,7 +296,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_bf16_kernel(const ExecTask *_
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * MH * BN);
                 for (int64_t kb = 0; kb < nk; ++kb) {
                     if (!mbar_wait(&full[stage], phase, abort_flag, P.err, 0x6703)) {
                         ok = false;
@@ -300,7 +308,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_bf16_kernel(const ExecTask *_
 #pragma unroll
                     for (int k = 0; k < BK / UMMA_K; ++k) {
                         const uint64_t koff = (uint64_t)((k * UMMA_K * 2) >> 4);
-                        umma(d_tmem, ad + koff, bd + koff, (kb > 0 || k > 0) ? 1u : 0u);
+#pragma unroll
+                        for (int h = 0; h < MH; ++h)  // M-half h: A rows h*UM.., accumulator columns h*BN..
+                            umma(d_tmem + (uint32_t)(h * BN), ad + (uint64_t)((h * UM * BK * 2) >> 4) + koff,
+                                 bd + koff, (kb > 0 || k > 0) ? 1u : 0u);
                     }
                     umma_commit(&empty[stage]);  // frees the stage once these MMAs have read it
                     if (++stage == STAGES) {
@@ -310,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_bf16_kernel(const ExecTask *_
                 }
                 if (!ok) break;
                 umma_commit(&acc_full[acc]);
-                if (++acc == 2) {
+                if (++acc == NACC) {
                     acc = 0;
                     acc_phase ^= 1;
                 }
@@ -331,12 +342,14 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_bf16_kernel(const ExecTask *_
             tc_fence_after();
             const ExecTask &t = tasks[ti.task];
             const DView cv = t.v[2];
-            const int64_t row = ti.m0 + q * 32 + lane;
-            float *crow = (float *)(cv.base + (uint64_t)(row * cv.s[0] * 4));
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
+            for (int hc = 0; hc < MH * (BN / 32); ++hc) {
+            const int h = hc / (BN / 32), c = hc % (BN / 32);
+            const int64_t row = ti.m0 + h * UM + q * 32 + lane;
+            float *crow = (float *)(cv.base + (uint64_t)(row * cv.s[0] * 4));
+            {
                 float v[32];
-                tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32), v);
+                tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * MH * BN + h * BN + c * 32), v);
                 const int64_t col = ti.n0 + c * 32;
                 if (row <= ti.m_last && col <= ti.n_last) {
                     if (col + 31 <= ti.n_last && cv.s[1] == 1) {
@@ -350,9 +363,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_bf16_kernel(const ExecTask *_
                     }
                 }
             }
+            }
             tc_fence_before();
             mbar_arrive(&acc_empty[acc]);
-            if (++acc == 2) {
+            if (++acc == NACC) {
                 acc = 0;
                 acc_phase ^= 1;
             }
