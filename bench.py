@@ -758,6 +758,30 @@ def run_gemm(args, rank, world, local, grp):
                      "peak_source": peaks["source"] + " bf16 sustained (burst %.1f)" % peaks["bf16_tflops"]},
         "gpu_launches": st["kernels"], "clocks": clocks,
     }
+    if not args.no_e2e:
+        # end to end through the public API: every step uploads A (8 GiB of
+        # bf16, row-major) from pinned host memory, multiplies by the resident
+        # B (the operand a caller keeps on the device, e.g. weights) and reads
+        # C (16 GiB of f32) back into pinned host memory
+        import numpy as np
+        import torch
+        h_a = torch.empty((n, n), dtype=torch.int16, pin_memory=True).numpy().view(np.uint16)
+        h_c = torch.empty((n, n), dtype=torch.float32, pin_memory=True).numpy()
+        A.read(out=h_a)
+        ctx.op_timing(False)
+        ctx.synchronize()
+        t0 = time.perf_counter()
+        nstep = max(1, args.steps // 2)
+        for _ in range(nstep):
+            A.write(h_a)
+            step()
+            Cm.read(out=h_c)
+        ctx.synchronize()
+        t1 = time.perf_counter()
+        res["e2e"] = {"value": round(grp.sum(flop * nstep / 1e12) / grp.max(t1 - t0), 1), "unit": "TFLOP/s",
+                      "h2d_bytes_per_step": int(h_a.nbytes), "d2h_bytes_per_step": int(h_c.nbytes),
+                      "how": "public Python API, wall clock; per step: upload of A from pinned host memory, the GEMM "
+                             "launch and synchronize, read of C into pinned host memory (B stays resident)"}
     ctx.close()
     return res
 
@@ -778,17 +802,21 @@ def run_batch(args, rank, world, local, grp):
                     [("U", lt.F32), ("V", lt.F32)])
     kh = ctx.kernel(lt.HIST256, "global i => read X[i], reduce(+) H[:]", [("X", lt.U8), ("H", lt.U32)])
     launches = []
+    inputs, hists = [], []  # the arrays a step reads (for the e2e upload) and the histograms it produces
     for q, s_ in enumerate(sides):
         s_ = int(s_)
         U = ctx.array(lt.F32, (s_, s_))
         V = ctx.array(lt.F32, (s_, s_))
         U.fill(L.LT_INIT_UNIFORM, seed=si.SEED_BATCH, stream=si.STREAM_BATCH_JACOBI0 + q)
         launches.append((kj, (s_, s_), (128, 4), (0, 0), [U, V], r.iters))
+        inputs.append(U)
     for h, n in enumerate(lens):
         X = ctx.array(lt.U8, (int(n),))
         H = ctx.array(lt.U32, (256,))
         X.fill(L.LT_INIT_U8, seed=si.SEED_BATCH, stream=si.STREAM_BATCH_HIST0 + h)
         launches.append((kh, (int(n),), (256,), (0,), [X, H], 1))
+        inputs.append(X)
+        hists.append(H)
     cells = float(sum(int(s_) ** 2 for s_ in sides))
     nbytes = 8.0 * cells * r.iters + float(sum(int(n) for n in lens)) + 1024.0 * len(lens)
     nlaunch = len(sides) * r.iters + len(lens)
@@ -830,6 +858,37 @@ def run_batch(args, rank, world, local, grp):
                   "launches": st_p["launches"], "speedup_batched_vs_plain": round(ms_p / ms_f, 2)},
         "gpu_launches": st["kernels"], "graph_replays": st["graph_replays"], "clocks": clocks,
     }
+    if not args.no_e2e:
+        # end to end through the public API: every step uploads every input
+        # array (the Jacobi grids and the histogrammed bytes, one pinned host
+        # buffer) with lt_array_write, runs the fused batch and reads the 1024
+        # histograms back
+        import numpy as np
+        import torch
+        views, off = [], 0
+        sizes = [int(np.prod(a.shape)) * (4 if a.dtype == lt.F32 else 1) for a in inputs]
+        host = torch.empty(sum(sizes), dtype=torch.uint8, pin_memory=True).numpy()
+        for a, sz in zip(inputs, sizes):
+            v = host[off:off + sz].view(np.float32 if a.dtype == lt.F32 else np.uint8).reshape(a.shape)
+            a.read(out=v)
+            views.append(v)
+            off += sz
+        hout = torch.empty((len(hists), 256), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        ctx.synchronize()
+        t0 = time.perf_counter()
+        nstep = max(1, args.steps // 2)
+        for _ in range(nstep):
+            for a, v in zip(inputs, views):
+                a.write(v)
+            ctx.launch_batch(launches, 0)
+            for i, H in enumerate(hists):
+                H.read(out=hout[i])
+        ctx.synchronize()
+        t1 = time.perf_counter()
+        res["e2e"] = {"value": round(grp.sum(nbytes * nstep / 1e9) / grp.max(t1 - t0), 2), "unit": "GB/s",
+                      "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(hout.nbytes),
+                      "how": "public Python API, wall clock; per step: lt_array_write of every input array from one "
+                             "pinned host buffer, the fused batch and synchronize, lt_array_read of every histogram"}
     ctx.close()
     return res
 
@@ -900,6 +959,40 @@ def run_adjoint(args, rank, world, local, grp):
                      "kernel": "diffusion_fwd_kernel + diffusion_adj_kernel (whole step, wall clock)"},
         "clocks": clocks,
     }
+    # kernels the library launches per step (its contexts count them)
+    from paper_2202_05549_gb300 import autograd as ag
+    for c in ag._ctx_cache.values():
+        c.reset_stats()
+    ours()
+    torch.cuda.synchronize(dev)
+    res["gpu_launches"] = args.steps * sum(c.stats()["kernels"] for c in ag._ctx_cache.values())
+    if not args.no_e2e:
+        # end to end: every step uploads u0 and kappa from pinned host memory,
+        # runs forward + gradient and reads both gradients back into pinned
+        # host memory
+        h_u, h_k = u0.cpu().pin_memory(), kap.cpu().pin_memory()
+        o_u = torch.empty_like(h_u).pin_memory()
+        o_k = torch.empty_like(h_k).pin_memory()
+
+        def e2e_step():
+            u = h_u.to(dev, non_blocking=True).requires_grad_(True)
+            k = h_k.to(dev, non_blocking=True).requires_grad_(True)
+            uT = DiffusionChunked.apply(u, k, T, ck, chunk, (chunk, chunk))
+            (uT * uT).sum().backward()
+            o_u.copy_(u.grad, non_blocking=True)
+            o_k.copy_(k.grad, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        e2e_step()
+        t0 = time.perf_counter()
+        nstep = max(1, args.steps // 2)
+        for _ in range(nstep):
+            e2e_step()
+        t1 = time.perf_counter()
+        res["e2e"] = {"value": round(grp.sum(nbytes * nstep / 1e9) / grp.max(t1 - t0), 2), "unit": "GB/s",
+                      "h2d_bytes_per_step": int(2 * h_u.numel() * 4), "d2h_bytes_per_step": int(2 * h_u.numel() * 4),
+                      "how": "wall clock; per step: u0 and kappa copied from pinned host memory, forward + gradient "
+                             "through the autograd wrapper, both gradients copied into pinned host memory"}
     return res
 
 
