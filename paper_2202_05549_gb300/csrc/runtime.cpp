@@ -103,6 +103,12 @@ struct Arena {
     std::map<size_t, Free> free_;
     size_t used = 0, peak = 0;
     uint64_t tick = 0;
+    // Oldest-first instead of best-fit: the host pool, whose requests are all
+    // chunk-sized evictions, takes the block freed longest ago (untouched
+    // space first), whose last users are most likely done.  Best-fit there
+    // picked the slot a fetch had just emptied over untouched space, so the
+    // eviction waited for that fetch and the two copy directions ran in turn.
+    bool oldest_first = false;
 
     void init(size_t c, char *b) {
         cap = c / ALIGN * ALIGN;
@@ -115,8 +121,10 @@ struct Arena {
         auto best = free_.end();
         for (auto it = free_.begin(); it != free_.end(); ++it) {
             if (it->second.size < sz) continue;
-            if (best == free_.end() || it->second.size < best->second.size ||
-                (it->second.size == best->second.size && it->second.tick < best->second.tick))
+            if (best == free_.end() ||
+                (oldest_first ? it->second.tick < best->second.tick
+                              : it->second.size < best->second.size ||
+                                    (it->second.size == best->second.size && it->second.tick < best->second.tick)))
                 best = it;
         }
         if (best == free_.end()) return false;
@@ -1058,6 +1066,7 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
         if (!budget) budget = (size_t)1 << 34;
         c->dev.init(budget, nullptr);
         c->host.init(cfg->host_pool_bytes, nullptr);
+        c->host.oldest_first = true;
         *out = c.release();
         return LT_OK;
     }
@@ -1091,6 +1100,7 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
         }
     }
     c->host.init(cfg->host_pool_bytes, c->host_base);
+    c->host.oldest_first = true;
     c->up_cap = (size_t)32 << 20;
     CK(cp, cudaHostAlloc((void **)&c->up_host, c->up_cap + TSLOTS * TSLOT_BYTES, cudaHostAllocDefault));
     CK(cp, cudaMalloc((void **)&c->up_dev, c->up_cap + TSLOTS * TSLOT_BYTES));
