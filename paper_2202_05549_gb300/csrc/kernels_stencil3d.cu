@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(ST) jacobi3d_scalar_kernel(const ExecTask *__r
 constexpr int TW = 128, TH = 32, TXH = 4;
 constexpr int BW = TW + 2 * TXH, BH = TH + 2;
 constexpr int NS = 5;      // plane slots
-constexpr int ZSEG = 32;   // planes per work unit
+constexpr int ZSEG = 16;   // planes per work unit (16: 0.958 of HBM at 1024^3; 32: 0.92, 64: 0.89)
 constexpr int TT = 256;    // threads per CTA: 8 warps x 4 rows
 constexpr int TCTA = 2;    // CTAs per SM
 constexpr uint32_t PLANE_BYTES = BW * BH * 4;                  // bytes one box load writes

@@ -43,7 +43,7 @@ def variants(ctx):
 
 @pytest.mark.parametrize("name", sorted(DISTS))
 def test_jacobi3d_bit_exact(name):
-    # 37 x 50 x 133: ragged against the staged kernel's 32-plane units,
+    # 37 x 50 x 133: ragged against the staged kernel's 16-plane units,
     # 32-row and 128-column tiles (the last column tile is 5 wide)
     nz, ny, nx, iters = 37, 50, 133, 3
     u0 = field3(nz, ny, nx)
