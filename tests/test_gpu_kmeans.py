@@ -3,6 +3,10 @@ reduce(+) of per-centre fp64 sums and counts, and the centre update, checked
 bit for bit against the oracle over several iterations.  Uniform features
 are multiples of 2^-24 in [0, 1), so every fp64 sum is exact whatever the
 order of its additions."""
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -118,3 +122,44 @@ def test_kmeans_fp64_fallback_path_bit_exact():
             assert np.array_equal(S.read().reshape(k, 5), s)
             assert np.array_equal(C2.read().reshape(k, 4), want_c)
             C, C2 = C2, C
+
+
+def _slice_sums(part):
+    """Oracle sums and counts of records [lo, hi) of the seeded records
+    (runs in a spawned worker process)."""
+    lo, hi, c = part
+    oracle.set_threads(1)
+    x = oracle.gen_uniform_f32(SEED, 0, 4 * lo, 4 * (hi - lo)).reshape(-1, 4)
+    return oracle.kmeans_assign(x, c)[0]
+
+
+@pytest.mark.gpu
+def test_kmeans_full_size_bit_exact():
+    """The launch configuration of the K-Means benchmark: 1e9 records (16 GB),
+    k = 40, 25M records per chunk and superblock, the first k records as
+    centres; one Lloyd iteration.  The oracle assigns slices of the records
+    in worker processes and adds their fp64 sums: every sum is a multiple of
+    2^-24 below 2^29, so it is exact whatever the order of the additions."""
+    n, k, per = 1_000_000_000, 40, 25_000_000
+    c = oracle.gen_uniform_f32(SEED, 0, 0, 4 * k).reshape(k, 4)
+    with lt.Context() as ctx:
+        X = ctx.array(lt.F32, (4 * n,), lt.Dist.rows(4 * per))
+        C = ctx.array(lt.F32, (4 * k,), lt.Dist.block())
+        C2 = ctx.array(lt.F32, (4 * k,), lt.Dist.block())
+        S = ctx.array(lt.F64, (5 * k,), lt.Dist.block())
+        X.fill(L.LT_INIT_UNIFORM, seed=SEED, stream=0)
+        C.write(c.reshape(-1))
+        ka, ku = kernels(ctx)
+        ka.launch(grid=(n,), block=(256,), superblock=(per,), args=[X, C, S, k])
+        ku.launch(grid=(k,), block=(64,), superblock=(0,), args=[S, C, C2])
+        got_s = S.read().reshape(k, 5)
+        got_c = C2.read().reshape(k, 4)
+    step = 15_625_000
+    parts = [(lo, min(lo + step, n), c) for lo in range(0, n, step)]
+    workers = max(1, min(16, len(os.sched_getaffinity(0))))
+    # spawned, not forked: this process holds a CUDA context
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as pool:
+        want_s = np.sum(list(pool.map(_slice_sums, parts)), axis=0)
+    assert want_s[:, 4].sum() == n
+    assert np.array_equal(got_s, want_s)
+    assert np.array_equal(got_c, oracle.kmeans_update(want_s, c))
