@@ -38,18 +38,21 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
 }
 
 __global__ void __launch_bounds__(BT, BOCC) batch_kernel(BatchParams P) {
-    __shared__ uint32_t s_item;
+    __shared__ uint32_t s_item[2];  // this item and the next one, claimed while this one runs
     __shared__ int s_stop;
     __shared__ uint32_t sh[BT / 32][256];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (;;) {
+    if (tid == 0) s_item[0] = atomicAdd(P.head, 1u);
+    for (uint32_t par = 0;; par ^= 1u) {
         if (tid == 0) {
-            s_item = atomicAdd(P.head, 1u);
-            s_stop = s_item >= P.nitems || ld_acquire(P.abort) != 0;
+            s_stop = s_item[par] >= P.nitems || ld_acquire(P.abort) != 0;
+            // Claiming the next item early keeps the queue's order argument:
+            // the earliest unfinished item is always one a CTA is running.
+            if (!s_stop) s_item[par ^ 1u] = atomicAdd(P.head, 1u);
         }
         __syncthreads();
         if (s_stop) break;
-        const BatchItem w = P.items[s_item];
+        const BatchItem w = P.items[s_item[par]];
         const uint32_t kind = w.kind_inst >> 30, inst = w.kind_inst & 0x3FFFFFFFu;
         if (kind == 0) {
             const BatchJacobi J = P.jac[inst];
@@ -76,9 +79,13 @@ __global__ void __launch_bounds__(BT, BOCC) batch_kernel(BatchParams P) {
             const int64_t ny = J.ny, nx = J.nx;
             const int64_t ye = min((int64_t)(w.row0 + w.nrows) - 1, ny - 1);
             const uint32_t sx = (uint32_t)((nx + JCOLS - 1) / JCOLS), sy = (w.nrows + BR - 1) / BR;
-            for (uint32_t s = warp; s < sx * sy; s += BT / 32) {  // 32-bit: tiles are small
-                const int64_t js = (int64_t)(s % sx) * JCOLS, r0 = (int64_t)w.row0 + (int64_t)(s / sx) * BR;
+            // strip s = cy * sx + cx, s = warp, warp + 8, ...; (cx, cy) advance
+            // without a division per strip (32-bit: tiles are small)
+            uint32_t cx = warp % sx, cy = warp / sx;
+            for (uint32_t s = warp; s < sx * sy; s += BT / 32) {
+                const int64_t js = (int64_t)cx * JCOLS, r0 = (int64_t)w.row0 + (int64_t)cy * BR;
                 if (r0 <= ye) jacobi_strip<true, BR>(src, ss, dst, sd, ny, nx, js, r0, nx - 1, ye, lane);
+                for (cx += BT / 32; cx >= sx; cx -= sx) ++cy;
             }
             __threadfence();
             __syncthreads();
