@@ -333,6 +333,9 @@ lt_status lt_launch(lt_ctx *ctx, lt_kernel *k, lt_dim3 grid, lt_dim3 block, cons
  * iteration of the batch (which writes only data the real run overwrites)
  * and caches the choice per batch shape.  Otherwise, or with
  * LT_BATCH_PLAIN, the launches are issued one by one (the plain form).
+ * The fused form checks every descriptor's annotation as lt_launch does,
+ * once: a call whose descriptors equal the last checked batch (kernels,
+ * grids, blocks, superblocks, arguments and repeats) skips the checks.
  * Asynchronous like lt_launch; the descriptors are read during the call. */
 typedef struct {
     lt_kernel *kernel;

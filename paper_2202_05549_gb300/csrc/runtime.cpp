@@ -25,6 +25,7 @@
 #include <memory>
 #include <sstream>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "core.hpp"
@@ -331,7 +332,9 @@ struct lt_ctx {
     std::vector<TableSlot> tslots;
     uint64_t tslot_tick = 0;
     uint32_t *err_word = nullptr;  // device error word
-    std::vector<std::unique_ptr<lt_array>> arrays;
+    std::vector<std::unique_ptr<lt_array>> arrays;       // creation order (iteration order)
+    std::unordered_set<const lt_array *> array_set;      // membership: handles are checked on every call
+    std::vector<uint64_t> batch_checked;  // the last fused batch whose launches passed prepare_plan
     std::vector<std::unique_ptr<lt_kernel>> kernels;
     uint64_t clock = 0;
     int64_t launch_id = 0;
@@ -789,9 +792,7 @@ lt_status check_ctx(lt_ctx *c) {
 }
 
 lt_array *find_array(lt_ctx *c, const lt_array *a) {
-    for (auto &p : c->arrays)
-        if (p.get() == a) return p.get();
-    return nullptr;
+    return c->array_set.count(a) ? const_cast<lt_array *>(a) : nullptr;
 }
 
 lt_kernel *find_kernel(lt_ctx *c, const lt_kernel *k) {
@@ -1159,6 +1160,7 @@ lt_status lt_array_create(lt_ctx *c, lt_dtype dtype, int32_t ndim, const int64_t
     a->cs.resize(a->g.chunks.size());
     a->id = c->next_array_id++;
     *out = a.get();
+    c->array_set.insert(a.get());
     c->arrays.push_back(std::move(a));
     return LT_OK;
 }
@@ -1192,6 +1194,7 @@ lt_status lt_array_wrap_device(lt_ctx *c, lt_dtype dtype, int32_t ndim, const in
     cs.off = (size_t)((uint64_t)(uintptr_t)ptr - (uint64_t)(uintptr_t)c->dev_base);
     a->id = c->next_array_id++;
     *out = a.get();
+    c->array_set.insert(a.get());
     c->arrays.push_back(std::move(a));
     return LT_OK;
 }
@@ -1216,6 +1219,7 @@ lt_status lt_array_destroy(lt_ctx *c, lt_array *arr) {
         if (s.loc == LOC_HOST) c->host.release(s.off, a->g.chunks[i].bytes, f);
         s.loc = LOC_NONE;
     }
+    c->array_set.erase(a);
     for (auto it = c->arrays.begin(); it != c->arrays.end(); ++it)
         if (it->get() == a) {
             c->arrays.erase(it);
@@ -1685,6 +1689,7 @@ lt_status lt_kernel_destroy(lt_ctx *c, lt_kernel *kk) {
                 cudaLibraryUnload(kk->ulib);
             }
             c->kernels.erase(it);
+            c->batch_checked.clear();  // a new kernel may reuse the address
             return LT_OK;
         }
     return fail(LT_ERR_INVALID_ARG, "unknown kernel");
@@ -2780,15 +2785,14 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
     // eligibility of the fused form
     BatchShape bs;
     bool fused = !(flags & LT_BATCH_PLAIN) && !c->dry && n > 0;
-    std::vector<lt_array *> seen;
+    std::unordered_set<const lt_array *> seen;
     for (int32_t i = 0; i < n && fused; ++i) {
         lt_kernel *k = d[i].kernel;
         std::vector<lt_array *> arrs;
         for (int32_t p = 0; p < d[i].nargs; ++p)
             if (k->params[(size_t)p].is_array) arrs.push_back(find_array(c, d[i].args[p].array));
         for (lt_array *a : arrs) {
-            if (!a || a->cs.size() != 1 || std::find(seen.begin(), seen.end(), a) != seen.end()) fused = false;
-            seen.push_back(a);
+            if (!a || a->cs.size() != 1 || !seen.insert(a).second) fused = false;
         }
         if (!fused) break;
         if (k->def->id == LT_K_JACOBI2D && arrs.size() == 2 && arrs[0] != arrs[1] &&
@@ -2802,12 +2806,33 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
             fused = false;
     }
     if (!fused) return batch_plain(c, d, n);
-    // the plain form validates annotations per launch; the fused form checks them once
+    // The plain form validates annotations per launch; the fused form checks
+    // each launch once and skips the check while the batch repeats exactly
+    // (same kernels, grids, blocks, superblocks, arguments and repeats; array
+    // ids are never reused).
+    std::vector<uint64_t> chk;
+    chk.reserve((size_t)n * 16);
     for (int32_t i = 0; i < n; ++i) {
-        std::shared_ptr<const PlanBundle> b;
-        std::vector<lt_array *> parr;
-        if ((st = prepare_plan(c, d[i].kernel, d[i].grid, d[i].block, &d[i].wd, d[i].args, d[i].nargs, &b, &parr)))
-            return st;
+        const lt_launch_desc &e = d[i];
+        chk.insert(chk.end(), {(uint64_t)(uintptr_t)e.kernel, e.grid.x, e.grid.y, e.grid.z, e.block.x, e.block.y,
+                               e.block.z, (uint64_t)e.wd.superblock[0], (uint64_t)e.wd.superblock[1],
+                               (uint64_t)e.wd.superblock[2], (uint64_t)e.repeat, (uint64_t)e.nargs});
+        for (int32_t p = 0; p < e.nargs; ++p) {
+            uint64_t fb;
+            std::memcpy(&fb, &e.args[p].f, sizeof fb);
+            const lt_array *a = e.kernel->params[(size_t)p].is_array ? find_array(c, e.args[p].array) : nullptr;
+            chk.insert(chk.end(), {a ? (uint64_t)a->id : ~0ull, fb, (uint64_t)e.args[p].i});
+        }
+    }
+    if (chk != c->batch_checked) {
+        c->batch_checked.clear();
+        for (int32_t i = 0; i < n; ++i) {
+            std::shared_ptr<const PlanBundle> b;
+            std::vector<lt_array *> parr;
+            if ((st = prepare_plan(c, d[i].kernel, d[i].grid, d[i].block, &d[i].wd, d[i].args, d[i].nargs, &b, &parr)))
+                return st;
+        }
+        c->batch_checked = std::move(chk);
     }
     if ((st = flush_pending(c))) return st;
     ++c->launch_id;

@@ -215,6 +215,29 @@ class Kernel:
         return json.loads(buf.value.decode())
 
 
+
+class Batch:
+    """The lt_launch_desc array of a batch of launches, built once.  It holds
+    the launches (and so their arrays and argument tables) alive; descriptors
+    are rebuilt only by preparing a new Batch."""
+
+    def __init__(self, launches):
+        self.launches = list(launches)
+        self.n = len(self.launches)
+        self.descs = (L.lt_launch_desc * self.n)()
+        self._args = []
+        for i, (k, grid, block, sb, args, rep) in enumerate(self.launches):
+            a = k._args(args)
+            self._args.append(a)
+            d = self.descs[i]
+            d.kernel = k.h
+            d.grid = _dim3(grid)
+            d.block = _dim3(block)
+            d.wd = L.lt_workdist((C.c_int64 * 3)(*(tuple(sb) + (0,) * (3 - len(sb)))))
+            d.args = C.cast(a, C.POINTER(L.lt_arg))
+            d.nargs = len(args)
+            d.repeat = rep
+
 class Context:
     def __init__(self, device=0, hbm_budget=0, host_pool=0, staging_cap=0, flags=0):
         cfg = L.lt_config(hbm_budget, host_pool, staging_cap, device, flags)
@@ -255,22 +278,14 @@ class Context:
         """Runtime-compiled user kernel (the paper's CudaKernelDef ... compile())."""
         return Kernel(self, L.LT_K_USER, annotation, params, source=source, name=name)
 
+    def prepare_batch(self, launches) -> "Batch":
+        """Marshal a batch once, for repeated launch_batch calls."""
+        return Batch(launches)
+
     def launch_batch(self, launches, flags=0):
-        """launches: list of (kernel, grid, block, superblock, args, repeat)."""
-        n = len(launches)
-        descs = (L.lt_launch_desc * n)()
-        keep = []
-        for i, (k, grid, block, sb, args, rep) in enumerate(launches):
-            a = k._args(args)
-            keep.append(a)
-            descs[i].kernel = k.h
-            descs[i].grid = _dim3(grid)
-            descs[i].block = _dim3(block)
-            descs[i].wd = L.lt_workdist((C.c_int64 * 3)(*(tuple(sb) + (0,) * (3 - len(sb)))))
-            descs[i].args = C.cast(a, C.POINTER(L.lt_arg))
-            descs[i].nargs = len(args)
-            descs[i].repeat = rep
-        check(L.load().lt_launch_batch(self.h, C.cast(descs, C.c_void_p), n, flags))
+        """launches: a Batch, or a list of (kernel, grid, block, superblock, args, repeat)."""
+        b = launches if isinstance(launches, Batch) else Batch(launches)
+        check(L.load().lt_launch_batch(self.h, C.cast(b.descs, C.c_void_p), b.n, flags))
 
     def synchronize(self):
         check(L.load().lt_synchronize(self.h))

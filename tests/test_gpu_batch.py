@@ -72,6 +72,29 @@ def test_batch_bit_exact_and_replay(flags):
                 assert s["graph_replays"] == 1
 
 
+def test_batch_replay_skips_the_checks_but_a_changed_launch_is_checked():
+    with lt.Context() as ctx:
+        launches, jac, hist = make(ctx, 2)
+        ctx.launch_batch(launches, 0)
+        reused = ctx.stats()["plans_reused"]
+        ctx.launch_batch(launches, 0)  # the same batch: its launches were checked already
+        ctx.synchronize()
+        check(jac, hist, 4)
+        assert ctx.stats()["plans_reused"] == reused
+        # a kernel whose annotation misses the halo the Jacobi body reads, in
+        # superblocks of 8 rows (one superblock would cover the whole array)
+        narrow = ctx.kernel(lt.JACOBI2D, "global [i, j] => read U[i, j], write V[i, j]",
+                            [("U", lt.F32), ("V", lt.F32)])
+        q = SHAPES.index((37, 129))
+        bad = list(launches)
+        bad[q] = (narrow, launches[q][1], launches[q][2], (129, 8), launches[q][4], launches[q][5])
+        with pytest.raises(lt.LightningError, match="does not contain"):
+            ctx.launch_batch(bad, 0)
+        ctx.launch_batch(launches, 0)  # checked again, then run
+        ctx.synchronize()
+        check(jac, hist, 6)
+
+
 def test_batch_with_chunked_arrays_falls_back_to_plain():
     with lt.Context() as ctx:
         kj = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])

@@ -448,6 +448,20 @@ def test_batch_in_dry_run_is_the_plain_sequence():
             assert a["id"] in b["deps"]
 
 
+def test_prepared_batch_is_the_same_sequence_as_the_list():
+    with dry() as ctx:
+        U, V, k = _jacobi_ctx(ctx, 64, 64, lt.Dist.block())
+        X = ctx.array(lt.U8, (1000,))
+        H = ctx.array(lt.U32, (256,))
+        kh = ctx.kernel(lt.HIST256, "global i => read X[i], reduce(+) H[:]", [("X", lt.U8), ("H", lt.U32)])
+        b = ctx.prepare_batch([(k, (64, 64), (64, 4), (0, 0), [U, V], 3), (kh, (1000,), (256,), (0,), [X, H], 1)])
+        assert b.n == 2 and b.descs[0].repeat == 3 and b.descs[1].nargs == 2
+        ctx.launch_batch(b)
+        ctx.launch_batch(b)
+        s = ctx.stats()
+        assert s["launches"] == 8 and s["batches_plain"] == 2
+
+
 def test_multi_step_annotation_must_cover_k_rings():
     with dry() as ctx:
         U = ctx.array(lt.F32, (64, 64), lt.Dist.rows(16, halo=3))
