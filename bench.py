@@ -622,9 +622,13 @@ def run_kmeans(args, rank, world, local, grp):
                     [("S", lt.F64), ("C", lt.F32), ("C2", lt.F32)])
     cen = [C, C2]
 
+    # A superblock is a whole number of blocks: 25M records are 390625 blocks
+    # of 64, so every superblock is exactly one chunk and reads it in place
+    # (blocks of 256 round the superblocks to 25,000,192 records and 39 of
+    # the 40 would pack their records first).
     def step():
         for _ in range(iters):
-            ka.launch(grid=(n,), block=(256,), superblock=(per_chunk,), args=[X, cen[0], S, k])
+            ka.launch(grid=(n,), block=(64,), superblock=(per_chunk,), args=[X, cen[0], S, k])
             ku.launch(grid=(k,), block=(64,), superblock=(0,), args=[S, cen[0], cen[1]])
             cen.reverse()
         ctx.synchronize()

@@ -150,10 +150,11 @@ def test_kmeans_full_size_bit_exact():
         X.fill(L.LT_INIT_UNIFORM, seed=SEED, stream=0)
         C.write(c.reshape(-1))
         ka, ku = kernels(ctx)
-        ka.launch(grid=(n,), block=(256,), superblock=(per,), args=[X, C, S, k])
+        ka.launch(grid=(n,), block=(64,), superblock=(per,), args=[X, C, S, k])
         ku.launch(grid=(k,), block=(64,), superblock=(0,), args=[S, C, C2])
         got_s = S.read().reshape(k, 5)
         got_c = C2.read().reshape(k, 4)
+        assert ctx.stats()["bytes_d2d"] == 0  # every superblock reads its own chunk in place
     step = 15_625_000
     parts = [(lo, min(lo + step, n), c) for lo in range(0, n, step)]
     workers = max(1, min(16, len(os.sched_getaffinity(0))))
