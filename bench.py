@@ -857,7 +857,8 @@ def run_batch(args, rank, world, local, grp):
                    "launches_per_step": nlaunch, "cells": cells,
                    "tuned_tile_rows": st["tuned_tile_rows"], "tuned_hist_slice": st["tuned_hist_slice"]},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None, "kernel": "batch_kernel",
+                     "frac": round(achieved / peaks["hbm_gbs"], 4),
+                     "traffic": kernel_traffic("batch_kernel", nbytes), "kernel": "batch_kernel",
                      "launch_ms": round(ex_ms, 3), "bytes_per_launch": nbytes},
         "plain": {"ms_per_step": round(ms_p, 2), "value": round(nbytes / (ms_p / 1e3) / 1e9, 2),
                   "launches": st_p["launches"], "speedup_batched_vs_plain": round(ms_p / ms_f, 2)},
