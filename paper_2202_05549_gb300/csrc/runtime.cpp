@@ -25,6 +25,7 @@
 #include <memory>
 #include <sstream>
 #include <string>
+#include <unordered_map>
 #include <unordered_set>
 #include <vector>
 
@@ -256,13 +257,21 @@ struct PlanBundle {
 };
 
 struct CachedPlan {
-    std::vector<int64_t> key;
     std::shared_ptr<const PlanBundle> b;
     uint64_t last_use = 0;
 };
 
+struct PlanKeyHash {
+    size_t operator()(const std::vector<int64_t> &v) const {
+        uint64_t h = 0x9E3779B97F4A7C15ull;
+        for (int64_t x : v) h = (h ^ (uint64_t)x) * 0x100000001B3ull + (h >> 29);
+        return (size_t)h;
+    }
+};
+
 struct lt_kernel {
-    std::vector<CachedPlan> plans;  // most recently used shapes (at most PLAN_CACHE)
+    // plans of the most recently used launch shapes (at most PLAN_CACHE), by key
+    std::unordered_map<std::vector<int64_t>, CachedPlan, PlanKeyHash> plans;
     uint64_t plan_tick = 0;
     const BuiltinDef *def = nullptr;
     std::unique_ptr<BuiltinDef> own_def;     // user kernels: their own signature
@@ -1695,7 +1704,7 @@ lt_status lt_kernel_destroy(lt_ctx *c, lt_kernel *kk) {
     return fail(LT_ERR_INVALID_ARG, "unknown kernel");
 }
 
-constexpr size_t PLAN_CACHE = 8;
+constexpr size_t PLAN_CACHE = 4096;
 
 static lt_status prepare_plan(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 block, const lt_workdist *wd,
                               const lt_arg *args, int32_t nargs, std::shared_ptr<const PlanBundle> *out,
@@ -1763,13 +1772,13 @@ static lt_status prepare_plan(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 blo
                                (int64_t)g.dist.kind, (int64_t)g.dist.order, g.dist.chunk[0], g.dist.chunk[1],
                                g.dist.chunk[2], g.dist.halo[0], g.dist.halo[1], g.dist.halo[2]});
     }
-    for (auto &e : k->plans)
-        if (e.key == key) {
-            e.last_use = ++k->plan_tick;
-            *out = e.b;
-            c->stats.plans_reused++;
-            return LT_OK;
-        }
+    auto hit = k->plans.find(key);
+    if (hit != k->plans.end()) {
+        hit->second.last_use = ++k->plan_tick;
+        *out = hit->second.b;
+        c->stats.plans_reused++;
+        return LT_OK;
+    }
     auto bundle = std::make_shared<PlanBundle>();
     LaunchPlan *plan = &bundle->plan;
     std::string err;
@@ -1801,17 +1810,16 @@ static lt_status prepare_plan(lt_ctx *c, lt_kernel *k, lt_dim3 grid, lt_dim3 blo
         }
     }
     bundle->dead = dead_by_param(*plan, *parr);
-    if (k->plans.size() >= PLAN_CACHE) {
-        size_t lru = 0;
-        for (size_t i = 1; i < k->plans.size(); ++i)
-            if (k->plans[i].last_use < k->plans[lru].last_use) lru = i;
-        k->plans.erase(k->plans.begin() + (std::ptrdiff_t)lru);
+    if (k->plans.size() >= PLAN_CACHE) {  // full: drop the least recently used shape
+        auto lru = k->plans.begin();
+        for (auto it = k->plans.begin(); it != k->plans.end(); ++it)
+            if (it->second.last_use < lru->second.last_use) lru = it;
+        k->plans.erase(lru);
     }
     CachedPlan ce;
-    ce.key = std::move(key);
     ce.b = bundle;
     ce.last_use = ++k->plan_tick;
-    k->plans.push_back(std::move(ce));
+    k->plans.emplace(std::move(key), std::move(ce));
     *out = std::move(bundle);
     return LT_OK;
 }

@@ -498,6 +498,23 @@ def test_plan_cache_reuses_plans_of_the_same_shape_only():
         ctx.synchronize()
 
 
+def test_plan_cache_keeps_4096_shapes_and_drops_the_least_recent():
+    with dry() as ctx:
+        A = ctx.array(lt.F32, (8192,), lt.Dist.block())
+        B = ctx.array(lt.F32, (8192,), lt.Dist.block())
+        k = ctx.kernel(lt.STENCIL1D, "global i => read input[i-1:i+1], write output[i]",
+                       [("n", lt.U32, False), ("output", lt.F32), ("input", lt.F32)])
+        for g in range(1, 4098):  # 4097 grids: the first one no longer fits
+            k.launch(grid=(g,), block=(1,), superblock=(0,), args=[8192, B, A])
+        ctx.reset_stats()
+        k.launch(grid=(4097,), block=(1,), superblock=(0,), args=[8192, B, A])
+        k.launch(grid=(2,), block=(1,), superblock=(0,), args=[8192, B, A])
+        assert ctx.stats()["plans_reused"] == 2
+        k.launch(grid=(1,), block=(1,), superblock=(0,), args=[8192, B, A])  # dropped: planned again
+        assert ctx.stats()["plans_reused"] == 2
+        ctx.synchronize()
+
+
 def test_plan_cache_tells_aliased_arguments_apart():
     # passing one array twice is a different plan input (the dead-data analysis
     # differs), so it must not reuse the plan of two distinct arrays
