@@ -35,7 +35,14 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lightning", choices=["lightning", "reference"])
-    p.add_argument("--workload", default="ooc", choices=["ooc", "incore", "gemm", "batch", "adjoint", "jacobi3d", "kmeans"])
+    p.add_argument("--workload", default="all",
+                   choices=["all", "ooc", "spill", "incore", "gemm", "batch", "adjoint", "jacobi3d", "kmeans"],
+                   help="all (default): the out-of-core headline, its streaming regime and the other workloads "
+                        "in one JSON line")
+    p.add_argument("--spill-gib", type=float, default=64.0,
+                   help="HBM budget of the streaming regime of the out-of-core grid (GiB, below one array)")
+    p.add_argument("--spill-steps", type=int, default=2, help="timed runs of the streaming regime")
+    p.add_argument("--spill-warmup", type=int, default=1, help="warm-up runs of the streaming regime")
     p.add_argument("--records", type=int, default=1_000_000_000, help="records of the kmeans workload")
     p.add_argument("--clusters", type=int, default=40, help="centres of the kmeans workload")
     p.add_argument("--n3", type=int, default=1024, help="side of the cubic grid of the jacobi3d workload")
@@ -44,6 +51,8 @@ def parse():
     p.add_argument("--batch-scale", type=int, default=1, help="divide the batch instance counts by this")
     p.add_argument("--gemm-n", type=int, default=65536, help="M = N = K of the GEMM workload")
     p.add_argument("--gemm-tile", type=int, default=8192, help="output tile chunk of the GEMM workload")
+    p.add_argument("--incore-chunks", default="4x4", choices=["4x4", "1"],
+                   help="in-core Jacobi: 4x4 tiles of 1024^2 with halo, or the whole grid as one chunk")
     p.add_argument("--rows", type=int, default=262144, help="grid rows (ooc)")
     p.add_argument("--cols", type=int, default=131072, help="grid columns (ooc)")
     p.add_argument("--band", type=int, default=8192)
@@ -60,6 +69,10 @@ def parse():
     p.add_argument("--user-kernel", action="store_true",
                    help="stencil workloads: run a Jacobi body compiled at run time (NVRTC) instead of the built-in")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--wl-steps", type=int, default=5, help="timed steps of each workload of the default run")
+    p.add_argument("--wl-warmup", type=int, default=3, help="warm-up steps of each workload of the default run")
+    p.add_argument("--wl-cpu-s", type=float, default=4.0, help="seconds of oracle work per workload CPU baseline")
+    p.add_argument("--only", default="", help="default run: comma-separated subset of its workloads")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
 
@@ -120,6 +133,16 @@ def mem_available():
     return 0
 
 
+def free_pinned():
+    """Return torch's cached pinned host blocks to the system (the e2e passes
+    pin up to 128 GiB; the next workload's pinned pool needs that memory)."""
+    import gc
+    import torch
+    gc.collect()
+    if hasattr(torch._C, "_host_emptyCache"):
+        torch._C._host_emptyCache()
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -173,10 +196,12 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def link_peaks(local):
-    """Pinned host<->device copy bandwidth (GB/s): H2D, D2H, both at once."""
+def link_peaks(local, trials=5, nbytes=2 * GIB):
+    """Pinned host<->device copy bandwidth (GB/s): H2D, D2H, both at once.
+    Each figure is the best of `trials` timings of 4 copies; the median, the
+    worst and every trial are kept as the spread."""
     import torch
-    n = 2 * GIB
+    n = nbytes
     dev = torch.device("cuda", local)
     h1 = torch.empty(n, dtype=torch.uint8, pin_memory=True)
     h2 = torch.empty(n, dtype=torch.uint8, pin_memory=True)
@@ -205,11 +230,17 @@ def link_peaks(local):
         h2d()
         d2h()
 
-    # best of three trials each: a single trial of the concurrent copies varied by 1.5x between runs
-    out = {"h2d": max(n / run(h2d) / 1e9 for _ in range(3)), "d2h": max(n / run(d2h) / 1e9 for _ in range(3)),
-           "bidir": max(2 * n / run(both) / 1e9 for _ in range(3))}
+    out, spread = {}, {}
+    for name, fn, mult in (("h2d", h2d, 1), ("d2h", d2h, 1), ("bidir", both, 2)):
+        v = sorted(mult * n / run(fn) / 1e9 for _ in range(trials))
+        out[name] = v[-1]
+        spread[name] = {"max": round(v[-1], 1), "median": round(statistics.median(v), 1), "min": round(v[0], 1),
+                        "trials": [round(x, 1) for x in v]}
     del h1, h2, d1, d2
     torch.cuda.empty_cache()
+    out["spread"] = spread
+    out["how"] = (f"torch copy_ of {n >> 30} GiB pinned buffers on side streams, 4 copies per trial, "
+                  f"{trials} trials; peak = best trial")
     return out
 
 
@@ -274,16 +305,31 @@ def jacobi_config(args, world):
         l2 = "inputs larger than L2 (129 MB)"
     else:
         ny = nx = 4096
-        wl = (f"in-core 2D 5-point Jacobi f32 4096x4096, 4x4 tiles of 1024^2 + {tb}-cell halo, "
+        layout = ("1 chunk (superblocks of 1024^2)" if args.incore_chunks == "1" else
+                  f"4x4 tiles of 1024^2 + {tb}-cell halo")
+        wl = (f"in-core 2D 5-point Jacobi f32 4096x4096, {layout}, "
               f"{iters} iterations per step, {tb} per launch")
         l2 = ("inputs larger than L2: two arrays of 16 chunks, 140.7 MB with halos and row padding, "
-              "against 129 MB of L2; not flushed (part of each launch's input is still in L2)")
+              "against 129 MB of L2; not flushed (part of each launch's input is still in L2)"
+              if args.incore_chunks != "1" else
+              "inputs larger than L2: two arrays of 67.1 MB, 134.2 MB against 129 MB of L2; not flushed "
+              "(part of each launch's input is still in L2)")
     return {"workload": wl, "grid": [ny, nx], "iterations_per_step": iters, "launches_per_step": iters // tb,
             "iterations_per_launch": tb, "parallelism": f"replicas x{world}", "l2": l2}
 
-def plan_ooc(args, world):
-    """HBM budget and host pool for the out-of-core grid on this machine."""
+def plan_ooc(args, world, hbm_gib=None):
+    """HBM budget and host pool for the out-of-core grid on this machine.
+
+    In-HBM regime (no cap): the pinned pool takes half of this rank's share
+    of MemAvailable and the HBM budget the rest of the data plus three
+    chunks, so the two 128 GiB buffers do not both fit in HBM.  Streaming
+    regime (hbm_gib, below one array): the budget is hbm_gib and the pool
+    holds the live set beyond it.  The live set is one array plus the bands
+    in flight: a band of the input is dead once its last reader has run (the
+    next launch overwrites it unread), so the pool holds the bands of one
+    array that are not in HBM plus four in flight."""
     ny, nx, band = args.rows, args.cols, args.band
+    hbm_gib = args.hbm_gib if hbm_gib is None else hbm_gib
     nb = (ny + band - 1) // band
     chunk = (band + 2 * max(1, args.tb)) * nx * 4
     # allocation size class: 1/128 of the power of two
@@ -294,17 +340,112 @@ def plan_ooc(args, world):
     host = min(int(0.5 * avail), total)
     host_slots = host // chunk_c
     dev_slots = max(2 * nb - host_slots + 3, 6)  # a band task pins 4 chunks
-    if args.hbm_gib > 0:
-        dev_slots = max(int(args.hbm_gib * 2**30) // chunk_c, 6)
-        host_slots = max(2 * nb - dev_slots + 3, 0)
-        if host_slots * chunk_c > 0.6 * avail:
-            raise SystemExit(f"--hbm-gib {args.hbm_gib}: the rest of the data does not fit in pinned host memory")
+    if hbm_gib > 0:
+        dev_slots = max(int(hbm_gib * 2**30) // chunk_c, 6)
+        host_slots = max(nb + 4 - dev_slots, 0)
+        if host_slots * chunk_c > 0.8 * avail:
+            raise SystemExit(f"HBM budget {hbm_gib} GiB: the rest of the live data does not fit in pinned host memory")
     budget = dev_slots * chunk_c + (64 << 20)
     return dict(ny=ny, nx=nx, band=band, nbands=nb, chunk_bytes=chunk, budget=budget,
-                host=host_slots * chunk_c + (1 << 20), data_bytes=2 * ny * nx * 4)
+                host=host_slots * chunk_c + (1 << 20), data_bytes=2 * ny * nx * 4, dev_slots=dev_slots,
+                host_slots=host_slots)
 
 
-def run_lightning(args, rank, world, local, grp):
+def run_spill(args, rank, world, local, grp, links=None):
+    """The out-of-core Jacobi on the full grid with an HBM budget below one
+    array: every launch streams bands through the pinned host pool.  One step
+    is one run (20 iterations, then synchronize).  Reports the launch rate,
+    the host-link bytes against the measured link peaks and the overlap of
+    the kernels with the copies, from per-operation CUDA events."""
+    from paper_2202_05549_gb300 import _lib as L
+    from paper_2202_05549_gb300 import lightning as lt
+    import synth_inputs as si
+
+    peaks = measured_peaks()
+    links = links or link_peaks(local)
+    budget_gib = args.spill_gib
+    pl = plan_ooc(args, world, hbm_gib=budget_gib)
+    ny, nx, band = pl["ny"], pl["nx"], pl["band"]
+    iters = args.iters or 20
+    steps, warm = args.spill_steps, args.spill_warmup
+    t_setup = time.perf_counter()
+    ctx = lt.Context(device=local, hbm_budget=pl["budget"], host_pool=pl["host"], flags=L.LT_FLAG_TIMING)
+    dist = lt.Dist.rows(band, halo=1)
+    U = ctx.array(lt.F32, (ny, nx), dist)
+    V = ctx.array(lt.F32, (ny, nx), dist)
+    U.fill(L.LT_INIT_UNIFORM, seed=si.SEED_JACOBI_OOC, stream=0)
+    k = ctx.kernel(lt.JACOBI2D, "global [i, j] => read U[i-1:i+1, j-1:j+1], write V[i, j]",
+                   [("U", lt.F32), ("V", lt.F32)])
+    bufs = [U, V]
+
+    def step():
+        for _ in range(iters):
+            k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=[bufs[0], bufs[1]])
+            bufs.reverse()
+        bufs[1].discard()
+        ctx.synchronize()
+
+    for _ in range(warm):
+        step()
+    ctx.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    # the per-operation events stay on: they give the kernel/copy overlap and
+    # cost a few microseconds per operation against copies of 20 ms
+    ctx.reset_stats()
+    grp.barrier()
+    clk = Clocks(local)
+    ctx.timer_start()
+    for _ in range(steps):
+        step()
+    ms = ctx.timer_stop()
+    clocks = clk.stop()
+    ctx.synchronize()
+    st = ctx.stats()
+    ctx.close()
+    t_s = ms / 1e3
+    t_max = grp.max(t_s)
+    cells = ny * nx * iters
+    value = grp.sum(8.0 * cells * steps / 1e9) / t_max
+    h2d, d2h = st["bytes_h2d"], st["bytes_d2h"]
+    floor = max(h2d / (links["h2d"] * 1e9), d2h / (links["d2h"] * 1e9), (h2d + d2h) / (links["bidir"] * 1e9))
+    n_ex = max(1, st["n_execute_kernels"])
+    ex_ms = st["ms_execute"] / n_ex
+    per_launch = 8.0 * cells * steps / n_ex
+    return {
+        "value": round(value, 2), "unit": "GB/s", "ms_per_step": round(t_max * 1e3 / steps, 1), "steps": steps,
+        "warmup": warm,
+        "config": {"workload": f"out-of-core 2D 5-point Jacobi f32 {ny}x{nx}, {band}-row bands + 1-row halo, "
+                               f"{iters} iterations per step, HBM budget {budget_gib:g} GiB (below one "
+                               f"{ny * nx * 4 / GIB:g} GiB array): bands stream through the pinned host pool",
+                   "hbm_budget_bytes": pl["budget"], "host_pool_bytes": pl["host"], "data_bytes": pl["data_bytes"],
+                   "stale_buffer": "discarded before the closing synchronize"},
+        "host_link": {"bytes_h2d_per_step": h2d / steps, "bytes_d2h_per_step": d2h / steps,
+                      "achieved_GBs": round((h2d + d2h) / t_s / 1e9, 1),
+                      "floor_ms_per_step": round(floor * 1e3 / steps, 1),
+                      "frac_of_link_roofline": round(floor / t_s, 4) if h2d + d2h else None,
+                      "measured_peak_GBs": {k2: round(links[k2], 1) for k2 in ("h2d", "d2h", "bidir")},
+                      "peak_spread": links.get("spread"), "peak_how": links.get("how"),
+                      "busy_frac": round(st["ms_link_busy"] / max(ms, 1e-9), 4),
+                      "both_directions_frac": round(st["ms_link_both"] / max(st["ms_link_busy"], 1e-9), 4),
+                      "instrumented_ms_per_step": {"execute": round(st["ms_execute"] / steps, 1),
+                                                   "h2d": round(st["ms_h2d"] / steps, 1),
+                                                   "d2h": round(st["ms_d2h"] / steps, 1),
+                                                   "link_busy": round(st["ms_link_busy"] / steps, 1),
+                                                   "both_directions": round(st["ms_link_both"] / steps, 1)}},
+        "overlap": {"kernel_ms_per_step": round(st["ms_execute"] / steps, 2),
+                    "kernel_hidden_ms_per_step": round(st["ms_exec_hidden"] / steps, 2),
+                    "frac_kernel_time_hidden": round(st["ms_exec_hidden"] / max(st["ms_execute"], 1e-9), 4),
+                    "how": "per-operation CUDA events: Execute-kernel time during which a fetch or an eviction "
+                           "was running, over all Execute-kernel time"},
+        "roofline": {"bound": "host link", "kernel": "jacobi2d_vec_kernel", "launch_ms": round(ex_ms, 4),
+                     "kernel_frac_of_hbm": round(per_launch / (ex_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4)},
+        "stats": {k2: st[k2] for k2 in ("fetches", "evictions", "dead_skips", "tasks_execute", "hbm_peak",
+                                        "kernels")},
+        "clocks": clocks, "setup_s": round(setup_s, 1),
+    }
+
+
+def run_lightning(args, rank, world, local, grp, links=None):
     import numpy as np  # noqa: F401
 
     from paper_2202_05549_gb300 import _lib as L
@@ -312,7 +453,7 @@ def run_lightning(args, rank, world, local, grp):
     import synth_inputs as si
 
     peaks = measured_peaks()
-    links = link_peaks(local)
+    links = links or link_peaks(local)
     tb = max(1, args.tb)
     ann = "global [i, j] => read U[i-1:i+1, j-1:j+1], write V[i, j]"
     if tb > 1:
@@ -333,9 +474,11 @@ def run_lightning(args, rank, world, local, grp):
         sb = (1024, 1024)
         band = 1024
         seed = si.SEED_JACOBI_INCORE
-        workload = (f"in-core 2D 5-point Jacobi f32 4096x4096, 4x4 tiles of 1024^2 + {tb}-cell halo, "
-                    f"{args.iters or 10} iterations per step, {tb} per launch")
-        dist = lt.Dist.tiles((1024, 1024), halo=(tb, tb))
+        workload = jacobi_config(args, world)["workload"]
+        if args.incore_chunks == "1":
+            dist = lt.Dist.block()
+        else:
+            dist = lt.Dist.tiles((1024, 1024), halo=(tb, tb))
     U = ctx.array(lt.F32, (ny, nx), dist)
     V = ctx.array(lt.F32, (ny, nx), dist)
     U.fill(L.LT_INIT_UNIFORM, seed=seed, stream=0)
@@ -385,7 +528,8 @@ def run_lightning(args, rank, world, local, grp):
     else:
         kname = {1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
     # DRAM traffic records: the in-core grid keeps part of its working set in L2
-    tkey = kname + ("@incore4096" if args.workload != "ooc" and tb == 1 else "")
+    tkey = kname + ("@incore4096" + ("_1chunk" if args.incore_chunks == "1" else "")
+                    if args.workload != "ooc" and tb == 1 else "")
     # the timed steps run without per-operation CUDA events (a few
     # microseconds of GPU time each, 12 % of an in-core launch); the kernel
     # durations for the roofline come from a second, instrumented pass
@@ -439,7 +583,7 @@ def run_lightning(args, rank, world, local, grp):
         "host_link": {"bytes_h2d_per_step": st_run["bytes_h2d"] / args.steps,
                       "bytes_d2h_per_step": st_run["bytes_d2h"] / args.steps,
                       "achieved_GBs": round(link_bytes / t_s / 1e9, 1),
-                      "measured_peak_GBs": {k2: round(v, 1) for k2, v in links.items()},
+                      "measured_peak_GBs": {k2: round(links[k2], 1) for k2 in ("h2d", "d2h", "bidir")},
                       "frac_of_link_roofline": round(t_link_floor / t_s, 4) if link_bytes else None,
                       "instrumented_ms_per_step": {"execute": round(st["ms_execute"] / n_inst, 2),
                                                    "h2d": round(st["ms_h2d"] / n_inst, 2),
@@ -480,8 +624,11 @@ def run_lightning(args, rank, world, local, grp):
                            [("U", lt.F32), ("V", lt.F32)] + extra_params)
             bufs[0].fill(L.LT_INIT_UNIFORM, seed=seed, stream=0)
         h_in = torch.empty((ny, nx), dtype=torch.float32, pin_memory=True).numpy()
-        h_out = torch.empty((ny, nx) if incore else (1, nx), dtype=torch.float32, pin_memory=True).numpy()
-        bufs[0].read(out=h_in)  # the input of every step
+        # in-core: a separate result buffer; out-of-core: a second 128 GiB
+        # pinned buffer does not fit, so the whole result is read back into
+        # the input buffer and the next step continues the iteration from it
+        h_out = torch.empty((ny, nx), dtype=torch.float32, pin_memory=True).numpy() if incore else h_in
+        bufs[0].read(out=h_in)  # the input of the first step
         if not incore:
             step()  # warm the new context: plans, descriptor tables, pools
         ctx.synchronize()
@@ -491,10 +638,7 @@ def run_lightning(args, rank, world, local, grp):
         for _ in range(nstep):
             bufs[0].write(h_in)
             step()
-            if incore:
-                bufs[0].read(out=h_out)
-            else:
-                h_out[:] = bufs[0].read_box((ny // 2, 0), (ny // 2, nx - 1))
+            bufs[0].read(out=h_out)
         ctx.synchronize()
         t1 = time.perf_counter()
         st2 = ctx.stats()
@@ -505,9 +649,11 @@ def run_lightning(args, rank, world, local, grp):
                       # everything the runtime moved over the link (the upload with its halo rows, any spill)
                       "runtime_link_bytes_per_step": int((st2["bytes_d2h"] + st2["bytes_h2d"]) / nstep),
                       "how": "public Python API, wall clock; per step: upload of the input grid from pinned host "
-                             "memory (lt_array_write), the step's launches and synchronize, read of the result into "
-                             "pinned host memory (" + ("the whole grid)" if incore else
-                                                       "one row: a second 128 GiB pinned buffer does not fit)")}
+                             "memory (lt_array_write), the step's launches and synchronize, read of the whole result "
+                             "into pinned host memory (lt_array_read" + (")" if incore else
+                                                                         "; into the input buffer, which the next "
+                                                                         "step uploads: a second 128 GiB pinned buffer "
+                                                                         "does not fit)")}
         if not incore:
             res["e2e"]["host_pool_bytes"] = small_pool
     ctx.close()
@@ -913,33 +1059,59 @@ def run_batch(args, rank, world, local, grp):
     return res
 
 
+def torch_diffusion(u0, kappa, steps):
+    """The diffusion forward map written with plain torch ops (several eager
+    kernels per step; autograd keeps every intermediate): a secondary
+    baseline, outside the engine, for the adjoint workload."""
+    import torch.nn.functional as F
+    u = u0
+    for _ in range(steps):
+        p = F.pad(u[None, None], (1, 1, 1, 1))[0, 0]
+        lap = p[:-2, 1:-1] + p[2:, 1:-1] + p[1:-1, :-2] + p[1:-1, 2:] - 4.0 * u
+        u = u + kappa * lap
+    return u
+
+
 def run_adjoint(args, rank, world, local, grp):
     """Gradient of J = sum u_T^2 for 50 diffusion steps on a 16384^2 grid:
-    chunked adjoint (checkpoints every 10 steps, recomputation) against the
-    plain form (torch ops, every state kept by autograd)."""
+    the chunked adjoint with checkpoints every 10 steps (recomputation)
+    against the engine's plain form -- the same forward and adjoint launches,
+    one per step, every state kept, nothing recomputed -- and, as a
+    secondary figure, torch eager autograd."""
     import torch
 
-    from paper_2202_05549_gb300.autograd import DiffusionChunked, PlainDiffusion
+    from paper_2202_05549_gb300 import _lib as L
+    from paper_2202_05549_gb300 import lightning as lt
+    from paper_2202_05549_gb300.autograd import DiffusionChunked
+    from paper_2202_05549_gb300 import autograd as ag
+    import synth_inputs as si
 
     peaks = measured_peaks()
     n, T, ck, chunk = args.adj_n, 50, 10, min(4096, args.adj_n)
     dev = torch.device("cuda", local)
-    g = torch.Generator(device=dev)
-    g.manual_seed(2207)
-    u0 = torch.rand((n, n), device=dev, generator=g)
-    kap = 0.05 + 0.15 * torch.rand((n, n), device=dev, generator=g)
+    torch.cuda.set_device(dev)
+    # seeded inputs (SplitMix64 recipe), generated by the engine's fill kernel
+    u0 = torch.empty((n, n), dtype=torch.float32, device=dev)
+    kap = torch.empty((n, n), dtype=torch.float32, device=dev)
+    with lt.Context(device=local, hbm_budget=4 * n * n * 4 + (64 << 20)) as gctx:
+        a = gctx.array(lt.F32, (n, n))
+        a.fill(L.LT_INIT_UNIFORM, seed=si.SEED_DIFFUSION, stream=si.STREAM_U)
+        a.read_device(u0.data_ptr(), n * n * 4)
+        a.fill(L.LT_INIT_KAPPA, seed=si.SEED_DIFFUSION, stream=si.STREAM_KAPPA)
+        a.read_device(kap.data_ptr(), n * n * 4)
+        gctx.synchronize()
 
-    def ours():
+    def grad(every):
         u = u0.detach().requires_grad_(True)
         k = kap.detach().requires_grad_(True)
-        uT = DiffusionChunked.apply(u, k, T, ck, chunk, (chunk, chunk))
+        uT = DiffusionChunked.apply(u, k, T, every, chunk, (chunk, chunk))
         (uT * uT).sum().backward()
         return u.grad, k.grad
 
-    def plain():
+    def eager():
         u = u0.detach().requires_grad_(True)
         k = kap.detach().requires_grad_(True)
-        uT = PlainDiffusion(u, k, T)
+        uT = torch_diffusion(u, k, T)
         (uT * uT).sum().backward()
         return u.grad, k.grad
 
@@ -955,35 +1127,53 @@ def run_adjoint(args, rank, world, local, grp):
 
     grp.barrier()
     clk = Clocks(local)
-    t_ours, (gu, gk) = timed(ours, args.steps, args.warmup)
+    t_ours, (gu, gk) = timed(lambda: grad(ck), args.steps, args.warmup)
     clocks = clk.stop()
-    t_plain, (pu, pk) = timed(plain, max(1, args.steps // 2), 1)
+    t_plain, (pu, pk) = timed(lambda: grad(1), args.steps, args.warmup)
+    for c in ag._ctx_cache.values():
+        c.close()
+    ag._ctx_cache.clear()
+    torch.cuda.empty_cache()
+    t_eager, (eu, ek) = timed(eager, max(1, args.steps // 2), 1)
     cells = float(n * n)
     nbytes = cells * (12.0 * T + 12.0 * (T - T // ck) + 24.0 * T)
+    nbytes_plain = cells * (12.0 * T + 24.0 * T)
     t_max = grp.max(t_ours)
     value = grp.sum(nbytes / 1e9) / t_max
-    agree_u = float((gu - pu).norm() / pu.norm())
-    agree_k = float((gk - pk).norm() / pk.norm())
+
+    def rel(a, b):
+        return float((a - b).norm() / b.norm())
+
     res = {
         "metric": "differentiable chunked stencil: adjoint GB/s (fwd 12 B + recompute 12 B + adjoint 24 B per cell-step)",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_max * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (torch generator, uniform u0, kappa in [0.05, 0.2))",
+        "dtype": "f32", "data": "synthetic (seeded SplitMix64: u0 uniform[0,1), kappa = 0.05 + 0.15 u)",
         "config": {"workload": f"diffusion {n}x{n}, {T} steps, checkpoints every {ck}, {chunk}^2 chunks + 1-cell halo; "
-                               "one step = forward + gradient of sum(u_T^2) via the autograd wrapper"},
-        "plain": {"ms_per_step": round(t_plain * 1e3, 2), "how": "torch ops, autograd keeps every state",
-                  "speedup_adjoint_vs_plain": round(t_plain / t_ours, 2),
-                  "rel_l2_difference_du0": agree_u, "rel_l2_difference_dkappa": agree_k},
+                               "one step = forward + gradient of sum(u_T^2) via the autograd wrapper",
+                   "fields_in_hbm": T // ck + 1 + (ck - 1) + 4, "fields_in_hbm_plain": T + 1 + 1 + 4},
+        "plain": {"ms_per_step": round(t_plain * 1e3, 2),
+                  "how": "the engine's plain form: one forward launch per step keeping all 50 states, then one "
+                         "adjoint launch per step on the stored states (no checkpoints, no recomputation), same "
+                         "kernels and chunking",
+                  "speedup_adjoint_vs_plain": round(t_plain / t_ours, 3),
+                  "GBs": round(nbytes_plain / t_plain / 1e9, 1),
+                  "max_abs_difference_du0": float((gu - pu).abs().max()),
+                  "max_abs_difference_dkappa": float((gk - pk).abs().max())},
+        "torch_eager": {"ms_per_step": round(t_eager * 1e3, 2),
+                        "how": "torch ops, autograd keeps every state (outside the engine)",
+                        "speedup_adjoint_vs_torch_eager": round(t_eager / t_ours, 2),
+                        "rel_l2_difference_du0": rel(gu, eu), "rel_l2_difference_dkappa": rel(gk, ek)},
         "roofline": {"bound": "hbm", "achieved": round(nbytes / t_ours / 1e9, 1), "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": round(nbytes / t_ours / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
                      "kernel": "diffusion_fwd_kernel + diffusion_adj_kernel (whole step, wall clock)"},
         "clocks": clocks,
     }
     # kernels the library launches per step (its contexts count them)
-    from paper_2202_05549_gb300 import autograd as ag
+    grad(ck)
     for c in ag._ctx_cache.values():
         c.reset_stats()
-    ours()
+    grad(ck)
     torch.cuda.synchronize(dev)
     res["gpu_launches"] = args.steps * sum(c.stats()["kernels"] for c in ag._ctx_cache.values())
     if not args.no_e2e:
@@ -1013,16 +1203,101 @@ def run_adjoint(args, rank, world, local, grp):
                       "h2d_bytes_per_step": int(2 * h_u.numel() * 4), "d2h_bytes_per_step": int(2 * h_u.numel() * 4),
                       "how": "wall clock; per step: u0 and kappa copied from pinned host memory, forward + gradient "
                              "through the autograd wrapper, both gradients copied into pinned host memory"}
+    for c in ag._ctx_cache.values():
+        c.close()
+    ag._ctx_cache.clear()
     return res
+
+
+WORKLOADS = (("incore_1chunk", "incore", {"incore_chunks": "1"}),
+             ("incore_4x4", "incore", {"incore_chunks": "4x4"}),
+             ("gemm", "gemm", {}), ("batch", "batch", {}), ("adjoint", "adjoint", {}))
+
+
+def run_workloads(args, rank, world, local, grp):
+    """The other configurations of the benchmark, each at its full size with
+    its own timed steps, clocks, roofline, end-to-end pass and CPU baseline:
+    the in-core 4096^2 Jacobi as one chunk and as 4x4 tiles, the 65536^3
+    GEMM, the batched uneven launches (fused against plain) and the
+    differentiable diffusion (checkpointed adjoint against the plain
+    store-every-state form)."""
+    import argparse as _ap
+    out = {}
+    for name, wl, extra in WORKLOADS:
+        if args.only and name not in args.only.split(","):
+            continue
+        a = _ap.Namespace(**vars(args))
+        a.workload, a.steps, a.warmup = wl, args.wl_steps, args.wl_warmup
+        a.iters, a.tb, a.hbm_gib = 0, 1, 0.0
+        for k2, v in extra.items():
+            setattr(a, k2, v)
+        t0 = time.perf_counter()
+        runner = {"incore": run_lightning, "gemm": run_gemm, "batch": run_batch, "adjoint": run_adjoint}[wl]
+        r = runner(a, rank, world, local, grp)
+        free_pinned()
+        for k2 in ("n_gpus", "scaling", "vs_baseline", "higher_is_better", "data"):
+            r.pop(k2, None)
+        if rank == 0 and not args.no_cpu:
+            r["cpu_baseline"] = cpu_baseline(a, budget_s=args.wl_cpu_s)
+        r["wall_s"] = round(time.perf_counter() - t0, 1)
+        out[name] = r
+    return out
 
 
 def cpu_baseline(args, threads=None, budget_s=15.0):
     """The oracle as it stands, on a bounded sample of the same workload."""
+    import numpy as np
     import oracle
     import synth_inputs as si
     if threads:
         oracle.set_threads(threads)
     cores = oracle.max_threads()
+
+    def repeat(fn):
+        t0 = time.perf_counter()
+        done = 0
+        while True:
+            done += fn()
+            if time.perf_counter() - t0 > budget_s:
+                break
+        return done, time.perf_counter() - t0
+
+    if args.workload == "gemm":
+        m = 512
+        a = si.bf16_bits_to_f32(si.gen_normal_bf16_bits(si.SEED_GEMM, si.STREAM_A, np.arange(m * m), 1 / 256.0))
+        b = si.bf16_bits_to_f32(si.gen_normal_bf16_bits(si.SEED_GEMM, si.STREAM_B, np.arange(m * m), 1 / 256.0))
+        a, b = a.reshape(m, m).astype(np.float64), b.reshape(m, m).astype(np.float64)
+        flop, dt = repeat(lambda: (oracle.gemm_f64(a, b), 2.0 * m ** 3)[1])
+        return {"value": round(flop / dt / 1e12, 6), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                "sample": f"{m}^3 fp64 GEMM of the bf16 inputs (the oracle's plain triple loop), "
+                          f"repeated for ~{budget_s:.0f}s"}
+    if args.workload == "batch":
+        r = si.BatchRecipe()
+        sides, lens = r.sides(), r.hist_lengths()
+        state = {"q": 0}
+
+        def one():
+            q = state["q"]
+            state["q"] += 1
+            s_ = int(sides[q % len(sides)])
+            u = si.uniform_field(si.SEED_BATCH, si.STREAM_BATCH_JACOBI0 + q % len(sides), s_, s_)
+            oracle.jacobi2d(u, r.iters)
+            x = si.u8_array(si.SEED_BATCH, si.STREAM_BATCH_HIST0 + q % len(lens), int(lens[q % len(lens)]))
+            oracle.hist256(x)
+            return 8.0 * s_ * s_ * r.iters + x.size + 1024.0
+        nbytes, dt = repeat(one)
+        return {"value": round(nbytes / dt / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                "sample": f"the batch's first {state['q']} Jacobi instances ({r.iters} iterations each) and as many "
+                          f"of its histograms, one after the other, for ~{budget_s:.0f}s (input generation included)"}
+    if args.workload == "adjoint":
+        m, T, ck = 256, 50, 10
+        u0 = si.uniform_field(si.SEED_DIFFUSION, si.STREAM_U, m, m)
+        kap = si.kappa_field(si.SEED_DIFFUSION, si.STREAM_KAPPA, m, m)
+        per = m * m * (12.0 * T + 12.0 * (T - T // ck) + 24.0 * T)
+        nbytes, dt = repeat(lambda: (oracle.diffusion_grad(u0, kap, T), per)[1])
+        return {"value": round(nbytes / dt / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                "sample": f"{m}x{m} grid, {T} steps, fp64 forward + adjoint (every state kept), counted in the "
+                          f"GPU metric's bytes, repeated for ~{budget_s:.0f}s"}
     if args.workload == "kmeans":
         nrec, kc = 1_000_000, args.clusters
         x = oracle.gen_uniform_f32(2209, 0, 0, 4 * nrec).reshape(nrec, 4)
@@ -1074,6 +1349,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
+        if args.workload == "all":
+            args.workload = "ooc"  # the headline's workload
         steps = []
         for _ in range(args.warmup):
             cpu_baseline(args, budget_s=1.0)
@@ -1090,7 +1367,24 @@ def main():
         print(json.dumps(out))
         return 0
     grp = Group(world, local)
-    if args.workload == "gemm":
+    if args.workload == "all":
+        # the out-of-core grid: the headline (in-HBM regime) and its streaming
+        # regime; the other workloads follow in the same JSON line
+        import argparse as _ap
+        links = link_peaks(local)
+        spill = run_spill(args, rank, world, local, grp, links)
+        free_pinned()
+        a2 = _ap.Namespace(**vars(args))
+        a2.workload = "ooc"
+        res = run_lightning(a2, rank, world, local, grp, links)
+        free_pinned()
+        res["spill"] = spill
+        res["workloads"] = run_workloads(args, rank, world, local, grp)
+        args.workload = "ooc"
+    elif args.workload == "spill":
+        res = run_spill(args, rank, world, local, grp)
+        args.no_cpu = True
+    elif args.workload == "gemm":
         res = run_gemm(args, rank, world, local, grp)
         args.no_cpu = True
     elif args.workload == "batch":

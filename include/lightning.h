@@ -409,6 +409,12 @@ typedef struct {
     uint64_t plans_reused;    /* launches whose plan came from the kernel's plan cache */
     uint64_t reduce_inplace;  /* reduce partials accumulated in their destination chunk (no copy) */
     uint64_t bytes_replica_wt; /* halo-replica bytes the Execute kernels wrote themselves (no copy step) */
+    /* with LT_FLAG_TIMING, from the start and end events of the timed
+     * operations, per synchronize (valid after lt_synchronize): */
+    double ms_span;           /* first operation's start to the last one's end, summed over synchronizes */
+    double ms_link_busy;      /* time a host<->device chunk copy (fetch or eviction) was running */
+    double ms_link_both;      /* time copies in both directions were running at once */
+    double ms_exec_hidden;    /* Execute kernel time during which a host<->device copy was running */
 } lt_stats;
 
 lt_status lt_stats_get(lt_ctx *ctx, lt_stats *out);
@@ -429,6 +435,14 @@ lt_status lt_plan_explain(lt_ctx *ctx, lt_kernel *k, lt_dim3 grid, lt_dim3 block
  * (lt_debug_log_enable), for tests. */
 lt_status lt_debug_log_enable(lt_ctx *ctx, int32_t enable);
 lt_status lt_debug_log(lt_ctx *ctx, char *buf, size_t cap, size_t *needed);
+/* JSON list of the operations timed with LT_FLAG_TIMING events while the log
+ * is enabled, collected at each lt_synchronize: task id (as in lt_debug_log),
+ * stream (0 compute, 1 host-to-device, 2 device-to-host), category (0 Execute
+ * kernel, 1 copy kernel, 2 fetch, 3 eviction, 4 fill), start and end in
+ * milliseconds.  Times within one synchronize share an origin; each later
+ * synchronize's times start after the previous ones.  Same buffer rules as
+ * lt_debug_log. */
+lt_status lt_debug_timeline(lt_ctx *ctx, char *buf, size_t cap, size_t *needed);
 
 /* ---- allocation-free Jacobi step -------------------------------------------
  * The paper has no counterpart to this call.  It serves callers that cannot
@@ -452,10 +466,15 @@ lt_status lt_debug_log(lt_ctx *ctx, char *buf, size_t cap, size_t *needed);
  * whose packed region exceeds it is rejected with LT_ERR_INVALID_ARG.
  * Every call shares the scratch and leaves the last call's contents in it:
  * calls that overlap on the GPU race, calls ordered on one stream do not.
- * The first call on a device looks up the scratch's device address and
- * caches it; make that first call before any stream capture.
- * Errors: LT_ERR_INVALID_ARG (bad pointers or sizes), LT_ERR_CUDA (a CUDA
- * call failed); lt_last_error() gives the message. */
+ * Every call looks up the scratch's device address on the current device
+ * (cudaGetSymbolAddress); the first call on a device also loads the module
+ * there, so make that first call before any stream capture.  The descriptor
+ * tables are uploaded from a host buffer that lives only for the call: on a
+ * stream that is capturing the call returns LT_ERR_UNSUPPORTED and enqueues
+ * nothing.
+ * Errors: LT_ERR_INVALID_ARG (bad pointers or sizes), LT_ERR_UNSUPPORTED
+ * (the stream is capturing), LT_ERR_CUDA (a CUDA call failed);
+ * lt_last_error() gives the message. */
 #define LT_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 lt_status lt_jacobi2d_packed_noalloc(const float *U, float *V, int64_t ny, int64_t nx, int64_t ld_u, int64_t ld_v,
                                      int64_t tile_rows, int64_t tile_cols, void *stream);

@@ -79,7 +79,9 @@ class lt_stats(C.Structure):
         ("n_copy_kernels", C.c_uint64), ("ms_h2d", C.c_double), ("ms_d2h", C.c_double), ("ms_fill", C.c_double),
         ("batches_fused", C.c_uint64), ("batches_plain", C.c_uint64), ("graph_replays", C.c_uint64),
         ("tuned_tile_rows", C.c_int64), ("tuned_hist_slice", C.c_int64), ("tables_resident", C.c_uint64),
-        ("plans_reused", C.c_uint64), ("reduce_inplace", C.c_uint64), ("bytes_replica_wt", C.c_uint64)]
+        ("plans_reused", C.c_uint64), ("reduce_inplace", C.c_uint64), ("bytes_replica_wt", C.c_uint64),
+        ("ms_span", C.c_double), ("ms_link_busy", C.c_double), ("ms_link_both", C.c_double),
+        ("ms_exec_hidden", C.c_double)]
 
 
 class lt_launch_desc(C.Structure):
@@ -127,6 +129,7 @@ SIGNATURES = {
                               C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "lt_debug_log_enable": (_st, [_vp, C.c_int32]),
     "lt_debug_log": (_st, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "lt_debug_timeline": (_st, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "lt_jacobi2d_packed_noalloc": (_st, [_vp, _vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
                                          C.c_int64, _vp]),
     "lt_selftest_div_const": (_st, [C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]),

@@ -13,16 +13,16 @@ halo reduce(+) of lambda):
     dkappa  += lambda_{t+1} * (L u_t)
 
 and returns dJ/du0 = lambda_0 and dJ/dkappa.  The incoming gradient
-grad_output is lambda_T (for J = sum u_T^2 it is 2 u_T).
+grad_output is lambda_T (for J = sum u_T^2 it is 2 u_T).  With
+ckpt_every = 1 every state is kept and nothing is recomputed (one forward
+and one adjoint launch per step).
 
-``PlainDiffusion`` is the same computation written with plain torch ops
-(each step several separate kernels, every state kept by autograd): the
-plain form the chunked adjoint is compared against.
+PyTorch only moves the fields between tensors and the engine's arrays
+(device-to-device copies); every step runs in the engine's kernels.
 """
 from __future__ import annotations
 
 import torch
-import torch.nn.functional as F
 
 from . import _lib as L
 from . import lightning as lt
@@ -154,17 +154,3 @@ class DiffusionChunked(torch.autograd.Function):
         plan.release()
         ctx.plan = None
         return du0, dk, None, None, None, None
-
-
-def plain_step(u, kappa):
-    p = F.pad(u[None, None], (1, 1, 1, 1))[0, 0]
-    lap = p[:-2, 1:-1] + p[2:, 1:-1] + p[1:-1, :-2] + p[1:-1, 2:] - 4.0 * u
-    return u + kappa * lap
-
-
-def PlainDiffusion(u0, kappa, steps: int):
-    """The same forward map with plain torch ops (autograd keeps every state)."""
-    u = u0
-    for _ in range(steps):
-        u = plain_step(u, kappa)
-    return u

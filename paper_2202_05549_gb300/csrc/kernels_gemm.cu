@@ -4,14 +4,21 @@
 // Sec. 4.2).  C = A B with bf16 inputs and f32 accumulation and output.
 //
 // One persistent kernel runs every superblock (output tile chunk) of a
-// launch.  Each CTA owns one SM and walks output tiles of 128 x 256:
-//   warp 0      TMA producer: A (128 x 64) and B (256 x 64) K-slices into a
-//               4-stage shared-memory ring, 128-byte swizzled;
-//   warp 1      MMA issuer: tcgen05.mma kind::f16 (M=128, N=256, K=16) into
-//               one of two TMEM accumulators (2 x 256 columns), commits to
-//               mbarriers that free ring stages and publish accumulators;
-//   warps 2-5   epilogue: tcgen05.ld of the accumulator (each warp reads its
-//               32-lane quarter), masked f32 stores to the C chunk.
+// launch.  Each CTA owns one SM and walks output tiles of 256 x 256, each
+// computed as two M = 128 halves that share the B operand of a stage:
+//   warp 0      TMA producer: A (256 x 64) and B (256 x 64) K-slices, 64 KB
+//               per stage, into a 3-stage shared-memory ring, 128-byte
+//               swizzled;
+//   warp 1      MMA issuer: per K-step of 16, two tcgen05.mma kind::f16
+//               (M=128, N=256), one per M-half, into a single TMEM
+//               accumulator of 2 x 256 = 512 columns; commits to mbarriers
+//               that free ring stages and publish the accumulator;
+//   warps 2-5   epilogue: tcgen05.ld of both halves (each warp reads its
+//               32-lane quarter), masked f32 stores to the C chunk, then
+//               release of the accumulator.
+// With one accumulator the MMA warp waits for the epilogue of a tile before
+// it starts the next one; at the K of the GEMM workload (65536) that wait is
+// a small fraction of a tile, at small K it is visible.
 // A must be stored row-major and B column-major (both K-contiguous), which
 // the column-major chunk order of the distribution provides.  Ragged M, N
 // and K are handled by TMA zero fill and masked stores.
@@ -33,7 +40,8 @@ namespace {
 // Tile BM x BN: MH M-halves of UM = 128 rows (one tcgen05.mma each, both
 // reading the same B stage), so a stage's B bytes serve MH MMAs.  The
 // accumulators of a tile take MH x BN TMEM columns; NACC tiles fit in the
-// 512 columns (NACC = 2 lets the epilogue of one tile overlap the next).
+// 512 columns.  At 256 x 256 that is one (a shape with NACC = 2 would let
+// the epilogue of one tile overlap the MMAs of the next).
 constexpr int MH = 2, UM = 128;
 constexpr int BM = MH * UM, BN = 256, BK = 64, UMMA_K = 16;
 constexpr int A_BYTES = BM * BK * 2;

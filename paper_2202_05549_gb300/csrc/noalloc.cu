@@ -12,13 +12,17 @@
 // The array exists once per device that loads the library and stays there
 // until the process exits.  Every call on a device shares it, so calls that
 // overlap on the GPU (different streams, no ordering between them) race;
-// calls ordered on one stream do not.  The first call on a device looks up
-// the array's device address (cudaGetSymbolAddress) and caches it; make
-// that first call before any stream capture.
+// calls ordered on one stream do not.  Every call looks up the array's
+// device address on the current device (cudaGetSymbolAddress, a few
+// microseconds), so the address stays right after the device's context is
+// torn down and made again.  The first call on a device also loads this
+// module there; make that first call before any stream capture.  The
+// descriptor tables are uploaded from a host buffer that lives only for the
+// call, so a call on a stream that is capturing returns LT_ERR_UNSUPPORTED
+// and enqueues nothing.
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -34,25 +38,15 @@ constexpr size_t kPackBytes = kScratchBytes - kDescBytes;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void *g_scratch_ptr[256] = {nullptr};
-
 lt_status nfail(lt_status s, const std::string &m) { return lt::set_last_error(s, m); }
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device.
 lt_status scratch_ptr(unsigned char **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256)
-        return nfail(LT_ERR_CUDA, "cudaGetDevice failed");
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return nfail(LT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
-    }
-    *out = (unsigned char *)g_scratch_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return nfail(LT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = (unsigned char *)p;
     return LT_OK;
 }
 
@@ -73,10 +67,16 @@ extern "C" lt_status lt_jacobi2d_packed_noalloc(const float *U, float *V, int64_
         return nfail(LT_ERR_INVALID_ARG, "a packed tile needs " + std::to_string(worst) +
                                              " bytes; the static scratch holds " + std::to_string(kPackBytes) +
                                              " (64 MiB less 1 MiB of descriptors)");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess) return nfail(LT_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+    if (cap != cudaStreamCaptureStatusNone)
+        return nfail(LT_ERR_UNSUPPORTED, "the stream is capturing: the descriptor upload reads a host buffer that "
+                                         "lives only for the call, so this call is not recorded");
     unsigned char *scr = nullptr;
     lt_status st = scratch_ptr(&scr);
     if (st) return st;
-    cudaStream_t s = (cudaStream_t)stream;
 
     DView uv{(uint64_t)(uintptr_t)U, {ld_u, 1, 0}, {0, 0, 0}, {ny - 1, nx - 1, 0}};
     DView vv{(uint64_t)(uintptr_t)V, {ld_v, 1, 0}, {0, 0, 0}, {ny - 1, nx - 1, 0}};

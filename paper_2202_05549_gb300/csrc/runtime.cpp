@@ -288,6 +288,8 @@ struct lt_kernel {
 struct TimedOp {
     int cat;
     cudaEvent_t a, b;
+    int64_t task = -1;
+    int stream = 0;
 };
 
 // A planned launch waiting for the next one (one launch of lookahead).
@@ -352,6 +354,9 @@ struct lt_ctx {
     lt_stats stats{};
     bool log_on = false;
     std::ostringstream log;
+    std::ostringstream tlog;  // start and end times of timed operations (while the log is on)
+    int tlog_n = 0;
+    double tlog_base = 0;
     int log_n = 0;
     std::vector<TimedOp> timed;
     std::vector<cudaEvent_t> tev_pool;
@@ -466,14 +471,67 @@ struct TimeScope {
         cudaEvent_t b = tev_get(c);
         if (b) {
             cudaEventRecord(b, c->st[c->cur_stream]);
-            c->timed.push_back({cat, a, b});
+            c->timed.push_back({cat, a, b, c->cur_task, c->cur_stream});
         }
         a = nullptr;
     }
     ~TimeScope() { end(); }
 };
 
+// Overlap of the timed operations collected at one synchronize (all streams
+// were idle before the first of them): the time the host link carried a
+// copy, the time it carried copies in both directions at once, and the
+// Execute-kernel time during which a copy ran (kernel time hidden under the
+// link).  Times are relative to the first operation's start event.
+lt_status timeline_overlap(lt_ctx *c) {
+    if (c->timed.empty()) return LT_OK;
+    struct Edge {
+        float t;
+        int cat;
+        int d;
+    };
+    std::vector<Edge> ev;
+    ev.reserve(c->timed.size() * 2);
+    float lo = 0, hi = 0;
+    for (size_t i = 0; i < c->timed.size(); ++i) {
+        const TimedOp &t = c->timed[i];
+        float t0 = 0, t1 = 0;
+        if (i) CK(c, cudaEventElapsedTime(&t0, c->timed[0].a, t.a));
+        CK(c, cudaEventElapsedTime(&t1, c->timed[0].a, t.b));
+        if (t1 < t0) t1 = t0;
+        if (c->log_on) {
+            c->tlog << (c->tlog_n++ ? "," : "") << "{\"id\":" << t.task << ",\"stream\":" << t.stream
+                    << ",\"cat\":" << t.cat << ",\"t0\":" << c->tlog_base + t0 << ",\"t1\":" << c->tlog_base + t1
+                    << "}";
+        }
+        lo = i ? std::min(lo, t0) : t0;
+        hi = i ? std::max(hi, t1) : t1;
+        if (t.cat != CAT_EXEC && t.cat != CAT_H2D && t.cat != CAT_D2H) continue;
+        ev.push_back({t0, t.cat, +1});
+        ev.push_back({t1, t.cat, -1});
+    }
+    std::sort(ev.begin(), ev.end(), [](const Edge &x, const Edge &y) { return x.t < y.t || (x.t == y.t && x.d < y.d); });
+    int n[5] = {0, 0, 0, 0, 0};
+    for (size_t i = 0; i < ev.size(); ++i) {
+        if (i) {
+            double dt = (double)ev[i].t - (double)ev[i - 1].t;
+            if (dt > 0) {
+                const bool h = n[CAT_H2D] > 0, d = n[CAT_D2H] > 0;
+                if (h || d) c->stats.ms_link_busy += dt;
+                if (h && d) c->stats.ms_link_both += dt;
+                if (n[CAT_EXEC] > 0 && (h || d)) c->stats.ms_exec_hidden += dt;
+            }
+        }
+        n[ev[i].cat] += ev[i].d;
+    }
+    c->stats.ms_span += (double)hi - (double)lo;
+    c->tlog_base += (double)hi + 1.0;  // the next synchronize's operations start after these
+    return LT_OK;
+}
+
 lt_status collect_timing(lt_ctx *c) {
+    lt_status ov = timeline_overlap(c);
+    if (ov) return ov;
     for (auto &t : c->timed) {
         float ms = 0;
         CK(c, cudaEventElapsedTime(&ms, t.a, t.b));
@@ -973,6 +1031,27 @@ void xfer_chunk_host(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *h
     int64_t gs[3] = {1, 1, 1};
     for (int d = g.nd - 2; d >= 0; --d) gs[d] = gs[d + 1] * g.shape[d + 1];
     int64_t e0 = box.extent(0), e1 = g.nd > 1 ? box.extent(1) : 1, e2 = g.nd > 2 ? box.extent(2) : 1;
+    if (cg.stride[g.nd - 1] == 1) {
+        // the innermost axis is contiguous in both: one memcpy per run
+        const int64_t run = g.nd == 1 ? e0 : (g.nd == 2 ? e1 : e2);
+        const int64_t outer0 = g.nd == 1 ? 1 : e0, outer1 = g.nd == 3 ? e1 : 1;
+        for (int64_t x = 0; x < outer0; ++x)
+            for (int64_t y = 0; y < outer1; ++y) {
+                int64_t idx[3] = {box.lo[0], box.lo[1], box.lo[2]};
+                if (g.nd >= 2) idx[0] += x;
+                if (g.nd == 3) idx[1] += y;
+                int64_t co = 0, ho = 0;
+                for (int d = 0; d < g.nd; ++d) {
+                    co += (idx[d] - cg.s_origin[d]) * cg.stride[d];
+                    ho += idx[d] * gs[d];
+                }
+                if (to_chunk)
+                    std::memcpy(base + co * (int64_t)es, hb + ho * (int64_t)es, (size_t)run * es);
+                else
+                    std::memcpy(hb + ho * (int64_t)es, base + co * (int64_t)es, (size_t)run * es);
+            }
+        return;
+    }
     for (int64_t x = 0; x < e0; ++x)
         for (int64_t y = 0; y < e1; ++y)
             for (int64_t z = 0; z < e2; ++z) {
@@ -3095,6 +3174,22 @@ lt_status lt_debug_log_enable(lt_ctx *c, int32_t enable) {
     c->log.str("");
     c->log.clear();
     c->log_n = 0;
+    c->tlog.str("");
+    c->tlog.clear();
+    c->tlog_n = 0;
+    c->tlog_base = 0;
+    return LT_OK;
+}
+
+lt_status lt_debug_timeline(lt_ctx *c, char *buf, size_t cap, size_t *needed) {
+    if (!c) return fail(LT_ERR_INVALID_ARG, "null context");
+    std::string js = "[" + c->tlog.str() + "]";
+    if (needed) *needed = js.size() + 1;
+    if (buf && cap) {
+        size_t n = std::min(cap - 1, js.size());
+        std::memcpy(buf, js.data(), n);
+        buf[n] = 0;
+    }
     return LT_OK;
 }
 

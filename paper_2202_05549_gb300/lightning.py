@@ -312,6 +312,14 @@ class Context:
     def log_enable(self, on=True):
         check(L.load().lt_debug_log_enable(self.h, 1 if on else 0))
 
+    def timeline(self):
+        """Start and end times (ms) of the operations timed while the log was on."""
+        need = C.c_size_t()
+        check(L.load().lt_debug_timeline(self.h, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value)
+        check(L.load().lt_debug_timeline(self.h, buf, need.value, None))
+        return json.loads(buf.value.decode())
+
     def log(self):
         need = C.c_size_t()
         check(L.load().lt_debug_log(self.h, None, 0, C.byref(need)))
