@@ -327,7 +327,9 @@ def plan_ooc(args, world, hbm_gib=None):
     holds the live set beyond it.  The live set is one array plus the bands
     in flight: a band of the input is dead once its last reader has run (the
     next launch overwrites it unread), so the pool holds the bands of one
-    array that are not in HBM plus four in flight."""
+    array that are not in HBM plus four in flight, and six more: the library
+    withholds the parts of a large pinned pool that copy slowly (measured at
+    creation), some gigabytes on some runs."""
     ny, nx, band = args.rows, args.cols, args.band
     hbm_gib = args.hbm_gib if hbm_gib is None else hbm_gib
     nb = (ny + band - 1) // band
@@ -342,7 +344,7 @@ def plan_ooc(args, world, hbm_gib=None):
     dev_slots = max(2 * nb - host_slots + 3, 6)  # a band task pins 4 chunks
     if hbm_gib > 0:
         dev_slots = max(int(hbm_gib * 2**30) // chunk_c, 6)
-        host_slots = max(nb + 4 - dev_slots, 0)
+        host_slots = max(nb + 4 - dev_slots, 0) + 6
         if host_slots * chunk_c > 0.8 * avail:
             raise SystemExit(f"HBM budget {hbm_gib} GiB: the rest of the live data does not fit in pinned host memory")
     budget = dev_slots * chunk_c + (64 << 20)
@@ -440,7 +442,7 @@ def run_spill(args, rank, world, local, grp, links=None):
         "roofline": {"bound": "host link", "kernel": "jacobi2d_vec_kernel", "launch_ms": round(ex_ms, 4),
                      "kernel_frac_of_hbm": round(per_launch / (ex_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4)},
         "stats": {k2: st[k2] for k2 in ("fetches", "evictions", "dead_skips", "tasks_execute", "hbm_peak",
-                                        "kernels")},
+                                        "kernels", "host_withheld_bytes")},
         "clocks": clocks, "setup_s": round(setup_s, 1),
     }
 

@@ -112,11 +112,16 @@ typedef struct {
  *   every launch (default: the order alternates between launches, so the
  *   chunks used last are reused first); LT_FLAG_NO_STAGED makes the stencil
  *   built-ins use their register kernels instead of the TMA-staged ones (same
- *   results; for comparing the two). */
+ *   results; for comparing the two); LT_FLAG_NO_LINK_SCREEN skips the
+ *   screening of the pinned host pool (a pool of at least 8 GiB is timed at
+ *   creation in 512 MiB pieces, one copy each way, and pieces slower than
+ *   half the median are withheld from allocation: parts of large pinned
+ *   allocations were measured to copy 5-50x slower than the rest). */
 #define LT_FLAG_TIMING 1
 #define LT_FLAG_DRYRUN 2
 #define LT_FLAG_FIXED_SWEEP 4
 #define LT_FLAG_NO_STAGED 8
+#define LT_FLAG_NO_LINK_SCREEN 16
 
 typedef struct {
     size_t hbm_budget_bytes;
@@ -281,10 +286,13 @@ lt_status lt_kernel_destroy(lt_ctx *ctx, lt_kernel *k);
  * array parameters as lightning::Vector<T> / Matrix<T> / Tensor<T> for 1, 2
  * or 3 indices in the annotation, indexed with global indices (v[i],
  * m(i, j) or m[i][j], t(k, i, j)); T is float, unsigned short (bf16 bits),
- * unsigned char or unsigned int.  Use virtBlockIdx instead of blockIdx;
- * blockDim and threadIdx are those of the launch.  The library generates the
- * wrapper kernel that maps physical to virtual blocks and builds the views
- * (the chunk offset subtracted once), compiles both with NVRTC for sm_103a
+ * unsigned char or unsigned int.  Use virtBlockIdx instead of blockIdx and
+ * gridDim; blockDim and threadIdx are those of the launch.  The library
+ * generates the wrapper kernel that maps physical to virtual blocks and
+ * builds the views (the chunk offset subtracted once).  The wrapper is
+ * persistent: each CTA calls the function for several virtual blocks in turn,
+ * with a __syncthreads() between two calls, so shared memory does not carry
+ * over from one virtual block to the next.  The library compiles both with NVRTC for sm_103a
  * (IEEE arithmetic, no FMA contraction) and loads them.  The annotation is
  * trusted: the kernel must not touch elements outside it.  At most 5 array,
  * 4 integer and 4 float parameters.  Errors: LT_ERR_PARSE, LT_ERR_COMPILE
@@ -415,6 +423,7 @@ typedef struct {
     double ms_link_busy;      /* time a host<->device chunk copy (fetch or eviction) was running */
     double ms_link_both;      /* time copies in both directions were running at once */
     double ms_exec_hidden;    /* Execute kernel time during which a host<->device copy was running */
+    uint64_t host_withheld_bytes; /* host pool bytes withheld at creation as slow to copy (screening) */
 } lt_stats;
 
 lt_status lt_stats_get(lt_ctx *ctx, lt_stats *out);

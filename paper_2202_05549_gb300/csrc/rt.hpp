@@ -159,6 +159,21 @@ struct Arena {
         coalesce();
         return take(sz, off, f);
     }
+    // Take [off, off + len) out of the free space for good (the range must be
+    // free; only called on a fresh pool).
+    void withhold(size_t off, size_t len) {
+        auto it = free_.upper_bound(off);
+        if (it == free_.begin()) return;
+        --it;
+        const size_t b = it->first, e = b + it->second.size;
+        if (off < b || off + len > e) return;
+        Free keep = it->second;
+        free_.erase(it);
+        if (off > b) free_[b] = {off - b, keep.f, keep.tick};
+        if (off + len < e) free_[off + len] = {e - off - len, keep.f, keep.tick};
+        withheld += len;
+    }
+    size_t withheld = 0;
     void release(size_t off, size_t sz, const FenceSet &f) {
         sz = size_class(sz);
         used -= sz;
@@ -243,6 +258,7 @@ struct lt_kernel {
     std::unique_ptr<BuiltinDef> own_def;     // user kernels: their own signature
     cudaLibrary_t ulib = nullptr;            // user kernels: loaded NVRTC cubin
     cudaKernel_t ufn = nullptr;
+    std::map<int, int> uocc;                 // user kernels: resident CTAs per SM by block size
     Annotation ann, canon;
     std::vector<lt_param> params;
     std::vector<std::string> names;
@@ -287,6 +303,9 @@ struct lt_ctx {
     lt_config cfg{};
     bool dry = false;
     bool no_staged = false;  // LT_FLAG_NO_STAGED
+    int sm_count = 1;        // streaming multiprocessors of the device
+    float link_screen_h2d = 0, link_screen_d2h = 0;  // median GB/s of the host pool's pieces (screening)
+    size_t link_piece = 0;   // host-link chunk copies in pieces of this many bytes (0: whole chunks)
     bool poisoned = false;
     cudaStream_t st[NSTREAM] = {nullptr, nullptr, nullptr};
     uint64_t seq[NSTREAM] = {0, 0, 0};
@@ -352,6 +371,7 @@ namespace rt {
 
 lt_status fail(lt_status st, const std::string &msg);
 const char *last_error_text();
+lt_status screen_host_pool(lt_ctx *c);
 
 // fences and timing (rt_streams.cpp)
 lt_status op_begin(lt_ctx *c, int s, const char *kind);
@@ -400,6 +420,7 @@ struct TimeScope {
 
 // memory (rt_memory.cpp)
 char *dptr(const lt_ctx *c, uint64_t off);
+cudaError_t link_copy(lt_ctx *c, void *dst, const void *src, size_t n, cudaMemcpyKind kind, cudaStream_t st);
 DView view_of(lt_ctx *c, const ArrayGeom &g, const ChunkGeom &cg, size_t off);
 bool droppable(const lt_ctx *c, const CState &s);
 bool pick_victim(lt_ctx *c, lt_array **va, int64_t *vc);

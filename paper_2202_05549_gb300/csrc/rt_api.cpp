@@ -56,6 +56,56 @@ const size_t kNumBuiltins = sizeof(kBuiltins) / sizeof(kBuiltins[0]);
 }  // namespace rt
 }  // namespace lt
 
+namespace lt {
+namespace rt {
+
+// Screening of the pinned host pool.  On the GB300 machines measured, some
+// gigabytes of a large pinned allocation can copy to and from the GPU 5 to
+// 50 times slower than the rest (which parts differs from one process to the
+// next; it looks like where the pages lie physically).  A chunk whose host
+// copy lands there turns one link transfer into hundreds of milliseconds and
+// stalls the streaming pipeline.  So a pool of at least 8 GiB is timed once,
+// in pieces of 512 MiB, one copy each way through the start of the HBM pool
+// (CUDA events), and pieces slower than half the median in either direction
+// are withheld from allocation for the life of the context
+// (lt_stats.host_withheld_bytes).
+lt_status screen_host_pool(lt_ctx *c) {
+    const size_t piece = (size_t)512 << 20;
+    if (c->dry || c->host.cap < ((size_t)8 << 30) || c->dev.cap < piece) return LT_OK;
+    const size_t n = c->host.cap / piece;
+    cudaEvent_t e[3];
+    for (auto &x : e) CK(c, cudaEventCreate(&x));
+    std::vector<float> h2d(n), d2h(n);
+    cudaStream_t st = c->st[S_H2D];
+    for (size_t i = 0; i < n; ++i) {
+        char *hp = c->host_base + i * piece;
+        CK(c, cudaEventRecord(e[0], st));
+        CK(c, cudaMemcpyAsync(c->dev_base, hp, piece, cudaMemcpyHostToDevice, st));
+        CK(c, cudaEventRecord(e[1], st));
+        CK(c, cudaMemcpyAsync(hp, c->dev_base, piece, cudaMemcpyDeviceToHost, st));
+        CK(c, cudaEventRecord(e[2], st));
+        CK(c, cudaEventSynchronize(e[2]));
+        float a = 0, b = 0;
+        CK(c, cudaEventElapsedTime(&a, e[0], e[1]));
+        CK(c, cudaEventElapsedTime(&b, e[1], e[2]));
+        h2d[i] = (float)piece / std::max(a, 1e-3f);
+        d2h[i] = (float)piece / std::max(b, 1e-3f);
+    }
+    for (auto &x : e) cudaEventDestroy(x);
+    std::vector<float> sh = h2d, sd = d2h;
+    std::nth_element(sh.begin(), sh.begin() + n / 2, sh.end());
+    std::nth_element(sd.begin(), sd.begin() + n / 2, sd.end());
+    const float mh = sh[n / 2], md = sd[n / 2];
+    for (size_t i = 0; i < n; ++i)
+        if (h2d[i] < 0.5f * mh || d2h[i] < 0.5f * md) c->host.withhold(i * piece, piece);
+    c->link_screen_h2d = mh * 1e3f / 1e9f;  // bytes per ms -> GB/s
+    c->link_screen_d2h = md * 1e3f / 1e9f;
+    return LT_OK;
+}
+
+}  // namespace rt
+}  // namespace lt
+
 extern "C" {
 
 lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
@@ -64,6 +114,7 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     c->cfg = *cfg;
     c->dry = (cfg->flags & LT_FLAG_DRYRUN) != 0;
     c->no_staged = (cfg->flags & LT_FLAG_NO_STAGED) != 0;
+    if (const char *e = std::getenv("LT_LINK_PIECE_BYTES")) c->link_piece = (size_t)std::strtoull(e, nullptr, 10);
     for (int s = 0; s < NSTREAM; ++s) {
         c->ev[s].assign(RING, nullptr);
         c->evseq[s].assign(RING, 0);
@@ -86,6 +137,7 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     if (major * 10 + minor != 103)
         return fail(LT_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300) only; device is sm_" +
                                             std::to_string(major) + std::to_string(minor));
+    CK(cp, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cfg->device));
     for (int s = 0; s < NSTREAM; ++s) {
         CK(cp, cudaStreamCreateWithFlags(&c->st[s], cudaStreamNonBlocking));
         for (int i = 0; i < RING; ++i) CK(cp, cudaEventCreateWithFlags(&c->ev[s][i], cudaEventDisableTiming));
@@ -109,6 +161,10 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     }
     c->host.init(cfg->host_pool_bytes, c->host_base);
     c->host.oldest_first = true;
+    if (!(cfg->flags & LT_FLAG_NO_LINK_SCREEN)) {
+        lt_status sst = screen_host_pool(cp);
+        if (sst) return sst;
+    }
     c->up_cap = (size_t)32 << 20;
     CK(cp, cudaHostAlloc((void **)&c->up_host, c->up_cap + TSLOTS * TSLOT_BYTES, cudaHostAllocDefault));
     CK(cp, cudaMalloc((void **)&c->up_dev, c->up_cap + TSLOTS * TSLOT_BYTES));
@@ -777,6 +833,7 @@ lt_status lt_stats_get(lt_ctx *c, lt_stats *out) {
     c->stats.hbm_in_use = c->dev.used;
     c->stats.hbm_peak = c->dev.peak;
     c->stats.host_in_use = c->host.used;
+    c->stats.host_withheld_bytes = c->host.withheld;
     *out = c->stats;
     return LT_OK;
 }

@@ -561,10 +561,21 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             if (!c->dry && ctas) {
                 TimeScope ts(c, CAT_EXEC);
                 if (k->ufn) {
+                    // the wrapper is persistent: as many CTAs as fit on the GPU at once, each looping over
+                    // the launch's blocks, so short blocks do not pay one CTA launch each
                     const ExecTask *tp = (const ExecTask *)dptr;
-                    void *kargs[] = {(void *)&tp, (void *)&ep};
+                    unsigned nblocks = ctas;
+                    void *kargs[] = {(void *)&tp, (void *)&ep, (void *)&nblocks};
                     dim3 blk((unsigned)ep.block[0], (unsigned)ep.block[1], (unsigned)ep.block[2]);
-                    CK(c, cudaLaunchKernel((const void *)k->ufn, dim3(ctas), blk, kargs, 0, c->st[S_COMP]));
+                    const int threads = (int)(blk.x * blk.y * blk.z);
+                    auto occ = k->uocc.find(threads);
+                    if (occ == k->uocc.end()) {
+                        int per_sm = 0;
+                        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k->ufn, threads, 0));
+                        occ = k->uocc.emplace(threads, std::max(1, per_sm)).first;
+                    }
+                    const uint32_t grid = (uint32_t)std::min<uint64_t>(ctas, (uint64_t)occ->second * c->sm_count);
+                    CK(c, cudaLaunchKernel((const void *)k->ufn, dim3(grid), blk, kargs, 0, c->st[S_COMP]));
                 } else {
                     CK(c, def->launch((const ExecTask *)dptr, ctas, ep, c->st[S_COMP]));
                 }

@@ -28,6 +28,17 @@ DView view_of(lt_ctx *c, const ArrayGeom &g, const ChunkGeom &cg, size_t off) {
     return v;
 }
 
+// One chunk copy over the host link, in pieces of c->link_piece bytes when
+// that is set (0: one copy).
+cudaError_t link_copy(lt_ctx *c, void *dst, const void *src, size_t n, cudaMemcpyKind kind, cudaStream_t st) {
+    const size_t piece = c->link_piece ? c->link_piece : n;
+    for (size_t o = 0; o < n; o += piece) {
+        cudaError_t e = cudaMemcpyAsync((char *)dst + o, (const char *)src + o, std::min(piece, n - o), kind, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // ---------------------------------------------------------------- memory manager
 
 // Pick the least-recently-used unpinned resident chunk.
@@ -129,12 +140,12 @@ lt_status evict(lt_ctx *c, lt_array *a, int64_t ci) {
     if (st) return st;
     if (!c->dry) {
         TimeScope ts(c, CAT_D2H);
-        CK(c, cudaMemcpyAsync(c->host_base + hoff, dptr(c, s.off), cg.bytes, cudaMemcpyDeviceToHost,
-                              c->st[S_D2H]));
+        CK(c, link_copy(c, c->host_base + hoff, dptr(c, s.off), cg.bytes, cudaMemcpyDeviceToHost, c->st[S_D2H]));
     }
     uint64_t q;
     std::ostringstream ex;
-    ex << ",\"array\":" << a->id << ",\"chunk\":" << ci << ",\"bytes\":" << cg.bytes;
+    ex << ",\"array\":" << a->id << ",\"chunk\":" << ci << ",\"bytes\":" << cg.bytes << ",\"host_off\":" << hoff
+       << ",\"dev_off\":" << s.off;
     st = op_end(c, &q, ex.str());
     if (st) return st;
     FenceSet rel = s.busy;
@@ -177,12 +188,13 @@ lt_status ensure_dev(lt_ctx *c, lt_array *a, int64_t ci, bool need_data, bool so
             if (st) return st;
             if (!c->dry) {
                 TimeScope ts(c, CAT_H2D);
-                CK(c, cudaMemcpyAsync(dptr(c, off), c->host_base + s.off, cg.bytes, cudaMemcpyHostToDevice,
-                                      c->st[S_H2D]));
+                CK(c, link_copy(c, dptr(c, off), c->host_base + s.off, cg.bytes, cudaMemcpyHostToDevice,
+                                c->st[S_H2D]));
             }
             uint64_t q;
             std::ostringstream ex;
-            ex << ",\"array\":" << a->id << ",\"chunk\":" << ci << ",\"bytes\":" << cg.bytes;
+            ex << ",\"array\":" << a->id << ",\"chunk\":" << ci << ",\"bytes\":" << cg.bytes
+               << ",\"host_off\":" << s.off << ",\"dev_off\":" << off;
             st = op_end(c, &q, ex.str());
             if (st) return st;
             FenceSet rel = s.busy;

@@ -114,13 +114,15 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
       << ", \"task layout\");\nstatic_assert(sizeof(LtParams) == " << sizeof(ExecParams) << ", \"params layout\");\n"
       << "#line 1 \"user_kernel.cu\"\n"
       << user << "\n"
-      << "extern \"C\" __global__ void lt_user_wrapper(const LtTask *__restrict__ tasks, LtParams P) {\n"
+      << "extern \"C\" __global__ void lt_user_wrapper(const LtTask *__restrict__ tasks, LtParams P, unsigned nblocks) {\n"
+         "  // persistent: each CTA runs the blocks b = blockIdx.x, blockIdx.x + gridDim.x, ... of the launch\n"
+         "  for (unsigned b = blockIdx.x; b < nblocks; b += gridDim.x) {\n"
          "  int lo = 0, hi = P.ntasks - 1;\n"
-         "  if (P.uniform_ctas > 0) lo = (int)(blockIdx.x / (unsigned)P.uniform_ctas);\n"
-         "  else while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (tasks[mid].cta_begin <= blockIdx.x) lo = mid; else hi = mid - 1; }\n"
+         "  if (P.uniform_ctas > 0) lo = (int)(b / (unsigned)P.uniform_ctas);\n"
+         "  else while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (tasks[mid].cta_begin <= b) lo = mid; else hi = mid - 1; }\n"
          "  const LtTask &t = tasks[lo];\n"
          "  // first virtual block and the task's extent in blocks along x and y (set by the host)\n"
-         "  const unsigned l = blockIdx.x - t.cta_begin, q = l / t.aux[3];\n"
+         "  const unsigned l = b - t.cta_begin, q = l / t.aux[3];\n"
          "  dim3 vb(t.aux[0] + (l - q * t.aux[3]), t.aux[1] + q % t.aux[4], t.aux[2] + q / t.aux[4]);\n";
     int slot = 0, fi = 0, ii = 0;
     std::ostringstream args;
@@ -150,7 +152,9 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
         args << "a" << slot;
         slot++;
     }
-    o << "  " << name << "(vb" << args.str() << ");\n}\n";
+    o << "  " << name << "(vb" << args.str() << ");\n"
+      << "  __syncthreads();  // the body's shared memory is free before the next block reuses it\n"
+      << "  }\n}\n";
     return o.str();
 }
 

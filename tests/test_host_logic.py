@@ -642,3 +642,31 @@ def test_reduce_into_a_discarded_array_makes_it_live():
     for key in ("evictions", "dead_skips", "bytes_d2h", "fetches"):
         assert a[key] == b[key], key
     assert a["evictions"] > 0
+
+
+def test_streaming_plan_of_the_full_out_of_core_grid_fits_its_pools(monkeypatch):
+    # the benchmark's streaming regime: the 262144 x 131072 grid (two 128 GiB
+    # arrays) through a 64 GiB HBM budget; the pinned pool is sized from the
+    # live set (one array plus bands in flight), not from both arrays
+    import sys
+    import bench
+    monkeypatch.setattr(bench, "mem_available", lambda: 209 * 10**9)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "spill"])
+    args = bench.parse()
+    pl = bench.plan_ooc(args, 1, hbm_gib=64)
+    assert pl["host"] < 0.6 * 209 * 10**9 and pl["budget"] < 64 * 2**30
+    ny, nx, band = pl["ny"], pl["nx"], pl["band"]
+    with dry(budget=pl["budget"], host=pl["host"]) as ctx:
+        U, V, k = _jacobi_ctx(ctx, ny, nx, lt.Dist.rows(band, halo=1))
+        U.fill(L.LT_INIT_UNIFORM, seed=3)
+        bufs = [U, V]
+        for _ in range(2):
+            for _ in range(20):
+                k.launch(grid=(nx, ny), block=(128, 4), superblock=(nx, band), args=bufs)
+                bufs.reverse()
+            bufs[1].discard()
+            ctx.synchronize()
+        s = ctx.stats()
+        assert s["fetches"] > 0 and s["evictions"] > 0
+        assert s["hbm_peak"] <= pl["budget"]
+        assert s["tasks_execute"] == 2 * 20 * (ny // band)
