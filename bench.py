@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--band", type=int, default=8192)
     p.add_argument("--keep-stale", action="store_true",
                    help="stencil runs: do not discard the stale ping-pong buffer before the closing synchronize")
+    p.add_argument("--no-pdl", action="store_true",
+                   help="launch every kernel in plain stream order (no programmatic dependent launch)")
     p.add_argument("--no-staged", action="store_true",
                    help="stencil built-ins use their register kernels instead of the TMA-staged ones")
     p.add_argument("--hbm-gib", type=float, default=0.0,
@@ -264,7 +266,8 @@ def ctx_flags(args):
     """Context flags of the timed runs: per-kernel CUDA events, and the
     register stencil kernels when --no-staged asks for them."""
     from paper_2202_05549_gb300 import _lib as L
-    return L.LT_FLAG_TIMING | (L.LT_FLAG_NO_STAGED if args.no_staged else 0)
+    return (L.LT_FLAG_TIMING | (L.LT_FLAG_NO_STAGED if args.no_staged else 0) |
+            (L.LT_FLAG_NO_PDL if args.no_pdl else 0))
 
 
 def hbm_cap(args):

@@ -112,16 +112,22 @@ typedef struct {
  *   every launch (default: the order alternates between launches, so the
  *   chunks used last are reused first); LT_FLAG_NO_STAGED makes the stencil
  *   built-ins use their register kernels instead of the TMA-staged ones (same
- *   results; for comparing the two); LT_FLAG_NO_LINK_SCREEN skips the
- *   screening of the pinned host pool (a pool of at least 8 GiB is timed at
- *   creation in 512 MiB pieces, one copy each way, and pieces slower than
- *   half the median are withheld from allocation: parts of large pinned
- *   allocations were measured to copy 5-50x slower than the rest). */
+ *   results; for comparing the two); LT_FLAG_NO_LINK_QUARANTINE turns off
+ *   the quarantine of slow host-pool ranges (every fetch and eviction of at
+ *   least 256 MiB is timed; one that ran at less than half the fastest copy
+ *   in its direction takes its host range out of the pool, up to a quarter
+ *   of the pool: parts of large pinned allocations were measured to copy
+ *   2-20x slower than the rest);
+ *   LT_FLAG_NO_PDL launches every kernel in the plain stream order (default:
+ *   a 2-D Jacobi launch that runs entirely in device memory, without copy
+ *   steps, starts as a programmatic dependent of the kernel before it, so its
+ *   CTAs launch while that kernel finishes). */
 #define LT_FLAG_TIMING 1
 #define LT_FLAG_DRYRUN 2
 #define LT_FLAG_FIXED_SWEEP 4
 #define LT_FLAG_NO_STAGED 8
-#define LT_FLAG_NO_LINK_SCREEN 16
+#define LT_FLAG_NO_LINK_QUARANTINE 16
+#define LT_FLAG_NO_PDL 32
 
 typedef struct {
     size_t hbm_budget_bytes;
@@ -423,7 +429,8 @@ typedef struct {
     double ms_link_busy;      /* time a host<->device chunk copy (fetch or eviction) was running */
     double ms_link_both;      /* time copies in both directions were running at once */
     double ms_exec_hidden;    /* Execute kernel time during which a host<->device copy was running */
-    uint64_t host_withheld_bytes; /* host pool bytes withheld at creation as slow to copy (screening) */
+    uint64_t host_withheld_bytes; /* host pool bytes withheld as slow to copy (quarantine), now */
+    uint64_t host_quarantined;    /* copies that put their host range in quarantine */
 } lt_stats;
 
 lt_status lt_stats_get(lt_ctx *ctx, lt_stats *out);

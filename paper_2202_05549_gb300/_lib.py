@@ -29,7 +29,8 @@ LT_F32, LT_BF16, LT_U8, LT_U32, LT_F64 = 0, 1, 2, 3, 4
 LT_DIST_BLOCK, LT_DIST_ROWS, LT_DIST_COLS, LT_DIST_TILES = 0, 1, 2, 3
 LT_ORDER_ROW, LT_ORDER_COL = 0, 1
 # flags
-LT_FLAG_TIMING, LT_FLAG_DRYRUN, LT_FLAG_FIXED_SWEEP, LT_FLAG_NO_STAGED, LT_FLAG_NO_LINK_SCREEN = 1, 2, 4, 8, 16
+LT_FLAG_TIMING, LT_FLAG_DRYRUN, LT_FLAG_FIXED_SWEEP, LT_FLAG_NO_STAGED, LT_FLAG_NO_LINK_QUARANTINE = 1, 2, 4, 8, 16
+LT_FLAG_NO_PDL = 32
 # fills
 (LT_INIT_ZERO, LT_INIT_CONST, LT_INIT_UNIFORM, LT_INIT_KAPPA, LT_INIT_NORMAL_BF16,
  LT_INIT_U8) = range(6)
@@ -81,7 +82,8 @@ class lt_stats(C.Structure):
         ("tuned_tile_rows", C.c_int64), ("tuned_hist_slice", C.c_int64), ("tables_resident", C.c_uint64),
         ("plans_reused", C.c_uint64), ("reduce_inplace", C.c_uint64), ("bytes_replica_wt", C.c_uint64),
         ("ms_span", C.c_double), ("ms_link_busy", C.c_double), ("ms_link_both", C.c_double),
-        ("ms_exec_hidden", C.c_double), ("host_withheld_bytes", C.c_uint64)]
+        ("ms_exec_hidden", C.c_double), ("host_withheld_bytes", C.c_uint64),
+        ("host_quarantined", C.c_uint64)]
 
 
 class lt_launch_desc(C.Structure):

@@ -60,7 +60,7 @@ struct ExecParams {
     uint32_t nreps;
     uint32_t rep_ctas;                // CTAs before the tasks' CTAs (set by the launch from rep_cells)
     int32_t no_staged;                // 1: prepare_* picks no TMA-staged kernel (context flag)
-    int32_t pad;
+    int32_t pdl;                      // 1: launched as a programmatic dependent of the previous kernel
 };
 
 // Box copy (pack / unpack / replica update): copy the global box [lo, hi]

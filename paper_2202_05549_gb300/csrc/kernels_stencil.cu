@@ -50,9 +50,22 @@ constexpr int JV = 8;        // rows per warp strip of the single-step kernel
 // strip re-reads come from L2.  The CTA index is split with 32-bit
 // arithmetic: a 64-bit division here costs registers and prologue latency in
 // every CTA.
+// Programmatic dependent launch: when p.pdl is set the kernel may start while
+// the previous kernel on the stream is finishing.  Every CTA lets the next
+// kernel launch at once (its CTAs take SM slots only as ours retire) and
+// waits for the previous kernel's completion and memory before it touches
+// array data; only the task table, which no kernel writes, is read before.
+__device__ __forceinline__ void pdl_trigger_and_wait(const ExecParams &p) {
+    if (p.pdl) {
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     if (blockIdx.x < p.rep_ctas) {  // write-through replica CTAs come first: their latency overlaps the strips
+        pdl_trigger_and_wait(p);
         jacobi_replica_cell(tasks, p, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
         return;
     }
@@ -69,6 +82,7 @@ __global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTas
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t js = x0 + (int64_t)(tx * JWARPS + warp) * JCOLS;  // first column of this warp's strip
     const int64_t r0 = y0 + (int64_t)ty * R;
+    pdl_trigger_and_wait(p);
     if (js > xe || r0 > ye) return;  // warp-uniform: nothing to write
     jacobi_strip<false, R>((const float *)t.v[0].base, t.v[0].s[0], (float *)t.v[1].base, t.v[1].s[0], NY, NX, js,
                            r0, xe, ye, lane);
@@ -150,6 +164,19 @@ cudaError_t launch_jacobi2d(const ExecTask *dev, uint32_t ctas, const ExecParams
     ExecParams q = p;
     q.rep_ctas = (uint32_t)extra;
     const uint32_t grid = ctas + (uint32_t)extra;
+    if (p.variant == 1 && p.pdl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(threads);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, jacobi2d_vec_kernel<JV>, dev, q);
+    }
+    q.pdl = 0;
     if (p.variant == 1)
         jacobi2d_vec_kernel<JV><<<grid, threads, 0, st>>>(dev, q);
     else

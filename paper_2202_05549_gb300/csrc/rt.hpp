@@ -159,25 +159,37 @@ struct Arena {
         coalesce();
         return take(sz, off, f);
     }
-    // Take [off, off + len) out of the free space for good (the range must be
-    // free; only called on a fresh pool).
-    void withhold(size_t off, size_t len) {
-        auto it = free_.upper_bound(off);
-        if (it == free_.begin()) return;
-        --it;
-        const size_t b = it->first, e = b + it->second.size;
-        if (off < b || off + len > e) return;
-        Free keep = it->second;
-        free_.erase(it);
-        if (off > b) free_[b] = {off - b, keep.f, keep.tick};
-        if (off + len < e) free_[off + len] = {e - off - len, keep.f, keep.tick};
-        withheld += len;
-    }
+    // Quarantine: ranges taken out of the free space for good.  A range is
+    // withheld where it is free now and, for the parts in use, when their
+    // block is released.
+    std::vector<std::pair<size_t, size_t>> bad;  // [begin, end)
     size_t withheld = 0;
+    void withhold_free(size_t b, size_t e) {
+        for (auto it = free_.begin(); it != free_.end();) {
+            const size_t fb = it->first, fe = fb + it->second.size;
+            const size_t lo = std::max(fb, b), hi = std::min(fe, e);
+            if (lo >= hi) {
+                ++it;
+                continue;
+            }
+            Free keep = it->second;
+            it = free_.erase(it);
+            if (lo > fb) free_[fb] = {lo - fb, keep.f, keep.tick};
+            if (fe > hi) free_[hi] = {fe - hi, keep.f, keep.tick};
+            withheld += hi - lo;
+            it = free_.upper_bound(lo);
+        }
+    }
+    void quarantine(size_t off, size_t len) {
+        bad.push_back({off, off + len});
+        withhold_free(off, off + len);
+    }
     void release(size_t off, size_t sz, const FenceSet &f) {
         sz = size_class(sz);
         used -= sz;
         free_[off] = {sz, f, ++tick};
+        for (const auto &r : bad)
+            if (r.first < off + sz && r.second > off) withhold_free(std::max(r.first, off), std::min(r.second, off + sz));
     }
 };
 
@@ -208,6 +220,7 @@ struct BuiltinDef {
     bool reduce_zero = true;  // reduce partials must start at the identity (else the kernel writes every cell)
     bool any_reduce_op = false;  // the reduce argument may use any of + * min max
     int write_through = -1;      // array slot whose halo replicas the kernel writes itself (ExecTask.rep_*)
+    bool pdl = false;            // the launch function supports programmatic dependent launch (ExecParams.pdl)
 };
 
 
@@ -303,15 +316,33 @@ struct lt_ctx {
     lt_config cfg{};
     bool dry = false;
     bool no_staged = false;  // LT_FLAG_NO_STAGED
+    bool no_pdl = false;     // LT_FLAG_NO_PDL
     int sm_count = 1;        // streaming multiprocessors of the device
-    float link_screen_h2d = 0, link_screen_d2h = 0;  // median GB/s of the host pool's pieces (screening)
-    size_t link_piece = 0;   // host-link chunk copies in pieces of this many bytes (0: whole chunks)
+    // Host-link copies being timed (quarantine of slow host-pool ranges).
+    struct LinkProbe {
+        cudaEvent_t a, b;
+        size_t host_off, bytes;
+        int dir;  // 0 fetch, 1 eviction
+    };
+    std::vector<LinkProbe> link_probes;
+    std::vector<cudaEvent_t> link_ev_pool;
+    double link_best[2] = {0, 0};  // fastest copy seen per direction (bytes per ms)
+    bool no_quarantine = false;     // LT_FLAG_NO_LINK_QUARANTINE
     bool poisoned = false;
     cudaStream_t st[NSTREAM] = {nullptr, nullptr, nullptr};
     uint64_t seq[NSTREAM] = {0, 0, 0};
     std::vector<cudaEvent_t> ev[NSTREAM];
     std::vector<uint64_t> evseq[NSTREAM];
     std::vector<int64_t> evtask[NSTREAM];
+    // Deferred fences: an operation may end without recording its event (so
+    // that two kernels follow each other directly on the stream and the
+    // second can use programmatic dependent launch).  Per ring slot: the
+    // deferred sequence number, its task, and the sequence number whose event
+    // covers it (0: none yet; ~0: known complete).  `deferred` lists the ones
+    // no event covers yet.
+    std::vector<uint64_t> dfseq[NSTREAM], dfcov[NSTREAM];
+    std::vector<int64_t> dftask[NSTREAM];
+    std::vector<uint64_t> deferred[NSTREAM];
     Arena dev, host;
     char *dev_base = nullptr;
     char *host_base = nullptr;
@@ -371,12 +402,14 @@ namespace rt {
 
 lt_status fail(lt_status st, const std::string &msg);
 const char *last_error_text();
-lt_status screen_host_pool(lt_ctx *c);
+lt_status link_copy_timed(lt_ctx *c, int dir, void *dst, const void *src, size_t n, size_t host_off);
+lt_status link_poll(lt_ctx *c);
 
 // fences and timing (rt_streams.cpp)
 lt_status op_begin(lt_ctx *c, int s, const char *kind);
 lt_status op_wait(lt_ctx *c, const FenceSet &f);
-lt_status op_end(lt_ctx *c, uint64_t *out_seq, const std::string &extra = "");
+lt_status op_end(lt_ctx *c, uint64_t *out_seq, const std::string &extra = "", bool defer = false);
+cudaEvent_t fence_event(lt_ctx *c, int t, uint64_t q, int64_t *task, bool flush);
 lt_status host_wait(lt_ctx *c, int s, uint64_t q);
 cudaEvent_t tev_get(lt_ctx *c);
 lt_status timeline_overlap(lt_ctx *c);
@@ -420,7 +453,6 @@ struct TimeScope {
 
 // memory (rt_memory.cpp)
 char *dptr(const lt_ctx *c, uint64_t off);
-cudaError_t link_copy(lt_ctx *c, void *dst, const void *src, size_t n, cudaMemcpyKind kind, cudaStream_t st);
 DView view_of(lt_ctx *c, const ArrayGeom &g, const ChunkGeom &cg, size_t off);
 bool droppable(const lt_ctx *c, const CState &s);
 bool pick_victim(lt_ctx *c, lt_array **va, int64_t *vc);

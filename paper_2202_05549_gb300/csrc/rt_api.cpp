@@ -11,7 +11,7 @@ const BuiltinDef kBuiltins[] = {
     {LT_K_STENCIL1D, "global i => write A0[i], read A1[i-1:i+1]", 2, {LT_F32, LT_F32}, {1, 1},
      k::prepare_stencil1d, k::launch_stencil1d},
     {LT_K_JACOBI2D, "global [i, j] => read A0[i-1:i+1, j-1:j+1], write A1[i, j]", 2, {LT_F32, LT_F32}, {2, 2},
-     k::prepare_jacobi2d, k::launch_jacobi2d, true, false, 1},
+     k::prepare_jacobi2d, k::launch_jacobi2d, true, false, 1, true},
     {LT_K_JACOBI3D, "global [k, i, j] => read A0[k-1:k+1, i-1:i+1, j-1:j+1], write A1[k, i, j]", 2,
      {LT_F32, LT_F32}, {3, 3}, k::prepare_jacobi3d, k::launch_jacobi3d},
     {LT_K_HIST256, "global i => read A0[i], reduce(+) A1[:]", 2, {LT_U8, LT_U32}, {1, 1}, k::prepare_hist256,
@@ -56,56 +56,6 @@ const size_t kNumBuiltins = sizeof(kBuiltins) / sizeof(kBuiltins[0]);
 }  // namespace rt
 }  // namespace lt
 
-namespace lt {
-namespace rt {
-
-// Screening of the pinned host pool.  On the GB300 machines measured, some
-// gigabytes of a large pinned allocation can copy to and from the GPU 5 to
-// 50 times slower than the rest (which parts differs from one process to the
-// next; it looks like where the pages lie physically).  A chunk whose host
-// copy lands there turns one link transfer into hundreds of milliseconds and
-// stalls the streaming pipeline.  So a pool of at least 8 GiB is timed once,
-// in pieces of 512 MiB, one copy each way through the start of the HBM pool
-// (CUDA events), and pieces slower than half the median in either direction
-// are withheld from allocation for the life of the context
-// (lt_stats.host_withheld_bytes).
-lt_status screen_host_pool(lt_ctx *c) {
-    const size_t piece = (size_t)512 << 20;
-    if (c->dry || c->host.cap < ((size_t)8 << 30) || c->dev.cap < piece) return LT_OK;
-    const size_t n = c->host.cap / piece;
-    cudaEvent_t e[3];
-    for (auto &x : e) CK(c, cudaEventCreate(&x));
-    std::vector<float> h2d(n), d2h(n);
-    cudaStream_t st = c->st[S_H2D];
-    for (size_t i = 0; i < n; ++i) {
-        char *hp = c->host_base + i * piece;
-        CK(c, cudaEventRecord(e[0], st));
-        CK(c, cudaMemcpyAsync(c->dev_base, hp, piece, cudaMemcpyHostToDevice, st));
-        CK(c, cudaEventRecord(e[1], st));
-        CK(c, cudaMemcpyAsync(hp, c->dev_base, piece, cudaMemcpyDeviceToHost, st));
-        CK(c, cudaEventRecord(e[2], st));
-        CK(c, cudaEventSynchronize(e[2]));
-        float a = 0, b = 0;
-        CK(c, cudaEventElapsedTime(&a, e[0], e[1]));
-        CK(c, cudaEventElapsedTime(&b, e[1], e[2]));
-        h2d[i] = (float)piece / std::max(a, 1e-3f);
-        d2h[i] = (float)piece / std::max(b, 1e-3f);
-    }
-    for (auto &x : e) cudaEventDestroy(x);
-    std::vector<float> sh = h2d, sd = d2h;
-    std::nth_element(sh.begin(), sh.begin() + n / 2, sh.end());
-    std::nth_element(sd.begin(), sd.begin() + n / 2, sd.end());
-    const float mh = sh[n / 2], md = sd[n / 2];
-    for (size_t i = 0; i < n; ++i)
-        if (h2d[i] < 0.5f * mh || d2h[i] < 0.5f * md) c->host.withhold(i * piece, piece);
-    c->link_screen_h2d = mh * 1e3f / 1e9f;  // bytes per ms -> GB/s
-    c->link_screen_d2h = md * 1e3f / 1e9f;
-    return LT_OK;
-}
-
-}  // namespace rt
-}  // namespace lt
-
 extern "C" {
 
 lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
@@ -114,11 +64,15 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     c->cfg = *cfg;
     c->dry = (cfg->flags & LT_FLAG_DRYRUN) != 0;
     c->no_staged = (cfg->flags & LT_FLAG_NO_STAGED) != 0;
-    if (const char *e = std::getenv("LT_LINK_PIECE_BYTES")) c->link_piece = (size_t)std::strtoull(e, nullptr, 10);
+    c->no_pdl = (cfg->flags & LT_FLAG_NO_PDL) != 0;
+    c->no_quarantine = (cfg->flags & LT_FLAG_NO_LINK_QUARANTINE) != 0;
     for (int s = 0; s < NSTREAM; ++s) {
         c->ev[s].assign(RING, nullptr);
         c->evseq[s].assign(RING, 0);
         c->evtask[s].assign(RING, -1);
+        c->dfseq[s].assign(RING, 0);
+        c->dfcov[s].assign(RING, 0);
+        c->dftask[s].assign(RING, -1);
     }
     size_t budget = cfg->hbm_budget_bytes;
     if (c->dry) {
@@ -161,10 +115,7 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     }
     c->host.init(cfg->host_pool_bytes, c->host_base);
     c->host.oldest_first = true;
-    if (!(cfg->flags & LT_FLAG_NO_LINK_SCREEN)) {
-        lt_status sst = screen_host_pool(cp);
-        if (sst) return sst;
-    }
+
     c->up_cap = (size_t)32 << 20;
     CK(cp, cudaHostAlloc((void **)&c->up_host, c->up_cap + TSLOTS * TSLOT_BYTES, cudaHostAllocDefault));
     CK(cp, cudaMalloc((void **)&c->up_dev, c->up_cap + TSLOTS * TSLOT_BYTES));
@@ -187,6 +138,11 @@ lt_status lt_ctx_destroy(lt_ctx *c) {
             cudaEventDestroy(t.b);
         }
         for (auto e : c->tev_pool) cudaEventDestroy(e);
+        for (auto &pr : c->link_probes) {
+            cudaEventDestroy(pr.a);
+            cudaEventDestroy(pr.b);
+        }
+        for (auto e : c->link_ev_pool) cudaEventDestroy(e);
         for (int i = 0; i < 2; ++i) {
             if (c->timer[i]) cudaEventDestroy(c->timer[i]);
             if (c->timer_join[i]) cudaEventDestroy(c->timer_join[i]);

@@ -538,6 +538,15 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             if ((st = op_wait(c, ex_wait))) return st;
             ep.ntasks = (int32_t)tasks.size();
             ep.uniform_ctas = 0;
+            // A launch that runs in device memory with no copy step before or
+            // after its kernel leaves the kernel next to the previous one on
+            // the compute stream: it starts as a programmatic dependent of
+            // that kernel and its fence event is deferred (an event between
+            // the two kernels would serialise them).  Not with per-operation
+            // timing (its events sit between the kernels anyway).
+            const bool pdl = def->pdl && !c->no_pdl && batched && temps.empty() && packs.empty() &&
+                             !(c->cfg.flags & LT_FLAG_TIMING);
+            ep.pdl = pdl ? 1 : 0;
             uint32_t ctas = def->prepare ? def->prepare(tasks.data(), (int)tasks.size(), ep) : 0;
             if (ctas != 0xFFFFFFFFu) ep.uniform_ctas = uniform_cta_count(tasks);
             if (ctas == 0xFFFFFFFFu)
@@ -589,7 +598,7 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 ex << "],\"variant\":" << ep.variant << ",\"ctas\":" << ctas << ",\"replicas\":" << reps.size();
                 extra = ex.str();
             }
-            if ((st = op_end(c, &exq, extra))) return st;
+            if ((st = op_end(c, &exq, extra, pdl))) return st;
             upload_done(c, roff, table.size(), exq);
             for (CState *d : wt_chunks) {
                 d->ready = FenceSet::one(S_COMP, exq);

@@ -28,15 +28,71 @@ DView view_of(lt_ctx *c, const ArrayGeom &g, const ChunkGeom &cg, size_t off) {
     return v;
 }
 
-// One chunk copy over the host link, in pieces of c->link_piece bytes when
-// that is set (0: one copy).
-cudaError_t link_copy(lt_ctx *c, void *dst, const void *src, size_t n, cudaMemcpyKind kind, cudaStream_t st) {
-    const size_t piece = c->link_piece ? c->link_piece : n;
-    for (size_t o = 0; o < n; o += piece) {
-        cudaError_t e = cudaMemcpyAsync((char *)dst + o, (const char *)src + o, std::min(piece, n - o), kind, st);
-        if (e != cudaSuccess) return e;
+// Quarantine of slow host-pool ranges.  On the GB300 machines measured, a few
+// 4 GiB stretches of a large pinned allocation copied to and from the GPU 2
+// to 20 times slower than the rest, for the whole life of the process (not in
+// the first process after the box started; which stretches differed from one
+// process to the next, mostly at the start and the end of the allocation; a
+// copy timed right after the allocation did not show it).  One such chunk in
+// a streaming launch stalls the pipeline for hundreds of milliseconds.  So
+// every fetch and eviction of at least 256 MiB is timed with two events; a
+// copy that ran at less than half the fastest copy seen in its direction
+// marks its host range bad, and the host pool withholds bad ranges from
+// allocation (at once where they are free, else when their block is
+// released), up to a quarter of the pool (lt_stats.host_withheld_bytes).
+lt_status link_copy_timed(lt_ctx *c, int dir, void *dst, const void *src, size_t n, size_t host_off) {
+    cudaStream_t st = c->st[dir == 0 ? S_H2D : S_D2H];
+    const cudaMemcpyKind kind = dir == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    const bool probe = !c->no_quarantine && n >= ((size_t)256 << 20);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (probe) {
+        for (auto &e : ev) {
+            if (!c->link_ev_pool.empty()) {
+                e = c->link_ev_pool.back();
+                c->link_ev_pool.pop_back();
+            } else {
+                CK(c, cudaEventCreate(&e));
+            }
+        }
+        CK(c, cudaEventRecord(ev[0], st));
     }
-    return cudaSuccess;
+    CK(c, cudaMemcpyAsync(dst, src, n, kind, st));
+    if (probe) {
+        CK(c, cudaEventRecord(ev[1], st));
+        c->link_probes.push_back({ev[0], ev[1], host_off, n, dir});
+    }
+    return LT_OK;
+}
+
+// Rate the timed copies that have finished; quarantine the slow ones' ranges.
+lt_status link_poll(lt_ctx *c) {
+    if (c->dry || c->link_probes.empty()) return LT_OK;
+    std::vector<lt_ctx::LinkProbe> keep;
+    std::vector<lt_ctx::LinkProbe> done;
+    for (auto &pr : c->link_probes) {
+        cudaError_t q = cudaEventQuery(pr.b);
+        if (q == cudaErrorNotReady) {
+            keep.push_back(pr);
+            continue;
+        }
+        CK(c, q);
+        done.push_back(pr);
+    }
+    c->link_probes.swap(keep);
+    for (auto &pr : done) {
+        float ms = 0;
+        CK(c, cudaEventElapsedTime(&ms, pr.a, pr.b));
+        c->link_ev_pool.push_back(pr.a);
+        c->link_ev_pool.push_back(pr.b);
+        const double rate = (double)pr.bytes / std::max(ms, 1e-3f);
+        double &best = c->link_best[pr.dir];
+        if (rate > best) best = rate;
+        if (rate < 0.5 * best && c->host.withheld + pr.bytes <= c->host.cap / 4) {
+            c->host.quarantine(pr.host_off, pr.bytes);
+            c->stats.host_quarantined++;
+        }
+    }
+    return LT_OK;
 }
 
 // ---------------------------------------------------------------- memory manager
@@ -140,7 +196,8 @@ lt_status evict(lt_ctx *c, lt_array *a, int64_t ci) {
     if (st) return st;
     if (!c->dry) {
         TimeScope ts(c, CAT_D2H);
-        CK(c, link_copy(c, c->host_base + hoff, dptr(c, s.off), cg.bytes, cudaMemcpyDeviceToHost, c->st[S_D2H]));
+        if ((st = link_poll(c))) return st;
+        if ((st = link_copy_timed(c, 1, c->host_base + hoff, dptr(c, s.off), cg.bytes, hoff))) return st;
     }
     uint64_t q;
     std::ostringstream ex;
@@ -188,8 +245,8 @@ lt_status ensure_dev(lt_ctx *c, lt_array *a, int64_t ci, bool need_data, bool so
             if (st) return st;
             if (!c->dry) {
                 TimeScope ts(c, CAT_H2D);
-                CK(c, link_copy(c, dptr(c, off), c->host_base + s.off, cg.bytes, cudaMemcpyHostToDevice,
-                                c->st[S_H2D]));
+                if ((st = link_poll(c))) return st;
+                if ((st = link_copy_timed(c, 0, dptr(c, off), c->host_base + s.off, cg.bytes, s.off))) return st;
             }
             uint64_t q;
             std::ostringstream ex;

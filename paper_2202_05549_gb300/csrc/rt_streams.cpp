@@ -24,37 +24,85 @@ lt_status op_begin(lt_ctx *c, int s, const char *kind) {
     return LT_OK;
 }
 
+// The event that marks fence (t, q) complete, or null when the operation is
+// known to be complete (its event slot was reused, which the bounded run-ahead
+// allows only after that event completed, or a synchronize passed it).  A
+// deferred fence maps to the event of a later operation on the same stream;
+// if none has been recorded yet and `flush` is set, one is recorded now (it
+// fires after everything enqueued on stream t so far: a later point than the
+// fence, which is safe).  *task: the operation's task id (for the log).
+cudaEvent_t fence_event(lt_ctx *c, int t, uint64_t q, int64_t *task, bool flush) {
+    const int slot = (int)(q % RING);
+    *task = -1;
+    if (c->evseq[t][slot] == q) {
+        *task = c->evtask[t][slot];
+        return c->ev[t][slot];
+    }
+    if (c->dfseq[t][slot] != q) return nullptr;
+    *task = c->dftask[t][slot];
+    uint64_t cov = c->dfcov[t][slot];
+    if (cov == ~(uint64_t)0) return nullptr;
+    if (cov == 0) {
+        if (!flush || c->dry) return nullptr;
+        // cover every deferred fence of stream t with one event in the ring
+        // slot of the newest of them (a slot its own deferral left unused)
+        const uint64_t last = c->deferred[t].back();
+        const int ls = (int)(last % RING);
+        if (c->evseq[t][ls] != 0 && cudaEventSynchronize(c->ev[t][ls]) != cudaSuccess) return nullptr;
+        if (cudaEventRecord(c->ev[t][ls], c->st[t]) != cudaSuccess) return nullptr;
+        c->evseq[t][ls] = last;
+        c->evtask[t][ls] = c->dftask[t][ls];
+        for (uint64_t d : c->deferred[t]) c->dfcov[t][d % RING] = last;
+        c->deferred[t].clear();
+        cov = last;
+    }
+    const int cs = (int)(cov % RING);
+    return c->evseq[t][cs] == cov ? c->ev[t][cs] : nullptr;
+}
+
 lt_status op_wait(lt_ctx *c, const FenceSet &f) {
     int s = c->cur_stream;
     for (int t = 0; t < NSTREAM; ++t) {
         uint64_t q = f.q[t];
         if (!q) continue;
-        int slot = (int)(q % RING);
-        bool live = c->evseq[t][slot] == q;
-        if (live) {
-            int64_t pt = c->evtask[t][slot];
-            if (pt >= 0 && std::find(c->cur_deps.begin(), c->cur_deps.end(), pt) == c->cur_deps.end()) {
-                c->cur_deps.push_back(pt);
-                c->stats.deps++;
-            }
+        int64_t pt = -1;
+        // a fence on the waiting stream itself needs no event (stream order)
+        cudaEvent_t e = fence_event(c, t, q, &pt, t != s);
+        if (pt >= 0 && (e || t == s) &&
+            std::find(c->cur_deps.begin(), c->cur_deps.end(), pt) == c->cur_deps.end()) {
+            c->cur_deps.push_back(pt);
+            c->stats.deps++;
         }
-        if (t == s || c->dry || !live) continue;
-        CK(c, cudaStreamWaitEvent(c->st[s], c->ev[t][slot], 0));
+        if (t == s || c->dry || !e) continue;
+        CK(c, cudaStreamWaitEvent(c->st[s], e, 0));
     }
     return LT_OK;
 }
 
-// Finish the current operation: record its fence on its stream.
-lt_status op_end(lt_ctx *c, uint64_t *out_seq, const std::string &extra) {
+// Finish the current operation: record its fence on its stream.  defer: do
+// not record an event now (see lt_ctx::deferred); a later operation's event,
+// or one recorded when something waits for this fence, stands for it.
+lt_status op_end(lt_ctx *c, uint64_t *out_seq, const std::string &extra, bool defer) {
     int s = c->cur_stream;
     uint64_t q = ++c->seq[s];
     int slot = (int)(q % RING);
-    if (!c->dry) {
-        if (c->evseq[s][slot] != 0) CK(c, cudaEventSynchronize(c->ev[s][slot]));  // bounded run-ahead
-        CK(c, cudaEventRecord(c->ev[s][slot], c->st[s]));
+    if (c->dry) defer = false;  // dry runs keep the plain bookkeeping the host-logic tests inspect
+    if (defer && c->deferred[s].size() >= RING / 2) defer = false;
+    if (defer) {
+        c->dfseq[s][slot] = q;
+        c->dfcov[s][slot] = 0;
+        c->dftask[s][slot] = c->cur_task;
+        c->deferred[s].push_back(q);
+    } else {
+        if (!c->dry) {
+            if (c->evseq[s][slot] != 0) CK(c, cudaEventSynchronize(c->ev[s][slot]));  // bounded run-ahead
+            CK(c, cudaEventRecord(c->ev[s][slot], c->st[s]));
+        }
+        c->evseq[s][slot] = q;
+        c->evtask[s][slot] = c->cur_task;
+        for (uint64_t d : c->deferred[s]) c->dfcov[s][d % RING] = q;  // this event fires after them
+        c->deferred[s].clear();
     }
-    c->evseq[s][slot] = q;
-    c->evtask[s][slot] = c->cur_task;
     if (c->log_on) {
         c->log << ",\"deps\":[";
         for (size_t i = 0; i < c->cur_deps.size(); ++i) c->log << (i ? "," : "") << c->cur_deps[i];
@@ -66,8 +114,9 @@ lt_status op_end(lt_ctx *c, uint64_t *out_seq, const std::string &extra) {
 
 lt_status host_wait(lt_ctx *c, int s, uint64_t q) {
     if (c->dry || !q) return LT_OK;
-    int slot = (int)(q % RING);
-    if (c->evseq[s][slot] == q) CK(c, cudaEventSynchronize(c->ev[s][slot]));
+    int64_t task;
+    cudaEvent_t e = fence_event(c, s, q, &task, true);
+    if (e) CK(c, cudaEventSynchronize(e));
     return LT_OK;
 }
 
@@ -269,6 +318,11 @@ int32_t uniform_cta_count(const std::vector<ExecTask> &tasks) {
 lt_status sync_all(lt_ctx *c) {
     if (c->dry) return LT_OK;
     for (int s = 0; s < NSTREAM; ++s) CK(c, cudaStreamSynchronize(c->st[s]));
+    if (lt_status lp = link_poll(c)) return lp;
+    for (int s = 0; s < NSTREAM; ++s) {  // every deferred fence is complete now
+        for (uint64_t d : c->deferred[s]) c->dfcov[s][d % RING] = ~(uint64_t)0;
+        c->deferred[s].clear();
+    }
     uint32_t e = 0;
     CK(c, cudaMemcpy(&e, c->err_word, 4, cudaMemcpyDeviceToHost));
     if (e) {

@@ -355,3 +355,32 @@ def test_multi_step_out_of_core_spill_bit_exact():
         got = U.read()
     assert s["evictions"] > 0 and s["fetches"] > 0
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("flags", [0, L.LT_FLAG_NO_PDL])
+def test_dependent_launches_and_deferred_fences_stay_exact(flags):
+    # In-place launches run as programmatic dependents with their fence
+    # events deferred.  A fill that needs the memory then evicts the results
+    # (the eviction on the copy stream must wait for the deferred kernels),
+    # and the next launches fetch them back.
+    ny, nx, iters = 1536, 2048, 9
+    u0 = si.uniform_field(si.SEED_JACOBI_INCORE, 5, ny, nx)
+    want = oracle.jacobi2d(u0, 2 * iters)
+    dist = lt.Dist.tiles((512, 512), halo=(1, 1))
+    field = 4 * ny * nx
+    with lt.Context(hbm_budget=int(2.6 * field), host_pool=4 * field, flags=flags) as ctx:
+        U = ctx.array(lt.F32, (ny, nx), dist)
+        V = ctx.array(lt.F32, (ny, nx), dist)
+        W = ctx.array(lt.F32, (ny, nx), dist)
+        U.write(u0)
+        k = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=(nx, ny), block=(128, 4), superblock=(512, 512), args=[U, V])
+            U, V = V, U
+        W.fill(L.LT_INIT_UNIFORM, seed=9, stream=0)   # evicts chunks written by the launches above
+        for _ in range(iters):
+            k.launch(grid=(nx, ny), block=(128, 4), superblock=(512, 512), args=[U, V])
+            U, V = V, U
+        ctx.synchronize()
+        assert ctx.stats()["evictions"] > 0
+        assert np.array_equal(U.read(), want)
