@@ -124,12 +124,26 @@ struct FillDesc {
 };
 
 // Batched persistent kernel: instance tables and the work queue.
+// One part of a batched Jacobi instance: a superblock of its launch, whose
+// cells it computes from the part's chunk of the input buffer into the
+// part's chunk of the output buffer (the buffers swap every iteration).
 struct BatchJacobi {
-    uint64_t u, v;     // views (global index base) of the two ping-pong buffers
+    uint64_t u, v;     // views (global index base) of the part's chunks of the two ping-pong buffers
     int64_t su, sv;    // row strides (elements)
-    int64_t ny, nx;
-    uint32_t tiles;    // work items per iteration
-    uint32_t done_off; // first completion counter (one per iteration)
+    int64_t ny, nx;    // the instance's global shape
+    int64_t y0, y1, x0, x1;  // output rows and columns of the part (inclusive, x0 % 4 == 0)
+    uint32_t tiles;    // work items per iteration of the instance (all its parts' tiles and replica items)
+    uint32_t done_off; // first completion counter of the instance (one per iteration)
+};
+// Halo replica of a chunked instance: cells [lo, hi] that part `part`
+// computes are also stored into the halo of another chunk (du / dv: that
+// chunk in either buffer), from the same input with the same operations.
+struct BatchRep {
+    uint64_t du, dv;
+    int64_t sdu, sdv;
+    int64_t lo[2], hi[2];  // rows, columns (inclusive)
+    uint32_t part;
+    uint32_t pad;
 };
 struct BatchHist {
     uint64_t x;   // u8 array (contiguous, 128-byte aligned)
@@ -137,16 +151,18 @@ struct BatchHist {
     uint64_t h;   // 256 u32 bins (contiguous)
 };
 struct BatchItem {
-    uint32_t kind_inst;  // kind << 30 | instance (0 Jacobi tile, 1 histogram slice)
+    uint32_t kind_inst;  // kind << 30 | index: 0 Jacobi tile (of part `index`), 1 histogram slice,
+                         // 2 Jacobi replica cells (of replica `index`)
     uint32_t iter;       // Jacobi iteration
-    uint32_t row0;       // first row (Jacobi) or slice index (histogram)
-    uint32_t nrows;
+    uint32_t row0;       // first row (tile), slice index (histogram) or first cell (replica)
+    uint32_t nrows;      // rows (tile) or cells (replica)
 };
 struct BatchParams {
     const BatchItem *items;
     uint64_t nitems;
     const BatchJacobi *jac;
     const BatchHist *hist;
+    const BatchRep *reps;
     uint32_t *head;   // queue head (zeroed before every run)
     uint32_t *done;   // completion counters (zeroed before every run)
     uint32_t *abort;  // set when a bounded wait expires

@@ -5,7 +5,12 @@
 //           iteration (ping-pong between the instance's two buffers);
 //   kind 1  histogram slice: bytes [slice*HS, (slice+1)*HS) of one array,
 //           counted in shared memory and added to H with integer atomics
-//           (the reduce(+) of Sec. 2.3 folded into one level).
+//           (the reduce(+) of Sec. 2.3 folded into one level);
+//   kind 2  halo replica cells of a chunked instance: cells of one part's
+//           output that other chunks hold in their halos, computed from the
+//           part's input like its own cells and stored into those halos.
+// A Jacobi instance is one or more parts (the superblocks of its launch, one
+// chunk each); its tiles and replica items of one iteration count together.
 // Items are queued iteration-major, so every item an item waits for was
 // dequeued before it by a resident CTA: a tile of iteration t waits (bounded)
 // until all tiles of iteration t-1 of its instance are done, and no wait can
@@ -54,8 +59,8 @@ __global__ void __launch_bounds__(BT, BOCC) batch_kernel(BatchParams P) {
         if (s_stop) break;
         const BatchItem w = P.items[s_item[par]];
         const uint32_t kind = w.kind_inst >> 30, inst = w.kind_inst & 0x3FFFFFFFu;
-        if (kind == 0) {
-            const BatchJacobi J = P.jac[inst];
+        if (kind != 1) {
+            const BatchJacobi J = P.jac[kind == 0 ? inst : P.reps[inst].part];
             if (w.iter > 0) {
                 if (tid == 0) {
                     const uint32_t *cnt = P.done + J.done_off + w.iter - 1;
@@ -74,18 +79,37 @@ __global__ void __launch_bounds__(BT, BOCC) batch_kernel(BatchParams P) {
             }
             const bool even = (w.iter & 1u) == 0;
             const float *src = (const float *)(even ? J.u : J.v);
-            float *dst = (float *)(even ? J.v : J.u);
-            const int64_t ss = even ? J.su : J.sv, sd = even ? J.sv : J.su;
+            const int64_t ss = even ? J.su : J.sv;
             const int64_t ny = J.ny, nx = J.nx;
-            const int64_t ye = min((int64_t)(w.row0 + w.nrows) - 1, ny - 1);
-            const uint32_t sx = (uint32_t)((nx + JCOLS - 1) / JCOLS), sy = (w.nrows + BR - 1) / BR;
-            // strip s = cy * sx + cx, s = warp, warp + 8, ...; (cx, cy) advance
-            // without a division per strip (32-bit: tiles are small)
-            uint32_t cx = warp % sx, cy = warp / sx;
-            for (uint32_t s = warp; s < sx * sy; s += BT / 32) {
-                const int64_t js = (int64_t)cx * JCOLS, r0 = (int64_t)w.row0 + (int64_t)cy * BR;
-                if (r0 <= ye) jacobi_strip<true, BR>(src, ss, dst, sd, ny, nx, js, r0, nx - 1, ye, lane);
-                for (cx += BT / 32; cx >= sx; cx -= sx) ++cy;
+            if (kind == 0) {
+                float *dst = (float *)(even ? J.v : J.u);
+                const int64_t sd = even ? J.sv : J.su;
+                const int64_t ye = min((int64_t)(w.row0 + w.nrows) - 1, J.y1);
+                const uint32_t sx = (uint32_t)((J.x1 - J.x0 + JCOLS) / JCOLS), sy = (w.nrows + BR - 1) / BR;
+                // strip s = cy * sx + cx, s = warp, warp + 8, ...; (cx, cy) advance
+                // without a division per strip (32-bit: tiles are small)
+                uint32_t cx = warp % sx, cy = warp / sx;
+                for (uint32_t s = warp; s < sx * sy; s += BT / 32) {
+                    const int64_t js = J.x0 + (int64_t)cx * JCOLS, r0 = (int64_t)w.row0 + (int64_t)cy * BR;
+                    if (r0 <= ye) jacobi_strip<true, BR>(src, ss, dst, sd, ny, nx, js, r0, J.x1, ye, lane);
+                    for (cx += BT / 32; cx >= sx; cx -= sx) ++cy;
+                }
+            } else {
+                // replica cells: the same five-point sum and division as the strips
+                const BatchRep R = P.reps[inst];
+                float *dst = (float *)(even ? R.dv : R.du);
+                const int64_t sd = even ? R.sdv : R.sdu;
+                const int64_t wdt = R.hi[1] - R.lo[1] + 1;
+                for (uint32_t e = tid; e < w.nrows; e += BT) {
+                    const int64_t l = (int64_t)w.row0 + e, i = R.lo[0] + l / wdt, j = R.lo[1] + l % wdt;
+                    const float *up = src + i * ss + j;
+                    const float c = ld1<true>(up);
+                    const float n = i > 0 ? ld1<true>(up - ss) : 0.f;
+                    const float so = i + 1 < ny ? ld1<true>(up + ss) : 0.f;
+                    const float we = j > 0 ? ld1<true>(up - 1) : 0.f;
+                    const float ea = j + 1 < nx ? ld1<true>(up + 1) : 0.f;
+                    dst[i * sd + j] = j5(c, n, so, we, ea);
+                }
             }
             __threadfence();
             __syncthreads();

@@ -307,6 +307,20 @@ struct BatchCache {
     cudaGraphExec_t exec = nullptr;
 };
 
+// The fused form of a batch of launches (rt_batch.cpp).
+struct BatchShape {
+    struct Jac {
+        lt_array *u, *v;
+        int repeat;
+        std::shared_ptr<const PlanBundle> plan;  // the launch's plan: superblocks over direct chunks
+    };
+    struct Hist {
+        lt_array *x, *h;
+    };
+    std::vector<Jac> jac;
+    std::vector<Hist> hist;
+};
+
 struct UploadUse {
     size_t off, end;
     uint64_t seq;
@@ -362,6 +376,7 @@ struct lt_ctx {
     std::vector<std::unique_ptr<lt_array>> arrays;       // creation order (iteration order)
     std::unordered_set<const lt_array *> array_set;      // membership: handles are checked on every call
     std::vector<uint64_t> batch_checked;  // the last fused batch whose launches passed prepare_plan
+    std::shared_ptr<BatchShape> batch_shape;  // and its fused form
     std::vector<std::unique_ptr<lt_kernel>> kernels;
     uint64_t clock = 0;
     int64_t launch_id = 0;

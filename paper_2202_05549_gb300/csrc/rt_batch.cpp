@@ -5,45 +5,76 @@
 extern "C" {
 
 // ---------------------------------------------------------------- batches
-struct BatchShape {
-    struct Jac {
-        lt_array *u, *v;
-        int repeat;
-    };
-    struct Hist {
-        lt_array *x, *h;
-    };
-    std::vector<Jac> jac;
-    std::vector<Hist> hist;
-};
-
 // Tables of one fused batch for tile height th and histogram slice hs;
 // `iters_cap` > 0 limits every instance to that many iterations (tuning).
+// A Jacobi instance becomes one part per superblock of its launch (one chunk
+// of each buffer) and one replica table entry per halo box its parts keep
+// current; both buffers share the distribution, so the same chunks serve
+// when they swap roles.
 static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int hs, int iters_cap,
-                         std::vector<BatchJacobi> *jac, std::vector<BatchHist> *hist, std::vector<BatchItem> *items,
-                         size_t *ncounters, bool stall = false) {
+                         std::vector<BatchJacobi> *jac, std::vector<BatchHist> *hist, std::vector<BatchRep> *reps,
+                         std::vector<BatchItem> *items, size_t *ncounters, bool stall = false) {
     jac->clear();
     hist->clear();
+    reps->clear();
     items->clear();
+    constexpr uint32_t REP_CELLS = 2048;  // replica cells per work item
+    struct Inst {
+        uint32_t part0, nparts, rep0, nreps, per_iter;
+        int repeat;
+    };
+    std::vector<Inst> inst;
     uint32_t done = 0;
     int rmax = 0;
     for (size_t q = 0; q < bs.jac.size(); ++q) {
         const auto &J = bs.jac[q];
         const ArrayGeom &g = J.u->g;
-        const ChunkGeom &cu = g.chunks[0], &cv = J.v->g.chunks[0];
-        BatchJacobi b{};
-        b.u = (uint64_t)(uintptr_t)(dptr(c, J.u->cs[0].off));
-        b.v = (uint64_t)(uintptr_t)(dptr(c, J.v->cs[0].off));
-        b.su = cu.stride[0];
-        b.sv = cv.stride[0];
-        b.ny = g.shape[0];
-        b.nx = g.shape[1];
-        b.tiles = (uint32_t)((g.shape[0] + th - 1) / th);
-        b.done_off = done;
-        int r = iters_cap > 0 ? std::min(iters_cap, J.repeat) : J.repeat;
-        done += (uint32_t)r;
-        rmax = std::max(rmax, r);
-        jac->push_back(b);
+        Inst in{(uint32_t)jac->size(), 0, (uint32_t)reps->size(), 0, 0, 0};
+        for (const auto &sb : J.plan->plan.sbs) {
+            const ArgPlan *au = nullptr, *av = nullptr;
+            for (const auto &ap : sb.args) {
+                if (ap.kind != ARG_DIRECT) continue;
+                if (ap.mode == MODE_READ) au = &ap; else av = &ap;
+            }
+            BatchJacobi b{};
+            const int64_t cu = au->chunk, cv = av->chunk;
+            b.u = view_of(c, g, g.chunks[(size_t)cu], J.u->cs[(size_t)cu].off).base;
+            b.v = view_of(c, J.v->g, J.v->g.chunks[(size_t)cv], J.v->cs[(size_t)cv].off).base;
+            b.su = g.chunks[(size_t)cu].stride[0];
+            b.sv = J.v->g.chunks[(size_t)cv].stride[0];
+            b.ny = g.shape[0];
+            b.nx = g.shape[1];
+            b.y0 = sb.threads.lo[1];
+            b.y1 = std::min<int64_t>(sb.threads.hi[1], g.shape[0] - 1);
+            b.x0 = sb.threads.lo[0];
+            b.x1 = std::min<int64_t>(sb.threads.hi[0], g.shape[1] - 1);
+            b.done_off = done;
+            const uint32_t part = (uint32_t)jac->size();
+            jac->push_back(b);
+            in.nparts++;
+            in.per_iter += (uint32_t)((b.y1 - b.y0 + th) / th);
+            for (const auto &pc : av->replicas) {
+                BatchRep r{};
+                const int64_t cj = pc.chunk;
+                r.du = view_of(c, g, g.chunks[(size_t)cj], J.u->cs[(size_t)cj].off).base;
+                r.dv = view_of(c, J.v->g, J.v->g.chunks[(size_t)cj], J.v->cs[(size_t)cj].off).base;
+                r.sdu = g.chunks[(size_t)cj].stride[0];
+                r.sdv = J.v->g.chunks[(size_t)cj].stride[0];
+                for (int d = 0; d < 2; ++d) {
+                    r.lo[d] = pc.box.lo[d];
+                    r.hi[d] = pc.box.hi[d];
+                }
+                r.part = part;
+                reps->push_back(r);
+                in.nreps++;
+                in.per_iter += (uint32_t)((pc.box.volume() + REP_CELLS - 1) / REP_CELLS);
+            }
+        }
+        for (uint32_t i = 0; i < in.nparts; ++i) (*jac)[in.part0 + i].tiles = in.per_iter;
+        in.repeat = iters_cap > 0 ? std::min(iters_cap, J.repeat) : J.repeat;
+        done += (uint32_t)in.repeat;
+        rmax = std::max(rmax, in.repeat);
+        inst.push_back(in);
     }
     for (size_t h = 0; h < bs.hist.size(); ++h) {
         BatchHist b{};
@@ -55,24 +86,32 @@ static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int hs, int it
         for (int64_t k = 0; k < ns; ++k) items->push_back({(1u << 30) | (uint32_t)h, 0u, (uint32_t)k, 0u});
     }
     for (int t = 0; t < rmax; ++t)
-        for (size_t q = 0; q < bs.jac.size(); ++q) {
-            int r = iters_cap > 0 ? std::min(iters_cap, bs.jac[q].repeat) : bs.jac[q].repeat;
-            if (t >= r) continue;
-            if (stall && t == 0 && r >= 2) continue;  // test hook: iteration 1 then waits forever (bounded)
-            const BatchJacobi &b = (*jac)[q];
-            for (uint32_t k = 0; k < b.tiles; ++k)
-                items->push_back({(uint32_t)q, (uint32_t)t, k * (uint32_t)th,
-                                  (uint32_t)std::min<int64_t>(th, b.ny - (int64_t)k * th)});
+        for (const Inst &in : inst) {
+            if (t >= in.repeat) continue;
+            if (stall && t == 0 && in.repeat >= 2) continue;  // test hook: iteration 1 then waits forever (bounded)
+            for (uint32_t p = in.part0; p < in.part0 + in.nparts; ++p) {
+                const BatchJacobi &b = (*jac)[p];
+                for (int64_t r = b.y0; r <= b.y1; r += th)
+                    items->push_back({p, (uint32_t)t, (uint32_t)r, (uint32_t)std::min<int64_t>(th, b.y1 - r + 1)});
+            }
+            for (uint32_t ri = in.rep0; ri < in.rep0 + in.nreps; ++ri) {
+                const BatchRep &r = (*reps)[ri];
+                const uint64_t cells = (uint64_t)(r.hi[0] - r.lo[0] + 1) * (uint64_t)(r.hi[1] - r.lo[1] + 1);
+                for (uint64_t e = 0; e < cells; e += REP_CELLS)
+                    items->push_back({(2u << 30) | ri, (uint32_t)t, (uint32_t)e,
+                                      (uint32_t)std::min<uint64_t>(REP_CELLS, cells - e)});
+            }
         }
     *ncounters = (size_t)done + 2;  // + queue head + abort flag
 }
 
 // Upload the tables into a fresh device block; fills cache fields.
 static lt_status batch_upload(lt_ctx *c, BatchCache *bc, const std::vector<BatchJacobi> &jac,
-                              const std::vector<BatchHist> &hist, const std::vector<BatchItem> &items,
-                              size_t ncounters) {
+                              const std::vector<BatchHist> &hist, const std::vector<BatchRep> &reps,
+                              const std::vector<BatchItem> &items, size_t ncounters) {
     size_t o_jac = 0, o_hist = align_up(jac.size() * sizeof(BatchJacobi), 256);
-    size_t o_items = o_hist + align_up(hist.size() * sizeof(BatchHist), 256);
+    size_t o_reps = o_hist + align_up(hist.size() * sizeof(BatchHist), 256);
+    size_t o_items = o_reps + align_up(reps.size() * sizeof(BatchRep), 256);
     size_t o_cnt = o_items + align_up(items.size() * sizeof(BatchItem), 256);
     size_t total = o_cnt + align_up(ncounters * 4, 256);
     FenceSet f;
@@ -83,6 +122,7 @@ static lt_status batch_upload(lt_ctx *c, BatchCache *bc, const std::vector<Batch
     char *base = dptr(c, bc->off);
     if (!jac.empty()) CK(c, cudaMemcpy(base + o_jac, jac.data(), jac.size() * sizeof(BatchJacobi), cudaMemcpyHostToDevice));
     if (!hist.empty()) CK(c, cudaMemcpy(base + o_hist, hist.data(), hist.size() * sizeof(BatchHist), cudaMemcpyHostToDevice));
+    if (!reps.empty()) CK(c, cudaMemcpy(base + o_reps, reps.data(), reps.size() * sizeof(BatchRep), cudaMemcpyHostToDevice));
     if (!items.empty())
         CK(c, cudaMemcpy(base + o_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
     BatchParams &bp = bc->bp;
@@ -90,6 +130,7 @@ static lt_status batch_upload(lt_ctx *c, BatchCache *bc, const std::vector<Batch
     bp.nitems = items.size();
     bp.jac = (const BatchJacobi *)(base + o_jac);
     bp.hist = (const BatchHist *)(base + o_hist);
+    bp.reps = (const BatchRep *)(base + o_reps);
     bp.head = (uint32_t *)(base + o_cnt);
     bp.abort = (uint32_t *)(base + o_cnt + 4);
     bp.done = (uint32_t *)(base + o_cnt + 8);
@@ -135,30 +176,6 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
             d[i].nargs != (int32_t)d[i].kernel->params.size() || (d[i].nargs && !d[i].args))
             return fail(LT_ERR_INVALID_ARG, "bad launch descriptor " + std::to_string(i));
     }
-    // eligibility of the fused form
-    BatchShape bs;
-    bool fused = !(flags & LT_BATCH_PLAIN) && !c->dry && n > 0;
-    std::unordered_set<const lt_array *> seen;
-    for (int32_t i = 0; i < n && fused; ++i) {
-        lt_kernel *k = d[i].kernel;
-        std::vector<lt_array *> arrs;
-        for (int32_t p = 0; p < d[i].nargs; ++p)
-            if (k->params[(size_t)p].is_array) arrs.push_back(find_array(c, d[i].args[p].array));
-        for (lt_array *a : arrs) {
-            if (!a || a->cs.size() != 1 || !seen.insert(a).second) fused = false;
-        }
-        if (!fused) break;
-        if (k->def->id == LT_K_JACOBI2D && arrs.size() == 2 && arrs[0] != arrs[1] &&
-            arrs[0]->g.shape[0] == arrs[1]->g.shape[0] && arrs[0]->g.shape[1] == arrs[1]->g.shape[1] &&
-            d[i].grid.x >= (uint64_t)arrs[0]->g.shape[1] && d[i].grid.y >= (uint64_t)arrs[0]->g.shape[0])
-            bs.jac.push_back({arrs[0], arrs[1], d[i].repeat});
-        else if (k->def->id == LT_K_HIST256 && arrs.size() == 2 && arrs[1]->g.shape[0] == 256 && d[i].repeat == 1 &&
-                 d[i].grid.x >= (uint64_t)arrs[0]->g.shape[0])
-            bs.hist.push_back({arrs[0], arrs[1]});
-        else
-            fused = false;
-    }
-    if (!fused) return batch_plain(c, d, n);
     // The plain form validates annotations per launch; the fused form checks
     // each launch once and skips the check while the batch repeats exactly
     // (same kernels, grids, blocks, superblocks, arguments and repeats; array
@@ -177,47 +194,118 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
             chk.insert(chk.end(), {a ? (uint64_t)a->id : ~0ull, fb, (uint64_t)e.args[p].i});
         }
     }
-    if (chk != c->batch_checked) {
+    const bool repeat_batch = chk == c->batch_checked && c->batch_shape;
+    if (!repeat_batch) {
         c->batch_checked.clear();
+        c->batch_shape.reset();
         for (int32_t i = 0; i < n; ++i) {
             std::shared_ptr<const PlanBundle> b;
             std::vector<lt_array *> parr;
             if ((st = prepare_plan(c, d[i].kernel, d[i].grid, d[i].block, &d[i].wd, d[i].args, d[i].nargs, &b, &parr)))
                 return st;
         }
-        c->batch_checked = std::move(chk);
     }
+    if (repeat_batch && !(flags & LT_BATCH_PLAIN)) {
+        // an identical batch: its shape (and plans) are those of the last call
+    } else if (repeat_batch) {
+        return batch_plain(c, d, n);
+    } else {
+        // eligibility of the fused form: Jacobi instances whose two buffers share
+        // one distribution and whose every superblock reads and writes a single
+        // chunk of each (halo replicas are kept by the batch kernel), superblocks
+        // starting on a multiple of 4 columns; histograms of one-chunk arrays
+        auto shape = std::make_shared<BatchShape>();
+        BatchShape &bs = *shape;
+        bool fused = !(flags & LT_BATCH_PLAIN) && !c->dry && n > 0;
+        std::unordered_set<const lt_array *> seen;
+        auto same_dist = [](const ArrayGeom &a, const ArrayGeom &b) {
+            if (a.nd != b.nd || a.dist.kind != b.dist.kind || a.dist.order != b.dist.order) return false;
+            for (int x = 0; x < 3; ++x)
+                if (a.shape[x] != b.shape[x] || a.dist.chunk[x] != b.dist.chunk[x] || a.dist.halo[x] != b.dist.halo[x])
+                    return false;
+            return true;
+        };
+        for (int32_t i = 0; i < n && fused; ++i) {
+            lt_kernel *k = d[i].kernel;
+            std::vector<lt_array *> arrs;
+            for (int32_t p = 0; p < d[i].nargs; ++p)
+                if (k->params[(size_t)p].is_array) arrs.push_back(find_array(c, d[i].args[p].array));
+            for (lt_array *a : arrs) {
+                if (!a || !seen.insert(a).second) fused = false;
+            }
+            if (!fused) break;
+            if (k->def->id == LT_K_JACOBI2D && arrs.size() == 2 && arrs[0] != arrs[1] && same_dist(arrs[0]->g, arrs[1]->g) &&
+                arrs[0]->g.dist.order == LT_ORDER_ROW && d[i].grid.x >= (uint64_t)arrs[0]->g.shape[1] &&
+                d[i].grid.y >= (uint64_t)arrs[0]->g.shape[0]) {
+                std::shared_ptr<const PlanBundle> b;
+                std::vector<lt_array *> parr;
+                if ((st = prepare_plan(c, k, d[i].grid, d[i].block, &d[i].wd, d[i].args, d[i].nargs, &b, &parr))) return st;
+                for (const auto &sb : b->plan.sbs) {
+                    int direct = 0;
+                    for (const auto &ap : sb.args) {
+                        if (ap.kind == ARG_VALUE || ap.kind == ARG_NONE) continue;
+                        if (ap.kind != ARG_DIRECT) fused = false;
+                        direct++;
+                    }
+                    if (direct != 2 || sb.threads.lo[0] % 4 != 0) fused = false;
+                }
+                if (fused) bs.jac.push_back({arrs[0], arrs[1], d[i].repeat, b});
+            } else if (k->def->id == LT_K_HIST256 && arrs.size() == 2 && arrs[0]->cs.size() == 1 &&
+                       arrs[1]->cs.size() == 1 && arrs[1]->g.shape[0] == 256 && d[i].repeat == 1 &&
+                       d[i].grid.x >= (uint64_t)arrs[0]->g.shape[0]) {
+                bs.hist.push_back({arrs[0], arrs[1]});
+            } else {
+                fused = false;
+            }
+        }
+        if (!fused) return batch_plain(c, d, n);
+        c->batch_checked = std::move(chk);
+        c->batch_shape = shape;
+    }
+    const BatchShape &bs = *c->batch_shape;
+
     if ((st = flush_pending(c))) return st;
     ++c->launch_id;
     c->stats.launches++;
-    // stage: outputs (V, H) are overwritten unread; inputs keep their data
-    std::vector<std::pair<lt_array *, bool>> uses;  // (array, written)
+    // stage every chunk: outputs (V, H) are overwritten unread (V's halos
+    // by the replica items); inputs keep their data
+    struct Use {
+        lt_array *a;
+        int64_t ci;
+        bool written;
+    };
+    std::vector<Use> uses;
     for (auto &J : bs.jac) {
-        uses.push_back({J.u, true});
-        uses.push_back({J.v, true});
-        J.v->cs[0].dead_launch = c->launch_id;
-        J.u->cs[0].discarded = false;  // both buffers of an instance are written (ping-pong)
-        J.v->cs[0].discarded = false;
+        for (int64_t ci = 0; ci < (int64_t)J.u->cs.size(); ++ci) {
+            uses.push_back({J.u, ci, true});
+            uses.push_back({J.v, ci, true});
+            J.v->cs[(size_t)ci].dead_launch = c->launch_id;
+            J.u->cs[(size_t)ci].discarded = false;  // both buffers of an instance are written (ping-pong)
+            J.v->cs[(size_t)ci].discarded = false;
+        }
     }
     for (auto &H : bs.hist) {
-        uses.push_back({H.x, false});
-        uses.push_back({H.h, true});
+        uses.push_back({H.x, 0, false});
+        uses.push_back({H.h, 0, true});
         H.h->cs[0].dead_launch = c->launch_id;
         H.h->cs[0].discarded = false;
     }
-    for (auto &u : uses) u.first->cs[0].pin++;
+    for (auto &u : uses) u.a->cs[(size_t)u.ci].pin++;
     auto unpin = [&]() {
-        for (auto &u : uses) u.first->cs[0].pin--;
+        for (auto &u : uses) u.a->cs[(size_t)u.ci].pin--;
     };
     for (auto &u : uses)
-        if ((st = ensure_dev(c, u.first, 0, true))) {
+        if ((st = ensure_dev(c, u.a, u.ci, true))) {
             unpin();
             return st;
         }
-    // cache key: arrays, their device offsets and repeats
+    // cache key: arrays, the device offsets of their chunks, repeats and plans
     std::vector<uint64_t> key;
-    for (auto &J : bs.jac) key.insert(key.end(), {(uint64_t)J.u->id, J.u->cs[0].off, (uint64_t)J.v->id, J.v->cs[0].off,
-                                                  (uint64_t)J.repeat});
+    for (auto &J : bs.jac) {
+        key.insert(key.end(), {(uint64_t)J.u->id, (uint64_t)J.v->id, (uint64_t)J.repeat,
+                               (uint64_t)(uintptr_t)J.plan.get()});
+        for (size_t ci = 0; ci < J.u->cs.size(); ++ci) key.insert(key.end(), {J.u->cs[ci].off, J.v->cs[ci].off});
+    }
     key.push_back(~0ull);
     for (auto &H : bs.hist) key.insert(key.end(), {(uint64_t)H.x->id, H.x->cs[0].off, (uint64_t)H.h->id, H.h->cs[0].off});
     const bool stall = (flags & LT_BATCH_TEST_STALL) != 0;
@@ -235,6 +323,7 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
         CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         std::vector<BatchJacobi> jac;
         std::vector<BatchHist> hist;
+        std::vector<BatchRep> reps;
         std::vector<BatchItem> items;
         size_t ncnt = 0;
         // autotuner: time every candidate on the first iteration of the batch
@@ -256,9 +345,9 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
                 for (int hs : hss) {
                     if (bs.hist.empty() && hs != hss[0]) continue;
                     if (bs.jac.empty() && th != ths[0]) continue;
-                    batch_tables(c, bs, th, hs, 1, &jac, &hist, &items, &ncnt);
+                    batch_tables(c, bs, th, hs, 1, &jac, &hist, &reps, &items, &ncnt);
                     BatchCache tc;
-                    if ((st = batch_upload(c, &tc, jac, hist, items, ncnt))) {
+                    if ((st = batch_upload(c, &tc, jac, hist, reps, items, ncnt))) {
                         unpin();
                         return st;
                     }
@@ -288,8 +377,8 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
         auto tp = c->tuned[shape_key];
         auto bc = std::make_unique<BatchCache>();
         bc->key = key;
-        batch_tables(c, bs, tp.first, tp.second, 0, &jac, &hist, &items, &ncnt, stall);
-        if ((st = batch_upload(c, bc.get(), jac, hist, items, ncnt))) {
+        batch_tables(c, bs, tp.first, tp.second, 0, &jac, &hist, &reps, &items, &ncnt, stall);
+        if ((st = batch_upload(c, bc.get(), jac, hist, reps, items, ncnt))) {
             unpin();
             return st;
         }
@@ -316,8 +405,8 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
     op_begin(c, S_COMP, "batch");
     FenceSet w;
     for (auto &u : uses) {
-        w.merge(u.first->cs[0].ready);
-        w.merge(u.first->cs[0].busy);
+        w.merge(u.a->cs[(size_t)u.ci].ready);
+        w.merge(u.a->cs[(size_t)u.ci].busy);
     }
     if ((st = op_wait(c, w))) {
         unpin();
@@ -337,8 +426,8 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
         return st;
     }
     for (auto &u : uses) {
-        CState &cs = u.first->cs[0];
-        if (u.second) cs.ready = FenceSet::one(S_COMP, q);
+        CState &cs = u.a->cs[(size_t)u.ci];
+        if (u.written) cs.ready = FenceSet::one(S_COMP, q);
         cs.busy.add(S_COMP, q);
     }
     unpin();

@@ -115,15 +115,24 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
       << "#line 1 \"user_kernel.cu\"\n"
       << user << "\n"
       << "extern \"C\" __global__ void lt_user_wrapper(const LtTask *__restrict__ tasks, LtParams P, unsigned nblocks) {\n"
-         "  // persistent: each CTA runs the blocks b = blockIdx.x, blockIdx.x + gridDim.x, ... of the launch\n"
+         "  // persistent: each CTA runs the blocks b = blockIdx.x, blockIdx.x + gridDim.x, ... of the launch;\n"
+         "  // one thread finds each block's task and virtual index and shares them\n"
+         "  __shared__ unsigned lt_map[4];\n"
+         "  const bool lt_lead = threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;\n"
          "  for (unsigned b = blockIdx.x; b < nblocks; b += gridDim.x) {\n"
-         "  int lo = 0, hi = P.ntasks - 1;\n"
-         "  if (P.uniform_ctas > 0) lo = (int)(b / (unsigned)P.uniform_ctas);\n"
-         "  else while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (tasks[mid].cta_begin <= b) lo = mid; else hi = mid - 1; }\n"
-         "  const LtTask &t = tasks[lo];\n"
-         "  // first virtual block and the task's extent in blocks along x and y (set by the host)\n"
-         "  const unsigned l = b - t.cta_begin, q = l / t.aux[3];\n"
-         "  dim3 vb(t.aux[0] + (l - q * t.aux[3]), t.aux[1] + q % t.aux[4], t.aux[2] + q / t.aux[4]);\n";
+         "  if (lt_lead) {\n"
+         "    int lo = 0, hi = P.ntasks - 1;\n"
+         "    if (P.uniform_ctas > 0) lo = (int)(b / (unsigned)P.uniform_ctas);\n"
+         "    else while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (tasks[mid].cta_begin <= b) lo = mid; else hi = mid - 1; }\n"
+         "    const LtTask &tt = tasks[lo];\n"
+         "    // first virtual block and the task's extent in blocks along x and y (set by the host)\n"
+         "    const unsigned l = b - tt.cta_begin, q = l / tt.aux[3];\n"
+         "    lt_map[0] = (unsigned)lo; lt_map[1] = tt.aux[0] + (l - q * tt.aux[3]);\n"
+         "    lt_map[2] = tt.aux[1] + q % tt.aux[4]; lt_map[3] = tt.aux[2] + q / tt.aux[4];\n"
+         "  }\n"
+         "  __syncthreads();\n"
+         "  const LtTask &t = tasks[lt_map[0]];\n"
+         "  dim3 vb(lt_map[1], lt_map[2], lt_map[3]);\n";
     int slot = 0, fi = 0, ii = 0;
     std::ostringstream args;
     for (size_t p = 0; p < params.size(); ++p) {

@@ -95,12 +95,54 @@ def test_batch_replay_skips_the_checks_but_a_changed_launch_is_checked():
         check(jac, hist, 6)
 
 
-def test_batch_with_chunked_arrays_falls_back_to_plain():
+@pytest.mark.parametrize("graph", [0, L.LT_BATCH_NO_GRAPH])
+def test_batch_of_chunked_instances_with_halos_is_fused_and_exact(graph):
+    # chunked instances in the device-side queue: row bands, 2-D tiles with
+    # halos (superblocks smaller than the chunks, and a ragged edge) next to
+    # one-chunk instances and histograms; the batch kernel keeps the halo
+    # replicas itself, so every iteration is bit-exact against the oracle
+    with lt.Context() as ctx:
+        kj = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        kh = ctx.kernel(lt.HIST256, HANN, [("X", lt.U8), ("H", lt.U32)])
+        cases = [((200, 300), lt.Dist.rows(64, halo=1), (300, 64)),
+                 ((333, 517), lt.Dist.tiles((128, 256), halo=(1, 1)), (256, 128)),
+                 ((512, 1024), lt.Dist.tiles((256, 512), halo=(1, 1)), (256, 128)),
+                 ((130, 130), None, (0, 0))]
+        launches, jac = [], []
+        for q, ((ny, nx), dist, sb) in enumerate(cases):
+            u0 = si.uniform_field(si.SEED_BATCH, si.STREAM_BATCH_JACOBI0 + 50 + q, ny, nx)
+            U = ctx.array(lt.F32, (ny, nx), dist)
+            V = ctx.array(lt.F32, (ny, nx), dist)
+            U.write(u0)
+            jac.append((u0, U, V))
+            launches.append((kj, (nx, ny), (128, 4), sb, [U, V], 5))
+        x = si.u8_array(si.SEED_BATCH, si.STREAM_BATCH_HIST0 + 50, 123457)
+        X = ctx.array(lt.U8, (x.size,))
+        H = ctx.array(lt.U32, (256,))
+        X.write(x)
+        launches.append((kh, (x.size,), (256,), (0,), [X, H], 1))
+        for rep in range(2):
+            ctx.launch_batch(launches, graph)
+            ctx.synchronize()
+            done = 5 * (rep + 1)
+            for u0, U, V in jac:
+                assert np.array_equal(V.read(), oracle.jacobi2d(u0, done))      # odd count: the result is in V
+                assert np.array_equal(U.read(), oracle.jacobi2d(u0, done - 1))
+            assert np.array_equal(H.read(), oracle.hist256(x))
+            # the next batch continues from V: the buffers swap roles
+            launches = [(k, g, b, sb, [a[1], a[0]] if k is kj else a, r) for (k, g, b, sb, a, r) in launches]
+            jac = [(u0, V, U) for (u0, U, V) in jac]
+        s = ctx.stats()
+        assert s["batches_fused"] == 2 and s["batches_plain"] == 0
+
+
+def test_batch_of_chunked_instances_without_halo_falls_back_to_plain():
+    # without a halo every superblock packs its read region first: the plain form
     with lt.Context() as ctx:
         kj = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
         u0 = si.uniform_field(2206, 5, 200, 300)
-        U = ctx.array(lt.F32, (200, 300), lt.Dist.rows(64, halo=1))
-        V = ctx.array(lt.F32, (200, 300), lt.Dist.rows(64, halo=1))
+        U = ctx.array(lt.F32, (200, 300), lt.Dist.rows(64))
+        V = ctx.array(lt.F32, (200, 300), lt.Dist.rows(64))
         U.write(u0)
         ctx.launch_batch([(kj, (300, 200), (128, 4), (300, 64), [U, V], 4)])
         ctx.synchronize()
