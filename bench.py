@@ -51,11 +51,16 @@ def parse():
     p.add_argument("--batch-scale", type=int, default=1, help="divide the batch instance counts by this")
     p.add_argument("--gemm-n", type=int, default=65536, help="M = N = K of the GEMM workload")
     p.add_argument("--gemm-tile", type=int, default=8192, help="output tile chunk of the GEMM workload")
-    p.add_argument("--incore-chunks", default="4x4", choices=["4x4", "1"],
-                   help="in-core Jacobi: 4x4 tiles of 1024^2 with halo, or the whole grid as one chunk")
+    p.add_argument("--incore-chunks", default="4x4", choices=["4x4", "1", "4x4-nohalo", "cols", "cols-halo"],
+                   help="in-core Jacobi: 4x4 tiles of 1024^2 with halo, the whole grid as one chunk, tiles without "
+                        "halo (every superblock packs its read region), or 4 column bands of 1024 without / with "
+                        "a 1-column halo")
     p.add_argument("--rows", type=int, default=262144, help="grid rows (ooc)")
     p.add_argument("--cols", type=int, default=131072, help="grid columns (ooc)")
     p.add_argument("--band", type=int, default=8192)
+    p.add_argument("--ooc-dist", default="rows", choices=["rows", "cols", "cols-halo"],
+                   help="out-of-core grid: row bands (the workload), or column bands of --band columns without / "
+                        "with a halo column (pack-path measurements)")
     p.add_argument("--keep-stale", action="store_true",
                    help="stencil runs: do not discard the stale ping-pong buffer before the closing synchronize")
     p.add_argument("--no-pdl", action="store_true",
@@ -303,13 +308,18 @@ def jacobi_config(args, world):
     iters = args.iters or (20 if args.workload == "ooc" else 10)
     if args.workload == "ooc":
         ny, nx = args.rows, args.cols
-        wl = (f"out-of-core 2D 5-point Jacobi f32 {ny}x{nx}, {args.band}-row bands + {tb}-row halo, "
+        bands = {"rows": f"{args.band}-row bands + {tb}-row halo",
+                 "cols": f"{args.band}-column bands without halo (read regions packed)",
+                 "cols-halo": f"{args.band}-column bands + {tb}-column halo"}[args.ooc_dist]
+        wl = (f"out-of-core 2D 5-point Jacobi f32 {ny}x{nx}, {bands}, "
               f"{iters} iterations per step, {tb} per launch")
         l2 = "inputs larger than L2 (129 MB)"
     else:
         ny = nx = 4096
-        layout = ("1 chunk (superblocks of 1024^2)" if args.incore_chunks == "1" else
-                  f"4x4 tiles of 1024^2 + {tb}-cell halo")
+        layout = {"1": "1 chunk (superblocks of 1024^2)", "4x4": f"4x4 tiles of 1024^2 + {tb}-cell halo",
+                  "4x4-nohalo": "4x4 tiles of 1024^2 without halo (read regions packed)",
+                  "cols": "4 column bands of 1024 without halo (read regions packed)",
+                  "cols-halo": f"4 column bands of 1024 + {tb}-column halo"}[args.incore_chunks]
         wl = (f"in-core 2D 5-point Jacobi f32 4096x4096, {layout}, "
               f"{iters} iterations per step, {tb} per launch")
         l2 = ("inputs larger than L2: two arrays of 16 chunks, 140.7 MB with halos and row padding, "
@@ -469,9 +479,13 @@ def run_lightning(args, rank, world, local, grp, links=None):
         ctx = lt.Context(device=local, hbm_budget=pl["budget"], host_pool=pl["host"], flags=ctx_flags(args))
         dist = lt.Dist.rows(band, halo=tb)
         sb = (nx, band)
+        if args.ooc_dist != "rows":
+            # column bands of `band` columns, with or without a halo column (then every superblock packs
+            # its read region: the column-wise multi-chunk read)
+            dist = lt.Dist.cols(band, halo=tb if args.ooc_dist == "cols-halo" else 0)
+            sb = (band, ny)
         seed = si.SEED_JACOBI_OOC
-        workload = (f"out-of-core 2D 5-point Jacobi f32 {ny}x{nx}, {band}-row bands + {tb}-row halo, "
-                    f"{args.iters or 20} iterations per step, {tb} per launch")
+        workload = jacobi_config(args, world)["workload"]
     else:
         ny = nx = 4096
         pl = dict(budget=0, host=0, chunk_bytes=None, data_bytes=2 * ny * nx * 4)
@@ -480,10 +494,11 @@ def run_lightning(args, rank, world, local, grp, links=None):
         band = 1024
         seed = si.SEED_JACOBI_INCORE
         workload = jacobi_config(args, world)["workload"]
-        if args.incore_chunks == "1":
-            dist = lt.Dist.block()
-        else:
-            dist = lt.Dist.tiles((1024, 1024), halo=(tb, tb))
+        dist = {"1": lt.Dist.block(), "4x4": lt.Dist.tiles((1024, 1024), halo=(tb, tb)),
+                "4x4-nohalo": lt.Dist.tiles((1024, 1024)), "cols": lt.Dist.cols(1024),
+                "cols-halo": lt.Dist.cols(1024, halo=tb)}[args.incore_chunks]
+        if args.incore_chunks.startswith("cols"):
+            sb = (1024, 4096)
     U = ctx.array(lt.F32, (ny, nx), dist)
     V = ctx.array(lt.F32, (ny, nx), dist)
     U.fill(L.LT_INIT_UNIFORM, seed=seed, stream=0)
@@ -533,7 +548,7 @@ def run_lightning(args, rank, world, local, grp, links=None):
     else:
         kname = {1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
     # DRAM traffic records: the in-core grid keeps part of its working set in L2
-    tkey = kname + ("@incore4096" + ("_1chunk" if args.incore_chunks == "1" else "")
+    tkey = kname + ("@incore4096" + ("" if args.incore_chunks == "4x4" else "_" + args.incore_chunks)
                     if args.workload != "ooc" and tb == 1 else "")
     # the timed steps run without per-operation CUDA events (a few
     # microseconds of GPU time each, 12 % of an in-core launch); the kernel
@@ -596,8 +611,17 @@ def run_lightning(args, rank, world, local, grp, links=None):
         "gpu_launches": st_run["kernels"],
         "clocks": clocks,
         "stats": {k2: st_run[k2] for k2 in ("fetches", "evictions", "dead_skips", "tasks_execute", "tasks_copy",
-                                            "hbm_peak", "bytes_replica_wt")},
+                                            "hbm_peak", "bytes_replica_wt", "bytes_d2d")},
     }
+    if st["n_copy_kernels"]:
+        # pack / unpack / replica copy kernels (copy_kernel): bytes moved read + written
+        res["copy_kernels"] = {"ms_per_launch": round(st["ms_copy_kernels"] / st["n_copy_kernels"], 4),
+                               "launches_per_step": st["n_copy_kernels"] / n_inst,
+                               "bytes_per_step": st["bytes_d2d"] / n_inst,
+                               "GBs": round(2.0 * st["bytes_d2d"] / (st["ms_copy_kernels"] / 1e3) / 1e9, 1),
+                               "frac_of_hbm": round(2.0 * st["bytes_d2d"] / (st["ms_copy_kernels"] / 1e3) / 1e9
+                                                    / peaks["hbm_gbs"], 4),
+                               "ms_per_step": round(st["ms_copy_kernels"] / n_inst, 4)}
     if not args.no_e2e:
         # end to end through the public API: every step uploads its input grid
         # from pinned host memory, runs and reads its result back (in-core: the

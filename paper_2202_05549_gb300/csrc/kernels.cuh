@@ -34,6 +34,16 @@ struct ReplicaTarget {
     int32_t pad;
 };
 
+// A warp's share of the write-through replicas (vector Jacobi kernel): 128
+// columns of a one-row replica box whose row is 16-byte aligned in its
+// chunk (row = 1, off = first column offset), or 32 cells of any other box
+// (row = 0, off = first cell offset).
+struct ReplicaUnit {
+    uint32_t rep;
+    uint32_t row : 1;
+    uint32_t off : 31;
+};
+
 // One Execute task: a superblock's thread box and its argument views.
 struct ExecTask {
     int64_t t_lo[3], t_hi[3];     // thread box (x, y, z), inclusive
@@ -61,6 +71,9 @@ struct ExecParams {
     uint32_t rep_ctas;                // CTAs before the tasks' CTAs (set by the launch from rep_cells)
     int32_t no_staged;                // 1: prepare_* picks no TMA-staged kernel (context flag)
     int32_t pdl;                      // 1: launched as a programmatic dependent of the previous kernel
+    const ReplicaUnit *runits;        // the replicas as warp units (vector Jacobi kernel)
+    uint32_t nunits;
+    uint32_t pad;
 };
 
 // Box copy (pack / unpack / replica update): copy the global box [lo, hi]

@@ -66,7 +66,7 @@ template <int R>
 __global__ void __launch_bounds__(JWARPS * 32) jacobi2d_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     if (blockIdx.x < p.rep_ctas) {  // write-through replica CTAs come first: their latency overlaps the strips
         pdl_trigger_and_wait(p);
-        jacobi_replica_cell(tasks, p, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
+        jacobi_replica_unit(tasks, p, blockIdx.x * JWARPS + (threadIdx.x >> 5), threadIdx.x & 31);
         return;
     }
     const uint32_t cta = blockIdx.x - p.rep_ctas;
@@ -159,7 +159,9 @@ uint32_t prepare_jacobi2d(ExecTask *t, int n, ExecParams &p) {
 // followed by the tasks' CTAs.
 cudaError_t launch_jacobi2d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
     const uint32_t threads = p.variant == 1 ? JWARPS * 32 : 256;
-    const uint64_t extra = (p.rep_cells + threads - 1) / threads;
+    // replica CTAs: warp units for the vector kernel, one thread per cell for the scalar one
+    const uint64_t extra = p.variant == 1 ? (p.rep_cells ? ((uint64_t)p.nunits + JWARPS - 1) / JWARPS : 0)
+                                          : (p.rep_cells + threads - 1) / threads;
     if ((uint64_t)ctas + extra > 0x7FFFFFFFull) return cudaErrorInvalidValue;
     ExecParams q = p;
     q.rep_ctas = (uint32_t)extra;

@@ -557,16 +557,36 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                                 "1 <= k <= 64 and arrays of 4k / 5k elements; a source kernel virtual block "
                                 "indices below 2^32");
             // one table: the tasks, then their replica targets
-            const size_t tbytes = tasks.size() * sizeof(ExecTask), rbytes = reps.size() * sizeof(ReplicaTarget);
-            std::vector<char> table(tbytes + rbytes);
+            // the replicas once more as warp units: 128 columns of an aligned one-row box, else 32 cells
+            std::vector<ReplicaUnit> units;
+            for (size_t ri = 0; ri < reps.size(); ++ri) {
+                const ReplicaTarget &r = reps[ri];
+                const int64_t w = r.hi[1] - r.lo[1] + 1, h = r.hi[0] - r.lo[0] + 1;
+                const bool row = h == 1 && r.lo[1] % 4 == 0 && r.dst.s[1] == 1 && r.dst.s[0] % 4 == 0 &&
+                                 (r.dst.base + (uint64_t)((r.lo[0] * r.dst.s[0] + r.lo[1]) * 4)) % 16 == 0;
+                const int64_t n = row ? w : w * h, step = row ? 128 : 32;
+                for (int64_t o = 0; o < n; o += step) {
+                    ReplicaUnit u{};
+                    u.rep = (uint32_t)ri;
+                    u.row = row ? 1u : 0u;
+                    u.off = (uint32_t)o;
+                    units.push_back(u);
+                }
+            }
+            const size_t tbytes = tasks.size() * sizeof(ExecTask), rbytes = reps.size() * sizeof(ReplicaTarget),
+                         ubytes = units.size() * sizeof(ReplicaUnit);
+            std::vector<char> table(tbytes + rbytes + ubytes);
             std::memcpy(table.data(), tasks.data(), tbytes);
             if (rbytes) std::memcpy(table.data() + tbytes, reps.data(), rbytes);
+            if (ubytes) std::memcpy(table.data() + tbytes + rbytes, units.data(), ubytes);
             void *dptr;
             size_t roff;
             if ((st = upload(c, table.data(), table.size(), &dptr, &roff))) return st;
             ep.reps = (rbytes && dptr) ? (const ReplicaTarget *)((const char *)dptr + tbytes) : nullptr;
             ep.nreps = (uint32_t)reps.size();
             ep.rep_cells = ep.reps ? rep_cells : 0;
+            ep.runits = (ubytes && dptr) ? (const ReplicaUnit *)((const char *)dptr + tbytes + rbytes) : nullptr;
+            ep.nunits = ep.runits ? (uint32_t)units.size() : 0;
             if (!c->dry && ctas) {
                 TimeScope ts(c, CAT_EXEC);
                 if (k->ufn) {

@@ -130,4 +130,34 @@ __device__ __forceinline__ void jacobi_replica_cell(const ExecTask *tasks, const
     ((float *)r.dst.base)[i * r.dst.s[0] + j * r.dst.s[1]] = j5(c, n, s, wv, e);
 }
 
+// Write-through replicas by warp units (ExecParams.runits): a row unit is
+// the strip body with one row, reading the owning task's input view and
+// storing into the replica's view; any other unit computes 32 cells, one per
+// lane, as jacobi_replica_cell does.  Same operations as the owning task.
+__device__ __forceinline__ void jacobi_replica_unit(const ExecTask *tasks, const ExecParams &p, uint32_t unit,
+                                                    int lane) {
+    if (unit >= p.nunits) return;
+    const ReplicaUnit u = p.runits[unit];
+    const ReplicaTarget &r = p.reps[u.rep];
+    const DView U = tasks[r.task].v[0];
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    if (u.row) {
+        jacobi_strip<false, 1>((const float *)U.base, U.s[0], (float *)r.dst.base, r.dst.s[0], NY, NX,
+                               r.lo[1] + (int64_t)u.off, r.lo[0], r.hi[1], r.lo[0], lane);
+        return;
+    }
+    const uint64_t w = (uint64_t)(r.hi[1] - r.lo[1] + 1), cells = w * (uint64_t)(r.hi[0] - r.lo[0] + 1);
+    const uint64_t l = (uint64_t)u.off + (uint64_t)lane;
+    if (l >= cells) return;
+    const int64_t i = r.lo[0] + (int64_t)(l / w), j = r.lo[1] + (int64_t)(l % w);
+    const float *uu = (const float *)U.base;
+    auto at = [&](int64_t a, int64_t b) { return uu[a * U.s[0] + b * U.s[1]]; };
+    const float c = at(i, j);
+    const float n = i > 0 ? at(i - 1, j) : 0.f;
+    const float s = i + 1 < NY ? at(i + 1, j) : 0.f;
+    const float wv = j > 0 ? at(i, j - 1) : 0.f;
+    const float e = j + 1 < NX ? at(i, j + 1) : 0.f;
+    ((float *)r.dst.base)[i * r.dst.s[0] + j * r.dst.s[1]] = j5(c, n, s, wv, e);
+}
+
 }  // namespace lt

@@ -108,7 +108,7 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
       << LT_MAX_ARRAYS << "][3]; int32_t nd[" << LT_MAX_ARRAYS
       << "]; int64_t block[3]; double f[4]; int64_t i[4]; uint32_t *err;"
          " int32_t ntasks, variant, red_op, uniform_ctas; const void *reps; uint64_t rep_cells;"
-         " uint32_t nreps, rep_ctas; int32_t no_staged, pad; };\n"
+         " uint32_t nreps, rep_ctas; int32_t no_staged, pdl; const void *runits; uint32_t nunits, pad; };\n"
          "static_assert(sizeof(LtView) == "
       << sizeof(DView) << ", \"view layout\");\nstatic_assert(sizeof(LtTask) == " << sizeof(ExecTask)
       << ", \"task layout\");\nstatic_assert(sizeof(LtParams) == " << sizeof(ExecParams) << ", \"params layout\");\n"
@@ -116,10 +116,13 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
       << user << "\n"
       << "extern \"C\" __global__ void lt_user_wrapper(const LtTask *__restrict__ tasks, LtParams P, unsigned nblocks) {\n"
          "  // persistent: each CTA runs the blocks b = blockIdx.x, blockIdx.x + gridDim.x, ... of the launch;\n"
-         "  // one thread finds each block's task and virtual index and shares them\n"
-         "  __shared__ unsigned lt_map[4];\n"
+         "  // one thread finds each block's task and virtual index and shares them (two slots, so that one\n"
+         "  // barrier per block orders the writes and the reads)\n"
+         "  __shared__ unsigned lt_maps[2][4];\n"
          "  const bool lt_lead = threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;\n"
-         "  for (unsigned b = blockIdx.x; b < nblocks; b += gridDim.x) {\n"
+         "  unsigned lt_par = 0;\n"
+         "  for (unsigned b = blockIdx.x; b < nblocks; b += gridDim.x, lt_par ^= 1u) {\n"
+         "  unsigned *lt_map = lt_maps[lt_par];\n"
          "  if (lt_lead) {\n"
          "    int lo = 0, hi = P.ntasks - 1;\n"
          "    if (P.uniform_ctas > 0) lo = (int)(b / (unsigned)P.uniform_ctas);\n"
@@ -161,9 +164,12 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
         args << "a" << slot;
         slot++;
     }
-    o << "  " << name << "(vb" << args.str() << ");\n"
-      << "  __syncthreads();  // the body's shared memory is free before the next block reuses it\n"
-      << "  }\n}\n";
+    o << "  " << name << "(vb" << args.str() << ");\n";
+    // a body that may use shared memory or barriers gets a barrier after each block, so that its shared
+    // memory is free before the next block reuses it
+    if (user.find("__shared__") != std::string::npos || user.find("sync") != std::string::npos)
+        o << "  __syncthreads();\n";
+    o << "  }\n}\n";
     return o.str();
 }
 

@@ -155,3 +155,45 @@ def test_user_kernel_block_local_bindings_bit_exact():
             U, V = V, U
         ctx.synchronize()
         assert np.array_equal(U.read(), oracle.jacobi2d(u0, 3))
+
+
+# A body that stages its block's cells and the two halo cells in shared
+# memory and waits at a barrier before it reads them: the persistent wrapper
+# must keep every virtual block's shared memory apart from the next one's.
+AVG3_SHARED = r"""
+__device__ void avg3s(dim3 vb, int64_t len, lightning::Vector<float> dst, lightning::Vector<float> src) {
+    __shared__ float tile[258];
+    const int64_t g = (int64_t)vb.x * blockDim.x + threadIdx.x;
+    const int t = threadIdx.x + 1;
+    tile[t] = g < len ? src[g] : 0.0f;
+    if (threadIdx.x == 0) tile[0] = g > 0 && g - 1 < len ? src[g - 1] : 0.0f;
+    if (threadIdx.x == blockDim.x - 1) tile[t + 1] = g + 1 < len ? src[g + 1] : 0.0f;
+    __syncthreads();
+    if (g >= len) return;
+    float acc = tile[t - 1];
+    acc = acc + tile[t];
+    acc = acc + tile[t + 1];
+    dst[g] = (float)((double)acc / 3.0);
+}
+"""
+
+
+@pytest.mark.gpu
+def test_user_kernel_with_shared_memory_and_barrier_bit_exact():
+    n = 3_000_017
+    x0 = si.uniform_field(2203, 12, 1, n).ravel()
+    want = x0.copy()
+    for _ in range(4):
+        want = oracle.stencil1d_paper(want)
+    with lt.Context() as ctx:
+        dist = lt.Dist.rows(500_000, halo=1)
+        src = ctx.array(lt.F32, (n,), dist)
+        dst = ctx.array(lt.F32, (n,), dist)
+        src.write(x0)
+        k = ctx.kernel_from_source(AVG3_SHARED, "avg3s", "global i => read src[i-1:i+1], write dst[i]",
+                                   [("len", lt.U32, False), ("dst", lt.F32), ("src", lt.F32)])
+        for _ in range(4):
+            k.launch(grid=(n,), block=(256,), superblock=(500_000,), args=[n, dst, src])
+            src, dst = dst, src
+        ctx.synchronize()
+        assert np.array_equal(src.read(), want)
