@@ -170,6 +170,57 @@ __global__ void __launch_bounds__(256, 3) copy_kernel(const CopyPiece *__restric
         }
         return;
     }
+    // Rows of equal misalignment in both (row pitches multiples of 16 bytes):
+    // the unit's 16-byte vectors are numbered across its rows and every
+    // thread keeps eight loads in flight before its stores, so short rows
+    // (a 1024-column tile row is 256 vectors, one per thread) no longer
+    // leave one load per thread in flight.
+    if (contig && p.nd == 2 && ((p.src.s[0] * es) & 15) == 0 && ((p.dst.s[0] * es) & 15) == 0) {
+        const int64_t col0 = p.lo[1] + c0, ncol = c1 - c0;
+        const char *sb = (const char *)(p.src.base + (uint64_t)((p.lo[0] + r0) * p.src.s[0] * es + col0 * es));
+        char *db = (char *)(p.dst.base + (uint64_t)((p.lo[0] + r0) * p.dst.s[0] * es + col0 * es));
+        if (((uintptr_t)sb & 15) == ((uintptr_t)db & 15)) {
+            const int64_t sp = p.src.s[0] * es, dp = p.dst.s[0] * es;
+            int64_t head = (int64_t)(((16 - ((uintptr_t)sb & 15)) & 15) / es);
+            if (head > ncol) head = ncol;
+            const uint32_t nv = (uint32_t)((ncol - head) * es / 16);
+            const int64_t tail0 = head + (int64_t)nv * 16 / es;
+            const uint32_t nr = (uint32_t)(r1 - r0);
+            // scalar heads and tails of every row
+            const uint32_t ns = (uint32_t)(head + (ncol - tail0));
+            for (uint32_t e = threadIdx.x; e < nr * ns; e += blockDim.x) {
+                const uint32_t r = e / ns, k = e % ns;
+                const int64_t col = k < (uint32_t)head ? (int64_t)k : tail0 + (int64_t)(k - (uint32_t)head);
+                copy_elem(sb + r * sp + col * es, db + r * dp + col * es, es);
+            }
+            if (nv) {
+                const uint32_t total = nr * nv;
+                const uint32_t minv = (uint32_t)(0xFFFFFFFFull / nv);  // row = idx / nv by multiply and one fix-up
+                const char *sv = sb + head * es;
+                char *dv = db + head * es;
+                for (uint32_t b = threadIdx.x; b < total; b += 8u * blockDim.x) {
+                    uint4 v[8];
+                    int64_t doff[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t i = b + (uint32_t)k * blockDim.x;
+                        doff[k] = -1;
+                        if (i < total) {
+                            uint32_t r = __umulhi(i, minv);
+                            if ((r + 1) * nv <= i) ++r;
+                            const uint32_t c = i - r * nv;
+                            v[k] = __ldcg((const uint4 *)(sv + r * sp) + c);
+                            doff[k] = r * dp + (int64_t)c * 16;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (doff[k] >= 0) *(uint4 *)(dv + doff[k]) = v[k];
+                }
+            }
+            return;
+        }
+    }
     for (int64_t r = r0; r < r1; ++r) {
         int64_t idx[3] = {0, 0, 0};
         if (p.nd == 3) {
