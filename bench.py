@@ -340,9 +340,9 @@ def plan_ooc(args, world, hbm_gib=None):
     holds the live set beyond it.  The live set is one array plus the bands
     in flight: a band of the input is dead once its last reader has run (the
     next launch overwrites it unread), so the pool holds the bands of one
-    array that are not in HBM plus four in flight, and six more: the library
-    withholds the parts of a large pinned pool that copy slowly (measured at
-    creation), some gigabytes on some runs."""
+    array that are not in HBM plus four in flight, and eight more: the library
+    withholds the parts of a large pinned pool that copy slowly (found by
+    timing its own transfers), some gigabytes on some runs."""
     ny, nx, band = args.rows, args.cols, args.band
     hbm_gib = args.hbm_gib if hbm_gib is None else hbm_gib
     nb = (ny + band - 1) // band
@@ -357,7 +357,7 @@ def plan_ooc(args, world, hbm_gib=None):
     dev_slots = max(2 * nb - host_slots + 3, 6)  # a band task pins 4 chunks
     if hbm_gib > 0:
         dev_slots = max(int(hbm_gib * 2**30) // chunk_c, 6)
-        host_slots = max(nb + 4 - dev_slots, 0) + 6
+        host_slots = max(nb + 4 - dev_slots, 0) + 8
         if host_slots * chunk_c > 0.8 * avail:
             raise SystemExit(f"HBM budget {hbm_gib} GiB: the rest of the live data does not fit in pinned host memory")
     budget = dev_slots * chunk_c + (64 << 20)
@@ -1401,6 +1401,7 @@ def main():
         # regime; the other workloads follow in the same JSON line
         import argparse as _ap
         links = link_peaks(local)
+        free_pinned()
         spill = run_spill(args, rank, world, local, grp, links)
         free_pinned()
         a2 = _ap.Namespace(**vars(args))

@@ -297,8 +297,8 @@ lt_status lt_kernel_destroy(lt_ctx *ctx, lt_kernel *k);
  * generates the wrapper kernel that maps physical to virtual blocks and
  * builds the views (the chunk offset subtracted once).  The wrapper is
  * persistent: each CTA calls the function for several virtual blocks in turn,
- * with a __syncthreads() between two calls, so shared memory does not carry
- * over from one virtual block to the next.  The library compiles both with NVRTC for sm_103a
+ * with a __syncthreads() before each call, so shared memory is not shared
+ * between two virtual blocks' calls.  The library compiles both with NVRTC for sm_103a
  * (IEEE arithmetic, no FMA contraction) and loads them.  The annotation is
  * trusted: the kernel must not touch elements outside it.  At most 5 array,
  * 4 integer and 4 float parameters.  Errors: LT_ERR_PARSE, LT_ERR_COMPILE

@@ -99,9 +99,13 @@ __host__ __device__ inline int64_t copy_piece_rows(const CopyPiece &p) {
     for (int d = 0; d + 1 < p.nd; ++d) r *= p.hi[d] - p.lo[d] + 1;
     return r;
 }
+// Narrow pieces (rows under 512 bytes: column halos) take units of 2048
+// elements, so a column of a few thousand rows spreads over several CTAs.
+#define LT_COPY_UNIT_NARROW 2048
 __host__ __device__ inline int64_t copy_piece_rows_per_unit(const CopyPiece &p) {
     int64_t w = copy_piece_width(p);
-    int64_t r = LT_COPY_UNIT / (w > 0 ? w : 1);
+    const int64_t unit = w * p.esize < 512 ? LT_COPY_UNIT_NARROW : LT_COPY_UNIT;
+    int64_t r = unit / (w > 0 ? w : 1);
     return r < 1 ? 1 : r;
 }
 __host__ __device__ inline uint64_t copy_piece_units(const CopyPiece &p) {

@@ -150,6 +150,17 @@ __global__ void __launch_bounds__(256, 3) copy_kernel(const CopyPiece *__restric
     if ((c1 - c0) * es < 512) {
         // narrow rows: spread the unit's elements (rows x columns) over the threads
         const uint32_t ncol = (uint32_t)(c1 - c0), nel = (uint32_t)((r1 - r0) * (c1 - c0));
+        if (p.nd == 2) {  // 2-D: one element per thread and step, 32-bit index arithmetic
+            const char *sb = (const char *)(p.src.base + (uint64_t)(((p.lo[0] + r0) * p.src.s[0] +
+                                                                     (p.lo[1] + c0) * p.src.s[1]) * es));
+            char *db = (char *)(p.dst.base + (uint64_t)(((p.lo[0] + r0) * p.dst.s[0] + (p.lo[1] + c0) * p.dst.s[1]) * es));
+            const int64_t sr = p.src.s[0] * es, sc = p.src.s[1] * es, dr = p.dst.s[0] * es, dc = p.dst.s[1] * es;
+            for (uint32_t e = threadIdx.x; e < nel; e += blockDim.x) {
+                const uint32_t r = ncol == 1 ? e : e / ncol, col = ncol == 1 ? 0u : e - r * ncol;
+                copy_elem(sb + r * sr + col * sc, db + r * dr + col * dc, es);
+            }
+            return;
+        }
         for (uint32_t e = threadIdx.x; e < nel; e += blockDim.x) {
             const int64_t r = r0 + e / ncol, col = p.lo[inner] + c0 + e % ncol;
             int64_t idx[3] = {0, 0, 0};

@@ -163,7 +163,21 @@ struct Arena {
     // withheld where it is free now and, for the parts in use, when their
     // block is released.
     std::vector<std::pair<size_t, size_t>> bad;  // [begin, end)
+    struct Held {
+        size_t off, size;
+        FenceSet f;  // the fences of the range's last users
+        uint64_t tick;
+    };
+    std::vector<Held> held;  // the ranges taken out of the free space
     size_t withheld = 0;
+    // Give every withheld range back (a slow pool beats no pool) and forget
+    // the bad ranges.
+    void release_quarantine() {
+        for (const Held &h : held) free_[h.off] = {h.size, h.f, h.tick};
+        held.clear();
+        bad.clear();
+        withheld = 0;
+    }
     void withhold_free(size_t b, size_t e) {
         for (auto it = free_.begin(); it != free_.end();) {
             const size_t fb = it->first, fe = fb + it->second.size;
@@ -176,6 +190,7 @@ struct Arena {
             it = free_.erase(it);
             if (lo > fb) free_[fb] = {lo - fb, keep.f, keep.tick};
             if (fe > hi) free_[hi] = {fe - hi, keep.f, keep.tick};
+            held.push_back({lo, hi - lo, keep.f, keep.tick});
             withheld += hi - lo;
             it = free_.upper_bound(lo);
         }

@@ -186,7 +186,12 @@ lt_status evict(lt_ctx *c, lt_array *a, int64_t ci) {
     }
     size_t hoff;
     FenceSet hf;
-    if (!c->host.alloc(cg.bytes, &hoff, &hf))
+    bool ok = c->host.alloc(cg.bytes, &hoff, &hf);
+    if (!ok && c->host.withheld) {  // quarantine only while the pool can spare it
+        c->host.release_quarantine();
+        ok = c->host.alloc(cg.bytes, &hoff, &hf);
+    }
+    if (!ok)
         return fail(LT_ERR_OOM_HOST, "pinned host pool too small to evict a chunk of " + std::to_string(cg.bytes) +
                                          " bytes (host pool " + std::to_string(c->host.cap) + " bytes)");
     op_begin(c, S_D2H, "evict");

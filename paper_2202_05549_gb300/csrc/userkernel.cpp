@@ -115,27 +115,29 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
       << "#line 1 \"user_kernel.cu\"\n"
       << user << "\n"
       << "extern \"C\" __global__ void lt_user_wrapper(const LtTask *__restrict__ tasks, LtParams P, unsigned nblocks) {\n"
-         "  // persistent: each CTA runs the blocks b = blockIdx.x, blockIdx.x + gridDim.x, ... of the launch;\n"
-         "  // one thread finds each block's task and virtual index and shares them (two slots, so that one\n"
-         "  // barrier per block orders the writes and the reads)\n"
+         "  // persistent: each CTA runs the blocks b = blockIdx.x, blockIdx.x + gridDim.x, ... of the launch.\n"
+         "  // One thread maps each block to its task and virtual index, one block ahead, into the other of two\n"
+         "  // shared slots; the barrier at the top of each block orders the writes and the reads.\n"
          "  __shared__ unsigned lt_maps[2][4];\n"
          "  const bool lt_lead = threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;\n"
-         "  unsigned lt_par = 0;\n"
-         "  for (unsigned b = blockIdx.x; b < nblocks; b += gridDim.x, lt_par ^= 1u) {\n"
-         "  unsigned *lt_map = lt_maps[lt_par];\n"
-         "  if (lt_lead) {\n"
+         "  auto lt_find = [&](unsigned b, unsigned *m) {\n"
          "    int lo = 0, hi = P.ntasks - 1;\n"
          "    if (P.uniform_ctas > 0) lo = (int)(b / (unsigned)P.uniform_ctas);\n"
          "    else while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (tasks[mid].cta_begin <= b) lo = mid; else hi = mid - 1; }\n"
          "    const LtTask &tt = tasks[lo];\n"
          "    // first virtual block and the task's extent in blocks along x and y (set by the host)\n"
          "    const unsigned l = b - tt.cta_begin, q = l / tt.aux[3];\n"
-         "    lt_map[0] = (unsigned)lo; lt_map[1] = tt.aux[0] + (l - q * tt.aux[3]);\n"
-         "    lt_map[2] = tt.aux[1] + q % tt.aux[4]; lt_map[3] = tt.aux[2] + q / tt.aux[4];\n"
-         "  }\n"
+         "    m[0] = (unsigned)lo; m[1] = tt.aux[0] + (l - q * tt.aux[3]);\n"
+         "    m[2] = tt.aux[1] + q % tt.aux[4]; m[3] = tt.aux[2] + q / tt.aux[4];\n"
+         "  };\n"
+         "  if (lt_lead && blockIdx.x < nblocks) lt_find(blockIdx.x, lt_maps[0]);\n"
+         "  unsigned lt_par = 0;\n"
+         "  for (unsigned b = blockIdx.x; b < nblocks; b += gridDim.x, lt_par ^= 1u) {\n"
          "  __syncthreads();\n"
+         "  const unsigned *lt_map = lt_maps[lt_par];\n"
          "  const LtTask &t = tasks[lt_map[0]];\n"
-         "  dim3 vb(lt_map[1], lt_map[2], lt_map[3]);\n";
+         "  dim3 vb(lt_map[1], lt_map[2], lt_map[3]);\n"
+         "  if (lt_lead && b + gridDim.x < nblocks) lt_find(b + gridDim.x, lt_maps[lt_par ^ 1u]);\n";
     int slot = 0, fi = 0, ii = 0;
     std::ostringstream args;
     for (size_t p = 0; p < params.size(); ++p) {
@@ -164,12 +166,8 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
         args << "a" << slot;
         slot++;
     }
-    o << "  " << name << "(vb" << args.str() << ");\n";
-    // a body that may use shared memory or barriers gets a barrier after each block, so that its shared
-    // memory is free before the next block reuses it
-    if (user.find("__shared__") != std::string::npos || user.find("sync") != std::string::npos)
-        o << "  __syncthreads();\n";
-    o << "  }\n}\n";
+    // the barrier at the top of the next block also keeps the body's shared memory apart between blocks
+    o << "  " << name << "(vb" << args.str() << ");\n  }\n}\n";
     return o.str();
 }
 

@@ -47,6 +47,14 @@ int main() {
     size_t big;
     EXPECT(a.alloc(24 * MB, &big, &f));
     EXPECT(!(big < o2 + 8 * MB && big + 24 * MB > o2));
+    // when the pool runs short, the quarantine gives its ranges back
+    const size_t before = a.withheld;
+    EXPECT(before > 0);
+    a.release_quarantine();
+    EXPECT(a.withheld == 0 && a.bad.empty());
+    size_t freed = 0;
+    for (auto &kv : a.free_) freed += kv.second.size;
+    EXPECT(freed + a.used == a.cap);
     std::printf("%s\n", fails ? "arena checks failed" : "arena checks ok");
     return fails ? 1 : 0;
 }
