@@ -272,6 +272,13 @@ typedef enum {
                                * k (1..64); "global i => read X[4*i:4*i+3], read C[:], reduce(+) S[:]" */
     LT_K_KMEANS_UPDATE = 11,  /* new centres: C2[4j+f] = f32(S[5j+f] / S[5j+4]), or C[4j+f] when the count
                                * is 0; "global j => read S[5*j:5*j+4], read C[4*j:4*j+3], write C2[4*j:4*j+3]" */
+    LT_K_LAPLACE2D = 12,      /* G = L U: ((((U[i-1,j] + U[i+1,j]) + U[i,j-1]) + U[i,j+1]) - 4 U[i,j]), zero ghosts, f32;
+                               * "global [i, j] => read U[i-1:i+1, j-1:j+1], write G[i, j]" */
+    LT_K_EWISE2D = 13,        /* C = A + B (value parameter op = 0) or C = A * B (op = 1), f32;
+                               * "global [i, j] => read A[i, j], read B[i, j], write C[i, j]" */
+    LT_K_MULADD2D = 14,       /* C = C + A * B, f32; "global [i, j] => read A[i, j], read B[i, j], readwrite C[i, j]"
+                               * (LAPLACE2D, EWISE2D and MULADD2D are the steps of the diffusion and of its adjoint
+                               * as separate launches: the unfused form the fused adjoint is measured against) */
     LT_K_USER = 100           /* (kernels from lt_kernel_register_source) */
 } lt_builtin;
 

@@ -40,6 +40,7 @@ LT_K_USER = 100
 LT_K_STENCIL1D, LT_K_JACOBI2D, LT_K_JACOBI3D, LT_K_GEMM_BF16, LT_K_HIST256 = 1, 2, 3, 4, 5
 LT_K_DIFFUSION2D, LT_K_DIFFUSION2D_ADJ, LT_K_ROWREDUCE, LT_K_JACOBI2D_MULTI = 6, 7, 8, 9
 LT_K_KMEANS_ASSIGN, LT_K_KMEANS_UPDATE = 10, 11
+LT_K_LAPLACE2D, LT_K_EWISE2D, LT_K_MULADD2D = 12, 13, 14
 
 
 class lt_dist(C.Structure):

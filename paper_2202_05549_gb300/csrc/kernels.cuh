@@ -211,6 +211,12 @@ uint32_t prepare_jacobi3d(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_jacobi3d(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_diffusion(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_diffusion(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
+uint32_t prepare_laplace(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_laplace(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
+uint32_t prepare_ewise(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_ewise(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
+uint32_t prepare_muladd(ExecTask *t, int n, ExecParams &p);
+cudaError_t launch_muladd(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_diffusion_adj(ExecTask *t, int n, ExecParams &p);
 cudaError_t launch_diffusion_adj(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st);
 uint32_t prepare_rowreduce(ExecTask *t, int n, ExecParams &p);

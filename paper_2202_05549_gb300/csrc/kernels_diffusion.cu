@@ -48,6 +48,8 @@ __device__ __forceinline__ void tile_of(uint32_t local, int64_t bx0, int64_t bx1
     *tx0 = bx0 + (int64_t)(local % gx) * TX;
 }
 
+// LAP: the Laplacian alone, G = L U (views U, G); else V = U + K (L U) (views U, K, V).
+template <bool LAP>
 __global__ void __launch_bounds__(DT) diffusion_fwd_scalar_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     __shared__ float su[TY + 2][SP];
     const int ti = task_of(tasks, p, blockIdx.x);
@@ -58,7 +60,7 @@ __global__ void __launch_bounds__(DT) diffusion_fwd_scalar_kernel(const ExecTask
     if (x1 < x0 || y1 < y0) return;
     int64_t ty0, tx0;
     tile_of(blockIdx.x - t.cta_begin, x0, x1, y0, &ty0, &tx0);
-    const DView U = t.v[0], K = t.v[1], V = t.v[2];
+    const DView U = t.v[0], K = t.v[1], V = t.v[LAP ? 1 : 2];
     // U over the tile plus a one-cell ring (zero outside the domain)
     for (int e = threadIdx.x; e < (TY + 2) * (TX + 2); e += DT) {
         const int li = e / (TX + 2), lj = e % (TX + 2);
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(DT) diffusion_fwd_scalar_kernel(const ExecTask
         if (i > y1 || j > x1) continue;
         const float c = su[li][lj];
         const float l = lap5(c, su[li - 1][lj], su[li + 1][lj], su[li][lj - 1], su[li][lj + 1]);
-        ((float *)V.base)[i * V.s[0] + j * V.s[1]] = __fadd_rn(c, __fmul_rn(at2(K, i, j), l));
+        ((float *)V.base)[i * V.s[0] + j * V.s[1]] = LAP ? l : __fadd_rn(c, __fmul_rn(at2(K, i, j), l));
     }
 }
 
@@ -145,6 +147,7 @@ constexpr int NS = ((TY + 2) * VQ + DT - 1) / DT;  // staging groups per thread 
 constexpr int NC = TY * VQ / DT;                   // compute groups per thread
 static_assert(TY * VQ % DT == 0, "compute groups divide evenly");
 
+template <bool LAP>
 __global__ void __launch_bounds__(DT) diffusion_fwd_vec_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     __shared__ __align__(16) float su[TY + 2][VP];
     const int ti = task_of(tasks, p, blockIdx.x);
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(DT) diffusion_fwd_vec_kernel(const ExecTask *_
     if (x1 < x0 || y1 < y0) return;
     int64_t ty0, tx0;
     tile_of(blockIdx.x - t.cta_begin, x0, x1, y0, &ty0, &tx0);
-    const DView U = t.v[0], K = t.v[1], V = t.v[2];
+    const DView U = t.v[0], K = t.v[1], V = t.v[LAP ? 1 : 2];
     const int64_t cmax = min(x1 + 1, NX - 1), rmin = max(y0 - 1, (int64_t)0), rmax = min(y1 + 1, NY - 1);
     float4 uv[NS], kv[NC];
 #pragma unroll
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(DT) diffusion_fwd_vec_kernel(const ExecTask *_
         const int e = threadIdx.x + c2 * DT;
         const int64_t i = ty0 + e / VQ, j = tx0 + 4 * (e % VQ);
         kv[c2] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i <= y1 && j <= x1) kv[c2] = ld4v(K, i, j);
+        if (!LAP && i <= y1 && j <= x1) kv[c2] = ld4v(K, i, j);
     }
     float ring = 0.f;
     const int re = threadIdx.x;
@@ -203,8 +206,8 @@ __global__ void __launch_bounds__(DT) diffusion_fwd_vec_kernel(const ExecTask *_
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const float cc = su[li][c + m];
-            o[m] = __fadd_rn(cc, __fmul_rn(kk[m], lap5(cc, su[li - 1][c + m], su[li + 1][c + m], su[li][c + m - 1],
-                                                       su[li][c + m + 1])));
+            const float l = lap5(cc, su[li - 1][c + m], su[li + 1][c + m], su[li][c + m - 1], su[li][c + m + 1]);
+            o[m] = LAP ? l : __fadd_rn(cc, __fmul_rn(kk[m], l));
         }
         float *dst = (float *)V.base + i * V.s[0] + j;
         if (j + 3 <= x1) {
@@ -490,9 +493,35 @@ uint32_t prepare_diffusion(ExecTask *t, int n, ExecParams &p) {
 
 cudaError_t launch_diffusion(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
     if (p.variant == 1)
-        diffusion_fwd_vec_kernel<<<ctas, DT, 0, st>>>(dev, p);
+        diffusion_fwd_vec_kernel<false><<<ctas, DT, 0, st>>>(dev, p);
     else
-        diffusion_fwd_scalar_kernel<<<ctas, DT, 0, st>>>(dev, p);
+        diffusion_fwd_scalar_kernel<false><<<ctas, DT, 0, st>>>(dev, p);
+    return cudaGetLastError();
+}
+
+// The Laplacian alone (G = L U): the forward kernel without its coefficient.
+uint32_t prepare_laplace(ExecTask *t, int n, ExecParams &p) {
+    const int64_t NY = p.shape[0][0], NX = p.shape[0][1];
+    bool vec = views_vec_ok(t, n, 2);
+    for (int i = 0; i < n; ++i)
+        if (t[i].t_lo[0] % 4 != 0) vec = false;
+    p.variant = vec ? 1 : 0;
+    uint32_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        int64_t w = std::min(t[i].t_hi[0], NX - 1) - t[i].t_lo[0] + 1;
+        int64_t h = std::min(t[i].t_hi[1], NY - 1) - t[i].t_lo[1] + 1;
+        t[i].cta_begin = total;
+        t[i].cta_count = (w > 0 && h > 0) ? (uint32_t)(((w + TX - 1) / TX) * ((h + TY - 1) / TY)) : 0;
+        total += t[i].cta_count;
+    }
+    return total;
+}
+
+cudaError_t launch_laplace(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
+    if (p.variant == 1)
+        diffusion_fwd_vec_kernel<true><<<ctas, DT, 0, st>>>(dev, p);
+    else
+        diffusion_fwd_scalar_kernel<true><<<ctas, DT, 0, st>>>(dev, p);
     return cudaGetLastError();
 }
 

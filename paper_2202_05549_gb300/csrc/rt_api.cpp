@@ -33,6 +33,12 @@ const BuiltinDef kBuiltins[] = {
      {LT_F64, LT_F32, LT_F32}, {1, 1, 1}, k::prepare_kmeans_update, k::launch_kmeans_update},
     {LT_K_GEMM_BF16, "global [i, j] => read A0[i, :], read A1[:, j], write A2[i, j]", 3, {LT_BF16, LT_BF16, LT_F32},
      {2, 2, 2}, k::prepare_gemm_bf16, k::launch_gemm_bf16},
+    {LT_K_LAPLACE2D, "global [i, j] => read A0[i-1:i+1, j-1:j+1], write A1[i, j]", 2, {LT_F32, LT_F32}, {2, 2},
+     k::prepare_laplace, k::launch_laplace},
+    {LT_K_EWISE2D, "global [i, j] => read A0[i, j], read A1[i, j], write A2[i, j]", 3, {LT_F32, LT_F32, LT_F32},
+     {2, 2, 2}, k::prepare_ewise, k::launch_ewise},
+    {LT_K_MULADD2D, "global [i, j] => read A0[i, j], read A1[i, j], readwrite A2[i, j]", 3, {LT_F32, LT_F32, LT_F32},
+     {2, 2, 2}, k::prepare_muladd, k::launch_muladd},
 };
 
 // Canonical annotation of a built-in; "{K}" stands for the launch's first

@@ -22,6 +22,7 @@ ROWREDUCE = L.LT_K_ROWREDUCE
 JACOBI2D_MULTI = L.LT_K_JACOBI2D_MULTI
 KMEANS_ASSIGN = L.LT_K_KMEANS_ASSIGN
 KMEANS_UPDATE = L.LT_K_KMEANS_UPDATE
+LAPLACE2D, EWISE2D, MULADD2D = L.LT_K_LAPLACE2D, L.LT_K_EWISE2D, L.LT_K_MULADD2D
 
 _NP = {F32: np.float32, BF16: np.uint16, U8: np.uint8, U32: np.uint32, F64: np.float64}
 

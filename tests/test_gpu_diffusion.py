@@ -142,3 +142,95 @@ def test_adjoint_staged_and_register_kernels_agree_bit_for_bit(dist_name):
     assert np.array_equal(out[0][1], out[1][1])
     _, du0, dk = oracle.diffusion_grad(u0.astype(np.float64), k.astype(np.float64), T)
     assert rel(out[0][0], du0) < 1e-4 and rel(out[0][1], dk) < 1e-4
+
+
+def _unfused_grad(u0, kap, T, chunk):
+    """Forward and gradient of J = sum u_T^2 as separate element-wise and
+    Laplacian launches, every state kept (the unfused form of the step)."""
+    n = u0.shape[0]
+    with lt.Context() as ctx:
+        dist = lt.Dist.tiles((chunk, chunk), halo=(1, 1))
+        mk = lambda: ctx.array(lt.F32, (n, n), dist)  # noqa: E731
+        K, H, W, G, DK = mk(), mk(), mk(), mk(), mk()
+        S = [mk() for _ in range(T + 1)]
+        lam = [mk(), mk()]
+        K.write(kap)
+        S[0].write(u0)
+        kl = ctx.kernel(lt.LAPLACE2D, "global [i, j] => read U[i-1:i+1, j-1:j+1], write G[i, j]",
+                        [("U", lt.F32), ("G", lt.F32)])
+        ke = ctx.kernel(lt.EWISE2D, "global [i, j] => read A[i, j], read B[i, j], write C[i, j]",
+                        [("A", lt.F32), ("B", lt.F32), ("C", lt.F32), ("op", lt.U32, False)])
+        km = ctx.kernel(lt.MULADD2D, "global [i, j] => read A[i, j], read B[i, j], readwrite C[i, j]",
+                        [("A", lt.F32), ("B", lt.F32), ("C", lt.F32)])
+        g = dict(grid=(n, n), block=(128, 2), superblock=(chunk, chunk))
+        for t in range(T):
+            kl.launch(**g, args=[S[t], H])
+            ke.launch(**g, args=[K, H, W, 1])
+            ke.launch(**g, args=[S[t], W, S[t + 1], 0])
+        ke.launch(**g, args=[S[T], S[T], lam[0], 0])
+        DK.fill(L.LT_INIT_ZERO)
+        for t in reversed(range(T)):
+            ke.launch(**g, args=[K, lam[0], W, 1])
+            kl.launch(**g, args=[W, G])
+            ke.launch(**g, args=[lam[0], G, lam[1], 0])
+            kl.launch(**g, args=[S[t], H])
+            km.launch(**g, args=[lam[0], H, DK])
+            lam.reverse()
+        ctx.synchronize()
+        return S[T].read(), lam[0].read(), DK.read()
+
+
+def test_unfused_laplace_and_elementwise_launches_match_numpy():
+    n = 300
+    a = si.uniform_field(2207, 20, n, n)
+    b = si.kappa_field(2207, 21, n, n)
+    c = si.uniform_field(2207, 22, n, n)
+    p = np.pad(a, 1)
+    lap = ((((p[:-2, 1:-1] + p[2:, 1:-1]) + p[1:-1, :-2]) + p[1:-1, 2:]) - np.float32(4.0) * a).astype(np.float32)
+    with lt.Context() as ctx:
+        dist = lt.Dist.tiles((128, 96), halo=(1, 1))
+        A, B, C, D = (ctx.array(lt.F32, (n, n), dist) for _ in range(4))
+        A.write(a)
+        B.write(b)
+        C.write(c)
+        kl = ctx.kernel(lt.LAPLACE2D, "global [i, j] => read U[i-1:i+1, j-1:j+1], write G[i, j]",
+                        [("U", lt.F32), ("G", lt.F32)])
+        ke = ctx.kernel(lt.EWISE2D, "global [i, j] => read A[i, j], read B[i, j], write C[i, j]",
+                        [("A", lt.F32), ("B", lt.F32), ("C", lt.F32), ("op", lt.U32, False)])
+        km = ctx.kernel(lt.MULADD2D, "global [i, j] => read A[i, j], read B[i, j], readwrite C[i, j]",
+                        [("A", lt.F32), ("B", lt.F32), ("C", lt.F32)])
+        g = dict(grid=(n, n), block=(128, 2), superblock=(96, 128))
+        kl.launch(**g, args=[A, D])
+        ctx.synchronize()
+        assert np.array_equal(D.read(), lap)
+        ke.launch(**g, args=[A, B, D, 0])
+        ctx.synchronize()
+        assert np.array_equal(D.read(), a + b)
+        ke.launch(**g, args=[A, B, D, 1])
+        ctx.synchronize()
+        assert np.array_equal(D.read(), a * b)
+        km.launch(**g, args=[A, B, C])
+        ctx.synchronize()
+        assert np.array_equal(C.read(), c + a * b)
+
+
+def test_unfused_gradient_matches_the_fp64_oracle_and_the_fused_adjoint():
+    n, T = 64, 12
+    u0 = si.uniform_field(si.SEED_DIFFUSION, si.STREAM_U, n, n)
+    kap = si.kappa_field(si.SEED_DIFFUSION, si.STREAM_KAPPA, n, n)
+    uT, du, dk = _unfused_grad(u0, kap, T, 32)
+    J, du_o, dk_o = oracle.diffusion_grad(u0, kap, T)
+    rel = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))  # noqa: E731
+    assert rel(du, du_o) <= 1e-4 and rel(dk, dk_o) <= 1e-4
+    # the forward steps as three launches each round like the fused step: the same states
+    with lt.Context() as ctx:
+        kf = ctx.kernel(lt.DIFFUSION2D, FWD, [("U", lt.F32), ("K", lt.F32), ("V", lt.F32)])
+        dist = lt.Dist.tiles((32, 32), halo=(1, 1))
+        U, V, K = (ctx.array(lt.F32, (n, n), dist) for _ in range(3))
+        U.write(u0)
+        K.write(kap)
+        for _ in range(T):
+            kf.launch(grid=(n, n), block=(128, 2), superblock=(32, 32), args=[U, K, V])
+            U, V = V, U
+        ctx.synchronize()
+        assert np.array_equal(uT, U.read())
