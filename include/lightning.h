@@ -374,6 +374,9 @@ typedef struct {
  * with repeat >= 2, so the later items' bounded waits (2 s) expire and
  * lt_synchronize reports LT_ERR_TIMEOUT without any fault.  Not cached. */
 #define LT_BATCH_TEST_STALL 256
+/* Test hook: skip the autotuner and use work items of 32 rows by 1024
+ * columns (so the column split of wide parts is exercised).  Not cached. */
+#define LT_BATCH_TEST_TILE_COLS 512
 
 lt_status lt_launch_batch(lt_ctx *ctx, const lt_launch_desc *descs, int32_t n, int32_t flags);
 
@@ -438,6 +441,7 @@ typedef struct {
     double ms_exec_hidden;    /* Execute kernel time during which a host<->device copy was running */
     uint64_t host_withheld_bytes; /* host pool bytes withheld as slow to copy (quarantine), now */
     uint64_t host_quarantined;    /* copies that put their host range in quarantine */
+    int64_t tuned_tile_cols;      /* autotuner choice of the last fused batch: tile columns (0: a part's width) */
 } lt_stats;
 
 lt_status lt_stats_get(lt_ctx *ctx, lt_stats *out);

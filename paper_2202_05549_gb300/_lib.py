@@ -84,7 +84,7 @@ class lt_stats(C.Structure):
         ("plans_reused", C.c_uint64), ("reduce_inplace", C.c_uint64), ("bytes_replica_wt", C.c_uint64),
         ("ms_span", C.c_double), ("ms_link_busy", C.c_double), ("ms_link_both", C.c_double),
         ("ms_exec_hidden", C.c_double), ("host_withheld_bytes", C.c_uint64),
-        ("host_quarantined", C.c_uint64)]
+        ("host_quarantined", C.c_uint64), ("tuned_tile_cols", C.c_int64)]
 
 
 class lt_launch_desc(C.Structure):
@@ -93,6 +93,7 @@ class lt_launch_desc(C.Structure):
 
 
 LT_BATCH_PLAIN, LT_BATCH_NO_GRAPH, LT_BATCH_RETUNE, LT_BATCH_TEST_STALL = 1, 2, 4, 256
+LT_BATCH_TEST_TILE_COLS = 512
 
 
 _vp = C.c_void_p

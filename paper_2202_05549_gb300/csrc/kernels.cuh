@@ -173,6 +173,8 @@ struct BatchItem {
     uint32_t iter;       // Jacobi iteration
     uint32_t row0;       // first row (tile), slice index (histogram) or first cell (replica)
     uint32_t nrows;      // rows (tile) or cells (replica)
+    uint32_t col0;       // tile: first column offset from the part's first column (a multiple of 128)
+    uint32_t ncols;      // tile: columns (0: to the part's last column)
 };
 struct BatchParams {
     const BatchItem *items;

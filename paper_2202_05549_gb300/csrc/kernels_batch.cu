@@ -85,13 +85,15 @@ __global__ void __launch_bounds__(BT, BOCC) batch_kernel(BatchParams P) {
                 float *dst = (float *)(even ? J.v : J.u);
                 const int64_t sd = even ? J.sv : J.su;
                 const int64_t ye = min((int64_t)(w.row0 + w.nrows) - 1, J.y1);
-                const uint32_t sx = (uint32_t)((J.x1 - J.x0 + JCOLS) / JCOLS), sy = (w.nrows + BR - 1) / BR;
+                const int64_t xa = J.x0 + (int64_t)w.col0;
+                const int64_t xe = w.ncols ? min(xa + (int64_t)w.ncols - 1, J.x1) : J.x1;
+                const uint32_t sx = (uint32_t)((xe - xa + JCOLS) / JCOLS), sy = (w.nrows + BR - 1) / BR;
                 // strip s = cy * sx + cx, s = warp, warp + 8, ...; (cx, cy) advance
                 // without a division per strip (32-bit: tiles are small)
                 uint32_t cx = warp % sx, cy = warp / sx;
                 for (uint32_t s = warp; s < sx * sy; s += BT / 32) {
-                    const int64_t js = J.x0 + (int64_t)cx * JCOLS, r0 = (int64_t)w.row0 + (int64_t)cy * BR;
-                    if (r0 <= ye) jacobi_strip<true, BR>(src, ss, dst, sd, ny, nx, js, r0, J.x1, ye, lane);
+                    const int64_t js = xa + (int64_t)cx * JCOLS, r0 = (int64_t)w.row0 + (int64_t)cy * BR;
+                    if (r0 <= ye) jacobi_strip<true, BR>(src, ss, dst, sd, ny, nx, js, r0, xe, ye, lane);
                     for (cx += BT / 32; cx >= sx; cx -= sx) ++cy;
                 }
             } else {

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cctype>
 #include <cstdio>
 #include <cstdlib>
@@ -408,7 +409,7 @@ struct lt_ctx {
     std::vector<cudaEvent_t> tev_pool;
     std::unique_ptr<PendingLaunch> pending;
     std::unique_ptr<BatchCache> batch;
-    std::map<std::pair<int64_t, int64_t>, std::pair<int, int>> tuned;  // batch shape -> (tile rows, slice)
+    std::map<std::pair<int64_t, int64_t>, std::array<int, 3>> tuned;  // batch shape -> (tile rows, cols, slice)
     int64_t cur_group = 0;
     cudaEvent_t timer[2] = {nullptr, nullptr};
     cudaEvent_t timer_join[2] = {nullptr, nullptr};

@@ -5,13 +5,14 @@
 extern "C" {
 
 // ---------------------------------------------------------------- batches
-// Tables of one fused batch for tile height th and histogram slice hs;
-// `iters_cap` > 0 limits every instance to that many iterations (tuning).
+// Tables of one fused batch for tiles of th rows by tw columns (0: the
+// part's width) and histogram slice hs; `iters_cap` > 0 limits every
+// instance to that many iterations (tuning).
 // A Jacobi instance becomes one part per superblock of its launch (one chunk
 // of each buffer) and one replica table entry per halo box its parts keep
 // current; both buffers share the distribution, so the same chunks serve
 // when they swap roles.
-static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int hs, int iters_cap,
+static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int tw, int hs, int iters_cap,
                          std::vector<BatchJacobi> *jac, std::vector<BatchHist> *hist, std::vector<BatchRep> *reps,
                          std::vector<BatchItem> *items, size_t *ncounters, bool stall = false) {
     jac->clear();
@@ -52,7 +53,8 @@ static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int hs, int it
             const uint32_t part = (uint32_t)jac->size();
             jac->push_back(b);
             in.nparts++;
-            in.per_iter += (uint32_t)((b.y1 - b.y0 + th) / th);
+            const int64_t pw = b.x1 - b.x0 + 1;
+            in.per_iter += (uint32_t)((b.y1 - b.y0 + th) / th) * (uint32_t)(tw ? (pw + tw - 1) / tw : 1);
             for (const auto &pc : av->replicas) {
                 BatchRep r{};
                 const int64_t cj = pc.chunk;
@@ -83,7 +85,7 @@ static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int hs, int it
         b.h = (uint64_t)(uintptr_t)(dptr(c, bs.hist[h].h->cs[0].off));
         hist->push_back(b);
         int64_t ns = (b.len + hs - 1) / hs;
-        for (int64_t k = 0; k < ns; ++k) items->push_back({(1u << 30) | (uint32_t)h, 0u, (uint32_t)k, 0u});
+        for (int64_t k = 0; k < ns; ++k) items->push_back({(1u << 30) | (uint32_t)h, 0u, (uint32_t)k, 0u, 0u, 0u});
     }
     for (int t = 0; t < rmax; ++t)
         for (const Inst &in : inst) {
@@ -91,15 +93,18 @@ static void batch_tables(lt_ctx *c, const BatchShape &bs, int th, int hs, int it
             if (stall && t == 0 && in.repeat >= 2) continue;  // test hook: iteration 1 then waits forever (bounded)
             for (uint32_t p = in.part0; p < in.part0 + in.nparts; ++p) {
                 const BatchJacobi &b = (*jac)[p];
+                const int64_t pw = b.x1 - b.x0 + 1;
                 for (int64_t r = b.y0; r <= b.y1; r += th)
-                    items->push_back({p, (uint32_t)t, (uint32_t)r, (uint32_t)std::min<int64_t>(th, b.y1 - r + 1)});
+                    for (int64_t c0 = 0; c0 < pw; c0 += tw ? tw : pw)
+                        items->push_back({p, (uint32_t)t, (uint32_t)r, (uint32_t)std::min<int64_t>(th, b.y1 - r + 1),
+                                          (uint32_t)c0, (uint32_t)(tw ? tw : 0)});
             }
             for (uint32_t ri = in.rep0; ri < in.rep0 + in.nreps; ++ri) {
                 const BatchRep &r = (*reps)[ri];
                 const uint64_t cells = (uint64_t)(r.hi[0] - r.lo[0] + 1) * (uint64_t)(r.hi[1] - r.lo[1] + 1);
                 for (uint64_t e = 0; e < cells; e += REP_CELLS)
                     items->push_back({(2u << 30) | ri, (uint32_t)t, (uint32_t)e,
-                                      (uint32_t)std::min<uint64_t>(REP_CELLS, cells - e)});
+                                      (uint32_t)std::min<uint64_t>(REP_CELLS, cells - e), 0u, 0u});
             }
         }
     *ncounters = (size_t)done + 2;  // + queue head + abort flag
@@ -309,7 +314,9 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
     key.push_back(~0ull);
     for (auto &H : bs.hist) key.insert(key.end(), {(uint64_t)H.x->id, H.x->cs[0].off, (uint64_t)H.h->id, H.h->cs[0].off});
     const bool stall = (flags & LT_BATCH_TEST_STALL) != 0;
+    const bool force_cols = (flags & LT_BATCH_TEST_TILE_COLS) != 0;
     if (stall) key.push_back(0x57A11ull);  // never matches a real batch
+    if (force_cols) key.push_back(0xC015ull);
     bool use_graph = !(flags & LT_BATCH_NO_GRAPH) && !stall;
     std::pair<int64_t, int64_t> shape_key = {(int64_t)bs.jac.size(), (int64_t)bs.hist.size()};
     if (!c->batch || c->batch->key != key || (flags & LT_BATCH_RETUNE) || (use_graph && !c->batch->exec)) {
@@ -328,44 +335,50 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
         size_t ncnt = 0;
         // autotuner: time every candidate on the first iteration of the batch
         // (it writes only V and H, which the real run overwrites)
-        if (stall && !c->tuned.count(shape_key)) c->tuned[shape_key] = {32, 256 << 10};
+        if (stall && !c->tuned.count(shape_key)) c->tuned[shape_key] = {32, 0, 256 << 10};
         if (!c->tuned.count(shape_key) || (flags & LT_BATCH_RETUNE)) {
             if ((st = sync_all(c))) {
                 unpin();
                 return st;
             }
+            // work-item shapes: tile rows, tile columns (0: a part's full width) and histogram slice
             const int ths[] = {16, 32, 64, 128};
+            const int tws[] = {0, 1024};
             const int hss[] = {64 << 10, 256 << 10, 1 << 20};
+            int64_t widest = 0;
+            for (auto &J : bs.jac) widest = std::max(widest, J.u->g.shape[1]);
             float best = 1e30f;
-            std::pair<int, int> pick = {32, 256 << 10};
+            std::array<int, 3> pick = {32, 0, 256 << 10};
             cudaEvent_t e0, e1;
             CK(c, cudaEventCreate(&e0));
             CK(c, cudaEventCreate(&e1));
             for (int th : ths)
-                for (int hs : hss) {
-                    if (bs.hist.empty() && hs != hss[0]) continue;
-                    if (bs.jac.empty() && th != ths[0]) continue;
-                    batch_tables(c, bs, th, hs, 1, &jac, &hist, &reps, &items, &ncnt);
-                    BatchCache tc;
-                    if ((st = batch_upload(c, &tc, jac, hist, reps, items, ncnt))) {
-                        unpin();
-                        return st;
+                for (int tw : tws)
+                    for (int hs : hss) {
+                        if (bs.hist.empty() && hs != hss[0]) continue;
+                        if (bs.jac.empty() && (th != ths[0] || tw != tws[0])) continue;
+                        if (tw && widest <= tw) continue;  // no part wider than the tile: same as full width
+                        batch_tables(c, bs, th, tw, hs, 1, &jac, &hist, &reps, &items, &ncnt);
+                        BatchCache tc;
+                        if ((st = batch_upload(c, &tc, jac, hist, reps, items, ncnt))) {
+                            unpin();
+                            return st;
+                        }
+                        tc.bp.hist_slice = hs;
+                        tc.ctas = sms * k::batch_ctas_per_sm();
+                        CK(c, cudaEventRecord(e0, c->st[S_COMP]));
+                        CK(c, batch_enqueue(c, tc, c->st[S_COMP]));
+                        CK(c, cudaEventRecord(e1, c->st[S_COMP]));
+                        CK(c, cudaEventSynchronize(e1));
+                        float ms = 0;
+                        CK(c, cudaEventElapsedTime(&ms, e0, e1));
+                        c->stats.kernels += 2;
+                        if (ms < best) {
+                            best = ms;
+                            pick = {th, tw, hs};
+                        }
+                        c->dev.release(tc.off, tc.bytes, FenceSet());
                     }
-                    tc.bp.hist_slice = hs;
-                    tc.ctas = sms * k::batch_ctas_per_sm();
-                    CK(c, cudaEventRecord(e0, c->st[S_COMP]));
-                    CK(c, batch_enqueue(c, tc, c->st[S_COMP]));
-                    CK(c, cudaEventRecord(e1, c->st[S_COMP]));
-                    CK(c, cudaEventSynchronize(e1));
-                    float ms = 0;
-                    CK(c, cudaEventElapsedTime(&ms, e0, e1));
-                    c->stats.kernels += 2;
-                    if (ms < best) {
-                        best = ms;
-                        pick = {th, hs};
-                    }
-                    c->dev.release(tc.off, tc.bytes, FenceSet());
-                }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             if ((st = sync_all(c))) {
@@ -375,14 +388,15 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
             c->tuned[shape_key] = pick;
         }
         auto tp = c->tuned[shape_key];
+        if (force_cols) tp = {32, 1024, 256 << 10};
         auto bc = std::make_unique<BatchCache>();
         bc->key = key;
-        batch_tables(c, bs, tp.first, tp.second, 0, &jac, &hist, &reps, &items, &ncnt, stall);
+        batch_tables(c, bs, tp[0], tp[1], tp[2], 0, &jac, &hist, &reps, &items, &ncnt, stall);
         if ((st = batch_upload(c, bc.get(), jac, hist, reps, items, ncnt))) {
             unpin();
             return st;
         }
-        bc->bp.hist_slice = tp.second;
+        bc->bp.hist_slice = tp[2];
         bc->ctas = sms * k::batch_ctas_per_sm();
         if (use_graph) {
             cudaGraph_t graph = nullptr;
@@ -399,8 +413,9 @@ lt_status lt_launch_batch(lt_ctx *c, const lt_launch_desc *d, int32_t n, int32_t
     } else if (use_graph) {
         c->stats.graph_replays++;
     }
-    c->stats.tuned_tile_rows = c->tuned[shape_key].first;
-    c->stats.tuned_hist_slice = c->tuned[shape_key].second;
+    c->stats.tuned_tile_rows = force_cols ? 32 : c->tuned[shape_key][0];
+    c->stats.tuned_tile_cols = force_cols ? 1024 : c->tuned[shape_key][1];
+    c->stats.tuned_hist_slice = force_cols ? (256 << 10) : c->tuned[shape_key][2];
     // run: wait for every staged chunk, then the graph (or the kernels)
     op_begin(c, S_COMP, "batch");
     FenceSet w;

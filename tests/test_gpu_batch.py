@@ -95,7 +95,7 @@ def test_batch_replay_skips_the_checks_but_a_changed_launch_is_checked():
         check(jac, hist, 6)
 
 
-@pytest.mark.parametrize("graph", [0, L.LT_BATCH_NO_GRAPH])
+@pytest.mark.parametrize("graph", [0, L.LT_BATCH_NO_GRAPH, L.LT_BATCH_TEST_TILE_COLS])
 def test_batch_of_chunked_instances_with_halos_is_fused_and_exact(graph):
     # chunked instances in the device-side queue: row bands, 2-D tiles with
     # halos (superblocks smaller than the chunks, and a ragged edge) next to
@@ -107,7 +107,8 @@ def test_batch_of_chunked_instances_with_halos_is_fused_and_exact(graph):
         cases = [((200, 300), lt.Dist.rows(64, halo=1), (300, 64)),
                  ((333, 517), lt.Dist.tiles((128, 256), halo=(1, 1)), (256, 128)),
                  ((512, 1024), lt.Dist.tiles((256, 512), halo=(1, 1)), (256, 128)),
-                 ((130, 130), None, (0, 0))]
+                 ((130, 130), None, (0, 0)),
+                 ((100, 2500), lt.Dist.rows(40, halo=1), (2500, 40))]    # parts wider than 1024 columns
         launches, jac = [], []
         for q, ((ny, nx), dist, sb) in enumerate(cases):
             u0 = si.uniform_field(si.SEED_BATCH, si.STREAM_BATCH_JACOBI0 + 50 + q, ny, nx)
@@ -134,6 +135,9 @@ def test_batch_of_chunked_instances_with_halos_is_fused_and_exact(graph):
             jac = [(u0, V, U) for (u0, U, V) in jac]
         s = ctx.stats()
         assert s["batches_fused"] == 2 and s["batches_plain"] == 0
+        assert s["tuned_tile_cols"] in (0, 1024)
+        if graph == L.LT_BATCH_TEST_TILE_COLS:
+            assert s["tuned_tile_cols"] == 1024
 
 
 def test_batch_of_chunked_instances_without_halo_falls_back_to_plain():
