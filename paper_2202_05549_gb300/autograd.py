@@ -103,6 +103,7 @@ class DiffusionPlan:
 
 
 _ctx_cache: dict = {}
+_plan_cache: dict = {}  # (context, shape, steps, ckpt, chunk, superblock) -> idle DiffusionPlans
 
 
 def _context(device: int, budget: int) -> lt.Context:
@@ -110,6 +111,26 @@ def _context(device: int, budget: int) -> lt.Context:
     if key not in _ctx_cache:
         _ctx_cache[key] = lt.Context(device=device, hbm_budget=budget)
     return _ctx_cache[key]
+
+
+def _plan(ectx, ny, nx, steps, ckpt, chunk, superblock, dist):
+    """An idle plan of this shape (its arrays and kernels are kept between
+    calls: creating 19 arrays and registering two kernels per call cost
+    host time the GPU waited for), or a new one."""
+    key = (id(ectx), ny, nx, steps, ckpt, chunk, tuple(superblock))
+    idle = _plan_cache.setdefault(key, [])
+    return idle.pop() if idle else DiffusionPlan(ectx, ny, nx, steps, ckpt, dist, superblock), key
+
+
+def clear_caches():
+    """Release the cached plans and contexts (their HBM pools)."""
+    for plans in _plan_cache.values():
+        for p in plans:
+            p.release()
+    _plan_cache.clear()
+    for c in _ctx_cache.values():
+        c.close()
+    _ctx_cache.clear()
 
 
 class DiffusionChunked(torch.autograd.Function):
@@ -128,7 +149,7 @@ class DiffusionChunked(torch.autograd.Function):
         budget = int(nfields * field * 1.15 + field * 2.5) + (256 << 20)
         ectx = _context(u0.device.index or 0, budget)
         dist = lt.Dist.tiles((chunk, chunk), halo=(1, 1)) if chunk else lt.Dist.block()
-        plan = DiffusionPlan(ectx, ny, nx, steps, ckpt_every, dist, superblock)
+        plan, key = _plan(ectx, ny, nx, steps, ckpt_every, chunk, superblock, dist)
         u0c, kc = u0.detach().contiguous(), kappa.detach().contiguous()
         torch.cuda.synchronize(u0.device)
         plan.K.write_device(kc.data_ptr(), field)
@@ -137,6 +158,7 @@ class DiffusionChunked(torch.autograd.Function):
         out = torch.empty_like(u0c)
         plan.ck[-1].read_device(out.data_ptr(), field)
         ctx.plan = plan
+        ctx.plan_key = key
         return out
 
     @staticmethod
@@ -151,6 +173,6 @@ class DiffusionChunked(torch.autograd.Function):
         dk = torch.empty_like(g)
         lam0.read_device(du0.data_ptr(), field)
         plan.G.read_device(dk.data_ptr(), field)
-        plan.release()
+        _plan_cache.setdefault(ctx.plan_key, []).append(plan)  # idle again: the next call of this shape reuses it
         ctx.plan = None
         return du0, dk, None, None, None, None
