@@ -73,8 +73,9 @@ def parse():
     p.add_argument("--tb", type=int, default=1, help="Jacobi iterations per launch (temporal blocking, halo = tb)")
     p.add_argument("--iters", type=int, default=0,
                    help="Jacobi iterations per step (one run of the workload; default 20 out-of-core, 10 in-core)")
-    p.add_argument("--user-kernel", action="store_true",
-                   help="stencil workloads: run a Jacobi body compiled at run time (NVRTC) instead of the built-in")
+    p.add_argument("--user-kernel", nargs="?", const="scalar", default=None, choices=["scalar", "vec"],
+                   help="stencil workloads: run a Jacobi body compiled at run time (NVRTC) instead of the built-in: "
+                        "one cell per thread (scalar, the default) or four cells per thread from float4 rows (vec)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--wl-steps", type=int, default=5, help="timed steps of each workload of the default run")
     p.add_argument("--wl-warmup", type=int, default=3, help="warm-up steps of each workload of the default run")
@@ -265,6 +266,42 @@ __device__ void jacobi(dim3 vb, int64_t ny, int64_t nx, lightning::Matrix<float>
     V(i, j) = a / 5.0f;
 }
 """
+
+
+# The same Jacobi with four cells per thread, as a user would write it for
+# speed: float4 loads of the three rows (rows of every chunk are 16-byte
+# aligned at global columns that are multiples of 4), the west and east
+# neighbours one by one, the same sum order and division per cell.  Its
+# annotation reads columns 4j-1 .. 4j+4 and writes 4j .. 4j+3.
+USER_JACOBI_VEC = r"""
+__device__ void jacobi4(dim3 vb, int64_t ny, int64_t nx, lightning::Matrix<float> U, lightning::Matrix<float> V) {
+    const int64_t i = (int64_t)vb.y * blockDim.y + threadIdx.y;
+    const int64_t j = 4 * ((int64_t)vb.x * blockDim.x + threadIdx.x);
+    if (i >= ny || j >= nx) return;
+    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float4 c = *(const float4 *)&U(i, j);
+    float4 n = i > 0 ? *(const float4 *)&U(i - 1, j) : z;
+    float4 s = i + 1 < ny ? *(const float4 *)&U(i + 1, j) : z;
+    const float w = j > 0 ? U(i, j - 1) : 0.0f;
+    const float e = j + 4 < nx ? U(i, j + 4) : 0.0f;
+    if (j + 1 >= nx) { c.y = 0.0f; n.y = 0.0f; s.y = 0.0f; }   // cells beyond the grid read as zero
+    if (j + 2 >= nx) { c.z = 0.0f; n.z = 0.0f; s.z = 0.0f; }
+    if (j + 3 >= nx) { c.w = 0.0f; n.w = 0.0f; s.w = 0.0f; }
+    float4 o;
+    o.x = (((((c.x + n.x) + s.x) + w) + c.y)) / 5.0f;
+    o.y = (((((c.y + n.y) + s.y) + c.x) + c.z)) / 5.0f;
+    o.z = (((((c.z + n.z) + s.z) + c.y) + c.w)) / 5.0f;
+    o.w = (((((c.w + n.w) + s.w) + c.z) + e)) / 5.0f;
+    if (j + 3 < nx) {
+        *(float4 *)&V(i, j) = o;
+    } else {
+        V(i, j) = o.x;
+        if (j + 1 < nx) V(i, j + 1) = o.y;
+        if (j + 2 < nx) V(i, j + 2) = o.z;
+    }
+}
+"""
+USER_JACOBI_VEC_ANN = "global [i, j] => read U[i-1:i+1, 4*j-1:4*j+4], write V[i, 4*j:4*j+3]"
 
 
 def ctx_flags(args):
@@ -505,6 +542,9 @@ def run_lightning(args, rank, world, local, grp, links=None):
     user = args.user_kernel and tb == 1
     if tb > 1:
         k = ctx.kernel(lt.JACOBI2D_MULTI, ann, [("U", lt.F32), ("V", lt.F32), ("k", lt.U32, False)])
+    elif user == "vec":
+        k = ctx.kernel_from_source(USER_JACOBI_VEC, "jacobi4", USER_JACOBI_VEC_ANN,
+                                   [("ny", lt.U32, False), ("nx", lt.U32, False), ("U", lt.F32), ("V", lt.F32)])
     elif user:
         k = ctx.kernel_from_source(USER_JACOBI, "jacobi", ann, [("ny", lt.U32, False), ("nx", lt.U32, False),
                                                                   ("U", lt.F32), ("V", lt.F32)])
@@ -523,7 +563,10 @@ def run_lightning(args, rank, world, local, grp, links=None):
     def step():
         extra = [tb] if tb > 1 else []
         for _ in range(launches):
-            if user:
+            if user == "vec":  # four columns per thread: the grid and superblocks are a quarter as wide
+                k.launch(grid=((nx + 3) // 4, ny), block=(64, 4), superblock=(sb[0] // 4, sb[1]),
+                         args=[ny, nx, bufs[0], bufs[1]])
+            elif user:
                 k.launch(grid=(nx, ny), block=(128, 4), superblock=sb, args=[ny, nx, bufs[0], bufs[1]])
             else:
                 k.launch(grid=(nx, ny), block=(128, 4), superblock=sb, args=[bufs[0], bufs[1]] + extra)
@@ -544,7 +587,7 @@ def run_lightning(args, rank, world, local, grp, links=None):
     if tb > 1:
         kname = "jacobi2d_multi_kernel"
     elif user:
-        kname = "lt_user_wrapper (NVRTC)"
+        kname = "lt_user_wrapper (NVRTC, %s body)" % user
     else:
         kname = {1: "jacobi2d_vec_kernel"}.get(variant, "jacobi2d_scalar_kernel")
     # DRAM traffic records: the in-core grid keeps part of its working set in L2
@@ -603,7 +646,7 @@ def run_lightning(args, rank, world, local, grp, links=None):
         "ms_per_step": round(t_max * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64 uniform[0,1))",
         "config": {**jacobi_config(args, world),
-                   "workload": workload + (" (Jacobi body compiled at run time)" if user else ""),
+                   "workload": workload + (f" (Jacobi body compiled at run time, {user})" if user else ""),
                    "stale_buffer": "written back at the closing synchronize" if args.keep_stale else
                    "discarded before the closing synchronize (lt_array_discard): the run needs only its result",
                    "hbm_budget_bytes": pl["budget"], "host_pool_bytes": pl["host"],

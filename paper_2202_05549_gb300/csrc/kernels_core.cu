@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "tma.cuh"
+#include "copy_staged.cuh"
 
 namespace lt {
 namespace {
@@ -132,8 +134,7 @@ __device__ __forceinline__ void copy_elem(const char *s, char *d, int esize) {
 // One CTA per work unit (a run of rows, or a segment of one long row, of
 // about LT_COPY_UNIT elements); the piece is found by binary search and read
 // in place (no local copy of the record).
-__global__ void __launch_bounds__(256, 3) copy_kernel(const CopyPiece *__restrict__ pieces, int n) {
-    const uint64_t u = blockIdx.x;
+__device__ __forceinline__ void copy_unit(const CopyPiece *__restrict__ pieces, int n, const uint64_t u) {
     const int pi = find_piece_u(pieces, n, u);
     const CopyPiece &p = pieces[pi];
     const int inner = p.nd - 1;
@@ -278,6 +279,103 @@ __global__ void __launch_bounds__(256, 3) copy_kernel(const CopyPiece *__restric
     }
 }
 
+__global__ void __launch_bounds__(256, 3) copy_kernel(const CopyPiece *__restrict__ pieces, int n) {
+    copy_unit(pieces, n, blockIdx.x);
+}
+
+// Staged variant: a unit of whole rows whose body (the 16-byte aligned part
+// of every row, equally aligned in source and destination) fits the stage
+// moves through shared memory with bulk asynchronous copies (TMA, no tensor
+// map): one thread issues a bulk load per row into the stage, completing on
+// an mbarrier, then a bulk store per row out of it; the other threads copy
+// the rows' unaligned heads and tails meanwhile.  Other units take the
+// register path.  The wait is bounded: on expiry the kernel records 0x6730,
+// lets its loads land (bounded) and returns.
+constexpr int BULK_STAGE = 64 * 1024;
+
+__device__ __forceinline__ void bulk_load_row(void *smem, const void *gmem, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            tma::smem_u32(smem)),
+        "l"(gmem), "r"(bytes), "r"(tma::smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_store_row(void *gmem, const void *smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gmem),
+                 "r"(tma::smem_u32(smem)), "r"(bytes)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(256, 3) copy_bulk_kernel(const CopyPiece *__restrict__ pieces, int n, uint32_t *err) {
+    extern __shared__ __align__(128) unsigned char stage[];
+    __shared__ __align__(8) uint64_t bar;
+    const uint64_t u = blockIdx.x;
+    const int pi = find_piece_u(pieces, n, u);
+    const CopyPiece &p = pieces[pi];
+    const int es = p.esize;
+    bool bulk = p.nd == 2 && p.src.s[1] == 1 && p.dst.s[1] == 1 && ((p.src.s[0] * es) & 15) == 0 &&
+                ((p.dst.s[0] * es) & 15) == 0;
+    int64_t r0 = 0, r1 = 0, head = 0, tail0 = 0, ncol = 0;
+    const char *sb = nullptr;
+    char *db = nullptr;
+    uint32_t rowbytes = 0;
+    if (bulk) {
+        const int64_t w = copy_piece_width(p), rows = copy_piece_rows(p), rpu = copy_piece_rows_per_unit(p);
+        bulk = w <= LT_COPY_UNIT && w * es >= 512;  // whole rows in the unit, not a narrow piece
+        if (bulk) {
+            const int64_t lu = (int64_t)(u - p.unit_begin);
+            r0 = lu * rpu;
+            r1 = min(r0 + rpu, rows);
+            ncol = w;
+            sb = (const char *)(p.src.base + (uint64_t)(((p.lo[0] + r0) * p.src.s[0] + p.lo[1]) * es));
+            db = (char *)(p.dst.base + (uint64_t)(((p.lo[0] + r0) * p.dst.s[0] + p.lo[1]) * es));
+            bulk = ((uintptr_t)sb & 15) == ((uintptr_t)db & 15);
+            head = (int64_t)(((16 - ((uintptr_t)sb & 15)) & 15) / es);
+            if (head > ncol) head = ncol;
+            rowbytes = (uint32_t)((ncol - head) * es / 16 * 16);
+            tail0 = head + rowbytes / es;
+            bulk = bulk && rowbytes > 0 && (r1 - r0) * (int64_t)rowbytes <= BULK_STAGE;
+        }
+    }
+    if (!bulk) {
+        copy_unit(pieces, n, u);
+        return;
+    }
+    const int64_t sp = p.src.s[0] * es, dp = p.dst.s[0] * es;
+    const uint32_t nr = (uint32_t)(r1 - r0);
+    if (threadIdx.x == 0) {
+        tma::mbar_init(&bar, 1);
+        tma::mbar_init_fence();
+    }
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        tma::mbar_expect_tx(&bar, nr * rowbytes);
+        for (uint32_t r = 0; r < nr; ++r) bulk_load_row(stage + r * rowbytes, sb + r * sp + head * es, rowbytes, &bar);
+    }
+    // the unaligned heads and tails of the rows, by the other threads
+    const uint32_t ns = (uint32_t)(head + (ncol - tail0));
+    for (uint32_t e = threadIdx.x; e < nr * ns; e += blockDim.x) {
+        const uint32_t r = e / ns, k = e % ns;
+        const int64_t col = k < (uint32_t)head ? (int64_t)k : tail0 + (int64_t)(k - (uint32_t)head);
+        copy_elem(sb + r * sp + col * es, db + r * dp + col * es, es);
+    }
+    if (threadIdx.x == 0) {
+        ok = tma::mbar_wait(&bar, 0, err, 0x6730u);
+        if (ok) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (uint32_t r = 0; r < nr; ++r) bulk_store_row(db + r * dp + head * es, stage + r * rowbytes, rowbytes);
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            // the stage must stay valid until the stores have read it
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        } else {
+            tma::mbar_drain(&bar, 0);  // let the loads in flight land before the CTA leaves
+        }
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ int find_rpiece(const ReducePiece *p, int n, uint64_t e) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -358,6 +456,19 @@ cudaError_t copy_pieces(const CopyPiece *dev, int n, uint64_t total_units, cudaS
     if (!n || !total_units) return cudaSuccess;
     if (total_units > 0x7FFFFFFFull) return cudaErrorInvalidValue;
     copy_kernel<<<(unsigned)total_units, 256, 0, st>>>(dev, n);
+    return cudaGetLastError();
+}
+
+cudaError_t copy_pieces_staged(const CopyPiece *dev, int n, uint64_t total_units, uint32_t *err, cudaStream_t st) {
+    if (!n || !total_units) return cudaSuccess;
+    if (total_units > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(copy_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BULK_STAGE);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    copy_bulk_kernel<<<(unsigned)total_units, 256, BULK_STAGE, st>>>(dev, n, err);
     return cudaGetLastError();
 }
 

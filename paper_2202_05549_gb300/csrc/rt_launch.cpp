@@ -2,6 +2,7 @@
 // (groups of superblocks, temporaries, pack, execute, unpack, reduce,
 // replica updates, streaming through the host pool); see rt.hpp.
 #include "rt.hpp"
+#include "copy_staged.cuh"
 
 namespace lt {
 namespace rt {
@@ -449,7 +450,9 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             if ((st = upload(c, packs.data(), packs.size() * sizeof(CopyPiece), &dptr, &roff))) return st;
             if (!c->dry) {
                 TimeScope ts(c, CAT_COPYK);
-                CK(c, k::copy_pieces((const CopyPiece *)dptr, (int)packs.size(), rows, c->st[S_COMP]));
+                CK(c, c->no_staged ? k::copy_pieces((const CopyPiece *)dptr, (int)packs.size(), rows, c->st[S_COMP])
+                                   : k::copy_pieces_staged((const CopyPiece *)dptr, (int)packs.size(), rows,
+                                                           c->err_word, c->st[S_COMP]));
                 c->stats.kernels++;
             }
             uint64_t q;
@@ -699,7 +702,9 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
             if ((st = upload(c, outs.data(), outs.size() * sizeof(CopyPiece), &dptr, &roff))) return st;
             if (!c->dry) {
                 TimeScope ts(c, CAT_COPYK);
-                CK(c, k::copy_pieces((const CopyPiece *)dptr, (int)outs.size(), rows, c->st[S_COMP]));
+                CK(c, c->no_staged ? k::copy_pieces((const CopyPiece *)dptr, (int)outs.size(), rows, c->st[S_COMP])
+                                   : k::copy_pieces_staged((const CopyPiece *)dptr, (int)outs.size(), rows,
+                                                           c->err_word, c->st[S_COMP]));
                 c->stats.kernels++;
             }
             if ((st = op_end(c, &outq))) return st;

@@ -384,3 +384,26 @@ def test_dependent_launches_and_deferred_fences_stay_exact(flags):
         ctx.synchronize()
         assert ctx.stats()["evictions"] > 0
         assert np.array_equal(U.read(), want)
+
+
+@pytest.mark.parametrize("flags", [0, L.LT_FLAG_NO_STAGED])
+@pytest.mark.parametrize("shape,dist,sb", [
+    ((301, 517), lt.Dist.tiles((64, 128)), (0, 0)),          # odd row pitch: unaligned heads and tails
+    ((301, 517), lt.Dist.tiles((64, 128)), (96, 160)),       # superblocks across chunks: packs and write-backs
+    ((200, 4100), lt.Dist.tiles((40, 3000)), (0, 0)),        # rows of 12 KB: several rows per stage
+    ((130, 1024), lt.Dist.rows(50), (0, 0)),                 # aligned rows, ragged bands
+    ((257, 600), lt.Dist.cols(200), (0, 0)),                 # one-column packs (narrow pieces)
+])
+def test_pack_through_shared_memory_and_registers_bit_exact(flags, shape, dist, sb):
+    # Packs and write-backs of whole aligned rows move through shared memory
+    # with bulk asynchronous copies; LT_FLAG_NO_STAGED keeps them on the
+    # register path.  Both are exact copies.
+    ny, nx = shape
+    u0 = si.uniform_field(si.SEED_JACOBI_INCORE, 7, ny, nx)
+    want = oracle.jacobi2d(u0, 3)
+    with lt.Context(flags=flags) as ctx:
+        ctx.log_enable()
+        got = run_jacobi(ctx, u0, dist, 3, block=(32, 4), superblock=sb)
+        kinds = {t["kind"] for t in ctx.log()}
+    assert "pack" in kinds
+    assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"

@@ -197,3 +197,28 @@ def test_user_kernel_with_shared_memory_and_barrier_bit_exact():
             src, dst = dst, src
         ctx.synchronize()
         assert np.array_equal(src.read(), want)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dist_kind", ["tiles_halo", "block", "rows_halo"])
+def test_user_kernel_four_cells_per_thread_bit_exact(dist_kind):
+    # the benchmark's vector body: four columns per thread from float4 rows,
+    # annotated "read U[i-1:i+1, 4*j-1:4*j+4], write V[i, 4*j:4*j+3]"; a ragged
+    # width (not a multiple of 4) exercises the masked edge
+    import bench
+    ny, nx, iters = 300, 517, 3
+    u0 = si.uniform_field(2203, 13, ny, nx)
+    dist, sb = {"tiles_halo": (lt.Dist.tiles((128, 256), halo=(1, 1)), (64, 128)),
+                "block": (lt.Dist.block(), (0, 0)),
+                "rows_halo": (lt.Dist.rows(100, halo=1), ((nx + 3) // 4, 100))}[dist_kind]
+    with lt.Context() as ctx:
+        U = ctx.array(lt.F32, (ny, nx), dist)
+        V = ctx.array(lt.F32, (ny, nx), dist)
+        U.write(u0)
+        k = ctx.kernel_from_source(bench.USER_JACOBI_VEC, "jacobi4", bench.USER_JACOBI_VEC_ANN,
+                                   [("ny", lt.U32, False), ("nx", lt.U32, False), ("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=((nx + 3) // 4, ny), block=(64, 4), superblock=sb, args=[ny, nx, U, V])
+            U, V = V, U
+        ctx.synchronize()
+        assert np.array_equal(U.read(), oracle.jacobi2d(u0, iters))
