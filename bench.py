@@ -539,7 +539,7 @@ def run_lightning(args, rank, world, local, grp, links=None):
     U = ctx.array(lt.F32, (ny, nx), dist)
     V = ctx.array(lt.F32, (ny, nx), dist)
     U.fill(L.LT_INIT_UNIFORM, seed=seed, stream=0)
-    user = args.user_kernel and tb == 1
+    user = args.user_kernel if tb == 1 else None
     if tb > 1:
         k = ctx.kernel(lt.JACOBI2D_MULTI, ann, [("U", lt.F32), ("V", lt.F32), ("k", lt.U32, False)])
     elif user == "vec":
