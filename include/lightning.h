@@ -111,8 +111,10 @@ typedef struct {
  *   the host logic; LT_FLAG_FIXED_SWEEP visits superblocks in index order
  *   every launch (default: the order alternates between launches, so the
  *   chunks used last are reused first); LT_FLAG_NO_STAGED makes the stencil
- *   built-ins use their register kernels instead of the TMA-staged ones (same
- *   results; for comparing the two); LT_FLAG_NO_LINK_QUARANTINE turns off
+ *   built-ins use their register kernels instead of the TMA-staged ones, and
+ *   packs, write-backs and replica updates copy through registers instead of
+ *   through shared memory with bulk asynchronous copies (same results; for
+ *   comparing the two); LT_FLAG_NO_LINK_QUARANTINE turns off
  *   the quarantine of slow host-pool ranges (every fetch and eviction of at
  *   least 256 MiB is timed; one that ran at less than half the fastest copy
  *   in its direction takes its host range out of the pool, up to a quarter

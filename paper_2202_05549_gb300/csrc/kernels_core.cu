@@ -110,14 +110,24 @@ __global__ void fill_kernel(FillDesc d) {
     }
 }
 
+// The piece holding work unit u: the last piece whose unit_begin <= u.  The
+// whole warp searches together: each round the 32 lanes test 32 evenly
+// spaced pieces of the remaining range at once and a ballot keeps the
+// segment after the last one at or below u, so a table of n pieces takes
+// ceil(log32 n) dependent loads instead of log2 n (a copy of a few hundred
+// pieces was measured to spend most of its time in the binary search).
+// Every lane of the warp must call it with the same u.
 __device__ __forceinline__ int find_piece_u(const CopyPiece *p, int n, uint64_t u) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (p[mid].unit_begin <= u)
-            lo = mid;
-        else
-            hi = mid - 1;
+    const int lane = threadIdx.x & 31;
+    int lo = 0, cnt = n;
+    while (cnt > 1) {
+        const int step = (cnt + 31) >> 5;
+        const int idx = lo + lane * step;
+        const bool le = lane * step < cnt && p[idx].unit_begin <= u;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, le);
+        const int last = 31 - __clz(m);  // lane 0 always qualifies: p[lo].unit_begin <= u
+        lo += last * step;
+        cnt = min(step, cnt - last * step);
     }
     return lo;
 }
@@ -134,8 +144,7 @@ __device__ __forceinline__ void copy_elem(const char *s, char *d, int esize) {
 // One CTA per work unit (a run of rows, or a segment of one long row, of
 // about LT_COPY_UNIT elements); the piece is found by binary search and read
 // in place (no local copy of the record).
-__device__ __forceinline__ void copy_unit(const CopyPiece *__restrict__ pieces, int n, const uint64_t u) {
-    const int pi = find_piece_u(pieces, n, u);
+__device__ __forceinline__ void copy_unit(const CopyPiece *__restrict__ pieces, const int pi, const uint64_t u) {
     const CopyPiece &p = pieces[pi];
     const int inner = p.nd - 1;
     const int64_t w = copy_piece_width(p), rows = copy_piece_rows(p);
@@ -280,7 +289,7 @@ __device__ __forceinline__ void copy_unit(const CopyPiece *__restrict__ pieces, 
 }
 
 __global__ void __launch_bounds__(256, 3) copy_kernel(const CopyPiece *__restrict__ pieces, int n) {
-    copy_unit(pieces, n, blockIdx.x);
+    copy_unit(pieces, find_piece_u(pieces, n, blockIdx.x), blockIdx.x);
 }
 
 // Staged variant: a unit of whole rows whose body (the 16-byte aligned part
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(256, 3) copy_bulk_kernel(const CopyPiece *__re
         }
     }
     if (!bulk) {
-        copy_unit(pieces, n, u);
+        copy_unit(pieces, pi, u);
         return;
     }
     const int64_t sp = p.src.s[0] * es, dp = p.dst.s[0] * es;
