@@ -165,6 +165,36 @@ __device__ __forceinline__ void copy_unit(const CopyPiece *__restrict__ pieces, 
                                                                      (p.lo[1] + c0) * p.src.s[1]) * es));
             char *db = (char *)(p.dst.base + (uint64_t)(((p.lo[0] + r0) * p.dst.s[0] + (p.lo[1] + c0) * p.dst.s[1]) * es));
             const int64_t sr = p.src.s[0] * es, sc = p.src.s[1] * es, dr = p.dst.s[0] * es, dc = p.dst.s[1] * es;
+            if (es == 4 || es == 8) {
+                // up to eight loads in flight per thread before the stores (a
+                // one-column halo of 2048 rows is eight strided elements per thread)
+                for (uint32_t e0 = threadIdx.x; e0 < nel; e0 += 8 * blockDim.x) {
+                    uint64_t v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t e = e0 + (uint32_t)k * blockDim.x;
+                        if (e < nel) {
+                            const uint32_t r = ncol == 1 ? e : e / ncol, col = ncol == 1 ? 0u : e - r * ncol;
+                            const char *sa = sb + r * sr + col * sc;
+                            v[k] = es == 4 ? (uint64_t)__ldcg((const unsigned int *)sa)
+                                           : (uint64_t)__ldcg((const unsigned long long *)sa);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t e = e0 + (uint32_t)k * blockDim.x;
+                        if (e < nel) {
+                            const uint32_t r = ncol == 1 ? e : e / ncol, col = ncol == 1 ? 0u : e - r * ncol;
+                            char *da = db + r * dr + col * dc;
+                            if (es == 4)
+                                *(unsigned int *)da = (unsigned int)v[k];
+                            else
+                                *(unsigned long long *)da = (unsigned long long)v[k];
+                        }
+                    }
+                }
+                return;
+            }
             for (uint32_t e = threadIdx.x; e < nel; e += blockDim.x) {
                 const uint32_t r = ncol == 1 ? e : e / ncol, col = ncol == 1 ? 0u : e - r * ncol;
                 copy_elem(sb + r * sr + col * sc, db + r * dr + col * dc, es);

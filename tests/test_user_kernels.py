@@ -222,3 +222,51 @@ def test_user_kernel_four_cells_per_thread_bit_exact(dist_kind):
             U, V = V, U
         ctx.synchronize()
         assert np.array_equal(U.read(), oracle.jacobi2d(u0, iters))
+
+
+HSUM_F64 = r"""
+__device__ void hsum(dim3 vb, int64_t ny, int64_t nx, lightning::Matrix<double> U, lightning::Matrix<double> V) {
+    const int64_t i = (int64_t)vb.y * blockDim.y + threadIdx.y, j = (int64_t)vb.x * blockDim.x + threadIdx.x;
+    if (i >= ny || j >= nx) return;
+    double a = j > 0 ? U(i, j - 1) : 0.0;
+    a = a + U(i, j);
+    a = a + (j + 1 < nx ? U(i, j + 1) : 0.0);
+    V(i, j) = a;
+}
+"""
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("halo", [0, 1])
+def test_user_kernel_f64_column_bands_pack_and_replicas_exact(halo):
+    # f64 arrays in column bands: without a halo every band's read region
+    # takes one column from each neighbour (8-byte one-column pack pieces);
+    # with a 1-column halo the written columns update the neighbours'
+    # replicas (8-byte one-column copies).  The sum of three doubles in this
+    # order is exact to compare: the same operations as the numpy expression.
+    ny, nx, iters = 2500, 700, 3
+    rng = np.random.default_rng(2203)
+    u0 = rng.standard_normal((ny, nx))
+    want = u0.copy()
+    for _ in range(iters):
+        left = np.zeros_like(want)
+        right = np.zeros_like(want)
+        left[:, 1:] = want[:, :-1]
+        right[:, :-1] = want[:, 1:]
+        want = (left + want) + right
+    with lt.Context() as ctx:
+        ctx.log_enable()
+        dist = lt.Dist.cols(96, halo=halo) if halo else lt.Dist.cols(96)
+        U = ctx.array(lt.F64, (ny, nx), dist)
+        V = ctx.array(lt.F64, (ny, nx), dist)
+        U.write(u0)
+        k = ctx.kernel_from_source(HSUM_F64, "hsum", "global [i, j] => read U[i, j-1:j+1], write V[i, j]",
+                                   [("ny", lt.U32, False), ("nx", lt.U32, False), ("U", lt.F64), ("V", lt.F64)])
+        for _ in range(iters):
+            k.launch(grid=(nx, ny), block=(32, 8), superblock=(96, ny), args=[ny, nx, U, V])
+            U, V = V, U
+        ctx.synchronize()
+        kinds = {t["kind"] for t in ctx.log()}
+        got = U.read()
+    assert ("pack" in kinds) if not halo else ("unpack" in kinds)
+    assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
