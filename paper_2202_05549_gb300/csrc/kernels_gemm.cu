@@ -6,8 +6,8 @@
 // One persistent kernel runs every superblock (output tile chunk) of a
 // launch.  Each CTA owns one SM and walks output tiles of 256 x 256, each
 // computed as two M = 128 halves that share the B operand of a stage:
-//   warp 0      TMA producer: A (256 x 64) and B (256 x 64) K-slices, 64 KB
-//               per stage, into a 3-stage shared-memory ring, 128-byte
+//   warp 0      TMA producer: A (256 x 32) and B (256 x 32) K-slices, 32 KB
+//               per stage, into a 7-stage shared-memory ring (224 KB), 64-byte
 //               swizzled;
 //   warp 1      MMA issuer: per K-step of 16, two tcgen05.mma kind::f16
 //               (M=128, N=256), one per M-half, into a single TMEM
@@ -43,15 +43,21 @@ namespace {
 // 512 columns.  At 256 x 256 that is one (a shape with NACC = 2 would let
 // the epilogue of one tile overlap the MMAs of the next).
 constexpr int MH = 2, UM = 128;
-constexpr int BM = MH * UM, BN = 256, BK = 64, UMMA_K = 16;
+// BK = 32: a stage is 32 KB, so the 224 KB ring holds 7 stages and a refill
+// has 6 stages of MMA time to land (with BK = 64 and 128-byte swizzle: 3
+// stages of 64 KB, 2 stages of cover, and the tensor pipe was active 84 % of
+// the time).  A stage's rows are 64 bytes: 64-byte swizzle.
+constexpr int BM = MH * UM, BN = 256, BK = 32, UMMA_K = 16;
+constexpr int SW_BYTES = BK * 2;  // bytes of one K-row of a stage = the swizzle span
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
+constexpr int STAGES = (224 * 1024) / STAGE_BYTES;
 constexpr int THREADS = 192;
 constexpr int TMEM_COLS = 512;
 constexpr int NACC = TMEM_COLS / (MH * BN);
 static_assert(NACC >= 1 && STAGES >= 2, "tile shape does not fit TMEM or shared memory");
+static_assert(SW_BYTES == 128 || SW_BYTES == 64, "one K-row of a stage must be a 128- or 64-byte swizzle span");
 constexpr int MAX_MAPS = 15;
 constexpr int GROUP_M = 16;  // tile raster: 16 M-tiles share each B panel
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
@@ -134,15 +140,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// K-major operand in shared memory, 128-byte swizzle: rows of 128 bytes,
-// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// K-major operand in shared memory, swizzled rows of SW_BYTES (the swizzle
+// span): 8-row groups 8 x SW_BYTES apart (stride byte offset), descriptor
+// version 1, layout type 2 (128-byte swizzle) or 4 (64-byte swizzle).
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
     d |= (uint64_t)(16 >> 4) << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)((8 * SW_BYTES) >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
+    d |= (uint64_t)(SW_BYTES == 128 ? 2 : 4) << 61;
     return d;
 }
 
@@ -312,7 +319,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_bf16_kernel(const ExecTask *_
                     }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
-                    const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+                    const uint64_t ad = sw_desc(sa), bd = sw_desc(sa + A_BYTES);
 #pragma unroll
                     for (int k = 0; k < BK / UMMA_K; ++k) {
                         const uint64_t koff = (uint64_t)((k * UMMA_K * 2) >> 4);
@@ -408,7 +415,7 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2-D K-major bf16 operand map over one chunk: inner extent k_valid, outer
-// extent rows_valid, row pitch in bytes, box 64 x box_rows, 128-byte swizzle.
+// extent rows_valid, row pitch in bytes, box BK x box_rows, SW_BYTES swizzle.
 bool make_map(CUtensorMap *m, uint64_t base, uint64_t k_valid, uint64_t rows_valid, uint64_t pitch_bytes,
               uint32_t box_rows) {
     EncodeTiledFn fn = encode_fn();
@@ -418,7 +425,8 @@ bool make_map(CUtensorMap *m, uint64_t base, uint64_t k_valid, uint64_t rows_val
     cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
     cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)(uintptr_t)base, dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, SW_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

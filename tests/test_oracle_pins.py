@@ -130,6 +130,24 @@ def test_jacobi_brute_force_tiny_grids():
     assert got[0, 1] == np.float32((1 + 4 + 0 + 2) / 5)
 
 
+
+def test_jacobi_f32_sum_order_is_centre_north_south_west_east():
+    # The sum order ((((c + n) + s) + w) + e) / 5 in f32, pinned by values
+    # whose rounded sums depend on it (worked by hand): c = 2^24, n = s = 1,
+    # w = -2^24, e = 0.5.  In that order c + n = 2^24 + 1 is a tie and rounds
+    # to the even 2^24, so does (c + n) + s, + w gives 0 and + e gives 0.5:
+    # the centre becomes 0.5f / 5 = f32(0.1).  Summing n + s first would give
+    # 2 + 2^24 (exact), then 2, 2.5 and 0.5; any order that adds w to c before
+    # n and s gives 2.5 as well.
+    u = np.zeros((3, 3), np.float32)
+    u[1, 1] = 2.0 ** 24
+    u[0, 1] = u[2, 1] = 1.0
+    u[1, 0] = -(2.0 ** 24)
+    u[1, 2] = 0.5
+    got = oracle.jacobi2d(u, 1)
+    assert got[1, 1] == np.float32(0.1)
+    assert got[1, 1] != np.float32(0.5)
+
 def _sine_mode(ny, nx, k, l):
     i = np.arange(ny)[:, None]
     j = np.arange(nx)[None, :]
