@@ -123,13 +123,22 @@ typedef struct {
  *   LT_FLAG_NO_PDL launches every kernel in the plain stream order (default:
  *   a 2-D Jacobi launch that runs entirely in device memory, without copy
  *   steps, starts as a programmatic dependent of the kernel before it, so its
- *   CTAs launch while that kernel finishes). */
+ *   CTAs launch while that kernel finishes);
+ *   LT_FLAG_NO_FUSED_REPLICAS updates the halo replicas that a source kernel
+ *   (lt_kernel_register_source) writes with a copy kernel after it (default:
+ *   the wrapper's CTAs copy them after a grid-wide barrier in the same
+ *   launch, which is then a cooperative launch); LT_FLAG_TEST_REPLICA_STALL
+ *   (tests only) makes that barrier wait for one CTA more than the launch
+ *   has, so its bounded wait (2 s) expires: the replicas are left as they
+ *   were and lt_synchronize reports LT_ERR_TIMEOUT. */
 #define LT_FLAG_TIMING 1
 #define LT_FLAG_DRYRUN 2
 #define LT_FLAG_FIXED_SWEEP 4
 #define LT_FLAG_NO_STAGED 8
 #define LT_FLAG_NO_LINK_QUARANTINE 16
 #define LT_FLAG_NO_PDL 32
+#define LT_FLAG_NO_FUSED_REPLICAS 64
+#define LT_FLAG_TEST_REPLICA_STALL 128
 
 typedef struct {
     size_t hbm_budget_bytes;
@@ -307,7 +316,13 @@ lt_status lt_kernel_destroy(lt_ctx *ctx, lt_kernel *k);
  * builds the views (the chunk offset subtracted once).  The wrapper is
  * persistent: each CTA calls the function for several virtual blocks in turn,
  * with a __syncthreads() before each call, so shared memory is not shared
- * between two virtual blocks' calls.  The library compiles both with NVRTC for sm_103a
+ * between two virtual blocks' calls.  When the launch writes an array whose
+ * chunks keep halo replicas, the wrapper's CTAs update those replicas
+ * themselves after all virtual blocks are done (a grid-wide barrier with a
+ * bounded wait; the launch is then cooperative, and the function must not
+ * end its block early with a trap or leave CTAs that never return); with
+ * LT_FLAG_NO_FUSED_REPLICAS a copy kernel after the launch does it.  T may
+ * also be double (LT_F64).  The library compiles both with NVRTC for sm_103a
  * (IEEE arithmetic, no FMA contraction) and loads them.  The annotation is
  * trusted: the kernel must not touch elements outside it.  At most 5 array,
  * 4 integer and 4 float parameters.  Errors: LT_ERR_PARSE, LT_ERR_COMPILE

@@ -31,6 +31,8 @@ LT_ORDER_ROW, LT_ORDER_COL = 0, 1
 # flags
 LT_FLAG_TIMING, LT_FLAG_DRYRUN, LT_FLAG_FIXED_SWEEP, LT_FLAG_NO_STAGED, LT_FLAG_NO_LINK_QUARANTINE = 1, 2, 4, 8, 16
 LT_FLAG_NO_PDL = 32
+LT_FLAG_NO_FUSED_REPLICAS = 64
+LT_FLAG_TEST_REPLICA_STALL = 128
 # fills
 (LT_INIT_ZERO, LT_INIT_CONST, LT_INIT_UNIFORM, LT_INIT_KAPPA, LT_INIT_NORMAL_BF16,
  LT_INIT_U8) = range(6)

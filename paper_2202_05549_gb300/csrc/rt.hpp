@@ -389,6 +389,14 @@ struct lt_ctx {
     std::vector<TableSlot> tslots;
     uint64_t tslot_tick = 0;
     uint32_t *err_word = nullptr;  // device error word
+    // Grid barrier of source kernels that update their replicas themselves:
+    // a device counter every CTA of such a launch increments once, and the
+    // host's running total of those increments (a launch waits for the total
+    // after its own CTAs have arrived).
+    unsigned long long *ubar = nullptr;
+    uint64_t ubar_total = 0;
+    bool no_fused_replicas = false;   // LT_FLAG_NO_FUSED_REPLICAS
+    bool test_replica_stall = false;  // LT_FLAG_TEST_REPLICA_STALL
     std::vector<std::unique_ptr<lt_array>> arrays;       // creation order (iteration order)
     std::unordered_set<const lt_array *> array_set;      // membership: handles are checked on every call
     std::vector<uint64_t> batch_checked;  // the last fused batch whose launches passed prepare_plan

@@ -72,6 +72,8 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     c->no_staged = (cfg->flags & LT_FLAG_NO_STAGED) != 0;
     c->no_pdl = (cfg->flags & LT_FLAG_NO_PDL) != 0;
     c->no_quarantine = (cfg->flags & LT_FLAG_NO_LINK_QUARANTINE) != 0;
+    c->no_fused_replicas = (cfg->flags & LT_FLAG_NO_FUSED_REPLICAS) != 0;
+    c->test_replica_stall = (cfg->flags & LT_FLAG_TEST_REPLICA_STALL) != 0;
     for (int s = 0; s < NSTREAM; ++s) {
         c->ev[s].assign(RING, nullptr);
         c->evseq[s].assign(RING, 0);
@@ -129,6 +131,8 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     for (auto &t : c->tslots) CK(cp, cudaEventCreateWithFlags(&t.staged, cudaEventDisableTiming));
     CK(cp, cudaMalloc((void **)&c->err_word, 16));
     CK(cp, cudaMemset(c->err_word, 0, 16));
+    CK(cp, cudaMalloc((void **)&c->ubar, sizeof(unsigned long long)));
+    CK(cp, cudaMemset(c->ubar, 0, sizeof(unsigned long long)));
     *out = c.release();
     return LT_OK;
 }
@@ -166,6 +170,7 @@ lt_status lt_ctx_destroy(lt_ctx *c) {
         if (c->up_host) cudaFreeHost(c->up_host);
         if (c->up_dev) cudaFree(c->up_dev);
         if (c->err_word) cudaFree(c->err_word);
+        if (c->ubar) cudaFree(c->ubar);
     }
     delete c;
     return LT_OK;

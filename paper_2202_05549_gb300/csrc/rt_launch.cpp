@@ -480,6 +480,15 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 if ((int)j != ap.param && parr[j] == parr[(size_t)ap.param]) return false;
             return true;
         };
+        // A source kernel copies the replicas of the arrays it writes itself,
+        // after a grid-wide barrier at the end of its launch (no copy kernel
+        // follows it for them).
+        auto fused_replicas = [&](const ArgPlan &ap) {
+            return k->own_def && !c->no_fused_replicas && ap.kind == ARG_DIRECT && ap.mode != MODE_READ &&
+                   !ap.replicas.empty();
+        };
+        std::vector<CopyPiece> ucopies;  // replica boxes the source kernel's wrapper copies
+        uint64_t ucopy_cells = 0;
         std::vector<ExecTask> tasks;
         std::vector<ReplicaTarget> reps;
         uint64_t rep_cells = 0;
@@ -519,6 +528,26 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                             r.cell_begin = rep_cells;
                             rep_cells += (uint64_t)pc.box.volume();
                             reps.push_back(r);
+                            ex_wait.merge(dcs.ready);
+                            ex_wait.merge(dcs.busy);
+                            wt_chunks.push_back(&dcs);
+                            c->stats.bytes_replica_wt += (uint64_t)pc.box.volume() * a->g.esize();
+                        }
+                    } else if (fused_replicas(ap)) {
+                        for (const auto &pc : ap.replicas) {
+                            CState &dcs = a->cs[(size_t)pc.chunk];
+                            CopyPiece cp{};
+                            cp.src = t.v[sl];
+                            cp.dst = view_of(c, a->g, a->g.chunks[(size_t)pc.chunk], dcs.off);
+                            cp.nd = a->g.nd;
+                            cp.esize = (int32_t)a->g.esize();
+                            for (int d = 0; d < 3; ++d) {
+                                cp.lo[d] = d < a->g.nd ? pc.box.lo[d] : 0;
+                                cp.hi[d] = d < a->g.nd ? pc.box.hi[d] : 0;
+                            }
+                            cp.unit_begin = ucopy_cells;  // here: the prefix of element counts
+                            ucopy_cells += (uint64_t)pc.box.volume();
+                            ucopies.push_back(cp);
                             ex_wait.merge(dcs.ready);
                             ex_wait.merge(dcs.busy);
                             wt_chunks.push_back(&dcs);
@@ -577,11 +606,12 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 }
             }
             const size_t tbytes = tasks.size() * sizeof(ExecTask), rbytes = reps.size() * sizeof(ReplicaTarget),
-                         ubytes = units.size() * sizeof(ReplicaUnit);
-            std::vector<char> table(tbytes + rbytes + ubytes);
+                         ubytes = units.size() * sizeof(ReplicaUnit), cbytes = ucopies.size() * sizeof(CopyPiece);
+            std::vector<char> table(tbytes + rbytes + ubytes + cbytes);
             std::memcpy(table.data(), tasks.data(), tbytes);
             if (rbytes) std::memcpy(table.data() + tbytes, reps.data(), rbytes);
             if (ubytes) std::memcpy(table.data() + tbytes + rbytes, units.data(), ubytes);
+            if (cbytes) std::memcpy(table.data() + tbytes + rbytes + ubytes, ucopies.data(), cbytes);
             void *dptr;
             size_t roff;
             if ((st = upload(c, table.data(), table.size(), &dptr, &roff))) return st;
@@ -597,7 +627,13 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                     // the launch's blocks, so short blocks do not pay one CTA launch each
                     const ExecTask *tp = (const ExecTask *)dptr;
                     unsigned nblocks = ctas;
-                    void *kargs[] = {(void *)&tp, (void *)&ep, (void *)&nblocks};
+                    const CopyPiece *ucp =
+                        cbytes ? (const CopyPiece *)((const char *)dptr + tbytes + rbytes + ubytes) : nullptr;
+                    unsigned nucp = (unsigned)ucopies.size();
+                    unsigned long long nel = ucopy_cells, target = 0;
+                    unsigned long long *bar = c->ubar;
+                    void *kargs[] = {(void *)&tp, (void *)&ep, (void *)&nblocks, (void *)&ucp,
+                                     (void *)&nucp, (void *)&nel, (void *)&bar, (void *)&target};
                     dim3 blk((unsigned)ep.block[0], (unsigned)ep.block[1], (unsigned)ep.block[2]);
                     const int threads = (int)(blk.x * blk.y * blk.z);
                     auto occ = k->uocc.find(threads);
@@ -607,7 +643,25 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                         occ = k->uocc.emplace(threads, std::max(1, per_sm)).first;
                     }
                     const uint32_t grid = (uint32_t)std::min<uint64_t>(ctas, (uint64_t)occ->second * c->sm_count);
-                    CK(c, cudaLaunchKernel((const void *)k->ufn, dim3(grid), blk, kargs, 0, c->st[S_COMP]));
+                    if (nucp) {
+                        // every CTA arrives once; the barrier completes at the running total of arrivals
+                        // (one more with the test flag, so that its bounded wait runs out)
+                        target = c->ubar_total + grid + (c->test_replica_stall ? 1u : 0u);
+                        cudaLaunchConfig_t cfg{};
+                        cfg.gridDim = dim3(grid);
+                        cfg.blockDim = blk;
+                        cfg.dynamicSmemBytes = 0;
+                        cfg.stream = c->st[S_COMP];
+                        cudaLaunchAttribute attr[1];
+                        attr[0].id = cudaLaunchAttributeCooperative;
+                        attr[0].val.cooperative = 1;
+                        cfg.attrs = attr;
+                        cfg.numAttrs = 1;
+                        CK(c, cudaLaunchKernelExC(&cfg, (const void *)k->ufn, kargs));
+                        c->ubar_total += grid;  // counted once the launch is in the stream
+                    } else {
+                        CK(c, cudaLaunchKernel((const void *)k->ufn, dim3(grid), blk, kargs, 0, c->st[S_COMP]));
+                    }
                 } else {
                     CK(c, def->launch((const ExecTask *)dptr, ctas, ep, c->st[S_COMP]));
                 }
@@ -650,7 +704,7 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 const auto &ap = sb.args[ai];
                 lt_array *a = ap.param >= 0 && ap.kind != ARG_VALUE ? parr[(size_t)ap.param] : nullptr;
                 if (ap.kind == ARG_DIRECT && ap.mode != MODE_READ &&
-                    !writes_through(ap, k->slot_of_param[(size_t)ap.param])) {
+                    !writes_through(ap, k->slot_of_param[(size_t)ap.param]) && !fused_replicas(ap)) {
                     for (const auto &pc : ap.replicas) {
                         CopyPiece cp{};
                         cp.src = view_of(c, a->g, a->g.chunks[(size_t)ap.chunk], a->cs[(size_t)ap.chunk].off);

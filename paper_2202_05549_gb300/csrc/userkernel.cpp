@@ -79,6 +79,68 @@ const char *ctype(int dtype) {
 
 }  // namespace
 
+// The replica phase of the wrapper: after the CTA's last block, one thread
+// per CTA adds the CTA to the grid barrier (a device counter) and waits until
+// the counter reaches the launch's target, which the host sets to the number
+// of arrivals once every CTA of this launch has arrived; the launch is
+// cooperative, so all its CTAs are resident together.  The wait is bounded
+// (2 s, %globaltimer): on expiry the CTA records 0x6750 in the error word and
+// leaves the replicas as they were.  Then the CTAs copy the elements of the
+// replica boxes (each LtCopy a box of the written chunk to its replica in a
+// neighbouring chunk; `first` is the prefix of element counts), element by
+// element, reading through L2: the written cells come from other SMs.
+static const char *kReplicaPhase =
+    "__device__ __forceinline__ unsigned long long lt_gtimer() {\n"
+    "  unsigned long long t; asm volatile(\"mov.u64 %0, %%globaltimer;\" : \"=l\"(t)); return t;\n"
+    "}\n"
+    "__device__ __noinline__ void lt_replicas(const LtCopy *__restrict__ cp, unsigned ncp, unsigned long long nel,\n"
+    "    unsigned long long *bar, unsigned long long target, uint32_t *err) {\n"
+    "  __shared__ int lt_ok;\n"
+    "  __syncthreads();\n"
+    "  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {\n"
+    "    __threadfence();\n"
+    "    atomicAdd(bar, 1ull);\n"
+    "    const unsigned long long t0 = lt_gtimer();\n"
+    "    int ok = 1;\n"
+    "    for (;;) {\n"
+    "      unsigned long long v;\n"
+    "      asm volatile(\"ld.acquire.gpu.global.u64 %0, [%1];\" : \"=l\"(v) : \"l\"(bar) : \"memory\");\n"
+    "      if (v >= target) break;\n"
+    "      if (lt_gtimer() - t0 > 2000000000ull) { atomicCAS(err, 0u, 0x6750u); ok = 0; break; }\n"
+    "      __nanosleep(100);\n"
+    "    }\n"
+    "    __threadfence();\n"
+    "    lt_ok = ok;\n"
+    "  }\n"
+    "  __syncthreads();\n"
+    "  if (!lt_ok) return;\n"
+    "  const unsigned nth = blockDim.x * blockDim.y * blockDim.z;\n"
+    "  const unsigned tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);\n"
+    "  for (unsigned long long e = (unsigned long long)blockIdx.x * nth + tid; e < nel;\n"
+    "       e += (unsigned long long)gridDim.x * nth) {\n"
+    "    int lo = 0, hi = (int)ncp - 1;\n"
+    "    while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (cp[mid].first <= e) lo = mid; else hi = mid - 1; }\n"
+    "    const LtCopy &c = cp[lo];\n"
+    "    unsigned long long l = e - c.first;\n"
+    "    int64_t g[3] = {0, 0, 0};\n"
+    "    for (int d = c.nd - 1; d >= 0; --d) {\n"
+    "      const unsigned long long w = (unsigned long long)(c.hi[d] - c.lo[d] + 1);\n"
+    "      g[d] = c.lo[d] + (int64_t)(l % w);\n"
+    "      l /= w;\n"
+    "    }\n"
+    "    int64_t os = 0, od = 0;\n"
+    "    for (int d = 0; d < c.nd; ++d) { os += g[d] * c.src.s[d]; od += g[d] * c.dst.s[d]; }\n"
+    "    const char *sa = (const char *)(c.src.base + (uint64_t)(os * c.esize));\n"
+    "    char *da = (char *)(c.dst.base + (uint64_t)(od * c.esize));\n"
+    "    switch (c.esize) {\n"
+    "      case 1: *(unsigned char *)da = __ldcg((const unsigned char *)sa); break;\n"
+    "      case 2: *(unsigned short *)da = __ldcg((const unsigned short *)sa); break;\n"
+    "      case 4: *(unsigned int *)da = __ldcg((const unsigned int *)sa); break;\n"
+    "      default: *(unsigned long long *)da = __ldcg((const unsigned long long *)sa); break;\n"
+    "    }\n"
+    "  }\n"
+    "}\n";
+
 std::string user_wrapper_source(const std::string &user, const std::string &name, const std::vector<UserParam> &params) {
     std::ostringstream o;
     o << "typedef long long int64_t;\ntypedef unsigned long long uint64_t;\ntypedef unsigned int uint32_t;\n"
@@ -112,9 +174,14 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
          "static_assert(sizeof(LtView) == "
       << sizeof(DView) << ", \"view layout\");\nstatic_assert(sizeof(LtTask) == " << sizeof(ExecTask)
       << ", \"task layout\");\nstatic_assert(sizeof(LtParams) == " << sizeof(ExecParams) << ", \"params layout\");\n"
-      << "#line 1 \"user_kernel.cu\"\n"
+      << "struct LtCopy { LtView src, dst; int64_t lo[3], hi[3]; int32_t nd, esize; uint64_t first; };\n"
+         "static_assert(sizeof(LtCopy) == "
+      << sizeof(CopyPiece) << ", \"copy layout\");\n"
+      << kReplicaPhase << "#line 1 \"user_kernel.cu\"\n"
       << user << "\n"
-      << "extern \"C\" __global__ void lt_user_wrapper(const LtTask *__restrict__ tasks, LtParams P, unsigned nblocks) {\n"
+      << "extern \"C\" __global__ void lt_user_wrapper(const LtTask *__restrict__ tasks, LtParams P, unsigned nblocks,\n"
+         "    const LtCopy *__restrict__ lt_cp, unsigned lt_ncp, unsigned long long lt_nel, unsigned long long *lt_bar,\n"
+         "    unsigned long long lt_target) {\n"
          "  // persistent: each CTA runs the blocks b = blockIdx.x, blockIdx.x + gridDim.x, ... of the launch.\n"
          "  // One thread maps each block to its task and virtual index, one block ahead, into the other of two\n"
          "  // shared slots; the barrier at the top of each block orders the writes and the reads.\n"
@@ -167,7 +234,8 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
         slot++;
     }
     // the barrier at the top of the next block also keeps the body's shared memory apart between blocks
-    o << "  " << name << "(vb" << args.str() << ");\n  }\n}\n";
+    o << "  " << name << "(vb" << args.str() << ");\n  }\n"
+      << "  if (lt_ncp) lt_replicas(lt_cp, lt_ncp, lt_nel, lt_bar, lt_target, P.err);\n}\n";
     return o.str();
 }
 

@@ -200,8 +200,9 @@ def test_user_kernel_with_shared_memory_and_barrier_bit_exact():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("flags", [0, L.LT_FLAG_NO_FUSED_REPLICAS])
 @pytest.mark.parametrize("dist_kind", ["tiles_halo", "block", "rows_halo"])
-def test_user_kernel_four_cells_per_thread_bit_exact(dist_kind):
+def test_user_kernel_four_cells_per_thread_bit_exact(dist_kind, flags):
     # the benchmark's vector body: four columns per thread from float4 rows,
     # annotated "read U[i-1:i+1, 4*j-1:4*j+4], write V[i, 4*j:4*j+3]"; a ragged
     # width (not a multiple of 4) exercises the masked edge
@@ -211,7 +212,7 @@ def test_user_kernel_four_cells_per_thread_bit_exact(dist_kind):
     dist, sb = {"tiles_halo": (lt.Dist.tiles((128, 256), halo=(1, 1)), (64, 128)),
                 "block": (lt.Dist.block(), (0, 0)),
                 "rows_halo": (lt.Dist.rows(100, halo=1), ((nx + 3) // 4, 100))}[dist_kind]
-    with lt.Context() as ctx:
+    with lt.Context(flags=flags) as ctx:
         U = ctx.array(lt.F32, (ny, nx), dist)
         V = ctx.array(lt.F32, (ny, nx), dist)
         U.write(u0)
@@ -237,8 +238,8 @@ __device__ void hsum(dim3 vb, int64_t ny, int64_t nx, lightning::Matrix<double> 
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("halo", [0, 1])
-def test_user_kernel_f64_column_bands_pack_and_replicas_exact(halo):
+@pytest.mark.parametrize("halo,flags", [(0, 0), (1, 0), (1, L.LT_FLAG_NO_FUSED_REPLICAS)])
+def test_user_kernel_f64_column_bands_pack_and_replicas_exact(halo, flags):
     # f64 arrays in column bands: without a halo every band's read region
     # takes one column from each neighbour (8-byte one-column pack pieces);
     # with a 1-column halo the written columns update the neighbours'
@@ -254,7 +255,7 @@ def test_user_kernel_f64_column_bands_pack_and_replicas_exact(halo):
         left[:, 1:] = want[:, :-1]
         right[:, :-1] = want[:, 1:]
         want = (left + want) + right
-    with lt.Context() as ctx:
+    with lt.Context(flags=flags) as ctx:
         ctx.log_enable()
         dist = lt.Dist.cols(96, halo=halo) if halo else lt.Dist.cols(96)
         U = ctx.array(lt.F64, (ny, nx), dist)
@@ -268,5 +269,61 @@ def test_user_kernel_f64_column_bands_pack_and_replicas_exact(halo):
         ctx.synchronize()
         kinds = {t["kind"] for t in ctx.log()}
         got = U.read()
-    assert ("pack" in kinds) if not halo else ("unpack" in kinds)
+    if not halo:
+        assert "pack" in kinds
+    else:  # the wrapper copies the replicas itself unless told not to
+        assert ("unpack" in kinds) == bool(flags & L.LT_FLAG_NO_FUSED_REPLICAS)
     assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
+
+
+def test_source_kernel_replicas_fused_into_the_launch_in_dry_run():
+    # a source kernel writing tiles with halos: no copy step follows its
+    # launch (the wrapper updates the replicas after a grid-wide barrier);
+    # with LT_FLAG_NO_FUSED_REPLICAS an unpack step does, for the same bytes
+    import bench
+    got = {}
+    for fl in (0, L.LT_FLAG_NO_FUSED_REPLICAS):
+        with lt.Context(hbm_budget=1 << 30, flags=L.LT_FLAG_DRYRUN | fl) as ctx:
+            k = ctx.kernel_from_source(bench.USER_JACOBI_VEC, "jacobi4", bench.USER_JACOBI_VEC_ANN,
+                                       [("ny", lt.U32, False), ("nx", lt.U32, False), ("U", lt.F32), ("V", lt.F32)])
+            ctx.log_enable()
+            dist = lt.Dist.tiles((1024, 1024), halo=(1, 1))
+            U = ctx.array(lt.F32, (4096, 4096), dist)
+            V = ctx.array(lt.F32, (4096, 4096), dist)
+            k.launch(grid=(1024, 4096), block=(64, 4), superblock=(256, 1024), args=[4096, 4096, U, V])
+            ctx.synchronize()
+            st = ctx.stats()
+            got[fl] = ({t["kind"] for t in ctx.log()}, st["bytes_replica_wt"], st["bytes_d2d"])
+    # 4 x 4 tiles of 1024^2: 24 inner edges, each copied both ways (1024 cells), and at each of the
+    # 9 inner corner points the 4 tiles' corner cells, each to its diagonal neighbour's corner halo
+    edge_bytes = 4 * (24 * 2 * 1024 + 9 * 4)
+    assert got[0] == ({"zero", "execute"}, edge_bytes, 0)
+    assert got[L.LT_FLAG_NO_FUSED_REPLICAS] == ({"zero", "execute", "unpack"}, 0, edge_bytes)
+
+
+@pytest.mark.gpu
+def test_source_kernel_replica_barrier_timeout_reports_and_context_survives():
+    # failure detection without a fault: the test flag makes the wrapper's
+    # grid barrier wait for one CTA more than the launch has, so its bounded
+    # wait (2 s) runs out; the replicas are left as they were, the host reads
+    # LT_ERR_TIMEOUT, and the same context then runs a launch without
+    # replicas (one chunk) correctly
+    import bench
+    ny, nx = 300, 517
+    u0 = si.uniform_field(2203, 17, ny, nx)
+    with lt.Context(flags=L.LT_FLAG_TEST_REPLICA_STALL) as ctx:
+        k = ctx.kernel_from_source(bench.USER_JACOBI_VEC, "jacobi4", bench.USER_JACOBI_VEC_ANN,
+                                   [("ny", lt.U32, False), ("nx", lt.U32, False), ("U", lt.F32), ("V", lt.F32)])
+        U = ctx.array(lt.F32, (ny, nx), lt.Dist.tiles((128, 256), halo=(1, 1)))
+        V = ctx.array(lt.F32, (ny, nx), lt.Dist.tiles((128, 256), halo=(1, 1)))
+        U.write(u0)
+        k.launch(grid=((nx + 3) // 4, ny), block=(64, 4), superblock=(64, 128), args=[ny, nx, U, V])
+        with pytest.raises(lt.LightningError) as e:
+            ctx.synchronize()
+        assert e.value.code == L.LT_ERR_TIMEOUT
+        A = ctx.array(lt.F32, (ny, nx), lt.Dist.block())
+        B = ctx.array(lt.F32, (ny, nx), lt.Dist.block())
+        A.write(u0)
+        k.launch(grid=((nx + 3) // 4, ny), block=(64, 4), superblock=(0, 0), args=[ny, nx, A, B])
+        ctx.synchronize()
+        assert np.array_equal(B.read(), oracle.jacobi2d(u0, 1))
