@@ -488,7 +488,7 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                    !ap.replicas.empty();
         };
         std::vector<CopyPiece> ucopies;  // replica boxes the source kernel's wrapper copies
-        uint64_t ucopy_cells = 0;
+        std::vector<uint32_t> uunits;    // their units of 32 elements: (box, first element) pairs
         std::vector<ExecTask> tasks;
         std::vector<ReplicaTarget> reps;
         uint64_t rep_cells = 0;
@@ -545,8 +545,13 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                                 cp.lo[d] = d < a->g.nd ? pc.box.lo[d] : 0;
                                 cp.hi[d] = d < a->g.nd ? pc.box.hi[d] : 0;
                             }
-                            cp.unit_begin = ucopy_cells;  // here: the prefix of element counts
-                            ucopy_cells += (uint64_t)pc.box.volume();
+                            const uint64_t vol = (uint64_t)pc.box.volume();
+                            if (vol > 0xFFFFFFE0ull)
+                                return fail(LT_ERR_UNSUPPORTED, "a halo replica box of 2^32 elements or more");
+                            for (uint64_t f = 0; f < vol; f += 32) {
+                                uunits.push_back((uint32_t)ucopies.size());
+                                uunits.push_back((uint32_t)f);
+                            }
                             ucopies.push_back(cp);
                             ex_wait.merge(dcs.ready);
                             ex_wait.merge(dcs.busy);
@@ -606,12 +611,14 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                 }
             }
             const size_t tbytes = tasks.size() * sizeof(ExecTask), rbytes = reps.size() * sizeof(ReplicaTarget),
-                         ubytes = units.size() * sizeof(ReplicaUnit), cbytes = ucopies.size() * sizeof(CopyPiece);
-            std::vector<char> table(tbytes + rbytes + ubytes + cbytes);
+                         ubytes = units.size() * sizeof(ReplicaUnit), cbytes = ucopies.size() * sizeof(CopyPiece),
+                         cubytes = uunits.size() * sizeof(uint32_t);
+            std::vector<char> table(tbytes + rbytes + ubytes + cbytes + cubytes);
             std::memcpy(table.data(), tasks.data(), tbytes);
             if (rbytes) std::memcpy(table.data() + tbytes, reps.data(), rbytes);
             if (ubytes) std::memcpy(table.data() + tbytes + rbytes, units.data(), ubytes);
             if (cbytes) std::memcpy(table.data() + tbytes + rbytes + ubytes, ucopies.data(), cbytes);
+            if (cubytes) std::memcpy(table.data() + tbytes + rbytes + ubytes + cbytes, uunits.data(), cubytes);
             void *dptr;
             size_t roff;
             if ((st = upload(c, table.data(), table.size(), &dptr, &roff))) return st;
@@ -629,11 +636,13 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                     unsigned nblocks = ctas;
                     const CopyPiece *ucp =
                         cbytes ? (const CopyPiece *)((const char *)dptr + tbytes + rbytes + ubytes) : nullptr;
-                    unsigned nucp = (unsigned)ucopies.size();
-                    unsigned long long nel = ucopy_cells, target = 0;
+                    const uint32_t *ucu =
+                        cubytes ? (const uint32_t *)((const char *)dptr + tbytes + rbytes + ubytes + cbytes) : nullptr;
+                    unsigned nucu = (unsigned)(uunits.size() / 2);
+                    unsigned long long target = 0;
                     unsigned long long *bar = c->ubar;
                     void *kargs[] = {(void *)&tp, (void *)&ep, (void *)&nblocks, (void *)&ucp,
-                                     (void *)&nucp, (void *)&nel, (void *)&bar, (void *)&target};
+                                     (void *)&ucu, (void *)&nucu, (void *)&bar, (void *)&target};
                     dim3 blk((unsigned)ep.block[0], (unsigned)ep.block[1], (unsigned)ep.block[2]);
                     const int threads = (int)(blk.x * blk.y * blk.z);
                     auto occ = k->uocc.find(threads);
@@ -643,7 +652,7 @@ lt_status emit_launch(lt_ctx *c, PendingLaunch &pl,
                         occ = k->uocc.emplace(threads, std::max(1, per_sm)).first;
                     }
                     const uint32_t grid = (uint32_t)std::min<uint64_t>(ctas, (uint64_t)occ->second * c->sm_count);
-                    if (nucp) {
+                    if (nucu) {
                         // every CTA arrives once; the barrier completes at the running total of arrivals
                         // (one more with the test flag, so that its bounded wait runs out)
                         target = c->ubar_total + grid + (c->test_replica_stall ? 1u : 0u);

@@ -85,16 +85,18 @@ const char *ctype(int dtype) {
 // of arrivals once every CTA of this launch has arrived; the launch is
 // cooperative, so all its CTAs are resident together.  The wait is bounded
 // (2 s, %globaltimer): on expiry the CTA records 0x6750 in the error word and
-// leaves the replicas as they were.  Then the CTAs copy the elements of the
-// replica boxes (each LtCopy a box of the written chunk to its replica in a
-// neighbouring chunk; `first` is the prefix of element counts), element by
-// element, reading through L2: the written cells come from other SMs.
+// leaves the replicas as they were.  Then the CTAs copy the replica boxes
+// (each LtCopy a box of the written chunk and its replica in a neighbouring
+// chunk), in units of 32 consecutive elements of a box (LtUnit: box, first
+// element), one element per thread, reading through L2: the written cells
+// come from other SMs.
 static const char *kReplicaPhase =
+    "struct LtUnit { unsigned box, first; };\n"
     "__device__ __forceinline__ unsigned long long lt_gtimer() {\n"
     "  unsigned long long t; asm volatile(\"mov.u64 %0, %%globaltimer;\" : \"=l\"(t)); return t;\n"
     "}\n"
-    "__device__ __noinline__ void lt_replicas(const LtCopy *__restrict__ cp, unsigned ncp, unsigned long long nel,\n"
-    "    unsigned long long *bar, unsigned long long target, uint32_t *err) {\n"
+    "__device__ __noinline__ void lt_replicas(const LtCopy *__restrict__ cp, const LtUnit *__restrict__ cu,\n"
+    "    unsigned nu, unsigned long long *bar, unsigned long long target, uint32_t *err) {\n"
     "  __shared__ int lt_ok;\n"
     "  __syncthreads();\n"
     "  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {\n"
@@ -107,7 +109,7 @@ static const char *kReplicaPhase =
     "      asm volatile(\"ld.acquire.gpu.global.u64 %0, [%1];\" : \"=l\"(v) : \"l\"(bar) : \"memory\");\n"
     "      if (v >= target) break;\n"
     "      if (lt_gtimer() - t0 > 2000000000ull) { atomicCAS(err, 0u, 0x6750u); ok = 0; break; }\n"
-    "      __nanosleep(100);\n"
+    "      __nanosleep(64);\n"
     "    }\n"
     "    __threadfence();\n"
     "    lt_ok = ok;\n"
@@ -116,20 +118,21 @@ static const char *kReplicaPhase =
     "  if (!lt_ok) return;\n"
     "  const unsigned nth = blockDim.x * blockDim.y * blockDim.z;\n"
     "  const unsigned tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);\n"
-    "  for (unsigned long long e = (unsigned long long)blockIdx.x * nth + tid; e < nel;\n"
+    "  const unsigned long long total = (unsigned long long)nu * 32ull;\n"
+    "  for (unsigned long long e = (unsigned long long)blockIdx.x * nth + tid; e < total;\n"
     "       e += (unsigned long long)gridDim.x * nth) {\n"
-    "    int lo = 0, hi = (int)ncp - 1;\n"
-    "    while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (cp[mid].first <= e) lo = mid; else hi = mid - 1; }\n"
-    "    const LtCopy &c = cp[lo];\n"
-    "    unsigned long long l = e - c.first;\n"
-    "    int64_t g[3] = {0, 0, 0};\n"
-    "    for (int d = c.nd - 1; d >= 0; --d) {\n"
-    "      const unsigned long long w = (unsigned long long)(c.hi[d] - c.lo[d] + 1);\n"
-    "      g[d] = c.lo[d] + (int64_t)(l % w);\n"
-    "      l /= w;\n"
-    "    }\n"
-    "    int64_t os = 0, od = 0;\n"
-    "    for (int d = 0; d < c.nd; ++d) { os += g[d] * c.src.s[d]; od += g[d] * c.dst.s[d]; }\n"
+    "    const LtUnit u = cu[e >> 5];\n"
+    "    const LtCopy &c = cp[u.box];\n"
+    "    const unsigned w0 = (unsigned)(c.hi[0] - c.lo[0] + 1), w1 = (unsigned)(c.hi[1] - c.lo[1] + 1),\n"
+    "                   w2 = (unsigned)(c.hi[2] - c.lo[2] + 1);\n"
+    "    unsigned l = u.first + (unsigned)(e & 31u);\n"
+    "    int64_t g0, g1 = 0, g2 = 0;\n"
+    "    if (c.nd == 1) { if (l >= w0) continue; g0 = c.lo[0] + l; }\n"
+    "    else if (c.nd == 2) { if (l >= w0 * w1) continue; g0 = c.lo[0] + l / w1; g1 = c.lo[1] + l % w1; }\n"
+    "    else { if (l >= w0 * w1 * w2) continue; const unsigned r = l / w2; g2 = c.lo[2] + l % w2;\n"
+    "           g1 = c.lo[1] + r % w1; g0 = c.lo[0] + r / w1; }\n"
+    "    const int64_t os = g0 * c.src.s[0] + g1 * c.src.s[1] + g2 * c.src.s[2];\n"
+    "    const int64_t od = g0 * c.dst.s[0] + g1 * c.dst.s[1] + g2 * c.dst.s[2];\n"
     "    const char *sa = (const char *)(c.src.base + (uint64_t)(os * c.esize));\n"
     "    char *da = (char *)(c.dst.base + (uint64_t)(od * c.esize));\n"
     "    switch (c.esize) {\n"
@@ -180,8 +183,8 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
       << kReplicaPhase << "#line 1 \"user_kernel.cu\"\n"
       << user << "\n"
       << "extern \"C\" __global__ void lt_user_wrapper(const LtTask *__restrict__ tasks, LtParams P, unsigned nblocks,\n"
-         "    const LtCopy *__restrict__ lt_cp, unsigned lt_ncp, unsigned long long lt_nel, unsigned long long *lt_bar,\n"
-         "    unsigned long long lt_target) {\n"
+         "    const LtCopy *__restrict__ lt_cp, const LtUnit *__restrict__ lt_cu, unsigned lt_nu,\n"
+         "    unsigned long long *lt_bar, unsigned long long lt_target) {\n"
          "  // persistent: each CTA runs the blocks b = blockIdx.x, blockIdx.x + gridDim.x, ... of the launch.\n"
          "  // One thread maps each block to its task and virtual index, one block ahead, into the other of two\n"
          "  // shared slots; the barrier at the top of each block orders the writes and the reads.\n"
@@ -235,7 +238,7 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
     }
     // the barrier at the top of the next block also keeps the body's shared memory apart between blocks
     o << "  " << name << "(vb" << args.str() << ");\n  }\n"
-      << "  if (lt_ncp) lt_replicas(lt_cp, lt_ncp, lt_nel, lt_bar, lt_target, P.err);\n}\n";
+      << "  if (lt_nu) lt_replicas(lt_cp, lt_cu, lt_nu, lt_bar, lt_target, P.err);\n}\n";
     return o.str();
 }
 

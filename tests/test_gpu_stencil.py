@@ -215,6 +215,30 @@ def test_out_of_core_lightcone_samples_small():
     assert np.array_equal(got[si_, sj_], want)
 
 
+def test_out_of_core_16384x8192_every_cell_vs_unchunked_oracle():
+    # the out-of-core launch shape at a size the oracle runs unchunked in a
+    # few seconds: 16384 x 8192 f32 in 1000-row bands + 1-row halo (17 bands,
+    # the last one 384 rows), an HBM budget of 5 bands for two 512 MiB
+    # arrays, 20 iterations; every cell compared
+    NY, NX, band, iters = 16384, 8192, 1000, 20
+    cb = (band + 2) * NX * 4
+    u0 = si.uniform_field(si.SEED_JACOBI_OOC, 0, NY, NX)
+    with lt.Context(hbm_budget=5 * cb + (1 << 20), host_pool=40 * cb) as ctx:
+        U = ctx.array(lt.F32, (NY, NX), lt.Dist.rows(band, halo=1))
+        V = ctx.array(lt.F32, (NY, NX), lt.Dist.rows(band, halo=1))
+        U.write(u0)
+        k = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=(NX, NY), block=(128, 4), superblock=(NX, band), args=[U, V])
+            U, V = V, U
+        ctx.synchronize()
+        s = ctx.stats()
+        got = U.read()
+    assert s["evictions"] > 0 and s["fetches"] > 0
+    want = oracle.jacobi2d(u0, iters)
+    assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
+
+
 def test_discard_of_the_stale_buffer_keeps_results_exact():
     # out of core (budget 5 bands of 16 + 16): runs of 3 iterations, each
     # ending with the stale ping-pong buffer discarded before the synchronize;
