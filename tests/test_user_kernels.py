@@ -327,3 +327,54 @@ def test_source_kernel_replica_barrier_timeout_reports_and_context_survives():
         k.launch(grid=((nx + 3) // 4, ny), block=(64, 4), superblock=(0, 0), args=[ny, nx, A, B])
         ctx.synchronize()
         assert np.array_equal(B.read(), oracle.jacobi2d(u0, 1))
+
+
+JAC3 = r"""
+__device__ void jac3(dim3 vb, int64_t nz, int64_t ny, int64_t nx, lightning::Tensor<float> U, lightning::Tensor<float> V) {
+    const int64_t k = (int64_t)vb.z * blockDim.z + threadIdx.z;
+    const int64_t i = (int64_t)vb.y * blockDim.y + threadIdx.y;
+    const int64_t j = (int64_t)vb.x * blockDim.x + threadIdx.x;
+    if (k >= nz || i >= ny || j >= nx) return;
+    float a = U(k, i, j);
+    a = a + (k > 0 ? U(k - 1, i, j) : 0.0f);
+    a = a + (k + 1 < nz ? U(k + 1, i, j) : 0.0f);
+    a = a + (i > 0 ? U(k, i - 1, j) : 0.0f);
+    a = a + (i + 1 < ny ? U(k, i + 1, j) : 0.0f);
+    a = a + (j > 0 ? U(k, i, j - 1) : 0.0f);
+    a = a + (j + 1 < nx ? U(k, i, j + 1) : 0.0f);
+    V(k, i, j) = a / 7.0f;
+}
+"""
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("flags", [0, L.LT_FLAG_NO_FUSED_REPLICAS])
+@pytest.mark.parametrize("block,sb", [((32, 4, 1), (64, 24, 13)), ((32, 4, 2), (64, 24, 14))])
+def test_user_kernel_3d_tiles_with_halos_replicas_bit_exact(flags, block, sb):
+    # a 7-point body over 3-D tiles with 1-cell halos: every launch updates
+    # face, edge and corner replicas of the written array (inside the launch
+    # by default); the same operation order as the oracle's 3-D Jacobi.
+    # Superblocks of one chunk each, or 14 planes deep across 13-plane chunks
+    # (packed reads, writes through temporaries and replicas together)
+    nz, ny, nx, iters = 37, 50, 133, 3
+    idx = np.arange(nz * ny * nx, dtype=np.uint64)
+    u0 = si.gen_uniform_f32(2203, 23, idx).reshape(nz, ny, nx)
+    dist = lt.Dist.tiles((13, 24, 64), halo=(1, 1, 1))
+    with lt.Context(flags=flags) as ctx:
+        ctx.log_enable()
+        U = ctx.array(lt.F32, (nz, ny, nx), dist)
+        V = ctx.array(lt.F32, (nz, ny, nx), dist)
+        U.write(u0)
+        k = ctx.kernel_from_source(JAC3, "jac3", "global [k, i, j] => read U[k-1:k+1, i-1:i+1, j-1:j+1], write V[k, i, j]",
+                                   [("nz", lt.U32, False), ("ny", lt.U32, False), ("nx", lt.U32, False),
+                                    ("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=(nx, ny, nz), block=block, superblock=sb, args=[nz, ny, nx, U, V])
+            U, V = V, U
+        ctx.synchronize()
+        kinds = {t["kind"] for t in ctx.log()}
+        got = U.read()
+    if sb[2] == 13:
+        assert ("unpack" in kinds) == bool(flags & L.LT_FLAG_NO_FUSED_REPLICAS)
+    want = oracle.jacobi3d(u0, iters)
+    assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
