@@ -378,3 +378,26 @@ def test_user_kernel_3d_tiles_with_halos_replicas_bit_exact(flags, block, sb):
         assert ("unpack" in kinds) == bool(flags & L.LT_FLAG_NO_FUSED_REPLICAS)
     want = oracle.jacobi3d(u0, iters)
     assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
+
+
+@pytest.mark.gpu
+def test_user_kernel_full_size_incore_4x4_as_benchmarked_bit_exact():
+    # the benchmark's source-kernel configuration: 4096^2 in 4 x 4 tiles of
+    # 1024^2 + halo, superblocks of 256 x 1024 threads (1024 columns), 10
+    # iterations, replicas updated inside each launch; every cell compared
+    import bench
+    n, iters = 4096, 10
+    u0 = si.uniform_field(si.SEED_JACOBI_INCORE, 0, n, n)
+    dist = lt.Dist.tiles((1024, 1024), halo=(1, 1))
+    with lt.Context() as ctx:
+        U = ctx.array(lt.F32, (n, n), dist)
+        V = ctx.array(lt.F32, (n, n), dist)
+        U.write(u0)
+        k = ctx.kernel_from_source(bench.USER_JACOBI_VEC, "jacobi4", bench.USER_JACOBI_VEC_ANN,
+                                   [("ny", lt.U32, False), ("nx", lt.U32, False), ("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=(n // 4, n), block=(64, 4), superblock=(256, 1024), args=[n, n, U, V])
+            U, V = V, U
+        ctx.synchronize()
+        got = U.read()
+    assert np.array_equal(got, oracle.jacobi2d(u0, iters))
