@@ -199,6 +199,21 @@ lt_status lt_array_discard(lt_ctx *ctx, lt_array *arr);
  * borrowed only during the call. */
 lt_status lt_array_write(lt_ctx *ctx, lt_array *arr, const void *host, size_t bytes);
 lt_status lt_array_read(lt_ctx *ctx, lt_array *arr, void *host, size_t bytes);
+/* The same without waiting (an extension: the paper's arrays are filled and
+ * read synchronously).  Each chunk's copy is enqueued as an operation on a
+ * copy stream (H2D for writes, D2H for reads) behind the operations that
+ * last produced or used the chunk, so the copies overlap kernels and copies
+ * of the other direction, and later launches wait only for the chunks they
+ * use.  The buffer must stay valid and must not be touched by the caller
+ * until lt_synchronize (or another synchronous call) returns; pinned host
+ * memory is needed for the copies to run asynchronously.  Several calls on
+ * the same buffer are ordered where their host regions overlap: a write of
+ * a chunk reads its whole box (halo included) from the buffer, a read writes
+ * the chunk's owned box into it.  Column-major arrays, and reads of arrays
+ * with chunks outside device memory, take the synchronous path.  Errors as
+ * for lt_array_write / lt_array_read. */
+lt_status lt_array_write_async(lt_ctx *ctx, lt_array *arr, const void *host, size_t bytes);
+lt_status lt_array_read_async(lt_ctx *ctx, lt_array *arr, void *host, size_t bytes);
 /* The same with a dense row-major DEVICE buffer of the context's device
  * (for instance a CUDA tensor).  Row-major chunks only
  * (LT_ERR_UNSUPPORTED otherwise).  Synchronous. */

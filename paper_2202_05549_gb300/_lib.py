@@ -111,6 +111,8 @@ SIGNATURES = {
     "lt_array_destroy": (_st, [_vp, _vp]),
     "lt_array_write": (_st, [_vp, _vp, _vp, C.c_size_t]),
     "lt_array_read": (_st, [_vp, _vp, _vp, C.c_size_t]),
+    "lt_array_write_async": (_st, [_vp, _vp, _vp, C.c_size_t]),
+    "lt_array_read_async": (_st, [_vp, _vp, _vp, C.c_size_t]),
     "lt_array_write_device": (_st, [_vp, _vp, _vp, C.c_size_t]),
     "lt_array_read_device": (_st, [_vp, _vp, _vp, C.c_size_t]),
     "lt_array_read_box": (_st, [_vp, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp, C.c_size_t]),

@@ -222,6 +222,10 @@ struct CState {
     int64_t last_use_group = -1;
     int64_t last_write_launch = -1;  // last launch that wrote it
     bool discarded = false;          // contents declared dead (lt_array_discard) and not written since
+    // the last asynchronous copies between this chunk and a host buffer
+    // (lt_array_write_async reads the chunk's box from the buffer,
+    // lt_array_read_async writes the chunk's owned box into it)
+    FenceSet host_write, host_read;
 };
 
 
@@ -499,7 +503,7 @@ lt_status dev_alloc(lt_ctx *c, size_t bytes, size_t *off, FenceSet *f, bool soft
 lt_status evict(lt_ctx *c, lt_array *a, int64_t ci);
 lt_status ensure_dev(lt_ctx *c, lt_array *a, int64_t ci, bool need_data, bool soft = false);
 lt_status xfer_chunk(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *hb, bool to_dev,
-                     bool other_is_device = false);
+                     bool other_is_device = false, int stream = S_COMP, bool wait = true);
 void xfer_chunk_host(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *hb, bool to_chunk);
 std::vector<std::pair<lt_array *, int64_t>> dead_chunks(const LaunchPlan &plan, const std::vector<lt_array *> &parr);
 std::vector<std::pair<int, int64_t>> dead_by_param(const LaunchPlan &plan, const std::vector<lt_array *> &parr);

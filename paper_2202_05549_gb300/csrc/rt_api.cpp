@@ -342,6 +342,77 @@ lt_status lt_array_read(lt_ctx *c, lt_array *arr, void *host, size_t bytes) {
     return LT_OK;
 }
 
+// Asynchronous host copies: each chunk's copy is an operation on a copy
+// stream, ordered by the chunk's fences like a launch's, so copies overlap
+// kernels and each other.  The host buffer is the caller's until the copies
+// end (lt_synchronize): a write of one chunk reads its whole box (halo
+// included) from the buffer, a read writes the chunk's owned box into it, so
+// each such copy also waits for the earlier copies of the other direction
+// whose host region overlaps its own.
+static lt_status array_copy_async(lt_ctx *c, lt_array *arr, void *host, size_t bytes, bool to_array) {
+    lt_status st = check_ctx(c);
+    if (st) return st;
+    lt_array *a = find_array(c, arr);
+    if (!a || (!host && !c->dry)) return fail(LT_ERR_INVALID_ARG, "unknown array or null buffer");
+    if (bytes != array_bytes(a)) return fail(LT_ERR_INVALID_ARG, "buffer size does not match the array");
+    if (a->g.dist.order == LT_ORDER_COL)
+        return to_array ? lt_array_write(c, arr, host, bytes) : lt_array_read(c, arr, host, bytes);
+    if (to_array) {
+        if ((st = flush_pending(c))) return st;
+        ++c->launch_id;
+        for (auto &cs : a->cs) {
+            cs.dead_launch = c->launch_id;
+            cs.discarded = false;
+        }
+    } else {
+        if (pending_writes(c, arr) && (st = flush_pending(c))) return st;
+        // chunks that are not in device memory take the synchronous path
+        for (const auto &cs : a->cs)
+            if (cs.loc != LOC_DEV && !c->dry) return lt_array_read(c, arr, host, bytes);
+    }
+    const int sid = to_array ? S_H2D : S_D2H;
+    for (size_t ci = 0; ci < a->cs.size(); ++ci) {
+        CState &s = a->cs[ci];
+        const ChunkGeom &cg = a->g.chunks[ci];
+        if (to_array) {
+            if (s.loc == LOC_HOST && !c->dry) {  // spilled: rewritten in place in the host pool
+                if ((st = sync_all(c))) return st;
+                xfer_chunk_host(c, a, (int64_t)ci, cg.box, (char *)host, true);
+                s.dead_launch = -1;
+                continue;
+            }
+            s.pin++;
+            st = ensure_dev(c, a, (int64_t)ci, false);
+            s.pin--;
+            if (st) return st;
+        }
+        const Box &hbox = to_array ? cg.box : cg.owned;  // the host region this copy touches
+        op_begin(c, sid, to_array ? "write" : "read");
+        FenceSet w = s.ready;
+        if (to_array) w.merge(s.busy);
+        for (int64_t o : chunks_intersecting(a->g, hbox)) {
+            const CState &os = a->cs[(size_t)o];
+            w.merge(to_array ? os.host_read : os.host_write);
+        }
+        if ((st = op_wait(c, w))) return st;
+        if (!c->dry && (st = xfer_chunk(c, a, (int64_t)ci, hbox, (char *)host, to_array, false, sid, false)))
+            return st;
+        uint64_t q;
+        if ((st = op_end(c, &q))) return st;
+        if (to_array) {
+            s.ready = FenceSet::one(sid, q);
+            s.busy = FenceSet::one(sid, q);
+            s.host_write = FenceSet::one(sid, q);
+            c->stats.bytes_h2d += cg.box.volume() * a->g.esize();
+        } else {
+            s.busy.add(sid, q);
+            s.host_read = FenceSet::one(sid, q);
+            c->stats.bytes_d2h += cg.owned.volume() * a->g.esize();
+        }
+    }
+    return LT_OK;
+}
+
 static lt_status array_copy_device(lt_ctx *c, lt_array *arr, void *dev, size_t bytes, bool to_array) {
     lt_status st = check_ctx(c);
     if (st) return st;
@@ -384,6 +455,14 @@ static lt_status array_copy_device(lt_ctx *c, lt_array *arr, void *dev, size_t b
         }
     }
     return LT_OK;
+}
+
+lt_status lt_array_write_async(lt_ctx *c, lt_array *arr, const void *host, size_t bytes) {
+    return array_copy_async(c, arr, const_cast<void *>(host), bytes, true);
+}
+
+lt_status lt_array_read_async(lt_ctx *c, lt_array *arr, void *host, size_t bytes) {
+    return array_copy_async(c, arr, host, bytes, false);
 }
 
 lt_status lt_array_write_device(lt_ctx *c, lt_array *arr, const void *dev, size_t bytes) {

@@ -299,7 +299,7 @@ lt_status ensure_dev(lt_ctx *c, lt_array *a, int64_t ci, bool need_data, bool so
 // Copy between the dense row-major host buffer `hb` (whole array) and the
 // part `box` of chunk ci that lives in device memory.
 lt_status xfer_chunk(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *hb, bool to_dev,
-                     bool other_is_device) {
+                     bool other_is_device, int stream, bool wait) {
     const ArrayGeom &g = a->g;
     const ChunkGeom &cg = g.chunks[(size_t)ci];
     CState &s = a->cs[(size_t)ci];
@@ -319,7 +319,7 @@ lt_status xfer_chunk(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *h
         for (int d = 0; d < g.nd; ++d) o += idx[d] * gs[d];
         return hb + o * (int64_t)es;
     };
-    cudaStream_t st = c->st[S_COMP];
+    cudaStream_t st = c->st[stream];
     const bool chunk_on_host = s.loc == LOC_HOST;
     char *cbase = chunk_on_host ? c->host_base + s.off : dev;
     if (other_is_device || chunk_on_host) {
@@ -420,7 +420,7 @@ lt_status xfer_chunk(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *h
         else
             CK(c, cudaMemcpy2DAsync(hp, hpitch, dp, dpitch, width, rows, cudaMemcpyDeviceToHost, st));
     }
-    CK(c, cudaStreamSynchronize(st));
+    if (wait) CK(c, cudaStreamSynchronize(st));
     return LT_OK;
 }
 

@@ -68,7 +68,7 @@ lt_status op_wait(lt_ctx *c, const FenceSet &f) {
         int64_t pt = -1;
         // a fence on the waiting stream itself needs no event (stream order)
         cudaEvent_t e = fence_event(c, t, q, &pt, t != s);
-        if (pt >= 0 && (e || t == s) &&
+        if (pt >= 0 && (e || t == s || c->dry) &&
             std::find(c->cur_deps.begin(), c->cur_deps.end(), pt) == c->cur_deps.end()) {
             c->cur_deps.push_back(pt);
             c->stats.deps++;

@@ -102,6 +102,23 @@ class Array:
         assert a.shape == self.shape, (a.shape, self.shape)
         check(L.load().lt_array_write(self.ctx.h, self.h, a.ctypes.data_as(C.c_void_p), a.nbytes))
 
+    def write_async(self, a: np.ndarray):
+        """Enqueue the copy from `a` (C-contiguous, this shape and dtype;
+        pinned memory for the copy to overlap) and return
+        (lt_array_write_async); the context keeps `a` until its next
+        synchronize, and the caller must not change it before then."""
+        assert a.shape == self.shape and a.dtype == _NP[self.dtype] and a.flags.c_contiguous
+        check(L.load().lt_array_write_async(self.ctx.h, self.h, a.ctypes.data_as(C.c_void_p), a.nbytes))
+        self.ctx._held.append(a)
+
+    def read_async(self, out: np.ndarray) -> np.ndarray:
+        """Enqueue the copy into `out` and return (lt_array_read_async); the
+        values are there after the context's next synchronize."""
+        assert out.shape == self.shape and out.dtype == _NP[self.dtype] and out.flags.c_contiguous
+        check(L.load().lt_array_read_async(self.ctx.h, self.h, out.ctypes.data_as(C.c_void_p), out.nbytes))
+        self.ctx._held.append(out)
+        return out
+
     def discard(self):
         """Declare the contents dead: dropped instead of written back when
         memory is needed (lt_array_discard)."""
@@ -239,12 +256,14 @@ class Batch:
             d.nargs = len(args)
             d.repeat = rep
 
+
 class Context:
     def __init__(self, device=0, hbm_budget=0, host_pool=0, staging_cap=0, flags=0):
         cfg = L.lt_config(hbm_budget, host_pool, staging_cap, device, flags)
         h = C.c_void_p()
         check(L.load().lt_ctx_create(C.byref(cfg), C.byref(h)))
         self.h = h
+        self._held = []  # host buffers of asynchronous copies, kept until the next synchronize
 
     def __enter__(self):
         return self
@@ -256,6 +275,7 @@ class Context:
         if self.h:
             L.load().lt_ctx_destroy(self.h)
             self.h = None
+        self._held = []
 
     def array(self, dtype, shape, dist: Dist | None = None) -> Array:
         return Array(self, dtype, shape, dist or Dist.block())
@@ -290,6 +310,7 @@ class Context:
 
     def synchronize(self):
         check(L.load().lt_synchronize(self.h))
+        self._held.clear()
 
     def timer_start(self):
         check(L.load().lt_timer_start(self.h))

@@ -431,3 +431,29 @@ def test_pack_through_shared_memory_and_registers_bit_exact(flags, shape, dist, 
         kinds = {t["kind"] for t in ctx.log()}
     assert "pack" in kinds
     assert np.array_equal(got, want), f"{np.sum(got != want)} cells differ"
+
+
+@pytest.mark.parametrize("dist", [lt.Dist.rows(100, halo=1), lt.Dist.tiles((128, 256), halo=(1, 1)),
+                                  lt.Dist.rows(100)])
+def test_async_host_copies_round_trip_through_one_buffer(dist):
+    # the end-to-end loop with asynchronous copies: upload from a pinned
+    # buffer, three launches, read the result back into the same buffer,
+    # upload it again, three more launches; the copies of one step overlap
+    # those of the next only where their host rows do not
+    import torch
+    ny, nx = 700, 1100
+    u0 = si.uniform_field(si.SEED_JACOBI_INCORE, 9, ny, nx)
+    h = torch.empty((ny, nx), dtype=torch.float32, pin_memory=True).numpy()
+    h[...] = u0
+    with lt.Context() as ctx:
+        U = ctx.array(lt.F32, (ny, nx), dist)
+        V = ctx.array(lt.F32, (ny, nx), dist)
+        k = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        for _ in range(2):
+            U.write_async(h)
+            for _ in range(3):
+                k.launch(grid=(nx, ny), block=(128, 4), superblock=(0, 0), args=[U, V])
+                U, V = V, U
+            U.read_async(h)
+        ctx.synchronize()
+    assert np.array_equal(h, oracle.jacobi2d(u0, 6))

@@ -670,3 +670,30 @@ def test_streaming_plan_of_the_full_out_of_core_grid_fits_its_pools(monkeypatch)
         assert s["fetches"] > 0 and s["evictions"] > 0
         assert s["hbm_peak"] <= pl["budget"]
         assert s["tasks_execute"] == 2 * 20 * (ny // band)
+
+
+def test_async_host_copies_order_overlapping_host_regions():
+    # lt_array_write_async reads a chunk's whole box (halo rows included) from
+    # the buffer, lt_array_read_async writes the chunk's owned rows into it:
+    # a write of band b waits for the reads of bands b-1..b+1 (their owned
+    # rows lie in its box) and a read of band b for the earlier writes of
+    # b-1..b+1; copies run on the H2D / D2H streams (dry run: no device)
+    import numpy as np
+    with lt.Context(hbm_budget=1 << 30, flags=L.LT_FLAG_DRYRUN) as ctx:
+        ctx.log_enable()
+        U = ctx.array(lt.F32, (64, 32), lt.Dist.rows(16, halo=1))
+        h = np.zeros((64, 32), np.float32)
+        U.write_async(h)
+        U.read_async(h)
+        U.write_async(h)
+        ctx.synchronize()
+        log = ctx.log()
+    w1 = [t for t in log if t["kind"] == "write" and t["launch"] == 1]
+    rd = [t for t in log if t["kind"] == "read"]
+    w2 = [t for t in log if t["kind"] == "write" and t["launch"] == 2]
+    assert len(w1) == len(rd) == len(w2) == 4
+    assert {t["stream"] for t in w1 + w2} == {1} and {t["stream"] for t in rd} == {2}
+    # fences keep the newest operation per stream: the newest overlapping one
+    for b in range(4):
+        assert rd[b]["deps"] == [w1[min(b + 1, 3)]["id"]]
+        assert w2[b]["deps"] == [w1[b]["id"], rd[min(b + 1, 3)]["id"]]
