@@ -88,3 +88,61 @@ def test_jacobi3d_random_configurations(case):
         got = U.read()
     want = oracle.jacobi3d(u0, iters)
     assert np.array_equal(got, want), (shape, sb, f"{np.sum(got != want)} cells differ")
+
+
+def _source_case(case):
+    """A random source-kernel launch configuration.  Half of the cases align
+    the superblocks with the chunks (chunks a whole number of blocks), so that
+    writes go straight into chunks with halo replicas to update; the others
+    take random superblocks (reads packed, writes through temporaries)."""
+    rng = np.random.default_rng(9500 + case)
+    ny, nx = int(rng.integers(1, 600)), int(rng.integers(1, 800))
+    iters = int(rng.integers(1, 4))
+    bx = int(rng.choice([1, 16, 32, 64]))
+    by = int(rng.choice([1, 2, 4, 8]))
+    if rng.random() < 0.5:
+        cy = by * int(rng.integers(1, max(2, ny // by + 1)))
+        cx = bx * int(rng.integers(1, max(2, nx // bx + 1)))
+        halo = int(rng.integers(0, 2)) if rng.random() < 0.3 else 1
+        if rng.random() < 0.5:
+            dist, sb = lt.Dist.rows(cy, halo=halo), (nx, cy)
+        else:
+            dist, sb = lt.Dist.tiles((cy, cx), halo=(halo, halo)), (cx, cy)
+    else:
+        sb = (int(rng.integers(1, nx + 1)), int(rng.integers(1, ny + 1))) if rng.random() < 0.8 else (0, 0)
+        dist = _dist(rng, (ny, nx))
+    flags = L.LT_FLAG_NO_FUSED_REPLICAS if rng.random() < 0.3 else 0
+    spill = rng.random() < 0.25
+    return ny, nx, iters, (bx, by), sb, dist, flags, spill
+
+
+@pytest.mark.parametrize("case", range(20))
+def test_source_kernel_random_configurations(case):
+    # the one-cell-per-thread source kernel (runtime-compiled) under random
+    # shapes, chunkings, superblocks and blocks: replicas updated inside the
+    # launch or by a copy kernel, reads packed across chunks, sometimes
+    # spilling; inputs and results through the asynchronous host copies
+    import bench
+    ny, nx, iters, block, sb, dist, flags, spill = _source_case(case)
+    u0 = si.uniform_field(2203, 500 + case, ny, nx)
+    cells = (ny + 2) * (nx + 64) * 4
+    kw = dict(hbm_budget=max(cells, 1 << 20) * 2, host_pool=cells * 8 + (8 << 20)) if spill else {}
+    h = np.ascontiguousarray(u0)
+    with lt.Context(flags=flags, **kw) as ctx:
+        U = ctx.array(lt.F32, (ny, nx), dist)
+        V = ctx.array(lt.F32, (ny, nx), dist)
+        U.write_async(h)
+        k = ctx.kernel_from_source(bench.USER_JACOBI, "jacobi", ANN2, [("ny", lt.U32, False), ("nx", lt.U32, False),
+                                                                        ("U", lt.F32), ("V", lt.F32)])
+        try:
+            for _ in range(iters):
+                k.launch(grid=(nx, ny), block=block, superblock=sb, args=[ny, nx, U, V])
+                U, V = V, U
+            out = np.empty((ny, nx), np.float32)
+            U.read_async(out)
+            ctx.synchronize()
+        except lt.LightningError as e:
+            assert spill and e.code == L.LT_ERR_OOM_DEVICE, e
+            return
+    want = oracle.jacobi2d(u0, iters)
+    assert np.array_equal(out, want), (ny, nx, sb, block, f"{np.sum(out != want)} cells differ")
