@@ -35,6 +35,8 @@ constexpr int KRPT = 8;    // records per thread and round (a warp's 32-bit tota
 constexpr int KROUNDS = 8; // rounds per CTA; the warps' totals fold into 64-bit CTA totals after each
 constexpr int KMAX = 64;   // most centres
 
+uint64_t g_cent_addr = 0;  // set by prepare for the launch that follows it: the centres' address, or 0
+
 // Is x a multiple of 2^-24 in [0, 1)?  Then *m = x * 2^24 exactly.
 __device__ __forceinline__ bool fixed24(float x, uint32_t *m) {
     const float t = __fmul_rn(x, 16777216.0f);  // exact: a power-of-two scale
@@ -64,6 +66,13 @@ __device__ __forceinline__ int nearest(const float4 *cs, int k, float4 x) {
     return best;
 }
 
+// The centres of the launch in the constant bank (copied from the centre
+// array on the stream before the kernel, when that array is one contiguous
+// view): the distance instructions then take them as constant operands, with
+// no shared-memory load per centre.
+__constant__ float4 c_cent[KMAX];
+
+template <bool CONSTC>
 __global__ void __launch_bounds__(KT) kmeans_assign_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
     __shared__ float4 cs[KMAX];
     __shared__ uint32_t iacc[KT / 32][KMAX * 5];  // a warp's fixed-point sums (2^-24 units) and counts
@@ -76,7 +85,7 @@ __global__ void __launch_bounds__(KT) kmeans_assign_kernel(const ExecTask *__res
     const int64_t n = p.shape[0][0] / 4;
     const int64_t i0 = t.t_lo[0], i1 = min(t.t_hi[0], n - 1);
     const DView X = t.v[0], Cv = t.v[1], S = t.v[2];
-    for (int e = threadIdx.x; e < k; e += KT) {
+    for (int e = threadIdx.x; e < (CONSTC ? 0 : k); e += KT) {
         const float *c = (const float *)Cv.base;
         cs[e] = make_float4(c[(4 * e) * Cv.s[0]], c[(4 * e + 1) * Cv.s[0]], c[(4 * e + 2) * Cv.s[0]],
                             c[(4 * e + 3) * Cv.s[0]]);
@@ -119,24 +128,59 @@ __global__ void __launch_bounds__(KT) kmeans_assign_kernel(const ExecTask *__res
             if (rb <= i1) {
                 const float4 xq = load(rb);
                 int ba = 0, bb = 0;
-                float da = dist2(xa, cs[0]), db = dist2(xq, cs[0]);
-#pragma unroll 4
-                for (int j = 1; j < k; ++j) {
-                    const float4 c = cs[j];
-                    const float d = dist2(xa, c), dq = dist2(xq, c);
-                    if (d < da) {
-                        da = d;
-                        ba = j;
+                float da, db;
+                if (CONSTC) {
+                    da = dist2(xa, c_cent[0]);
+                    db = dist2(xq, c_cent[0]);
+#pragma unroll
+                    for (int j = 1; j < KMAX; ++j) {
+                        if (j >= k) break;
+                        const float d = dist2(xa, c_cent[j]), dq = dist2(xq, c_cent[j]);
+                        if (d < da) {
+                            da = d;
+                            ba = j;
+                        }
+                        if (dq < db) {
+                            db = dq;
+                            bb = j;
+                        }
                     }
-                    if (dq < db) {
-                        db = dq;
-                        bb = j;
+                } else {
+                    da = dist2(xa, cs[0]);
+                    db = dist2(xq, cs[0]);
+#pragma unroll 4
+                    for (int j = 1; j < k; ++j) {
+                        const float4 c = cs[j];
+                        const float d = dist2(xa, c), dq = dist2(xq, c);
+                        if (d < da) {
+                            da = d;
+                            ba = j;
+                        }
+                        if (dq < db) {
+                            db = dq;
+                            bb = j;
+                        }
                     }
                 }
                 add(ba, xa);
                 add(bb, xq);
             } else {
-                add(nearest(cs, k, xa), xa);
+                int ba = 0;
+                if (CONSTC) {
+                    float da = dist2(xa, c_cent[0]);
+#pragma unroll
+                    for (int j = 1; j < KMAX; ++j) {
+                        if (j >= k) break;
+                        const float d = dist2(xa, c_cent[j]);
+                        if (d < da) {
+                            da = d;
+                            ba = j;
+                        }
+                    }
+                } else {
+                    ba = nearest(cs, k, xa);
+                }
+                add(ba, xa);
             }
         }
         __syncthreads();
@@ -194,6 +238,15 @@ uint32_t prepare_kmeans_assign(ExecTask *t, int n, ExecParams &p) {
     for (int i = 0; i < n && vec; ++i)
         if (t[i].v[0].s[0] != 1 || t[i].v[0].base % 16 != 0) vec = false;
     p.variant = vec ? 1 : 0;
+    // one contiguous view of the centres shared by every task: the constant-bank kernel
+    g_cent_addr = 0;
+    if (n > 0 && t[0].v[1].s[0] == 1) {
+        const uint64_t a0 = t[0].v[1].base;  // byte address of centre feature 0
+        bool same = true;
+        for (int i = 1; i < n && same; ++i) same = t[i].v[1].base == a0 && t[i].v[1].s[0] == 1;
+        const int64_t lo = t[0].v[1].org[0], hi = t[0].v[1].hi[0];
+        if (same && lo <= 0 && hi >= 4 * k - 1) g_cent_addr = a0;
+    }
     uint32_t total = 0;
     for (int i = 0; i < n; ++i) {
         const int64_t cnt = std::min(t[i].t_hi[0], nrec - 1) - t[i].t_lo[0] + 1;
@@ -205,7 +258,15 @@ uint32_t prepare_kmeans_assign(ExecTask *t, int n, ExecParams &p) {
 }
 
 cudaError_t launch_kmeans_assign(const ExecTask *dev, uint32_t ctas, const ExecParams &p, cudaStream_t st) {
-    kmeans_assign_kernel<<<ctas, KT, 0, st>>>(dev, p);
+    if (g_cent_addr) {
+        // the centres (4k contiguous floats) into the constant bank, in stream order
+        cudaError_t e = cudaMemcpyToSymbolAsync(c_cent, (const void *)(uintptr_t)g_cent_addr,
+                                                (size_t)p.i[0] * sizeof(float4), 0, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        kmeans_assign_kernel<true><<<ctas, KT, 0, st>>>(dev, p);
+    } else {
+        kmeans_assign_kernel<false><<<ctas, KT, 0, st>>>(dev, p);
+    }
     return cudaGetLastError();
 }
 
