@@ -70,7 +70,13 @@ __device__ __forceinline__ int nearest(const float4 *cs, int k, float4 x) {
 // array on the stream before the kernel, when that array is one contiguous
 // view): the distance instructions then take them as constant operands, with
 // no shared-memory load per centre.
-__constant__ float4 c_cent[KMAX];
+// Entries k .. k+3 are +infinity: a centre there is never nearer (its
+// distance is +inf, or NaN for a non-finite record, and neither compares
+// below a distance already taken), so the loop tests its bound once per four
+// centres.
+__constant__ float4 c_cent[KMAX + 4];
+__device__ const float4 c_pad[4] = {{INFINITY, INFINITY, INFINITY, INFINITY}, {INFINITY, INFINITY, INFINITY, INFINITY},
+                                    {INFINITY, INFINITY, INFINITY, INFINITY}, {INFINITY, INFINITY, INFINITY, INFINITY}};
 
 template <bool CONSTC>
 __global__ void __launch_bounds__(KT) kmeans_assign_kernel(const ExecTask *__restrict__ tasks, ExecParams p) {
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(KT) kmeans_assign_kernel(const ExecTask *__res
                     db = dist2(xq, c_cent[0]);
 #pragma unroll
                     for (int j = 1; j < KMAX; ++j) {
-                        if (j >= k) break;
+                        if ((j & 3) == 1 && j >= k) break;  // once per four centres: padded with +inf
                         const float d = dist2(xa, c_cent[j]), dq = dist2(xq, c_cent[j]);
                         if (d < da) {
                             da = d;
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(KT) kmeans_assign_kernel(const ExecTask *__res
                     float da = dist2(xa, c_cent[0]);
 #pragma unroll
                     for (int j = 1; j < KMAX; ++j) {
-                        if (j >= k) break;
+                        if ((j & 3) == 1 && j >= k) break;
                         const float d = dist2(xa, c_cent[j]);
                         if (d < da) {
                             da = d;
@@ -262,6 +268,11 @@ cudaError_t launch_kmeans_assign(const ExecTask *dev, uint32_t ctas, const ExecP
         // the centres (4k contiguous floats) into the constant bank, in stream order
         cudaError_t e = cudaMemcpyToSymbolAsync(c_cent, (const void *)(uintptr_t)g_cent_addr,
                                                 (size_t)p.i[0] * sizeof(float4), 0, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        static void *pad = nullptr;  // the +inf entries after the centres
+        if (!pad && (e = cudaGetSymbolAddress(&pad, c_pad)) != cudaSuccess) return e;
+        e = cudaMemcpyToSymbolAsync(c_cent, pad, 4 * sizeof(float4), (size_t)p.i[0] * sizeof(float4),
+                                    cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
         kmeans_assign_kernel<true><<<ctas, KT, 0, st>>>(dev, p);
     } else {
