@@ -393,6 +393,7 @@ struct lt_ctx {
     std::vector<TableSlot> tslots;
     uint64_t tslot_tick = 0;
     uint32_t *err_word = nullptr;  // device error word
+    uint32_t *err_host = nullptr;  // pinned host copy of the error word, read back in stream order by sync_all
     // Grid barrier of source kernels that update their replicas themselves:
     // a device counter every CTA of such a launch increments once, and the
     // host's running total of those increments (a launch waits for the total

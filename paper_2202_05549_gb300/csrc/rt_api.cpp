@@ -131,6 +131,8 @@ lt_status lt_ctx_create(const lt_config *cfg, lt_ctx **out) {
     for (auto &t : c->tslots) CK(cp, cudaEventCreateWithFlags(&t.staged, cudaEventDisableTiming));
     CK(cp, cudaMalloc((void **)&c->err_word, 16));
     CK(cp, cudaMemset(c->err_word, 0, 16));
+    CK(cp, cudaHostAlloc((void **)&c->err_host, 64, cudaHostAllocDefault));
+    *c->err_host = 0;
     CK(cp, cudaMalloc((void **)&c->ubar, sizeof(unsigned long long)));
     CK(cp, cudaMemset(c->ubar, 0, sizeof(unsigned long long)));
     *out = c.release();
@@ -170,6 +172,7 @@ lt_status lt_ctx_destroy(lt_ctx *c) {
         if (c->up_host) cudaFreeHost(c->up_host);
         if (c->up_dev) cudaFree(c->up_dev);
         if (c->err_word) cudaFree(c->err_word);
+        if (c->err_host) cudaFreeHost(c->err_host);
         if (c->ubar) cudaFree(c->ubar);
     }
     delete c;
@@ -413,6 +416,10 @@ static lt_status array_copy_async(lt_ctx *c, lt_array *arr, void *host, size_t b
     return LT_OK;
 }
 
+// Copies between an array and a dense device buffer: each chunk's copy is an
+// operation on the compute stream behind the operations on that chunk (as for
+// the asynchronous host copies), and the call returns once all of them are
+// done, so the buffer is the caller's again.
 static lt_status array_copy_device(lt_ctx *c, lt_array *arr, void *dev, size_t bytes, bool to_array) {
     lt_status st = check_ctx(c);
     if (st) return st;
@@ -422,39 +429,42 @@ static lt_status array_copy_device(lt_ctx *c, lt_array *arr, void *dev, size_t b
     if (a->g.dist.order == LT_ORDER_COL) return fail(LT_ERR_UNSUPPORTED, "device copies need row-major chunks");
     if (c->dry) return fail(LT_ERR_UNSUPPORTED, "device copies need a device");
     if ((st = flush_pending(c))) return st;
-    if ((st = sync_all(c))) return st;
     if (to_array) {
         ++c->launch_id;
-        for (size_t ci = 0; ci < a->cs.size(); ++ci) {
-            a->cs[ci].dead_launch = c->launch_id;
-            a->cs[ci].discarded = false;
+        for (auto &cs : a->cs) {
+            cs.dead_launch = c->launch_id;
+            cs.discarded = false;
         }
     }
     for (size_t ci = 0; ci < a->cs.size(); ++ci) {
         CState &s = a->cs[ci];
         const ChunkGeom &cg = a->g.chunks[ci];
-        if (!to_array && s.loc == LOC_NONE) {
-            // never written: zero the owned part of the destination
-            int64_t gs0 = a->g.nd > 1 ? a->g.shape[a->g.nd - 1] : 1;
-            (void)gs0;
-            if ((st = ensure_dev(c, a, (int64_t)ci, true))) return st;
-            if ((st = sync_all(c))) return st;
-        }
-        if (to_array && s.loc != LOC_HOST) {
+        // a chunk never written reads as zeros (zero-filled in device memory); a write
+        // into a chunk that is not in the host pool needs it in device memory
+        if ((!to_array && s.loc == LOC_NONE) || (to_array && s.loc != LOC_HOST)) {
             s.pin++;
-            st = ensure_dev(c, a, (int64_t)ci, false);
+            st = ensure_dev(c, a, (int64_t)ci, !to_array);
             s.pin--;
             if (st) return st;
-            if ((st = sync_all(c))) return st;
         }
         s.dead_launch = -1;
-        if ((st = xfer_chunk(c, a, (int64_t)ci, to_array ? cg.box : cg.owned, (char *)dev, to_array, true))) return st;
+        op_begin(c, S_COMP, to_array ? "write_device" : "read_device");
+        FenceSet w = s.ready;
+        if (to_array) w.merge(s.busy);
+        if ((st = op_wait(c, w))) return st;
+        if ((st = xfer_chunk(c, a, (int64_t)ci, to_array ? cg.box : cg.owned, (char *)dev, to_array, true, S_COMP,
+                             false)))
+            return st;
+        uint64_t q;
+        if ((st = op_end(c, &q))) return st;
         if (to_array) {
-            s.ready = FenceSet();
-            s.busy = FenceSet();
+            s.ready = FenceSet::one(S_COMP, q);
+            s.busy = FenceSet::one(S_COMP, q);
+        } else {
+            s.busy.add(S_COMP, q);
         }
     }
-    return LT_OK;
+    return sync_all(c);
 }
 
 lt_status lt_array_write_async(lt_ctx *c, lt_array *arr, const void *host, size_t bytes) {

@@ -363,7 +363,7 @@ lt_status xfer_chunk(lt_ctx *c, lt_array *a, int64_t ci, const Box &box, char *h
             else
                 CK(c, cudaMemcpy2DAsync(hptr, hp, cptr, cp, width, rows, cudaMemcpyDefault, st));
         }
-        CK(c, cudaStreamSynchronize(st));
+        if (wait) CK(c, cudaStreamSynchronize(st));
         return LT_OK;
     }
     if (g.dist.order == LT_ORDER_COL) {

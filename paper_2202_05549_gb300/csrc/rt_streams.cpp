@@ -317,14 +317,17 @@ int32_t uniform_cta_count(const std::vector<ExecTask> &tasks) {
 
 lt_status sync_all(lt_ctx *c) {
     if (c->dry) return LT_OK;
+    // Every kernel that can record an error runs on the compute stream, so a
+    // copy of the error word queued there behind them lands in pinned host
+    // memory by the time that stream is idle: no separate round trip.
+    CK(c, cudaMemcpyAsync(c->err_host, c->err_word, 4, cudaMemcpyDeviceToHost, c->st[S_COMP]));
     for (int s = 0; s < NSTREAM; ++s) CK(c, cudaStreamSynchronize(c->st[s]));
     if (lt_status lp = link_poll(c)) return lp;
     for (int s = 0; s < NSTREAM; ++s) {  // every deferred fence is complete now
         for (uint64_t d : c->deferred[s]) c->dfcov[s][d % RING] = ~(uint64_t)0;
         c->deferred[s].clear();
     }
-    uint32_t e = 0;
-    CK(c, cudaMemcpy(&e, c->err_word, 4, cudaMemcpyDeviceToHost));
+    const uint32_t e = *(volatile uint32_t *)c->err_host;
     if (e) {
         CK(c, cudaMemset(c->err_word, 0, 4));
         return fail(e >= 0x6700 && e < 0x6900 ? LT_ERR_TIMEOUT : LT_ERR_DEVICE_CHECK,
