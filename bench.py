@@ -175,6 +175,13 @@ class Clocks:
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        # nvidia-smi's start-up (NVML initialisation) stalls this process's
+        # CUDA calls for a while: the timed region starts once it is sampling
+        t0 = time.perf_counter()
+        while self.p is not None and time.perf_counter() - t0 < 3.0 and self.p.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.p is None:

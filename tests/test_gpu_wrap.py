@@ -5,6 +5,7 @@ import pytest
 
 import oracle
 import synth_inputs as si
+from paper_2202_05549_gb300 import _lib as L
 from paper_2202_05549_gb300 import lightning as lt
 
 torch = pytest.importorskip("torch")
@@ -52,3 +53,18 @@ def test_wrapped_input_feeds_chunked_array_with_pitch():
         ctx.synchronize()
         got = V.read()
     assert np.array_equal(got, oracle.jacobi2d(u0, 1))
+
+
+def test_zero_fill_of_a_wrapped_view_leaves_its_row_padding():
+    # a zero fill writes the box rows only: the columns past the view's width
+    # (another tensor's data in the caller's allocation) keep their values
+    ny, nx, pitch = 129, 517, 640
+    big = torch.full((ny, pitch), 5.0, dtype=torch.float32, device="cuda")
+    with lt.Context() as ctx:
+        A = ctx.wrap(big[:, :nx])
+        A.fill(L.LT_INIT_ZERO)
+        ctx.synchronize()
+        A.destroy()
+    got = big.cpu().numpy()
+    assert not got[:, :nx].any()
+    assert (got[:, nx:] == 5.0).all()
