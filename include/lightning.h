@@ -544,7 +544,8 @@ lt_status lt_jacobi2d_packed_noalloc(const float *U, float *V, int64_t ny, int64
  * instead of a full IEEE division.  This call runs that sequence on `device`
  * for all 2^32 float bit patterns and counts the inputs where it differs
  * from the IEEE quotient (any two NaNs count as equal) into *mismatches
- * (0 expected).  divisor: 5 or 7.  Synchronous; allocates 8 bytes of device
+ * (0 expected); it runs the four-wide form (one range test for four
+ * quotients) the same way, each pattern in each of the four positions.  divisor: 5 or 7.  Synchronous; allocates 8 bytes of device
  * memory for the count.  Errors: LT_ERR_INVALID_ARG (other divisor, null
  * output), LT_ERR_CUDA (a CUDA call failed). */
 lt_status lt_selftest_div_const(int32_t device, int32_t divisor, uint64_t *mismatches);

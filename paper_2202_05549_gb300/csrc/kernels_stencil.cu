@@ -264,11 +264,10 @@ __device__ __forceinline__ void multi_segment(const float *__restrict__ ub, int6
             const float4 up = q2[l], mid = q1[l], dn = cur;
             const float wv = __shfl_up_sync(0xffffffffu, mid.w, 1);
             const float ev = __shfl_down_sync(0xffffffffu, mid.x, 1);
-            float4 o;
-            o.x = j5(mid.x, up.x, dn.x, wv, mid.y);
-            o.y = j5(mid.y, up.y, dn.y, mid.x, mid.z);
-            o.z = j5(mid.z, up.z, dn.z, mid.y, mid.w);
-            o.w = j5(mid.w, up.w, dn.w, mid.z, ev);
+            float4 o = div4_const_rn<5>(make_float4(sum5(mid.x, up.x, dn.x, wv, mid.y),
+                                                    sum5(mid.y, up.y, dn.y, mid.x, mid.z),
+                                                    sum5(mid.z, up.z, dn.z, mid.y, mid.w),
+                                                    sum5(mid.w, up.w, dn.w, mid.z, ev)));
             if (EDGE) {
                 const int64_t r = tr - l - 1;
                 const bool rin = r >= 0 && r < NY;

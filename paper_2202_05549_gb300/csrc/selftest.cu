@@ -24,6 +24,30 @@ __global__ void div_const_check(unsigned long long *mismatches) {
     if (bad) atomicAdd(mismatches, bad);
 }
 
+// div4_const_rn against __fdiv_rn: every pattern a in each of the four
+// positions, next to three in-range values, so that the one range test for
+// the four must send every out-of-range a (zero, tiny, huge, inf, NaN) to
+// the exact path.
+template <int C>
+__global__ void div4_const_check(unsigned long long *mismatches) {
+    unsigned long long bad = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (1ull << 32); i += stride) {
+        const float a = __uint_as_float((uint32_t)i);
+        float v[4] = {1.0f, 0.3f, 7.5f, 123.0f};
+        v[i & 3] = a;
+        const float4 got = div4_const_rn<C>(make_float4(v[0], v[1], v[2], v[3]));
+        const float g[4] = {got.x, got.y, got.z, got.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float want = __fdiv_rn(v[k], (float)C);
+            const bool same = __float_as_uint(g[k]) == __float_as_uint(want) || (g[k] != g[k] && want != want);
+            bad += same ? 0 : 1;
+        }
+    }
+    if (bad) atomicAdd(mismatches, bad);
+}
+
 }  // namespace
 }  // namespace lt
 
@@ -34,10 +58,13 @@ extern "C" lt_status lt_selftest_div_const(int32_t device, int32_t divisor, uint
     if (cudaMalloc((void **)&d, sizeof(*d)) != cudaSuccess) return LT_ERR_CUDA;
     cudaError_t e = cudaMemset(d, 0, sizeof(*d));
     if (e == cudaSuccess) {
-        if (divisor == 5)
+        if (divisor == 5) {
             lt::div_const_check<5><<<152 * 8, 256>>>(d);
-        else
+            lt::div4_const_check<5><<<152 * 8, 256>>>(d);
+        } else {
             lt::div_const_check<7><<<152 * 8, 256>>>(d);
+            lt::div4_const_check<7><<<152 * 8, 256>>>(d);
+        }
         e = cudaGetLastError();
     }
     unsigned long long h = 0;

@@ -17,12 +17,15 @@ namespace lt {
 constexpr int JR = 16;      // output rows per warp strip
 constexpr int JCOLS = 128;  // columns per warp strip (4 per lane)
 
-__device__ __forceinline__ float j5(float c, float n, float s, float w, float e) {
+__device__ __forceinline__ float sum5(float c, float n, float s, float w, float e) {
     float acc = __fadd_rn(c, n);
     acc = __fadd_rn(acc, s);
     acc = __fadd_rn(acc, w);
-    acc = __fadd_rn(acc, e);
-    return div_const_rn<5>(acc);
+    return __fadd_rn(acc, e);
+}
+
+__device__ __forceinline__ float j5(float c, float n, float s, float w, float e) {
+    return div_const_rn<5>(sum5(c, n, s, w, e));
 }
 
 template <bool L2ONLY>
@@ -85,11 +88,10 @@ __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float 
         float w = lane == 0 ? wl[k] : w_in;
         float e = lane == 31 ? er[k] : e_in;
         if (r > rlast || j0 > xe) continue;
-        float4 o;
-        o.x = j5(mid.x, up.x, dn.x, w, mid.y);
-        o.y = j5(mid.y, up.y, dn.y, mid.x, mid.z);
-        o.z = j5(mid.z, up.z, dn.z, mid.y, mid.w);
-        o.w = j5(mid.w, up.w, dn.w, mid.z, e);
+        const float4 o = div4_const_rn<5>(make_float4(sum5(mid.x, up.x, dn.x, w, mid.y),
+                                                      sum5(mid.y, up.y, dn.y, mid.x, mid.z),
+                                                      sum5(mid.z, up.z, dn.z, mid.y, mid.w),
+                                                      sum5(mid.w, up.w, dn.w, mid.z, e)));
         float *dst = vb + r * sv + j0;
         if (j0 + 3 <= xe) {
             *(float4 *)dst = o;
