@@ -294,11 +294,9 @@ __device__ void jacobi4(dim3 vb, int64_t ny, int64_t nx, lightning::Matrix<float
     if (j + 1 >= nx) { c.y = 0.0f; n.y = 0.0f; s.y = 0.0f; }   // cells beyond the grid read as zero
     if (j + 2 >= nx) { c.z = 0.0f; n.z = 0.0f; s.z = 0.0f; }
     if (j + 3 >= nx) { c.w = 0.0f; n.w = 0.0f; s.w = 0.0f; }
-    float4 o;
-    o.x = (((((c.x + n.x) + s.x) + w) + c.y)) / 5.0f;
-    o.y = (((((c.y + n.y) + s.y) + c.x) + c.z)) / 5.0f;
-    o.z = (((((c.z + n.z) + s.z) + c.y) + c.w)) / 5.0f;
-    o.w = (((((c.w + n.w) + s.w) + c.z) + e)) / 5.0f;
+    // the four sums, divided by 5 with IEEE rounding by the library's helper (one range test for four)
+    const float4 o = lightning::div4_rn<5>(make_float4((((c.x + n.x) + s.x) + w) + c.y, (((c.y + n.y) + s.y) + c.x) + c.z,
+                                                       (((c.z + n.z) + s.z) + c.y) + c.w, (((c.w + n.w) + s.w) + c.z) + e));
     if (j + 3 < nx) {
         *(float4 *)&V(i, j) = o;
     } else {

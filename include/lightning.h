@@ -325,7 +325,10 @@ lt_status lt_kernel_destroy(lt_ctx *ctx, lt_kernel *k);
  * array parameters as lightning::Vector<T> / Matrix<T> / Tensor<T> for 1, 2
  * or 3 indices in the annotation, indexed with global indices (v[i],
  * m(i, j) or m[i][j], t(k, i, j)); T is float, unsigned short (bf16 bits),
- * unsigned char or unsigned int.  Use virtBlockIdx instead of blockIdx and
+ * unsigned char or unsigned int.  lightning::div_rn<C>(float) and
+ * lightning::div4_rn<C>(float4) divide by a small integer constant C with
+ * IEEE rounding (equal to x / C) in a few instructions, as the built-in
+ * stencils do.  Use virtBlockIdx instead of blockIdx and
  * gridDim; blockDim and threadIdx are those of the launch.  The library
  * generates the wrapper kernel that maps physical to virtual blocks and
  * builds the views (the chunk offset subtracted once).  The wrapper is

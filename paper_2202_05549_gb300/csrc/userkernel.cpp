@@ -7,7 +7,9 @@
 // value parameters: int64_t (integer) or double (float); arrays:
 // lightning::Vector<T> (1-D, v[i]), Matrix<T> (2-D, m(i, j) or m[i][j]) and
 // Tensor<T> (3-D, t(k, i, j)), T = float, double, unsigned short (bf16 bits),
-// unsigned char or unsigned int.
+// unsigned char or unsigned int.  lightning::div_rn<C>(float) and
+// div4_rn<C>(float4) divide by a small integer constant with IEEE rounding in
+// a few instructions (the built-in stencils' method).
 //
 // Like the generated wrapper of Listing 3, the library adds a __global__
 // wrapper that turns the physical block index into the virtual one and builds
@@ -90,6 +92,33 @@ const char *ctype(int dtype) {
 // chunk), in units of 32 consecutive elements of a box (LtUnit: box, first
 // element), one element per thread, reading through L2: the written cells
 // come from other SMs.
+// Correctly rounded division by a small integer constant for user bodies,
+// the method of the built-in stencils (Markstein's correction step, P.
+// Markstein, IBM J. Res. Dev. 34(1), 1990): with y = RN(1/C), q0 = RN(a*y),
+// r = fma(-q0, C, a) is exact and RN(q0 + r*y) is the IEEE quotient for
+// 1e-30 <= |a| <= 1e30; other values take the IEEE division.  div4_rn<C>
+// tests the range once for four values (the largest magnitude taken
+// NaN-propagating, so a NaN fails the test).
+static const char *kDivHelpers =
+    "template <int C> __device__ __forceinline__ float div_rn(float a) {\n"
+    "  const float y = 1.0f / (float)C, m = fabsf(a);\n"
+    "  if (!(m >= 1e-30f && m <= 1e30f)) return __fdiv_rn(a, (float)C);\n"
+    "  const float q0 = __fmul_rn(a, y);\n"
+    "  return __fmaf_rn(__fmaf_rn(-q0, (float)C, a), y, q0);\n"
+    "}\n"
+    "__device__ __forceinline__ float max_nan(float a, float b) {\n"
+    "  float r; asm(\"max.NaN.f32 %0, %1, %2;\" : \"=f\"(r) : \"f\"(a), \"f\"(b)); return r;\n"
+    "}\n"
+    "template <int C> __device__ __forceinline__ float4 div4_rn(float4 a) {\n"
+    "  const float y = 1.0f / (float)C;\n"
+    "  const float ax = fabsf(a.x), ay = fabsf(a.y), az = fabsf(a.z), aw = fabsf(a.w);\n"
+    "  const float lo = fminf(fminf(ax, ay), fminf(az, aw)), hi = max_nan(max_nan(ax, ay), max_nan(az, aw));\n"
+    "  if (!(lo >= 1e-30f && hi <= 1e30f)) return make_float4(div_rn<C>(a.x), div_rn<C>(a.y), div_rn<C>(a.z), div_rn<C>(a.w));\n"
+    "  const float qx = __fmul_rn(a.x, y), qy = __fmul_rn(a.y, y), qz = __fmul_rn(a.z, y), qw = __fmul_rn(a.w, y);\n"
+    "  return make_float4(__fmaf_rn(__fmaf_rn(-qx, (float)C, a.x), y, qx), __fmaf_rn(__fmaf_rn(-qy, (float)C, a.y), y, qy),\n"
+    "                     __fmaf_rn(__fmaf_rn(-qz, (float)C, a.z), y, qz), __fmaf_rn(__fmaf_rn(-qw, (float)C, a.w), y, qw));\n"
+    "}\n";
+
 static const char *kReplicaPhase =
     "struct LtUnit { unsigned box, first; };\n"
     "__device__ __forceinline__ unsigned long long lt_gtimer() {\n"
@@ -164,7 +193,7 @@ std::string user_wrapper_source(const std::string &user, const std::string &name
          "  T *p; int64_t s0, s1, s2;\n"
          "  __device__ T &operator()(int64_t k, int64_t i, int64_t j) const { return p[k * s0 + i * s1 + j * s2]; }\n"
          "};\n"
-         "}  // namespace lightning\n"
+      << kDivHelpers << "}  // namespace lightning\n"
          "struct LtView { uint64_t base; int64_t s[3]; int64_t org[3]; int64_t hi[3]; };\n"
          "struct LtTask { int64_t t_lo[3], t_hi[3]; LtView v["
       << LT_MAX_ARRAYS

@@ -401,3 +401,58 @@ def test_user_kernel_full_size_incore_4x4_as_benchmarked_bit_exact():
         ctx.synchronize()
         got = U.read()
     assert np.array_equal(got, oracle.jacobi2d(u0, iters))
+
+
+DIV_HELPERS = r"""
+__device__ void div1(dim3 vb, int64_t n, lightning::Vector<float> q, lightning::Vector<float> a) {
+    const int64_t g = (int64_t)vb.x * blockDim.x + threadIdx.x;
+    if (g < n) q[g] = lightning::div_rn<5>(a[g]);
+}
+__device__ void div4(dim3 vb, int64_t n4, lightning::Vector<float> q, lightning::Vector<float> a) {
+    const int64_t g = (int64_t)vb.x * blockDim.x + threadIdx.x;
+    if (g >= n4) return;
+    const float4 r = lightning::div4_rn<7>(make_float4(a[4 * g], a[4 * g + 1], a[4 * g + 2], a[4 * g + 3]));
+    q[4 * g] = r.x; q[4 * g + 1] = r.y; q[4 * g + 2] = r.z; q[4 * g + 3] = r.w;
+}
+"""
+
+
+def _division_inputs():
+    # random bit patterns (NaNs, infinities, subnormals and all) plus the
+    # edges of the fast path's range, each special value in every one of
+    # the four positions of a group, next to ordinary values
+    rng = np.random.default_rng(2202)
+    bits = rng.integers(0, 2 ** 32, size=1 << 16, dtype=np.uint64).astype(np.uint32)
+    special = np.array([0.0, -0.0, 1e-30, -1e-30, 9.99e-31, 1e30, -1e30, 1.01e30, 1e-45, -1e-45, 1.17549435e-38,
+                        3.4028235e38, np.inf, -np.inf, np.nan, 1.0, 5.0, 7.0, 0.2, 1.0 / 3.0], dtype=np.float32)
+    groups = []
+    for v in special:
+        for pos in range(4):
+            g = np.array([0.75, 1.5, 3.25, 6.0], dtype=np.float32)
+            g[pos] = v
+            groups.append(g)
+    return np.concatenate([bits.view(np.float32), np.concatenate(groups)])
+
+
+@pytest.mark.gpu
+def test_source_kernel_division_helpers_match_ieee_division():
+    a = _division_inputs()
+    n = a.size
+    assert n % 4 == 0
+    with lt.Context() as ctx:
+        A = ctx.array(lt.F32, (n,), lt.Dist.rows(n // 3 // 4 * 4, halo=0))
+        Q = ctx.array(lt.F32, (n,), lt.Dist.rows(n // 3 // 4 * 4, halo=0))
+        A.write(a)
+        k1 = ctx.kernel_from_source(DIV_HELPERS, "div1", "global i => read a[i], write q[i]",
+                                    [("n", lt.U32, False), ("q", lt.F32), ("a", lt.F32)])
+        k1.launch(grid=(n,), block=(128,), superblock=(n // 3 // 4 * 4,), args=[n, Q, A])
+        got5 = Q.read()
+        k4 = ctx.kernel_from_source(DIV_HELPERS, "div4", "global i => read a[4*i:4*i+3], write q[4*i:4*i+3]",
+                                    [("n4", lt.U32, False), ("q", lt.F32), ("a", lt.F32)])
+        k4.launch(grid=(n // 4,), block=(128,), superblock=(n // 3 // 16 * 4,), args=[n // 4, Q, A])
+        got7 = Q.read()
+    with np.errstate(all="ignore"):
+        for got, c in ((got5, 5), (got7, 7)):
+            want = a / np.float32(c)
+            same = (got.view(np.uint32) == want.view(np.uint32)) | (np.isnan(got) & np.isnan(want))
+            assert same.all(), (c, a[~same][:8], got[~same][:8], want[~same][:8])
