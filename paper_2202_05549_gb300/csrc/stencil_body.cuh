@@ -55,29 +55,30 @@ __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float 
     const int64_t cmax = min(xe + 1, NX - 1);  // last column that may be read
     const bool ld = j0 <= cmax;
     float4 row[R + 2];
-    float wl[R], er[R];
+    float side[R];  // lane 0: the west halo column, lane 31: the east one
 #pragma unroll
     for (int k = 0; k < R + 2; ++k) {
         int64_t r = r0 - 1 + k;
         row[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ld && r >= 0 && r < NY && r <= rlast + 1) row[k] = ld4<L2ONLY>(ub + r * su + j0);
     }
+    const bool side_ok = lane == 0 ? (j0 - 1 >= 0 && ld) : (lane == 31 && j0 + 4 <= cmax);
+    const int64_t sc = lane == 0 ? j0 - 1 : j0 + 4;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         int64_t r = r0 + k;
-        wl[k] = 0.f;
-        er[k] = 0.f;
-        if (r <= rlast) {
-            if (lane == 0 && j0 - 1 >= 0 && ld) wl[k] = ld1<L2ONLY>(ub + r * su + j0 - 1);
-            if (lane == 31 && j0 + 4 <= cmax) er[k] = ld1<L2ONLY>(ub + r * su + j0 + 4);
-        }
+        side[k] = 0.f;
+        if (side_ok && r <= rlast) side[k] = ld1<L2ONLY>(ub + r * su + sc);
     }
-    // columns of this lane that lie outside the domain read as 0
+    // columns of this lane that lie outside the domain read as 0 (the last
+    // strip of a row of the grid only)
+    if (j0 + 3 > NX - 1) {
 #pragma unroll
-    for (int k = 0; k < R + 2; ++k) {
-        if (j0 + 1 > NX - 1) row[k].y = 0.f;
-        if (j0 + 2 > NX - 1) row[k].z = 0.f;
-        if (j0 + 3 > NX - 1) row[k].w = 0.f;
+        for (int k = 0; k < R + 2; ++k) {
+            if (j0 + 1 > NX - 1) row[k].y = 0.f;
+            if (j0 + 2 > NX - 1) row[k].z = 0.f;
+            row[k].w = 0.f;
+        }
     }
 #pragma unroll
     for (int k = 0; k < R; ++k) {
@@ -85,8 +86,8 @@ __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float 
         const float4 up = row[k], mid = row[k + 1], dn = row[k + 2];
         float w_in = __shfl_up_sync(0xffffffffu, mid.w, 1);
         float e_in = __shfl_down_sync(0xffffffffu, mid.x, 1);
-        float w = lane == 0 ? wl[k] : w_in;
-        float e = lane == 31 ? er[k] : e_in;
+        float w = lane == 0 ? side[k] : w_in;
+        float e = lane == 31 ? side[k] : e_in;
         if (r > rlast || j0 > xe) continue;
         const float4 o = div4_const_rn<5>(make_float4(sum5(mid.x, up.x, dn.x, w, mid.y),
                                                       sum5(mid.y, up.y, dn.y, mid.x, mid.z),
