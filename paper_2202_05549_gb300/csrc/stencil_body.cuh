@@ -63,12 +63,24 @@ __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float 
         if (ld && r >= 0 && r < NY && r <= rlast + 1) row[k] = ld4<L2ONLY>(ub + r * su + j0);
     }
     const bool side_ok = lane == 0 ? (j0 - 1 >= 0 && ld) : (lane == 31 && j0 + 4 <= cmax);
-    const int64_t sc = lane == 0 ? j0 - 1 : j0 + 4;
+    if (L2ONLY) {
+        // (the batch kernel) the halo column's address computed for each row
+        const int64_t sc = lane == 0 ? j0 - 1 : j0 + 4;
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        int64_t r = r0 + k;
-        side[k] = 0.f;
-        if (side_ok && r <= rlast) side[k] = ld1<L2ONLY>(ub + r * su + sc);
+        for (int k = 0; k < R; ++k) {
+            side[k] = 0.f;
+            if (side_ok && r0 + k <= rlast) side[k] = ld1<L2ONLY>(ub + (r0 + k) * su + sc);
+        }
+    } else {
+        // (the single-launch kernels) a pointer that walks down the halo
+        // column: fewer instructions there, more registers in the batch
+        // kernel (measured both ways on each)
+        const float *sp = ub + r0 * su + (lane == 0 ? j0 - 1 : j0 + 4);
+#pragma unroll
+        for (int k = 0; k < R; ++k, sp += su) {
+            side[k] = 0.f;
+            if (side_ok && r0 + k <= rlast) side[k] = ld1<L2ONLY>(sp);
+        }
     }
     // columns of this lane that lie outside the domain read as 0 (the last
     // strip of a row of the grid only)
