@@ -54,12 +54,13 @@ __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float 
     const int64_t rlast = min(r0 + R - 1, ye);
     const int64_t cmax = min(xe + 1, NX - 1);  // last column that may be read
     const bool ld = j0 <= cmax;
+    const int kr = (int)(rlast - r0);  // output rows r0 .. r0+kr (0 <= kr < R): a 32-bit test per row
     float4 row[R + 2];
     float side[R];  // lane 0: the west halo column, lane 31: the east one
 #pragma unroll
     for (int k = 0; k < R + 2; ++k) {
-        int64_t r = r0 - 1 + k;
         row[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int64_t r = r0 - 1 + k;
         if (ld && r >= 0 && r < NY && r <= rlast + 1) row[k] = ld4<L2ONLY>(ub + r * su + j0);
     }
     const bool side_ok = lane == 0 ? (j0 - 1 >= 0 && ld) : (lane == 31 && j0 + 4 <= cmax);
@@ -69,7 +70,7 @@ __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float 
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             side[k] = 0.f;
-            if (side_ok && r0 + k <= rlast) side[k] = ld1<L2ONLY>(ub + (r0 + k) * su + sc);
+            if (side_ok && k <= kr) side[k] = ld1<L2ONLY>(ub + (r0 + k) * su + sc);
         }
     } else {
         // (the single-launch kernels) a pointer that walks down the halo
@@ -79,7 +80,7 @@ __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float 
 #pragma unroll
         for (int k = 0; k < R; ++k, sp += su) {
             side[k] = 0.f;
-            if (side_ok && r0 + k <= rlast) side[k] = ld1<L2ONLY>(sp);
+            if (side_ok && k <= kr) side[k] = ld1<L2ONLY>(sp);
         }
     }
     // columns of this lane that lie outside the domain read as 0 (the last
@@ -94,13 +95,13 @@ __device__ __forceinline__ void jacobi_strip(const float *ub, int64_t su, float 
     }
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        int64_t r = r0 + k;
+        const int64_t r = r0 + k;
         const float4 up = row[k], mid = row[k + 1], dn = row[k + 2];
         float w_in = __shfl_up_sync(0xffffffffu, mid.w, 1);
         float e_in = __shfl_down_sync(0xffffffffu, mid.x, 1);
         float w = lane == 0 ? side[k] : w_in;
         float e = lane == 31 ? side[k] : e_in;
-        if (r > rlast || j0 > xe) continue;
+        if (k > kr || j0 > xe) continue;
         const float4 o = div4_const_rn<5>(make_float4(sum5(mid.x, up.x, dn.x, w, mid.y),
                                                       sum5(mid.y, up.y, dn.y, mid.x, mid.z),
                                                       sum5(mid.z, up.z, dn.z, mid.y, mid.w),
