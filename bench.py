@@ -883,9 +883,10 @@ def run_kmeans(args, rank, world, local, grp):
     # of 64, so every superblock is exactly one chunk and reads it in place
     # (blocks of 256 round the superblocks to 25,000,192 records and 39 of
     # the 40 would pack their records first).
-    def step():
+    def step(records=None):
         for _ in range(iters):
-            ka.launch(grid=(n,), block=(64,), superblock=(per_chunk,), args=[X, cen[0], S, k])
+            rec = X if records is None else records
+            ka.launch(grid=(n,), block=(64,), superblock=(per_chunk,), args=[rec, cen[0], S, k])
             ku.launch(grid=(k,), block=(64,), superblock=(0,), args=[S, cen[0], cen[1]])
             cen.reverse()
         ctx.synchronize()
@@ -939,22 +940,30 @@ def run_kmeans(args, rank, world, local, grp):
         "clocks": clocks,
     }
     if not args.no_e2e:
-        # end to end through the public API: every step uploads the records
+        # end to end through the public API: every step uploads its records
         # and the starting centres from pinned host memory, runs the
-        # iterations and reads the final centres back
+        # iterations and reads the final centres back.  The records go to two
+        # arrays in turn, so the next step's upload (asynchronous, on the
+        # host-to-device stream) runs while this step iterates on the other
         import torch
         h_x = torch.empty((4 * n,), dtype=torch.float32, pin_memory=True).numpy()
         h_c = torch.empty((4 * k,), dtype=torch.float32, pin_memory=True).numpy()
         h_out = torch.empty((4 * k,), dtype=torch.float32, pin_memory=True).numpy()
         X.read(out=h_x)
         cen[0].read(out=h_c)
+        X2 = ctx.array(lt.F32, (4 * n,), lt.Dist.rows(4 * per_chunk))
+        recs = [X, X2]
         ctx.reset_stats()
         t0 = time.perf_counter()
         nstep = min(200, max(1, args.steps // 2))
-        for _ in range(nstep):
-            X.write_async(h_x)
+        recs[0].write_async(h_x)
+        for s in range(nstep):
+            # (the copy stream is in order: the centres go first, so that this
+            # step's kernels do not wait behind the next step's records)
             cen[0].write_async(h_c)
-            step()
+            if s + 1 < nstep:
+                recs[(s + 1) % 2].write_async(h_x)  # the next step's records
+            step(recs[s % 2])
             cen[0].read_async(h_out)
         ctx.synchronize()
         t1 = time.perf_counter()
@@ -962,7 +971,9 @@ def run_kmeans(args, rank, world, local, grp):
                       "h2d_bytes_per_step": int(h_x.nbytes + h_c.nbytes), "d2h_bytes_per_step": int(h_out.nbytes),
                       "how": "public Python API, wall clock; per step: upload of the records and the starting "
                              "centres from pinned host memory, the iterations and synchronize, read of the "
-                             "final centres (asynchronous copies)"}
+                             "final centres (asynchronous copies); the records alternate between two arrays, "
+                             "so the next step's upload overlaps this step's iterations"}
+        X2.destroy()
     ctx.close()
     return res
 
