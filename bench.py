@@ -73,9 +73,10 @@ def parse():
     p.add_argument("--tb", type=int, default=1, help="Jacobi iterations per launch (temporal blocking, halo = tb)")
     p.add_argument("--iters", type=int, default=0,
                    help="Jacobi iterations per step (one run of the workload; default 20 out-of-core, 10 in-core)")
-    p.add_argument("--user-kernel", nargs="?", const="scalar", default=None, choices=["scalar", "vec"],
+    p.add_argument("--user-kernel", nargs="?", const="scalar", default=None, choices=["scalar", "vec", "vec4"],
                    help="stencil workloads: run a Jacobi body compiled at run time (NVRTC) instead of the built-in: "
-                        "one cell per thread (scalar, the default) or four cells per thread from float4 rows (vec)")
+                        "one cell per thread (scalar, the default), four cells per thread from float4 rows (vec) or "
+                        "four rows of four cells per thread (vec4)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--wl-steps", type=int, default=5, help="timed steps of each workload of the default run")
     p.add_argument("--wl-warmup", type=int, default=3, help="warm-up steps of each workload of the default run")
@@ -307,6 +308,53 @@ __device__ void jacobi4(dim3 vb, int64_t ny, int64_t nx, lightning::Matrix<float
 }
 """
 USER_JACOBI_VEC_ANN = "global [i, j] => read U[i-1:i+1, 4*j-1:4*j+4], write V[i, 4*j:4*j+3]"
+
+# Four rows of four cells per thread: the six input rows i0-1 .. i0+4 are
+# loaded once for the four output rows (a thread of the body above loads
+# three rows for one), the west and east neighbours one by one, the same sum
+# order and division per cell.
+USER_JACOBI_VEC4 = r"""
+__device__ void jacobi16(dim3 vb, int64_t ny, int64_t nx, lightning::Matrix<float> U, lightning::Matrix<float> V) {
+    const int64_t i0 = 4 * ((int64_t)vb.y * blockDim.y + threadIdx.y);
+    const int64_t j = 4 * ((int64_t)vb.x * blockDim.x + threadIdx.x);
+    if (i0 >= ny || j >= nx) return;
+    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float4 r[6];  // rows i0-1 .. i0+4 (zero outside the grid)
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        const int64_t i = i0 - 1 + t;
+        r[t] = (i >= 0 && i < ny) ? *(const float4 *)&U(i, j) : z;
+        if (j + 1 >= nx) r[t].y = 0.0f;   // cells beyond the grid read as zero
+        if (j + 2 >= nx) r[t].z = 0.0f;
+        if (j + 3 >= nx) r[t].w = 0.0f;
+    }
+    float w[4], e[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int64_t i = i0 + t;
+        w[t] = (i < ny && j > 0) ? U(i, j - 1) : 0.0f;
+        e[t] = (i < ny && j + 4 < nx) ? U(i, j + 4) : 0.0f;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int64_t i = i0 + t;
+        if (i >= ny) break;
+        const float4 n = r[t], c = r[t + 1], s = r[t + 2];
+        const float4 o = lightning::div4_rn<5>(make_float4((((c.x + n.x) + s.x) + w[t]) + c.y,
+                                                           (((c.y + n.y) + s.y) + c.x) + c.z,
+                                                           (((c.z + n.z) + s.z) + c.y) + c.w,
+                                                           (((c.w + n.w) + s.w) + c.z) + e[t]));
+        if (j + 3 < nx) {
+            *(float4 *)&V(i, j) = o;
+        } else {
+            V(i, j) = o.x;
+            if (j + 1 < nx) V(i, j + 1) = o.y;
+            if (j + 2 < nx) V(i, j + 2) = o.z;
+        }
+    }
+}
+"""
+USER_JACOBI_VEC4_ANN = "global [i, j] => read U[4*i-1:4*i+4, 4*j-1:4*j+4], write V[4*i:4*i+3, 4*j:4*j+3]"
 
 
 def ctx_flags(args):
@@ -550,6 +598,9 @@ def run_lightning(args, rank, world, local, grp, links=None):
     elif user == "vec":
         k = ctx.kernel_from_source(USER_JACOBI_VEC, "jacobi4", USER_JACOBI_VEC_ANN,
                                    [("ny", lt.U32, False), ("nx", lt.U32, False), ("U", lt.F32), ("V", lt.F32)])
+    elif user == "vec4":
+        k = ctx.kernel_from_source(USER_JACOBI_VEC4, "jacobi16", USER_JACOBI_VEC4_ANN,
+                                   [("ny", lt.U32, False), ("nx", lt.U32, False), ("U", lt.F32), ("V", lt.F32)])
     elif user:
         k = ctx.kernel_from_source(USER_JACOBI, "jacobi", ann, [("ny", lt.U32, False), ("nx", lt.U32, False),
                                                                   ("U", lt.F32), ("V", lt.F32)])
@@ -570,6 +621,9 @@ def run_lightning(args, rank, world, local, grp, links=None):
         for _ in range(launches):
             if user == "vec":  # four columns per thread: the grid and superblocks are a quarter as wide
                 k.launch(grid=((nx + 3) // 4, ny), block=(64, 4), superblock=(sb[0] // 4, sb[1]),
+                         args=[ny, nx, bufs[0], bufs[1]])
+            elif user == "vec4":  # four rows and four columns per thread: a quarter as wide and as high
+                k.launch(grid=((nx + 3) // 4, (ny + 3) // 4), block=(64, 4), superblock=(sb[0] // 4, sb[1] // 4),
                          args=[ny, nx, bufs[0], bufs[1]])
             elif user:
                 k.launch(grid=(nx, ny), block=(128, 4), superblock=sb, args=[ny, nx, bufs[0], bufs[1]])
@@ -1386,8 +1440,8 @@ WORKLOADS = (("incore_1chunk", "incore", {"incore_chunks": "1"}),
              ("incore_4x4", "incore", {"incore_chunks": "4x4"}),
              ("gemm", "gemm", {}), ("batch", "batch", {}), ("adjoint", "adjoint", {}),
              ("jacobi3d", "jacobi3d", {}), ("kmeans", "kmeans", {}),
-             # the in-core 4x4 tiles again through a runtime-compiled source kernel (four cells per thread)
-             ("source_kernel_4x4", "incore", {"incore_chunks": "4x4", "user_kernel": "vec"}))
+             # the in-core 4x4 tiles again through a runtime-compiled source kernel (four rows of four cells per thread)
+             ("source_kernel_4x4", "incore", {"incore_chunks": "4x4", "user_kernel": "vec4"}))
 NO_CPU_BASELINE = {"source_kernel_4x4"}  # the same oracle computation as incore_4x4
 
 

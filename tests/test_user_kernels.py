@@ -403,6 +403,57 @@ def test_user_kernel_full_size_incore_4x4_as_benchmarked_bit_exact():
     assert np.array_equal(got, oracle.jacobi2d(u0, iters))
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("flags", [0, L.LT_FLAG_NO_FUSED_REPLICAS])
+@pytest.mark.parametrize("dist_kind", ["tiles_halo", "block", "rows_halo", "cols_halo", "tiles_nohalo"])
+def test_user_kernel_sixteen_cells_per_thread_bit_exact(dist_kind, flags):
+    # the benchmark's body with four rows of four cells per thread, annotated
+    # "read U[4*i-1:4*i+4, 4*j-1:4*j+4], write V[4*i:4*i+3, 4*j:4*j+3]"; a
+    # height and width that are not multiples of 4 exercise the masked edges,
+    # tiles without halo the pack and temporary-write paths
+    import bench
+    ny, nx, iters = 301, 517, 3
+    u0 = si.uniform_field(2203, 14, ny, nx)
+    dist, sb = {"tiles_halo": (lt.Dist.tiles((128, 256), halo=(1, 1)), (64, 32)),
+                "block": (lt.Dist.block(), (0, 0)),
+                "rows_halo": (lt.Dist.rows(100, halo=1), ((nx + 3) // 4, 25)),
+                "cols_halo": (lt.Dist.cols(128, halo=1), (32, (ny + 3) // 4)),
+                "tiles_nohalo": (lt.Dist.tiles((128, 256), halo=(0, 0)), (64, 32))}[dist_kind]
+    with lt.Context(flags=flags) as ctx:
+        U = ctx.array(lt.F32, (ny, nx), dist)
+        V = ctx.array(lt.F32, (ny, nx), dist)
+        U.write(u0)
+        k = ctx.kernel_from_source(bench.USER_JACOBI_VEC4, "jacobi16", bench.USER_JACOBI_VEC4_ANN,
+                                   [("ny", lt.U32, False), ("nx", lt.U32, False), ("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=((nx + 3) // 4, (ny + 3) // 4), block=(64, 4), superblock=sb, args=[ny, nx, U, V])
+            U, V = V, U
+        ctx.synchronize()
+        assert np.array_equal(U.read(), oracle.jacobi2d(u0, iters))
+
+
+@pytest.mark.gpu
+def test_user_kernel_sixteen_cells_full_size_incore_4x4_bit_exact():
+    # the benchmarked configuration of that body: 4096^2 in 4 x 4 tiles of
+    # 1024^2 + halo, superblocks of 256 x 256 threads, 10 iterations
+    import bench
+    n, iters = 4096, 10
+    u0 = si.uniform_field(si.SEED_JACOBI_INCORE, 0, n, n)
+    dist = lt.Dist.tiles((1024, 1024), halo=(1, 1))
+    with lt.Context() as ctx:
+        U = ctx.array(lt.F32, (n, n), dist)
+        V = ctx.array(lt.F32, (n, n), dist)
+        U.write(u0)
+        k = ctx.kernel_from_source(bench.USER_JACOBI_VEC4, "jacobi16", bench.USER_JACOBI_VEC4_ANN,
+                                   [("ny", lt.U32, False), ("nx", lt.U32, False), ("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=(n // 4, n // 4), block=(64, 4), superblock=(256, 256), args=[n, n, U, V])
+            U, V = V, U
+        ctx.synchronize()
+        got = U.read()
+    assert np.array_equal(got, oracle.jacobi2d(u0, iters))
+
+
 DIV_HELPERS = r"""
 __device__ void div1(dim3 vb, int64_t n, lightning::Vector<float> q, lightning::Vector<float> a) {
     const int64_t g = (int64_t)vb.x * blockDim.x + threadIdx.x;
