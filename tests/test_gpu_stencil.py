@@ -457,3 +457,62 @@ def test_async_host_copies_round_trip_through_one_buffer(dist):
             U.read_async(h)
         ctx.synchronize()
     assert np.array_equal(h, oracle.jacobi2d(u0, 6))
+
+
+def _with_special_values(u, seed):
+    # about one cell in eight replaced by a value the fast division path
+    # must hand to the IEEE division (zeros of both signs, subnormals, sums
+    # that cancel below 1e-30, huge values whose sums overflow, infinities,
+    # NaN) or that sits at the edge of its range
+    rng = np.random.default_rng(seed)
+    special = np.array([0.0, -0.0, 1e-40, -1e-42, 1e-35, -1e-35, 3e38, -3e38, np.inf, -np.inf, np.nan,
+                        1e30, -1e30, 5e-30, 1e-30, 2.5e29], dtype=np.float32)
+    u = u.copy()
+    mask = rng.random(u.shape) < 0.125
+    u[mask] = rng.choice(special, size=int(mask.sum()))
+    return u
+
+
+def _same(got, want):
+    # bit for bit, any two NaNs equal (their payloads are not specified)
+    return (got.view(np.uint32) == want.view(np.uint32)) | (np.isnan(got) & np.isnan(want))
+
+
+@pytest.mark.parametrize("kind", ["strips_tiles_halo", "strips_block", "multi_step_rows_halo"])
+def test_jacobi_special_values_match_the_oracle(kind):
+    # the strips divide four sums with one range test and fall back to the
+    # IEEE division for all four when one is out of range; the multi-step
+    # kernel does the same: both must match the oracle's float division
+    ny, nx = 203, 390
+    u0 = _with_special_values(si.uniform_field(si.SEED_JACOBI_INCORE, 40, ny, nx), 40)
+    with np.errstate(all="ignore"):
+        if kind == "multi_step_rows_halo":
+            k, launches = 3, 2
+            want = oracle.jacobi2d(u0, k * launches)
+        else:
+            launches = 3
+            want = oracle.jacobi2d(u0, launches)
+    with lt.Context() as ctx:
+        if kind == "multi_step_rows_halo":
+            dist, sb = lt.Dist.rows(64, halo=k), (nx, 64)
+        elif kind == "strips_tiles_halo":
+            dist, sb = lt.Dist.tiles((64, 128), halo=(1, 1)), (128, 64)
+        else:
+            dist, sb = lt.Dist.block(), (0, 0)
+        U = ctx.array(lt.F32, (ny, nx), dist)
+        V = ctx.array(lt.F32, (ny, nx), dist)
+        U.write(u0)
+        if kind == "multi_step_rows_halo":
+            kern = ctx.kernel(lt.JACOBI2D_MULTI, MANN.format(k=k), [("U", lt.F32), ("V", lt.F32), ("k", lt.U32, False)])
+            extra = [k]
+        else:
+            kern = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+            extra = []
+        for _ in range(launches):
+            kern.launch(grid=(nx, ny), block=(128, 4), superblock=sb, args=[U, V] + extra)
+            U, V = V, U
+        ctx.synchronize()
+        got = U.read()
+    same = _same(got, want)
+    assert np.isnan(want).any() and np.isinf(want).any() and (want == 0).any()
+    assert same.all(), f"{int((~same).sum())} cells differ, e.g. got {got[~same][:4]} want {want[~same][:4]}"
