@@ -228,3 +228,33 @@ def test_batch_full_size_sampled_vs_oracle():
     for h, n in enumerate(lens):
         x = oracle.gen_u8(si.SEED_BATCH, si.STREAM_BATCH_HIST0 + h, 0, n)
         assert np.array_equal(got_h[h], oracle.hist256(x)), f"histogram {h} differs"
+
+
+def test_batch_special_values_match_the_oracle():
+    # the fused kernel's strips on instances where one cell in eight is a
+    # zero of either sign, a subnormal, a value whose sums overflow or cancel
+    # below 1e-30, an infinity or NaN (any two NaNs count as equal)
+    rng = np.random.default_rng(42)
+    special = np.array([0.0, -0.0, 1e-40, -1e-42, 1e-35, 3e38, -3e38, np.inf, -np.inf, np.nan, 1e30, 5e-30],
+                       dtype=np.float32)
+    with lt.Context() as ctx:
+        kj = ctx.kernel(lt.JACOBI2D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        launches, jac = [], []
+        for q, (ny, nx) in enumerate([(63, 65), (130, 130), (300, 517)]):
+            u0 = si.uniform_field(si.SEED_BATCH, si.STREAM_BATCH_JACOBI0 + 60 + q, ny, nx)
+            mask = rng.random(u0.shape) < 0.125
+            u0[mask] = rng.choice(special, size=int(mask.sum()))
+            U = ctx.array(lt.F32, (ny, nx))
+            V = ctx.array(lt.F32, (ny, nx))
+            U.write(u0)
+            jac.append((u0, U, V))
+            launches.append((kj, (nx, ny), (128, 4), (0, 0), [U, V], 3))
+        ctx.launch_batch(launches, 0)
+        ctx.synchronize()
+        assert ctx.stats()["batches_fused"] == 1
+        for u0, U, V in jac:
+            with np.errstate(all="ignore"):
+                want = oracle.jacobi2d(u0, 3)
+            got = V.read()  # three iterations: the newest state is in V
+            same = (got.view(np.uint32) == want.view(np.uint32)) | (np.isnan(got) & np.isnan(want))
+            assert same.all(), f"{int((~same).sum())} cells differ"

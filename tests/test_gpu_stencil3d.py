@@ -155,3 +155,37 @@ def test_jacobi3d_degenerate_and_larger():
             U, V = V, U
         ctx.synchronize()
         assert np.array_equal(U.read(), oracle.jacobi3d(u0, 2))
+
+
+@pytest.mark.parametrize("name", ["tiles_halo", "odd_sb", "many_chunks"])
+def test_jacobi3d_special_values_match_the_oracle(name):
+    # one cell in eight a zero of either sign, a subnormal, a value whose
+    # sums overflow or cancel below 1e-30, an infinity or NaN: the division
+    # by 7 must fall back to the IEEE division exactly where the oracle's
+    # float division differs from the fast path (any two NaNs count as equal)
+    nz, ny, nx, iters = 21, 40, 133, 2
+    rng = np.random.default_rng(41)
+    special = np.array([0.0, -0.0, 1e-40, -1e-42, 1e-35, 3e38, -3e38, np.inf, -np.inf, np.nan, 1e30, 5e-30],
+                       dtype=np.float32)
+    u0 = field3(nz, ny, nx, stream=5)
+    mask = rng.random(u0.shape) < 0.125
+    u0[mask] = rng.choice(special, size=int(mask.sum()))
+    with np.errstate(all="ignore"):
+        want = oracle.jacobi3d(u0, iters)
+    if name == "many_chunks":
+        dist, block, sb = lt.Dist.tiles((1, 8, 32), halo=(1, 1, 1)), (32, 4, 1), (32, 8, 1)
+    else:
+        dist, block, sb, _ = DISTS[name]
+    with lt.Context() as ctx:
+        U = ctx.array(lt.F32, (nz, ny, nx), dist)
+        V = ctx.array(lt.F32, (nz, ny, nx), dist)
+        U.write(u0)
+        k = ctx.kernel(lt.JACOBI3D, ANN, [("U", lt.F32), ("V", lt.F32)])
+        for _ in range(iters):
+            k.launch(grid=(nx, ny, nz), block=block, superblock=sb, args=[U, V])
+            U, V = V, U
+        ctx.synchronize()
+        got = U.read()
+    same = (got.view(np.uint32) == want.view(np.uint32)) | (np.isnan(got) & np.isnan(want))
+    assert np.isnan(want).any() and np.isinf(want).any()
+    assert same.all(), f"{int((~same).sum())} cells differ"
